@@ -1,0 +1,178 @@
+/*
+ * sccg.h - C ABI of the GB300 (sm_103a) spatial cross-comparison library.
+ *
+ * The library computes, for two sets of integer polygons segmented from the same image (the two
+ * "result sets" of Sec. 2.1 of Wang et al., "Accelerating Pathology Image Data Cross-Comparison on
+ * CPU-GPU Hybrid Systems"), the exact pixel areas of intersection and union of every pair of
+ * polygons whose bounding boxes overlap, and reduces them to Jaccard similarities.
+ *
+ * Pixel model (Sec. 3.1, Fig. 4a/4b). Pixel (x, y) is the unit square [x, x+1) x [y, y+1). It belongs
+ * to polygon p when a ray cast from its centre (x + 1/2, y + 1/2) towards +x crosses p's boundary an
+ * odd number of times. An edge whose x at the ray's row equals the centre's x exactly (the centre
+ * lies on that edge) is not counted. ||p|| is the number of pixels belonging to p; ||p n q|| and
+ * ||p u q|| the numbers belonging to both and to either. Areas are exact int64 counts.
+ *
+ * Conventions for every call:
+ *   - Array arguments are DEVICE pointers owned by the caller (unless a parameter says "host").
+ *     The library never frees caller memory.
+ *   - Calls are enqueued on the given CUDA stream (a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream). Outputs are valid once the stream has reached the call, except
+ *     where a call is documented as synchronous.
+ *   - Every call returns an sccg_status; 0 is success. No C++ exception crosses the ABI.
+ *   - Scratch memory comes from the context (allocated on first need and grown on demand; growing
+ *     synchronises the device). One context must not be used from two host threads at once.
+ *   - Coordinates must satisfy |x|, |y| <= 2^28 and every polygon's bounding box must be at most
+ *     16384 pixels wide and high: all GPU arithmetic is exact in int32 under these bounds.
+ *     sccg_prepare checks them (SCCG_ERANGE).
+ */
+#ifndef SCCG_H
+#define SCCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------------------------- */
+/* status codes                                                                                 */
+/* ------------------------------------------------------------------------------------------- */
+typedef enum sccg_status {
+    SCCG_OK = 0,
+    SCCG_EINVAL = 1,     /* bad argument: NULL or host pointer where device memory is required,
+                            negative size, polygon with fewer than 3 vertices, tiles not sorted */
+    SCCG_ERANGE = 2,     /* coordinate beyond +-2^28 or polygon bounding box wider/higher than 16384 */
+    SCCG_ECAPACITY = 3,  /* output array too small; the required count is still reported */
+    SCCG_ENOMEM = 4,     /* scratch allocation failed */
+    SCCG_ECUDA = 5,      /* a CUDA runtime call or kernel launch failed (see sccg_last_error) */
+    SCCG_ETIMEOUT = 6,   /* a bounded device-side wait gave up; the kernel returned cleanly */
+    SCCG_ENOTSUP = 7     /* operation not supported by this build or device */
+} sccg_status;
+
+/* Short description of a status code (static string). */
+const char* sccg_status_str(int status);
+
+/* ------------------------------------------------------------------------------------------- */
+/* context                                                                                      */
+/* ------------------------------------------------------------------------------------------- */
+typedef struct sccg_ctx sccg_ctx;
+
+/* Tunable parameters (Sec. 3.4: pixelization threshold T; threads per pair; the persistent form's
+ * work split). All have defaults; sccg_ctx_set_param changes one by name. */
+typedef struct sccg_params {
+    int32_t T;               /* a box is pixelized once it holds fewer than T pixels (Sec. 3.2) */
+    int32_t warps_per_cta;   /* warps per CTA in the pair-area kernels (one pair per warp) */
+    int32_t split_pixels;    /* persistent form: a pair's window is cut into work items of at
+                                most about this many pixels (heavy pairs spread across warps) */
+    int32_t ctas_per_sm;     /* persistent form: resident CTAs per SM (0 = occupancy maximum) */
+} sccg_params;
+
+/* Create a context on CUDA device `device`. params_json may be NULL or a flat JSON object with any
+ * of the sccg_params field names, e.g. {"T": 1024, "warps_per_cta": 8}. */
+int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out);
+int sccg_ctx_destroy(sccg_ctx* ctx);
+int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value);
+int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out /* host */);
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* sccg_last_error(const sccg_ctx* ctx);
+
+/* ------------------------------------------------------------------------------------------- */
+/* polygon sets                                                                                 */
+/* ------------------------------------------------------------------------------------------- */
+/* One result set in CSR form. Polygon i has vertices off[i] .. off[i+1]-1; vertex v is
+ * (xy[2v], xy[2v+1]); the ring closes implicitly from the last vertex back to the first. Polygons
+ * are grouped by image tile (Sec. 2.1: one polygon file per tile): tile[] is non-decreasing. */
+typedef struct sccg_polyset {
+    int64_t n;              /* number of polygons (>= 0) */
+    const int64_t* off;     /* device, [n+1], off[0] = 0, non-decreasing */
+    const int32_t* xy;      /* device, [2*off[n]], 8-byte aligned */
+    const int32_t* tile;    /* device, [n], >= 0, non-decreasing; NULL = every polygon in tile 0 */
+    int32_t* mbr;           /* device, [4n], written by sccg_prepare: min x, min y, max x, max y */
+    int64_t* area;          /* device, [n], written by sccg_prepare: ||p|| */
+    /* host-side summary written by sccg_prepare */
+    int32_t max_nv;         /* largest vertex count */
+    int32_t max_extent;     /* largest bounding-box width or height */
+    int32_t n_tiles;        /* largest tile id + 1 */
+    int32_t reserved;       /* set by sccg_prepare once the set is valid; do not modify */
+} sccg_polyset;
+
+/* Step 1 of the path: per-polygon bounding box (MBR) and pixel area ||p|| (Sec. 3.2 computes ||p||
+ * with the shoelace formula for the paper's rectilinear polygons; here ||p|| is the pixel count
+ * itself, which equals the shoelace area on pixel-aligned rectilinear polygons and is the value
+ * that makes ||p u q|| = ||p|| + ||q|| - ||p n q|| exact for every polygon).
+ * Validates the set (>= 3 vertices, coordinate bounds, tile order) and fills the host summary
+ * fields; SYNCHRONISES the stream once to read the validation result back.
+ * Returns SCCG_EINVAL or SCCG_ERANGE for invalid sets (mbr/area contents then unspecified). */
+int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream);
+
+/* ------------------------------------------------------------------------------------------- */
+/* the hot path                                                                                 */
+/* ------------------------------------------------------------------------------------------- */
+
+/* Filter stage (Sec. 4.1 stage 3; the && operator of Fig. 1b): every pair (a, b) with
+ * tile_A[a] == tile_B[b] whose closed MBRs overlap (ax0 <= bx1 && bx0 <= ax1 && ay0 <= by1 &&
+ * by0 <= ay1), written to pa[k], pb[k] in ascending (a, b) order. Both sets must be prepared.
+ *   capacity        entries available in pa/pb
+ *   n_pairs         HOST out: total number of pairs (also when it exceeds capacity)
+ *   tile_pair_off   device out [n_tiles + 1] (may be NULL): first pair index of each tile, where
+ *                   n_tiles = max(A.n_tiles, B.n_tiles); tile t owns pairs
+ *                   tile_pair_off[t] .. tile_pair_off[t+1]-1.
+ * SYNCHRONISES the stream once (to return the count). SCCG_ECAPACITY if the pairs do not fit
+ * (nothing beyond capacity is written). */
+int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
+                         int32_t* pa, int32_t* pb, int64_t capacity, int64_t* n_pairs,
+                         int64_t* tile_pair_off, void* stream);
+
+/* Aggregator stage (Sec. 3, Algorithm 1): for each pair k, inter[k] = ||p n q|| and
+ * uni[k] = ||p|| + ||q|| - ||p n q|| (Sec. 3.2, areas of union computed indirectly), with
+ * p = A polygon pa[k] and q = B polygon pb[k]. A pair whose indices fall outside [0, A.n) or
+ * [0, B.n) is not evaluated: its inter and uni are set to -1. ||p n q|| is found by recursive sampling-box
+ * subdivision of the pair's window MBR(p) n MBR(q) (Sec. 3.2): boxes entirely inside both polygons
+ * add their pixel count, boxes outside either add nothing, and boxes still mixed once they hold
+ * fewer than T pixels are pixelized (Sec. 3.1). Both sets must be prepared. Asynchronous.
+ *   mode SCCG_MODE_PLAIN       one warp per pair, grid-stride over the n_pairs given (the caller
+ *                              launches once per tile for the one-launch-per-tile form)
+ *   mode SCCG_MODE_PERSISTENT  resident CTAs pull work items from a device queue; pairs with large
+ *                              windows are cut into several items whose partial counts are added
+ *                              with 64-bit atomics (Sec. 4.1's batching, on the device) */
+#define SCCG_MODE_PLAIN 0
+#define SCCG_MODE_PERSISTENT 1
+int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
+                    const int32_t* pa, const int32_t* pb, int64_t n_pairs,
+                    int64_t* inter, int64_t* uni, int mode, void* stream);
+
+/* Jaccard reductions of Sec. 2.1 over the pairs with inter > 0 (Sec. 4.1: pairs that do not
+ * actually intersect are not considered):
+ *   J  = sum inter / sum union                 (double(sum_inter) / double(sum_union))
+ *   J' = (1/n_nonzero) sum inter_k / union_k   (Eq. 1)
+ * Each ratio is the IEEE double quotient; the ratios are summed exactly in 128-bit fixed point and
+ * rounded once to the nearest double, then divided by n_nonzero, so J' does not depend on the
+ * summation order. Both are 0 when no pair intersects.
+ * `out` may be a host pointer (the call then SYNCHRONISES the stream) or a device pointer (the
+ * call stays asynchronous and writes the struct on the stream). */
+typedef struct sccg_jaccard_result {
+    int64_t sum_inter;
+    int64_t sum_union;
+    int64_t n_nonzero;
+    int64_t n_pairs;
+    double J;
+    double Jprime;
+} sccg_jaccard_result;
+int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_t n_pairs,
+                 sccg_jaccard_result* out, void* stream);
+
+/* ------------------------------------------------------------------------------------------- */
+/* work accounting                                                                              */
+/* ------------------------------------------------------------------------------------------- */
+/* With sccg_ctx_set_param(ctx, "count_work", 1) the prepare and pair-area kernels run an
+ * instrumented build that counts the work the method performs; the counts accumulate in the
+ * context until read. out4 (host, 4 entries): [0] (32-pixel row strip, edge) evaluations,
+ * [1] (pixel, edge) point-in-polygon tests inside those strips, [2] (sampling box, edge)
+ * classifications, [3] sampling boxes classified. Synchronous. reset != 0 zeroes the counters. */
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out4, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCCG_H */

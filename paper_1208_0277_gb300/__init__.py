@@ -1,0 +1,188 @@
+"""GB300-native exact pixel-area cross-comparison of two polygon result sets.
+
+Implements the aggregator path of Wang et al., "Accelerating Pathology Image Data Cross-Comparison
+on CPU-GPU Hybrid Systems" (PVLDB 5(11), 2012): candidate pairs by MBR overlap within tiles
+(Sec. 4.1, the && filter of Fig. 1b), exact intersection and union pixel areas by PixelBox
+sampling-box subdivision with per-pixel ray casting (Sec. 3, Algorithm 1), and the Jaccard
+similarities J and J' (Sec. 2.1, Eq. 1).
+
+All computation runs in the CUDA library ``libsccg.so`` (hand-written sm_103a kernels behind the C
+ABI in ``include/sccg.h``). This module only marshals arguments: torch supplies device memory and
+streams. There is no CPU fallback; calls raise if the library or a GPU is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+from . import _native
+from ._native import build  # noqa: F401
+
+SCCG_OK = 0
+SCCG_ECAPACITY = 3
+MODE_PLAIN = 0
+MODE_PERSISTENT = 1
+
+
+class SccgError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        lib = _native.load()
+        msg = lib.sccg_status_str(status).decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclasses.dataclass
+class DevicePolySet:
+    """A prepared polygon set resident in device memory (torch tensors) plus its C descriptor."""
+    off: object
+    xy: object
+    tile: object
+    mbr: object
+    area: object
+    c: _native.PolySetC
+
+    @property
+    def n(self) -> int:
+        return int(self.c.n)
+
+
+class Context:
+    """An sccg context on one CUDA device (scratch memory, tunables)."""
+
+    def __init__(self, device: int = 0, params: dict | None = None):
+        import json
+        self.lib = _native.load()
+        self.device = device
+        h = ctypes.c_void_p()
+        js = json.dumps(params).encode() if params else None
+        st = self.lib.sccg_ctx_create(device, js, ctypes.byref(h))
+        if st != SCCG_OK:
+            raise SccgError(st, "sccg_ctx_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sccg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, where: str):
+        if st != SCCG_OK:
+            raise SccgError(st, where, self.lib.sccg_last_error(self.h).decode())
+
+    def set_param(self, name: str, value: int):
+        self._check(self.lib.sccg_ctx_set_param(self.h, name.encode(), int(value)), "sccg_ctx_set_param")
+
+    def params(self) -> dict:
+        p = _native.ParamsC()
+        self._check(self.lib.sccg_ctx_get_params(self.h, ctypes.byref(p)), "sccg_ctx_get_params")
+        return {k: getattr(p, k) for k, _ in p._fields_}
+
+    # ------------------------------------------------------------------ sets
+    def upload(self, ps, stream=None) -> DevicePolySet:
+        """Copy a host PolySet (workload.PolySet) to the device and prepare it (MBRs, areas)."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        off = torch.from_numpy(ps.off).to(dev)
+        xy = torch.from_numpy(ps.xy).to(dev)
+        tile = torch.from_numpy(ps.tile).to(dev)
+        return self.prepare(off, xy, tile, stream)
+
+    def prepare(self, off, xy, tile=None, stream=None) -> DevicePolySet:
+        import torch
+        n = off.numel() - 1
+        mbr = torch.empty((max(n, 1), 4), dtype=torch.int32, device=off.device)
+        area = torch.empty(max(n, 1), dtype=torch.int64, device=off.device)
+        if xy.numel() == 0:
+            xy = torch.zeros(2, dtype=torch.int32, device=off.device)
+        c = _native.PolySetC(n=n, off=off.data_ptr(), xy=xy.data_ptr(), tile=_ptr(tile),
+                             mbr=mbr.data_ptr(), area=area.data_ptr())
+        self._check(self.lib.sccg_prepare(self.h, ctypes.byref(c), _stream(stream)), "sccg_prepare")
+        return DevicePolySet(off, xy, tile, mbr, area, c)
+
+    # ------------------------------------------------------------------ hot path
+    def candidate_pairs(self, A: DevicePolySet, B: DevicePolySet, capacity: int | None = None,
+                        stream=None, with_tile_offsets: bool = False):
+        """(pa, pb[, tile_pair_off]) int32 device tensors of all same-tile MBR-overlapping pairs."""
+        import torch
+        dev = A.off.device
+        n = ctypes.c_int64(0)
+        n_tiles = max(A.c.n_tiles, B.c.n_tiles, 1)
+        tpo = torch.empty(n_tiles + 1, dtype=torch.int64, device=dev) if with_tile_offsets else None
+        if capacity is None:
+            st =self.lib.sccg_candidate_pairs(self.h, ctypes.byref(A.c), ctypes.byref(B.c), None, None, 0,
+                                               ctypes.byref(n), _ptr(tpo), _stream(stream))
+            if st not in (SCCG_OK, SCCG_ECAPACITY):
+                self._check(st, "sccg_candidate_pairs")
+            capacity = int(n.value)
+        pa = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+        pb = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+        self._check(self.lib.sccg_candidate_pairs(self.h, ctypes.byref(A.c), ctypes.byref(B.c), pa.data_ptr(),
+                                                  pb.data_ptr(), capacity, ctypes.byref(n), _ptr(tpo),
+                                                  _stream(stream)), "sccg_candidate_pairs")
+        k = int(n.value)
+        if with_tile_offsets:
+            return pa[:k], pb[:k], tpo
+        return pa[:k], pb[:k]
+
+    def pair_areas(self, A: DevicePolySet, B: DevicePolySet, pa, pb, mode: int = MODE_PLAIN,
+                   out=None, stream=None):
+        """(inter, uni) int64 device tensors: ||p n q|| and ||p|| + ||q|| - ||p n q|| per pair."""
+        import torch
+        n = pa.numel()
+        if out is None:
+            inter = torch.empty(max(n, 1), dtype=torch.int64, device=pa.device)
+            uni = torch.empty(max(n, 1), dtype=torch.int64, device=pa.device)
+        else:
+            inter, uni = out
+        self._check(self.lib.sccg_pair_areas(self.h, ctypes.byref(A.c), ctypes.byref(B.c), pa.data_ptr(),
+                                             pb.data_ptr(), n, inter.data_ptr(), uni.data_ptr(), int(mode),
+                                             _stream(stream)), "sccg_pair_areas")
+        return inter[:n], uni[:n]
+
+    def pair_areas_raw(self, A, B, pa_ptr: int, pb_ptr: int, n: int, inter_ptr: int, uni_ptr: int,
+                       mode: int = MODE_PLAIN, stream=None):
+        """Pointer-level variant of pair_areas (used for per-tile slices)."""
+        self._check(self.lib.sccg_pair_areas(self.h, ctypes.byref(A.c), ctypes.byref(B.c), pa_ptr, pb_ptr, n,
+                                             inter_ptr, uni_ptr, int(mode), _stream(stream)), "sccg_pair_areas")
+
+    def jaccard(self, inter, uni, stream=None) -> dict:
+        r = _native.JaccardC()
+        n = inter.numel()
+        self._check(self.lib.sccg_jaccard(self.h, _ptr(inter) if n else None, _ptr(uni) if n else None, n,
+                                          ctypes.byref(r), _stream(stream)), "sccg_jaccard")
+        return {k: getattr(r, k) for k, _ in r._fields_}
+
+    def jaccard_device(self, inter, uni, out, stream=None):
+        """Asynchronous Jaccard into a device buffer `out` (uint8 tensor of 48 bytes)."""
+        n = inter.numel()
+        self._check(self.lib.sccg_jaccard(self.h, _ptr(inter) if n else None, _ptr(uni) if n else None, n,
+                                          ctypes.c_void_p(out.data_ptr()), _stream(stream)), "sccg_jaccard")
+
+    def work_counters(self, reset: bool = True) -> dict:
+        a = (ctypes.c_uint64 * 4)()
+        self._check(self.lib.sccg_work_counters(self.h, a, int(reset)), "sccg_work_counters")
+        return dict(strip_edges=a[0], pixel_edges=a[1], box_edges=a[2], boxes=a[3])
+
+
+def cross_compare(ctx: Context, A: DevicePolySet, B: DevicePolySet, mode: int = MODE_PLAIN, stream=None):
+    """The whole path on prepared sets: candidate pairs, pair areas, Jaccard."""
+    pa, pb = ctx.candidate_pairs(A, B, stream=stream)
+    inter, uni = ctx.pair_areas(A, B, pa, pb, mode=mode, stream=stream)
+    return dict(pa=pa, pb=pb, inter=inter, uni=uni, jaccard=ctx.jaccard(inter, uni, stream=stream))

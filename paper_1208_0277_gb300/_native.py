@@ -1,0 +1,120 @@
+"""Build and load the CUDA library libsccg.so (sm_103a) and declare its C ABI for ctypes.
+
+The library is compiled in-tree with nvcc into ``paper_1208_0277_gb300/_build/``. Loading it needs
+no GPU; calling into it does. There is no fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+CSRC = os.path.join(_PKG, "csrc")
+INCLUDE = os.path.join(_ROOT, "include")
+BUILD_DIR = os.path.join(_PKG, "_build")
+LIB_PATH = os.path.join(BUILD_DIR, "libsccg.so")
+SOURCES = ["sccg_api.cu"]
+HEADERS = ["pixelbox.cuh", "kernels.cuh"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+# Every symbol include/sccg.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "sccg_status_str", "sccg_ctx_create", "sccg_ctx_destroy", "sccg_ctx_set_param",
+    "sccg_ctx_get_params", "sccg_last_error", "sccg_prepare", "sccg_candidate_pairs",
+    "sccg_pair_areas", "sccg_jaccard", "sccg_work_counters",
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def nvcc_command(out: str) -> list[str]:
+    nvcc = os.environ.get("NVCC", "nvcc")
+    srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    return [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+            f"-I{INCLUDE}", "-o", out] + srcs
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "sccg.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libsccg.so for sm_103a (no GPU needed)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if force or _stale():
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        cmd = nvcc_command(tmp)
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class PolySetC(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("off", ctypes.c_void_p),
+        ("xy", ctypes.c_void_p),
+        ("tile", ctypes.c_void_p),
+        ("mbr", ctypes.c_void_p),
+        ("area", ctypes.c_void_p),
+        ("max_nv", ctypes.c_int32),
+        ("max_extent", ctypes.c_int32),
+        ("n_tiles", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class ParamsC(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("split_pixels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+
+class JaccardC(ctypes.Structure):
+    _fields_ = [("sum_inter", ctypes.c_int64), ("sum_union", ctypes.c_int64),
+                ("n_nonzero", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("J", ctypes.c_double), ("Jprime", ctypes.c_double)]
+
+
+def load(path: str | None = None):
+    """Load libsccg.so and declare argument types. Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libsccg.so not found at {p}: build it with "
+                               "paper_1208_0277_gb300.build() (nvcc, sm_103a)")
+        lib = ctypes.CDLL(p)
+        V, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        PS = ctypes.POINTER(PolySetC)
+        sig = {
+            "sccg_status_str": ([I], ctypes.c_char_p),
+            "sccg_ctx_create": ([I, ctypes.c_char_p, ctypes.POINTER(V)], I),
+            "sccg_ctx_destroy": ([V], I),
+            "sccg_ctx_set_param": ([V, ctypes.c_char_p, I64], I),
+            "sccg_ctx_get_params": ([V, ctypes.POINTER(ParamsC)], I),
+            "sccg_last_error": ([V], ctypes.c_char_p),
+            "sccg_prepare": ([V, PS, V], I),
+            "sccg_candidate_pairs": ([V, PS, PS, V, V, I64, ctypes.POINTER(I64), V, V], I),
+            "sccg_pair_areas": ([V, PS, PS, V, V, I64, V, V, I, V], I),
+            "sccg_jaccard": ([V, V, V, I64, V, V], I),
+            "sccg_work_counters": ([V, ctypes.POINTER(ctypes.c_uint64), I], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        if path is None:
+            _lib = lib
+        return lib

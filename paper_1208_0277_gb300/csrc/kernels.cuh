@@ -1,0 +1,431 @@
+// Kernels of the cross-comparison path: set preparation (MBR + ||p||), candidate pairs (filter),
+// pair areas (aggregator, plain and persistent forms) and the Jaccard reduction.
+#pragma once
+#include <cstdint>
+
+#include "pixelbox.cuh"
+
+namespace sccg {
+
+constexpr int kCoordLimit = 1 << 28;   // |x|, |y| <= 2^28
+constexpr int kExtentLimit = 16384;    // bounding box width / height
+constexpr int kMaxVertices = 1 << 24;
+
+// error bits reported by the prepare kernel
+constexpr int kErrFewVertices = 1;
+constexpr int kErrRange = 2;
+constexpr int kErrTiles = 4;
+
+struct PrepStats {
+    int err;
+    int max_nv;
+    int max_extent;
+    int n_tiles;
+    long long first_bad;
+};
+
+__device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
+{
+    unsigned long long a = wc.strip_edges, b = wc.pixel_edges, c = wc.box_edges, d = wc.boxes;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+        c += __shfl_xor_sync(kFull, c, o);
+        d += __shfl_xor_sync(kFull, d, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out->strip_edges, a);
+        atomicAdd(&out->pixel_edges, b);
+        atomicAdd(&out->box_edges, c);
+        atomicAdd(&out->boxes, d);
+    }
+}
+
+// ----------------------------------------------------------------------------------------------
+// a1 + a2: per-polygon MBR, validation and pixel area ||p||. One warp per polygon.
+// ----------------------------------------------------------------------------------------------
+struct PrepArgs {
+    long long n;
+    const int64_t* off;
+    const int32_t* xy;
+    const int32_t* tile;
+    int4* mbr;
+    int64_t* area;
+    PrepStats* stats;
+    int T;
+    WorkCounters* counters;
+};
+
+template <int CAP, int STK, bool COUNT>
+__global__ void __launch_bounds__(256) k_prepare(const PrepArgs a)
+{
+    extern __shared__ int4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    WorkCounters wc = {0, 0, 0, 0};
+    int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
+    long long first_bad = 0x7fffffffffffffffLL;
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
+        const long long o0 = a.off[i], o1 = a.off[i + 1];
+        const long long nvl = o1 - o0;
+        const int2* v = reinterpret_cast<const int2*>(a.xy) + o0;
+        int e = 0;
+        int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -0x7fffffff, y1 = -0x7fffffff;
+        if (nvl < 3 || nvl > kMaxVertices) {
+            e = kErrFewVertices;
+        } else {
+            const int nv = (int)nvl;
+            for (int base = 0; base < nv; base += 32) {
+                const int k = base + lane;
+                if (k < nv) {
+                    const int2 p = v[k];
+                    x0 = min(x0, p.x); x1 = max(x1, p.x);
+                    y0 = min(y0, p.y); y1 = max(y1, p.y);
+                }
+            }
+            x0 = warp_min(x0); y0 = warp_min(y0);
+            x1 = warp_max(x1); y1 = warp_max(y1);
+            if (x0 < -kCoordLimit || y0 < -kCoordLimit || x1 > kCoordLimit || y1 > kCoordLimit ||
+                x1 - x0 > kExtentLimit || y1 - y0 > kExtentLimit)
+                e = kErrRange;
+        }
+        uint32_t area = 0;
+        if (e == 0 && x1 > x0 && y1 > y0) {
+            const int nv = (int)nvl;
+            const bool res = nv <= CAP;
+            __syncwarp();
+            if (res) stage_edges(v, nv, 0, nv, S.ep, S.rp, lane);
+            __syncwarp();
+            const PolyPair pp{v, nv, res, v, nv, res};
+            area = pixelbox<false, COUNT>(pp, x0, y0, x1, y1, a.T, S, lane, wc);
+        }
+        int t = 0;
+        if (a.tile) {
+            t = a.tile[i];
+            if (t < 0 || (i > 0 && a.tile[i - 1] > t)) e |= kErrTiles;
+        }
+        if (lane == 0) {
+            a.mbr[i] = make_int4(x0, y0, x1, y1);
+            a.area[i] = (int64_t)area;
+        }
+        if (e) { err |= e; first_bad = min(first_bad, i); }
+        max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
+        if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
+        max_tile = max(max_tile, t);
+    }
+    if (lane == 0) {
+        if (err) { atomicOr(&a.stats->err, err); atomicMin(&a.stats->first_bad, first_bad); }
+        atomicMax(&a.stats->max_nv, max_nv);
+        atomicMax(&a.stats->max_extent, max_ext);
+        atomicMax(&a.stats->n_tiles, max_tile + 1);
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
+// ----------------------------------------------------------------------------------------------
+// a3: candidate pairs (filter). Tiles hold contiguous polygon ranges in both sets.
+// ----------------------------------------------------------------------------------------------
+__global__ void k_tile_ranges(const int32_t* tile, long long n, int n_tiles, long long* start)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n_tiles) return;
+    if (!tile) { start[t] = t == 0 ? 0 : n; return; }
+    long long lo = 0, hi = n;          // first index with tile[idx] >= t
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (tile[mid] < t) lo = mid + 1; else hi = mid;
+    }
+    start[t] = lo;
+}
+
+// One thread per A polygon: scan the B polygons of its tile in ascending order. COUNT_ONLY writes
+// the number of overlapping B polygons; otherwise the pairs are written from offs[a] on.
+template <bool COUNT_ONLY>
+__global__ void __launch_bounds__(256) k_pairs(const int4* __restrict__ mbrA, const int32_t* __restrict__ tileA,
+                                               long long nA, const int4* __restrict__ mbrB,
+                                               const long long* __restrict__ bstart, int n_tiles_b,
+                                               long long* __restrict__ counts_or_offs,
+                                               int32_t* __restrict__ pa, int32_t* __restrict__ pb,
+                                               long long cap)
+{
+    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nA) return;
+    const int t = tileA ? tileA[a] : 0;
+    long long cnt = 0;
+    if (t < n_tiles_b) {
+        const int4 A = mbrA[a];
+        const long long b0 = bstart[t], b1 = bstart[t + 1];
+        long long o = COUNT_ONLY ? 0 : counts_or_offs[a];
+        for (long long b = b0; b < b1; ++b) {
+            const int4 B = mbrB[b];
+            if (A.x <= B.z && B.x <= A.z && A.y <= B.w && B.y <= A.w) {
+                if (!COUNT_ONLY && o < cap) { pa[o] = (int32_t)a; pb[o] = (int32_t)b; }
+                ++o; ++cnt;
+            }
+        }
+    }
+    if (COUNT_ONLY) counts_or_offs[a] = cnt;
+}
+
+__global__ void k_gather_tile_offsets(const long long* offs, const long long* astart, int n_tiles,
+                                      int n_tiles_a, long long nA, int64_t* out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n_tiles) return;
+    const long long a = t <= n_tiles_a ? astart[t] : nA;
+    out[t] = offs[a];
+}
+
+// ----------------------------------------------------------------------------------------------
+// device-wide exclusive scan of int64 counts (three passes)
+// ----------------------------------------------------------------------------------------------
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ long long block_incl_scan(long long v, long long* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        long long s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += u;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const long long r = v + (warp > 0 ? sh[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_reduce(const long long* in, long long n, long long* bsum)
+{
+    __shared__ long long sh[32];
+    const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+    const long long v = i < n ? in[i] : 0;
+    const long long s = block_incl_scan(v, sh);
+    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_top(long long* bsum, long long nb)
+{
+    __shared__ long long sh[32];
+    __shared__ long long tot;
+    long long carry = 0;
+    for (long long base = 0; base < nb; base += kScanBlock) {
+        const long long i = base + threadIdx.x;
+        const long long v = i < nb ? bsum[i] : 0;
+        const long long s = block_incl_scan(v, sh);
+        if (i < nb) bsum[i] = carry + s - v;   // exclusive
+        if (threadIdx.x == kScanBlock - 1) tot = s;
+        __syncthreads();
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_apply(const long long* in, long long n, const long long* bsum,
+                                                           long long* out /* [n+1] */)
+{
+    __shared__ long long sh[32];
+    const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+    const long long v = i < n ? in[i] : 0;
+    const long long s = block_incl_scan(v, sh);
+    const long long base = bsum[blockIdx.x];
+    if (i < n) out[i] = base + s - v;
+    if (i == n - 1) out[n] = base + s;
+}
+
+// ----------------------------------------------------------------------------------------------
+// a4 + a5: pair areas, plain form (one warp per pair, grid-stride)
+// ----------------------------------------------------------------------------------------------
+struct AreasArgs {
+    long long n;
+    long long nA, nB;
+    const int32_t* pa;
+    const int32_t* pb;
+    const int64_t* offA; const int32_t* xyA; const int4* mbrA; const int64_t* areaA;
+    const int64_t* offB; const int32_t* xyB; const int4* mbrB; const int64_t* areaB;
+    int64_t* inter;
+    int64_t* uni;
+    int T;
+    WorkCounters* counters;
+};
+
+template <int CAP, int STK, bool COUNT>
+__global__ void __launch_bounds__(256) k_pair_areas_plain(const AreasArgs a)
+{
+    extern __shared__ int4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    WorkCounters wc = {0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
+        const int ia = a.pa[i], ib = a.pb[i];
+        int64_t out_i = -1, out_u = -1;      // invalid pair: flagged, not read
+        if (ia >= 0 && ia < a.nA && ib >= 0 && ib < a.nB) {
+            const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
+            const int wx0 = max(ma.x, mb.x), wy0 = max(ma.y, mb.y);
+            const int wx1 = min(ma.z, mb.z), wy1 = min(ma.w, mb.w);
+            uint32_t inter = 0;
+            if (wx1 > wx0 && wy1 > wy0) {
+                const long long pa0 = a.offA[ia], pa1 = a.offA[ia + 1];
+                const long long qb0 = a.offB[ib], qb1 = a.offB[ib + 1];
+                PolyPair pp;
+                pp.vp = reinterpret_cast<const int2*>(a.xyA) + pa0; pp.np = (int)(pa1 - pa0);
+                pp.vq = reinterpret_cast<const int2*>(a.xyB) + qb0; pp.nq = (int)(qb1 - qb0);
+                pp.rp_res = pp.np <= CAP;
+                pp.rq_res = pp.nq <= CAP;
+                __syncwarp();
+                if (pp.rp_res) stage_edges(pp.vp, pp.np, 0, pp.np, S.ep, S.rp, lane);
+                if (pp.rq_res) stage_edges(pp.vq, pp.nq, 0, pp.nq, S.eq, S.rq, lane);
+                __syncwarp();
+                inter = pixelbox<true, COUNT>(pp, wx0, wy0, wx1, wy1, a.T, S, lane, wc);
+            }
+            out_i = (int64_t)inter;
+            out_u = a.areaA[ia] + a.areaB[ib] - (int64_t)inter;
+        }
+        if (lane == 0) {
+            a.inter[i] = out_i;
+            a.uni[i] = out_u;
+        }
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
+// ----------------------------------------------------------------------------------------------
+// a6: Jaccard reductions (exact integer sums; ratios summed in 128-bit fixed point, scale 2^100)
+// ----------------------------------------------------------------------------------------------
+struct JPart {
+    unsigned long long si, su, nz, fx_lo, fx_hi;
+};
+
+// r = inter/union as an IEEE double, returned as r * 2^100 (exact: r >= 2^-30, so its last
+// significand bit has weight >= 2^-82).
+__device__ __forceinline__ unsigned __int128 ratio_fixed(long long inter, long long uni)
+{
+    const double r = __ddiv_rn((double)inter, (double)uni);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    const unsigned long long man = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = min(max(ex - 1075 + 100, 0), 74);   // in range whenever 0 < inter <= union < 2^31
+    return (unsigned __int128)man << sh;
+}
+
+__device__ __forceinline__ unsigned long long shfl_down_u64(unsigned long long v, int o)
+{
+    return __shfl_down_sync(kFull, v, o);
+}
+
+__global__ void __launch_bounds__(256) k_jaccard_partial(const int64_t* __restrict__ inter,
+                                                         const int64_t* __restrict__ uni, long long n,
+                                                         JPart* parts)
+{
+    unsigned long long si = 0, su = 0, nz = 0;
+    unsigned __int128 fx = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long in = inter[i];
+        if (in > 0) {
+            const long long un = uni[i];
+            si += (unsigned long long)in;
+            su += (unsigned long long)un;
+            nz += 1;
+            fx += ratio_fixed(in, un);
+        }
+    }
+    unsigned long long lo = (unsigned long long)fx, hi = (unsigned long long)(fx >> 64);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        si += shfl_down_u64(si, o);
+        su += shfl_down_u64(su, o);
+        nz += shfl_down_u64(nz, o);
+        const unsigned long long l2 = shfl_down_u64(lo, o), h2 = shfl_down_u64(hi, o);
+        const unsigned long long nl = lo + l2;
+        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+    __shared__ JPart sh[8];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[warp] = JPart{si, su, nz, lo, hi};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        JPart t = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            t.si += sh[w].si; t.su += sh[w].su; t.nz += sh[w].nz;
+            const unsigned long long nl = t.fx_lo + sh[w].fx_lo;
+            t.fx_hi += sh[w].fx_hi + (nl < t.fx_lo ? 1ull : 0ull);
+            t.fx_lo = nl;
+        }
+        parts[blockIdx.x] = t;
+    }
+}
+
+struct JaccardOut {          // mirrors sccg_jaccard_result
+    long long sum_inter, sum_union, n_nonzero, n_pairs;
+    double J, Jprime;
+};
+
+// Round a nonnegative 128-bit integer to the nearest double (ties to even) and scale by 2^e.
+__device__ __forceinline__ double u128_to_double_scaled(unsigned __int128 s, int e)
+{
+    if (s == 0) return 0.0;
+    const unsigned long long hi = (unsigned long long)(s >> 64), lo = (unsigned long long)s;
+    const int top = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    unsigned long long m;
+    int sh = 0;
+    if (top <= 52) {
+        m = lo;
+    } else {
+        sh = top - 52;
+        m = (unsigned long long)(s >> sh);
+        const unsigned __int128 rem = s & ((((unsigned __int128)1) << sh) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            m += 1;
+            if (m == (1ull << 53)) { m >>= 1; sh += 1; }
+        }
+    }
+    // m < 2^53 converts exactly; the power of two is built from its exponent bits
+    const int pe = sh + e;
+    const double p2 = __longlong_as_double((long long)(1023 + pe) << 52);
+    return (double)m * p2;
+}
+
+__global__ void k_jaccard_final(const JPart* parts, int nparts, long long n_pairs, JaccardOut* out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long si = 0, su = 0, nz = 0, lo = 0, hi = 0;
+    for (int i = 0; i < nparts; ++i) {
+        si += parts[i].si; su += parts[i].su; nz += parts[i].nz;
+        const unsigned long long nl = lo + parts[i].fx_lo;
+        hi += parts[i].fx_hi + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+    JaccardOut r;
+    r.sum_inter = (long long)si;
+    r.sum_union = (long long)su;
+    r.n_nonzero = (long long)nz;
+    r.n_pairs = n_pairs;
+    if (nz == 0) {
+        r.J = 0.0; r.Jprime = 0.0;
+    } else {
+        r.J = __ddiv_rn(__ll2double_rn((long long)si), __ll2double_rn((long long)su));
+        const unsigned __int128 s = ((unsigned __int128)hi << 64) | lo;
+        const double sum = u128_to_double_scaled(s, -100);
+        r.Jprime = __ddiv_rn(sum, __ll2double_rn((long long)nz));
+    }
+    *out = r;
+}
+
+}  // namespace sccg

@@ -1,0 +1,483 @@
+// C ABI of the cross-comparison library (declared in include/sccg.h): argument validation, scratch
+// management and kernel launches. Every step of the path runs in the kernels of kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "kernels.cuh"
+#include "sccg.h"
+
+using namespace sccg;
+
+namespace {
+
+constexpr int kStack = 160;         // sampling-box stack entries per warp
+constexpr uint32_t kPreparedMagic = 0x5CC6A11u;
+
+}  // namespace
+
+struct sccg_ctx {
+    int device = 0;
+    int sm_count = 0;
+    sccg_params params{};
+    void* ws = nullptr;             // device scratch
+    size_t ws_size = 0;
+    void* pinned = nullptr;         // small host-pinned staging area
+    WorkCounters* counters = nullptr;   // device work counters (counting mode)
+    int count_work = 0;
+    char last_err[256] = {0};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int cuda_fail(sccg_ctx* ctx, cudaError_t e, const char* where)
+{
+    if (ctx) snprintf(ctx->last_err, sizeof ctx->last_err, "%s: %s", where, cudaGetErrorString(e));
+    return SCCG_ECUDA;
+}
+
+#define SCCG_CUDA(ctx, call)                                          \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);    \
+    } while (0)
+
+#define SCCG_LAUNCHED(ctx, what)                                      \
+    do {                                                              \
+        cudaError_t e_ = cudaGetLastError();                          \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, what);     \
+    } while (0)
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Grow the device scratch to at least `bytes` (synchronises the device when it grows).
+int ws_reserve(sccg_ctx* ctx, size_t bytes)
+{
+    if (bytes <= ctx->ws_size) return SCCG_OK;
+    size_t want = std::max(bytes, ctx->ws_size * 3 / 2);
+    want = (want + 0xFFFFF) & ~size_t(0xFFFFF);
+    if (ctx->ws) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_size = 0;
+    }
+    if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(ctx->last_err, sizeof ctx->last_err, "scratch allocation of %zu bytes failed", want);
+        return SCCG_ENOMEM;
+    }
+    ctx->ws_size = want;
+    return SCCG_OK;
+}
+
+// Bump allocator over the scratch (256-byte aligned pieces).
+struct Carve {
+    char* base;
+    size_t used = 0;
+    explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count)
+    {
+        used = (used + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + used);
+        used += count * sizeof(T);
+        return p;
+    }
+};
+template <class T>
+size_t carve_size(size_t count) { return ((count * sizeof(T) + 255) & ~size_t(255)) + 256; }
+
+int edge_cap_for(int max_nv) { return max_nv <= 32 ? 32 : (max_nv <= 64 ? 64 : 128); }
+
+template <int CAP>
+size_t warp_smem() { return sizeof(WarpSmem<CAP, kStack>); }
+
+template <class K>
+int set_smem(sccg_ctx* ctx, K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024)
+        SCCG_CUDA(ctx, cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return SCCG_OK;
+}
+
+long long grid_for(const sccg_ctx* ctx, long long items, int per_block, int max_blocks_per_sm)
+{
+    long long g = (items + per_block - 1) / per_block;
+    const long long cap = (long long)ctx->sm_count * max_blocks_per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return g;
+}
+
+template <int CAP>
+int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
+{
+    const int wpc = std::max(1, std::min(8, ctx->params.warps_per_cta));
+    const size_t smem = warp_smem<CAP>() * wpc;
+    const long long grid = grid_for(ctx, a.n, wpc, 64);
+    if (ctx->count_work) {
+        int r = set_smem(ctx, k_prepare<CAP, kStack, true>, smem);
+        if (r) return r;
+        k_prepare<CAP, kStack, true><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
+    } else {
+        int r = set_smem(ctx, k_prepare<CAP, kStack, false>, smem);
+        if (r) return r;
+        k_prepare<CAP, kStack, false><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
+    }
+    SCCG_LAUNCHED(ctx, "k_prepare");
+    return SCCG_OK;
+}
+
+template <int CAP>
+int launch_plain(sccg_ctx* ctx, const AreasArgs& a, cudaStream_t st)
+{
+    const int wpc = std::max(1, std::min(8, ctx->params.warps_per_cta));
+    const size_t smem = warp_smem<CAP>() * wpc;
+    const long long grid = grid_for(ctx, a.n, wpc, 64);
+    if (ctx->count_work) {
+        int r = set_smem(ctx, k_pair_areas_plain<CAP, kStack, true>, smem);
+        if (r) return r;
+        k_pair_areas_plain<CAP, kStack, true><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
+    } else {
+        int r = set_smem(ctx, k_pair_areas_plain<CAP, kStack, false>, smem);
+        if (r) return r;
+        k_pair_areas_plain<CAP, kStack, false><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
+    }
+    SCCG_LAUNCHED(ctx, "k_pair_areas_plain");
+    return SCCG_OK;
+}
+
+int check_prepared(const sccg_polyset* s)
+{
+    if (!s) return SCCG_EINVAL;
+    if ((uint32_t)s->reserved != kPreparedMagic) return SCCG_EINVAL;
+    if (s->n < 0 || s->n > 0x7fffffffLL) return SCCG_EINVAL;
+    return SCCG_OK;
+}
+
+// exclusive scan of counts[n] into offs[n+1]; scratch from carve
+int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* offs, long long* bsum,
+                cudaStream_t st)
+{
+    if (n == 0) {
+        SCCG_CUDA(ctx, cudaMemsetAsync(offs, 0, sizeof(long long), st));
+        return SCCG_OK;
+    }
+    const long long nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_reduce<<<(unsigned)nb, kScanBlock, 0, st>>>(counts, n, bsum);
+    k_scan_top<<<1, kScanBlock, 0, st>>>(bsum, nb);
+    k_scan_apply<<<(unsigned)nb, kScanBlock, 0, st>>>(counts, n, bsum, offs);
+    SCCG_LAUNCHED(ctx, "device_scan");
+    return SCCG_OK;
+}
+
+int parse_params(const char* js, sccg_params* p)
+{
+    if (!js) return SCCG_OK;
+    static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm"};
+    int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm};
+    for (int k = 0; k < 4; ++k) {
+        char key[64];
+        snprintf(key, sizeof key, "\"%s\"", names[k]);
+        const char* at = strstr(js, key);
+        if (!at) continue;
+        at = strchr(at + strlen(key), ':');
+        if (!at) return SCCG_EINVAL;
+        char* end = nullptr;
+        const long v = strtol(at + 1, &end, 10);
+        if (end == at + 1) return SCCG_EINVAL;
+        *fields[k] = (int32_t)v;
+    }
+    return SCCG_OK;
+}
+
+int validate_params(const sccg_params& p)
+{
+    if (p.T < 2 || p.T > (1 << 28)) return SCCG_EINVAL;
+    if (p.warps_per_cta < 1 || p.warps_per_cta > 8) return SCCG_EINVAL;
+    if (p.split_pixels < 32) return SCCG_EINVAL;
+    if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return SCCG_EINVAL;
+    return SCCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sccg_status_str(int s)
+{
+    switch (s) {
+        case SCCG_OK: return "ok";
+        case SCCG_EINVAL: return "invalid argument";
+        case SCCG_ERANGE: return "coordinate or polygon extent out of range";
+        case SCCG_ECAPACITY: return "output capacity too small";
+        case SCCG_ENOMEM: return "out of device memory";
+        case SCCG_ECUDA: return "CUDA error";
+        case SCCG_ETIMEOUT: return "device wait timed out";
+        case SCCG_ENOTSUP: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
+{
+    if (!out) return SCCG_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return ndev == 0 ? SCCG_ENOTSUP : SCCG_EINVAL;
+    }
+    sccg_ctx* ctx = new (std::nothrow) sccg_ctx();
+    if (!ctx) return SCCG_ENOMEM;
+    ctx->device = device;
+    ctx->params.T = 1024;
+    ctx->params.warps_per_cta = 8;
+    ctx->params.split_pixels = 4096;
+    ctx->params.ctas_per_sm = 0;
+    int r = parse_params(params_json, &ctx->params);
+    if (!r) r = validate_params(ctx->params);
+    if (r) { delete ctx; return r; }
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete ctx; return SCCG_ECUDA; }
+    ctx->sm_count = prop.multiProcessorCount;
+    if (cudaMallocHost(&ctx->pinned, 4096) != cudaSuccess) { cudaGetLastError(); delete ctx; return SCCG_ENOMEM; }
+    if (cudaMalloc(&ctx->counters, sizeof(WorkCounters)) != cudaSuccess ||
+        cudaMemset(ctx->counters, 0, sizeof(WorkCounters)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(ctx->pinned);
+        delete ctx;
+        return SCCG_ENOMEM;
+    }
+    *out = ctx;
+    return SCCG_OK;
+}
+
+int sccg_ctx_destroy(sccg_ctx* ctx)
+{
+    if (!ctx) return SCCG_EINVAL;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        if (ctx->ws) cudaFree(ctx->ws);
+        if (ctx->counters) cudaFree(ctx->counters);
+        if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    }
+    delete ctx;
+    return SCCG_OK;
+}
+
+int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
+{
+    if (!ctx || !name) return SCCG_EINVAL;
+    sccg_params p = ctx->params;
+    if (!strcmp(name, "T")) p.T = (int32_t)value;
+    else if (!strcmp(name, "warps_per_cta")) p.warps_per_cta = (int32_t)value;
+    else if (!strcmp(name, "split_pixels")) p.split_pixels = (int32_t)value;
+    else if (!strcmp(name, "ctas_per_sm")) p.ctas_per_sm = (int32_t)value;
+    else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
+    else return SCCG_EINVAL;
+    const int r = validate_params(p);
+    if (r) return r;
+    ctx->params = p;
+    return SCCG_OK;
+}
+
+int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out)
+{
+    if (!ctx || !out) return SCCG_EINVAL;
+    *out = ctx->params;
+    return SCCG_OK;
+}
+
+const char* sccg_last_error(const sccg_ctx* ctx) { return ctx ? ctx->last_err : ""; }
+
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out4, int reset)
+{
+    if (!ctx || !out4) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    WorkCounters h;
+    SCCG_CUDA(ctx, cudaMemcpy(&h, ctx->counters, sizeof h, cudaMemcpyDeviceToHost));
+    out4[0] = h.strip_edges; out4[1] = h.pixel_edges; out4[2] = h.box_edges; out4[3] = h.boxes;
+    if (reset) SCCG_CUDA(ctx, cudaMemset(ctx->counters, 0, sizeof(WorkCounters)));
+    return SCCG_OK;
+}
+
+int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
+{
+    if (!ctx || !s || s->n < 0 || s->n > 0x7fffffffLL) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    s->reserved = 0;
+    if (!is_device_ptr(s->off) || !is_device_ptr(s->mbr) || !is_device_ptr(s->area)) return SCCG_EINVAL;
+    if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
+    if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
+    if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
+    int r = ws_reserve(ctx, carve_size<PrepStats>(1));
+    if (r) return r;
+    Carve cv(ctx->ws);
+    PrepStats* stats = cv.take<PrepStats>(1);
+    PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL};
+    // the initial stats are written by a copy from pinned memory, kept ordered on the stream
+    PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
+    *hstats = init;
+    SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, sizeof init, cudaMemcpyHostToDevice, st));
+    if (s->n > 0) {
+        PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats,
+                   ctx->params.T, ctx->counters};
+        // the largest vertex count is not known yet: use the chunked 64-edge buffers
+        r = launch_prepare<64>(ctx, a, st);
+        if (r) return r;
+    }
+    SCCG_CUDA(ctx, cudaMemcpyAsync(hstats, stats, sizeof init, cudaMemcpyDeviceToHost, st));
+    SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+    const PrepStats res = *hstats;
+    s->max_nv = res.max_nv;
+    s->max_extent = res.max_extent;
+    s->n_tiles = std::max(res.n_tiles, s->n > 0 ? 1 : 0);
+    if (res.err & (kErrFewVertices | kErrTiles)) {
+        snprintf(ctx->last_err, sizeof ctx->last_err, "invalid polygon set (flags %d, first bad polygon %lld)",
+                 res.err, res.first_bad);
+        return SCCG_EINVAL;
+    }
+    if (res.err & kErrRange) {
+        snprintf(ctx->last_err, sizeof ctx->last_err, "coordinate/extent out of range at polygon %lld",
+                 res.first_bad);
+        return SCCG_ERANGE;
+    }
+    s->reserved = (int32_t)kPreparedMagic;
+    return SCCG_OK;
+}
+
+int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, int32_t* pa,
+                         int32_t* pb, int64_t capacity, int64_t* n_pairs, int64_t* tile_pair_off,
+                         void* stream)
+{
+    if (!ctx || !n_pairs || capacity < 0) return SCCG_EINVAL;
+    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
+    if (capacity > 0 && (!is_device_ptr(pa) || !is_device_ptr(pb))) return SCCG_EINVAL;
+    if (tile_pair_off && !is_device_ptr(tile_pair_off)) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n_tiles = std::max(std::max(A->n_tiles, B->n_tiles), 1);
+    const long long nA = A->n, nB = B->n;
+    const long long nb = (nA + kScanBlock - 1) / kScanBlock + 1;
+    const size_t need = carve_size<long long>(n_tiles + 1) * 2 + carve_size<long long>(nA + 1) * 2 +
+                        carve_size<long long>(nb);
+    int r = ws_reserve(ctx, need);
+    if (r) return r;
+    Carve cv(ctx->ws);
+    long long* astart = cv.take<long long>(n_tiles + 1);
+    long long* bstart = cv.take<long long>(n_tiles + 1);
+    long long* counts = cv.take<long long>(nA + 1);
+    long long* offs = cv.take<long long>(nA + 1);
+    long long* bsum = cv.take<long long>(nb);
+    const unsigned tg = (unsigned)((n_tiles + 1 + 255) / 256);
+    k_tile_ranges<<<tg, 256, 0, st>>>(A->tile, nA, n_tiles, astart);
+    k_tile_ranges<<<tg, 256, 0, st>>>(B->tile, nB, n_tiles, bstart);
+    SCCG_LAUNCHED(ctx, "k_tile_ranges");
+    const int4* mA = reinterpret_cast<const int4*>(A->mbr);
+    const int4* mB = reinterpret_cast<const int4*>(B->mbr);
+    if (nA > 0) {
+        const unsigned ga = (unsigned)((nA + 255) / 256);
+        k_pairs<true><<<ga, 256, 0, st>>>(mA, A->tile, nA, mB, bstart, n_tiles, counts, nullptr, nullptr, 0);
+        SCCG_LAUNCHED(ctx, "k_pairs(count)");
+    }
+    r = device_scan(ctx, counts, nA, offs, bsum, st);
+    if (r) return r;
+    if (nA > 0 && capacity > 0) {
+        const unsigned ga = (unsigned)((nA + 255) / 256);
+        k_pairs<false><<<ga, 256, 0, st>>>(mA, A->tile, nA, mB, bstart, n_tiles, offs, pa, pb, capacity);
+        SCCG_LAUNCHED(ctx, "k_pairs(write)");
+    }
+    if (tile_pair_off) {
+        k_gather_tile_offsets<<<tg, 256, 0, st>>>(offs, astart, n_tiles, n_tiles, nA, tile_pair_off);
+        SCCG_LAUNCHED(ctx, "k_gather_tile_offsets");
+    }
+    long long* h = static_cast<long long*>(ctx->pinned);
+    SCCG_CUDA(ctx, cudaMemcpyAsync(h, offs + nA, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+    *n_pairs = *h;
+    return *h > capacity ? SCCG_ECAPACITY : SCCG_OK;
+}
+
+int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa,
+                    const int32_t* pb, int64_t n_pairs, int64_t* inter, int64_t* uni, int mode, void* stream)
+{
+    if (!ctx || n_pairs < 0) return SCCG_EINVAL;
+    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
+    if (mode != SCCG_MODE_PLAIN && mode != SCCG_MODE_PERSISTENT) return SCCG_EINVAL;
+    if (n_pairs == 0) return SCCG_OK;
+    if (!is_device_ptr(pa) || !is_device_ptr(pb) || !is_device_ptr(inter) || !is_device_ptr(uni))
+        return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    AreasArgs a{n_pairs, A->n, B->n, pa, pb,
+                A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
+                B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
+                inter, uni, ctx->params.T, ctx->counters};
+    const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
+    if (mode == SCCG_MODE_PERSISTENT) return SCCG_ENOTSUP;
+    switch (cap) {
+        case 32: return launch_plain<32>(ctx, a, st);
+        case 64: return launch_plain<64>(ctx, a, st);
+        default: return launch_plain<128>(ctx, a, st);
+    }
+}
+
+int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_t n_pairs,
+                 sccg_jaccard_result* out, void* stream)
+{
+    static_assert(sizeof(JaccardOut) == sizeof(sccg_jaccard_result), "layout");
+    if (!ctx || !out || n_pairs < 0) return SCCG_EINVAL;
+    if (n_pairs > 0 && (!is_device_ptr(inter) || !is_device_ptr(uni))) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool dev_out = is_device_ptr(out);
+    const int nparts = (int)std::max(1LL, std::min<long long>((n_pairs + 255) / 256, 4LL * ctx->sm_count));
+    int r = ws_reserve(ctx, carve_size<JPart>(nparts) + carve_size<JaccardOut>(1));
+    if (r) return r;
+    Carve cv(ctx->ws);
+    JPart* parts = cv.take<JPart>(nparts);
+    JaccardOut* res = dev_out ? reinterpret_cast<JaccardOut*>(out) : cv.take<JaccardOut>(1);
+    k_jaccard_partial<<<nparts, 256, 0, st>>>(inter, uni, n_pairs, parts);
+    k_jaccard_final<<<1, 32, 0, st>>>(parts, nparts, n_pairs, res);
+    SCCG_LAUNCHED(ctx, "k_jaccard");
+    if (!dev_out) {
+        SCCG_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, res, sizeof(JaccardOut), cudaMemcpyDeviceToHost, st));
+        SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+        memcpy(out, ctx->pinned, sizeof(JaccardOut));
+    }
+    return SCCG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+"""CPU checks of the boundary: the library builds for sm_103a, loads without a GPU and exports every
+entry point include/sccg.h declares; the binding's structs match the header's layout."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1208_0277_gb300 import _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _native.build()
+    return ctypes.CDLL(_native.LIB_PATH)
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "sccg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sccg_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_what_the_binding_lists():
+    assert header_functions() == sorted(_native.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    f = lib.sccg_status_str
+    f.restype = ctypes.c_char_p
+    f.argtypes = [ctypes.c_int]
+    assert f(0) == b"ok"
+    assert f(3) == b"output capacity too small"
+    assert f(99) == b"unknown status"
+
+
+def test_struct_sizes_match_header():
+    assert ctypes.sizeof(_native.PolySetC) == 8 * 6 + 4 * 4
+    assert ctypes.sizeof(_native.JaccardC) == 48
+    assert ctypes.sizeof(_native.ParamsC) == 16
+
+
+def test_ctx_create_without_gpu_reports_not_supported(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    f = lib.sccg_ctx_create
+    f.argtypes = [ctypes.c_int, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    h = ctypes.c_void_p()
+    st = f(0, None, ctypes.byref(h))
+    assert st != 0 and not h.value
+
+
+def test_product_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1208_0277_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, fn
+                assert "sccg_oracle" not in txt, fn

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Areas, MBRs, pair lists and the Jaccard values are integers or fixed doubles, so every comparison
+is exact (tolerance 0)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1208_0277_gb300 import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sccg():
+    import paper_1208_0277_gb300 as P
+    P.build()
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(sccg):
+    return sccg.Context(0)
+
+
+def gpu_run(ctx, w, mode=0):
+    import paper_1208_0277_gb300 as P
+    A = ctx.upload(w.A)
+    B = ctx.upload(w.B)
+    r = P.cross_compare(ctx, A, B, mode=mode)
+    torch.cuda.synchronize()
+    return dict(area_a=A.area.cpu().numpy()[: w.A.n], area_b=B.area.cpu().numpy()[: w.B.n],
+                mbr_a=A.mbr.cpu().numpy()[: w.A.n], mbr_b=B.mbr.cpu().numpy()[: w.B.n],
+                pa=r["pa"].cpu().numpy().astype(np.int64), pb=r["pb"].cpu().numpy().astype(np.int64),
+                inter=r["inter"].cpu().numpy(), uni=r["uni"].cpu().numpy(), jaccard=r["jaccard"])
+
+
+def assert_same(g, ref):
+    np.testing.assert_array_equal(g["mbr_a"], ref["mbr_a"])
+    np.testing.assert_array_equal(g["mbr_b"], ref["mbr_b"])
+    np.testing.assert_array_equal(g["area_a"], ref["area_a"])
+    np.testing.assert_array_equal(g["area_b"], ref["area_b"])
+    np.testing.assert_array_equal(g["pa"], ref["pa"])
+    np.testing.assert_array_equal(g["pb"], ref["pb"])
+    np.testing.assert_array_equal(g["inter"], ref["inter"])
+    np.testing.assert_array_equal(g["uni"], ref["uni"])
+    for k in ("sum_inter", "sum_union", "n_nonzero", "J", "Jprime"):
+        assert g["jaccard"][k] == ref["jaccard"][k], k
+
+
+# ------------------------------------------------------------------------------- workloads
+
+def test_single_tile_bit_exact(ctx):
+    w = W.single_tile(seed=0)
+    assert_same(gpu_run(ctx, w), O.cross_compare(w.A, w.B))
+
+
+@pytest.mark.parametrize("T", [2, 33, 200, 1024, 4096, 1 << 22])
+def test_threshold_does_not_change_results(sccg, T):
+    """T only decides where subdivision stops (Sec. 3.4); results must be identical for every T."""
+    w = W.single_tile(seed=3, n=400)
+    c = sccg.Context(0, {"T": T})
+    assert_same(gpu_run(c, w), O.cross_compare(w.A, w.B))
+
+
+@pytest.mark.parametrize("wpc", [1, 3, 8])
+def test_warps_per_cta(sccg, wpc):
+    w = W.single_tile(seed=4, n=300)
+    c = sccg.Context(0, {"warps_per_cta": wpc, "T": 64})
+    assert_same(gpu_run(c, w), O.cross_compare(w.A, w.B))
+
+
+def medium_polygons(seed, n=60, s_lo=60.0, s_hi=300.0, nv_hi=300, kind="nucleus"):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cx = rng.uniform(0, 1500, n)
+    cy = rng.uniform(-800, 700, n)
+    s = rng.uniform(s_lo, s_hi, n)
+    nv = rng.integers(3, nv_hi + 1, n)
+    x, y, c = W.star_rings(rng, cx, cy, s, nv, kind)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(c, out=off[1:])
+    xy = np.empty(2 * x.shape[0], dtype=np.int32)
+    xy[0::2], xy[1::2] = x, y
+    return W.PolySet(off, xy, np.zeros(n, dtype=np.int32))
+
+
+@pytest.mark.parametrize("T", [2, 64, 512, 4096])
+def test_medium_and_large_polygons_subdivision_and_chunked_edges(sccg, T):
+    """Windows of 60..300 px (several subdivision levels) and up to 300 vertices (edge buffers
+    re-staged chunk by chunk); concave 'tissue' rings as well."""
+    A = medium_polygons(10)
+    B = medium_polygons(11, kind="tissue")
+    w = W.Workload("medium", A, B, 1, 2048, 0)
+    c = sccg.Context(0, {"T": T})
+    g = gpu_run(c, w)
+    ref = O.cross_compare(A, B, method="rle")
+    assert_same(g, ref)
+    idx = np.arange(0, len(ref["pa"]), max(1, len(ref["pa"]) // 25))
+    bi, bu = O.pair_areas(A, B, ref["pa"][idx], ref["pb"][idx], method="brute")
+    np.testing.assert_array_equal(g["inter"][idx], bi)
+    np.testing.assert_array_equal(g["uni"][idx], bu)
+
+
+def test_whole_slide_tiles_sampled(ctx):
+    """Several tiles of the whole-slide workload: every pair against the row-interval oracle and a
+    sample against the brute force."""
+    w = W.subset_tiles(W.whole_slide(seed=0), [0, 1, 26, 312, 624])
+    g = gpu_run(ctx, w)
+    ref = O.cross_compare(w.A, w.B, method="rle")
+    assert_same(g, ref)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(len(ref["pa"]), 2000, replace=False)
+    bi, bu = O.pair_areas(w.A, w.B, ref["pa"][idx], ref["pb"][idx], method="brute")
+    np.testing.assert_array_equal(g["inter"][idx], bi)
+    np.testing.assert_array_equal(g["uni"][idx], bu)
+
+
+def test_tile_pair_offsets(ctx):
+    w = W.subset_tiles(W.whole_slide(seed=0), [3, 4, 5])
+    A, B = ctx.upload(w.A), ctx.upload(w.B)
+    pa, pb, tpo = ctx.candidate_pairs(A, B, with_tile_offsets=True)
+    tpo = tpo.cpu().numpy()
+    pa = pa.cpu().numpy()
+    assert tpo[0] == 0 and tpo[-1] == len(pa)
+    for t in range(3):
+        assert np.all(w.A.tile[pa[tpo[t]:tpo[t + 1]]] == t)
+
+
+# ------------------------------------------------------------------------------- edge cases
+
+def rings_workload(rings_a, rings_b):
+    return W.Workload("rings", W.from_rings(rings_a), W.from_rings(rings_b), 1, 0, 0)
+
+
+def test_edge_cases_ties_degenerate_selfintersecting(ctx):
+    tri = [[0, 0], [4, 0], [0, 4]]
+    tri2 = [[0, 0], [4, 0], [4, 4]]
+    tri3 = [[0, 0], [4, 4], [0, 4]]
+    diamond = [[2, 0], [4, 2], [2, 4], [0, 2]]
+    collinear = [[0, 0], [5, 0], [10, 0]]                 # zero area, zero-height window
+    thin = [[0, 0], [10, 0], [10, 1], [0, 1]]             # 1-row window
+    tall = [[3, -20], [4, -20], [4, 30], [3, 30]]         # 1-column window
+    dup = [[0, 0], [0, 0], [6, 0], [6, 0], [6, 5], [0, 5], [0, 5]]   # repeated vertices
+    bowtie = [[0, 0], [8, 8], [8, 0], [0, 8]]             # self-intersecting ring (even-odd)
+    spike = [[0, 0], [9, 1], [0, 2], [9, 3], [0, 4], [9, 5], [0, 6]]  # centres on many edges
+    rect_stack = [[1, 1], [7, 1], [7, 7], [1, 7]]
+    rings = [tri, tri2, tri3, diamond, collinear, thin, tall, dup, bowtie, spike, rect_stack]
+    w = rings_workload(rings, rings[::-1])
+    assert_same(gpu_run(ctx, w), O.cross_compare(w.A, w.B))
+
+
+def test_rectilinear_staircases_match_shoelace(ctx):
+    rng = np.random.Generator(np.random.PCG64(7))
+    rings, heights = W.staircase_rings(rng, 200, max_cols=40, max_h=30)
+    w = rings_workload(rings, rings)
+    g = gpu_run(ctx, w)
+    np.testing.assert_array_equal(g["area_a"], [int(h.sum()) for h in heights])
+    assert_same(g, O.cross_compare(w.A, w.B))
+
+
+def test_coordinate_and_extent_limits(ctx):
+    L = 1 << 28
+    big = [[L - 16384, L - 5], [L, L - 5], [L, L], [L - 16384, L]]            # extent exactly 16384
+    neg = [[-L, -L], [-L + 300, -L + 7], [-L + 11, -L + 290]]
+    diag = [[0, 0], [16384, 1], [1, 16384]]                                    # 16384^2 window
+    w = rings_workload([big, neg, diag], [big, neg, [[5, 5], [16000, 40], [30, 16200]]])
+    g = gpu_run(ctx, w)
+    ref = O.cross_compare(w.A, w.B, method="rle")
+    assert_same(g, ref)
+
+
+def test_empty_sets_and_no_pairs(ctx):
+    w = rings_workload([[[0, 0], [3, 0], [0, 3]]], [[[10, 10], [13, 10], [10, 13]]])
+    g = gpu_run(ctx, w)
+    assert len(g["pa"]) == 0
+    assert g["jaccard"]["n_nonzero"] == 0 and g["jaccard"]["J"] == 0.0
+    import paper_1208_0277_gb300 as P
+    E = ctx.prepare(torch.zeros(1, dtype=torch.int64, device="cuda"),
+                    torch.zeros(0, dtype=torch.int32, device="cuda"), None)
+    pa, pb = ctx.candidate_pairs(E, E)
+    assert pa.numel() == 0
+    assert P.cross_compare(ctx, E, E)["jaccard"]["n_pairs"] == 0
+
+
+# ------------------------------------------------------------------------------- errors
+
+def test_invalid_inputs_rejected_on_the_host(ctx, sccg):
+    with pytest.raises(sccg.SccgError) as e:
+        ctx.upload(W.from_rings([[[0, 0], [1, 1]]]))
+    assert e.value.status == 1
+    with pytest.raises(sccg.SccgError) as e:
+        ctx.upload(W.from_rings([[[0, 0], [16385, 0], [0, 3]]]))
+    assert e.value.status == 2
+    with pytest.raises(sccg.SccgError) as e:
+        ctx.upload(W.from_rings([[[0, 0], [3, 0], [0, 3]], [[0, 0], [3, 0], [0, 3]]], tiles=[1, 0]))
+    assert e.value.status == 1
+    # a host pointer where device memory is required
+    A = ctx.upload(W.from_rings([[[0, 0], [3, 0], [0, 3]]]))
+    host = np.zeros(4, dtype=np.int64)
+    st = ctx.lib.sccg_pair_areas(ctx.h, ctypes.byref(A.c), ctypes.byref(A.c), host.ctypes.data,
+                                 host.ctypes.data, 1, host.ctypes.data, host.ctypes.data, 0, None)
+    assert st == 1
