@@ -1,0 +1,458 @@
+#!/usr/bin/env python3
+"""Throughput of the exact cross-comparison path on GB300: polygon pairs/s with bit-exact int64
+intersection/union pixel areas.
+
+One step = the whole path over one synthetic workload resident in HBM:
+  a1+a2  prepare both result sets (MBRs, validation, ||p|| per polygon)
+  a3     candidate pairs (same tile, overlapping MBRs)
+  a4+a5  pair areas ||p n q|| and ||p u q|| (one kernel launch per tile, as in the per-tile form of
+         Sec. 4.1), or the persistent single-launch form (--form persistent)
+  a6     Jaccard J and J' (Sec. 2.1)
+
+Default workload: a 100,000 x 100,000 px slide cut into 4096^2 tiles, ~1M nucleus polygons per set
+(synthetic, seeded; stands in for the paper's pathology datasets, Sec. 5.1).
+
+Prints ONE JSON line (rank 0). Launch N>1 with torch.distributed.run: each rank processes its own
+slide (seed 1 + rank), no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "polygon pairs/s (bit-exact inter/union areas) on 1 GB300; % ALU peak; p99 job ms"
+UNIT = "pairs/s"
+
+# Algorithmic int32/fp32 ALU operations per unit of work, counted from the exact tests as
+# formulated ("Roofline"): one 32-pixel row strip against one edge, and one
+# sampling box against one edge.
+OPS_PER_STRIP_EDGE = 17
+OPS_PER_BOX_EDGE = 33
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--form", choices=["tiles", "persistent"], default="tiles")
+    p.add_argument("--config", type=int, default=2, help="1 single tile, 2 whole slide (default)")
+    p.add_argument("--tiles", type=int, default=0, help="restrict to the first N tiles (profiling runs)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--params", type=str, default="", help="JSON tunables for the context")
+    p.add_argument("--profile-once", action="store_true",
+                   help="run a single step of --form and exit (for ncu captures; prints no bench line)")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------------------
+
+def make_workload(config: int, seed: int, tiles: int):
+    from paper_1208_0277_gb300 import workload as W
+    if config == 1:
+        w = W.single_tile(seed=seed)
+        desc = {"workload": "single 2048x2048 tile, 1,000 star polygons per set (8-64 vertices, MBR 10-40 px)"}
+    elif config == 2:
+        w = W.whole_slide(seed=seed)
+        desc = {"workload": "whole slide 100,000x100,000 px, 4096x4096 tiles (625), ~1M star nuclei per set "
+                            "(8-64 vertices, MBR 10-40 px, 100 per 10^6 px^2); B = A jittered +-3, shifted +-5, "
+                            "10% dropped, 10% new"}
+    else:
+        raise SystemExit(f"--config {config} is not a bench workload here")
+    if tiles:
+        w = W.subset_tiles(w, range(min(tiles, w.n_tiles)))
+        desc["workload"] += f" (first {tiles} tiles)"
+    return w, desc
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pixelbox.cuh", "kernels.cuh", "sccg_api.cu"):
+        with open(os.path.join(ROOT, "paper_1208_0277_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample(w, target_s: float):
+    """Run the CPU oracle (brute force, all host cores) on the first tiles of the workload, growing
+    the sample geometrically until one run costs at least target_s / 2 (or the whole workload is
+    covered). Returns (result dict, tiles, seconds of the last run)."""
+    import oracle as O
+    from paper_1208_0277_gb300 import workload as W
+    tiles = 1
+    while True:
+        sub = W.subset_tiles(w, range(tiles)) if tiles < w.n_tiles else w
+        t0 = time.perf_counter()
+        res = O.cross_compare(sub.A, sub.B)
+        elapsed = time.perf_counter() - t0
+        if elapsed >= target_s / 2 or tiles >= w.n_tiles:
+            return res, tiles, elapsed
+        grow = max(2.0, min(8.0, target_s / max(elapsed, 1e-3)))
+        tiles = min(w.n_tiles, int(tiles * grow) + 1)
+
+
+def reference_arm(args):
+    """The CPU oracle as the reference arm: each step is a bounded sample of the same workload."""
+    import oracle as O
+    from paper_1208_0277_gb300 import workload as W
+    w, desc = make_workload(args.config, 1, args.tiles)
+    O.build()
+    # size one step so that warm-up plus timed steps take about two minutes
+    res, tiles, el = oracle_sample(w, target_s=max(1.0, 120.0 / (args.steps + args.warmup)))
+    sub = W.subset_tiles(w, range(tiles)) if tiles < w.n_tiles else w
+    for _ in range(args.warmup):
+        O.cross_compare(sub.A, sub.B)
+    times, pairs = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.cross_compare(sub.A, sub.B)
+        times.append(time.perf_counter() - t0)
+        pairs = len(r["pa"])
+    tot = sum(times)
+    value = pairs * args.steps / tot
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": desc,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {tiles} of {w.n_tiles} tiles per step ({pairs} candidate pairs; "
+                                   "brute-force pixel areas, candidate pairs and Jaccard)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1208_0277_gb300 as P
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    P.build()
+    params = json.loads(args.params) if args.params else None
+    ctx = P.Context(local_rank, params)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    w, desc = make_workload(args.config, 1 + rank, args.tiles)
+    gen_s = time.perf_counter() - t0
+
+    # inputs resident in HBM (also kept in pinned host memory for the end-to-end measurement)
+    host = {}
+    devb = {}
+    for name, ps in (("A", w.A), ("B", w.B)):
+        for f in ("off", "xy", "tile"):
+            a = torch.from_numpy(getattr(ps, f)).pin_memory()
+            host[name + f] = a
+            devb[name + f] = a.to(dev)
+    nA, nB = w.A.n, w.B.n
+    outs = {
+        "Ambr": torch.empty((nA, 4), dtype=torch.int32, device=dev), "Aarea": torch.empty(nA, dtype=torch.int64, device=dev),
+        "Bmbr": torch.empty((nB, 4), dtype=torch.int32, device=dev), "Barea": torch.empty(nB, dtype=torch.int64, device=dev),
+    }
+    A = ctx.prepare(devb["Aoff"], devb["Axy"], devb["Atile"], out=(outs["Ambr"], outs["Aarea"]))
+    B = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
+    pa0, pb0, tpo0 = ctx.candidate_pairs(A, B, with_tile_offsets=True)
+    n_pairs = int(pa0.numel())
+    cap = n_pairs
+    pa = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    pb = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    inter = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+    uni = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+    del pa0, pb0
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(form: str, phases=None):
+        e = [ev() for _ in range(5)] if phases is not None else None
+        if e: e[0].record(stream)
+        a = ctx.prepare(devb["Aoff"], devb["Axy"], devb["Atile"], out=(outs["Ambr"], outs["Aarea"]))
+        b = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
+        if e: e[1].record(stream)
+        p_a, p_b, tpo = ctx.candidate_pairs(a, b, capacity=cap, with_tile_offsets=True, out=(pa, pb))
+        if e: e[2].record(stream)
+        if form == "tiles":
+            i, u = ctx.pair_areas_tiles(a, b, p_a, p_b, tpo, out=(inter, uni))
+        else:
+            i, u = ctx.pair_areas(a, b, p_a, p_b, mode=P.MODE_PERSISTENT, out=(inter, uni))
+        if e: e[3].record(stream)
+        J = ctx.jaccard(i, u)
+        if e:
+            e[4].record(stream)
+            phases.append(e)
+        return J
+
+    if args.profile_once:
+        J = step(args.form)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_once": args.form, "pairs": n_pairs, "J": J["J"]}), flush=True)
+        return
+
+    # one counting step (untimed): algorithmic work per phase for the roofline
+    ctx.set_param("count_work", 1)
+    ctx.work_counters(reset=True)
+    a_ = ctx.prepare(devb["Aoff"], devb["Axy"], devb["Atile"], out=(outs["Ambr"], outs["Aarea"]))
+    b_ = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
+    work_prep = ctx.work_counters(reset=True)
+    p_a, p_b, tpo = ctx.candidate_pairs(a_, b_, capacity=cap, with_tile_offsets=True, out=(pa, pb))
+    ctx.pair_areas_tiles(a_, b_, p_a, p_b, tpo, out=(inter, uni))
+    torch.cuda.synchronize()
+    work_areas = ctx.work_counters(reset=True)
+    ctx.set_param("count_work", 0)
+
+    def ops(wc):
+        return wc["strip_edges"] * OPS_PER_STRIP_EDGE + wc["box_edges"] * OPS_PER_BOX_EDGE
+
+    results = {}
+    for form in (args.form, "persistent" if args.form == "tiles" else "tiles"):
+        for _ in range(max(args.warmup, 3)):
+            step(form)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        phases = []
+        launches0 = ctx.launch_count()
+        sampler = ClockSampler(local_rank) if form == args.form else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        torch.cuda.synchronize()
+        start, end = ev(), ev()
+        start.record(stream)
+        J = None
+        for _ in range(args.steps):
+            J = step(form, phases)
+        end.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        launches = ctx.launch_count() - launches0
+        ms = start.elapsed_time(end)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        ph = np.array([[p[k].elapsed_time(p[k + 1]) for k in range(4)] for p in phases])
+        results[form] = dict(ms=ms, J=J, launches=launches, clocks=clocks,
+                             phases_ms=dict(zip(["prepare", "candidate_pairs", "pair_areas", "jaccard"],
+                                                ph.mean(axis=0).round(4).tolist())))
+
+    main_r = results[args.form]
+    ms_per_step = main_r["ms"] / args.steps
+    total_pairs = n_pairs * world
+    value = total_pairs * args.steps / (main_r["ms"] / 1e3)
+
+    # roofline of the dominant kernel (average over the timed steps, CUDA events on its stream)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tops = sms * 4 * 32 * 2070e6 / 1e12
+    ph = main_r["phases_ms"]
+    if ph["pair_areas"] >= ph["prepare"]:
+        dom, dom_ms, dom_ops, dom_launches = ("k_pair_areas_plain" if args.form == "tiles" else
+                                              "k_pair_areas_persistent"), ph["pair_areas"], ops(work_areas), None
+    else:
+        dom, dom_ms, dom_ops, dom_launches = "k_prepare", ph["prepare"], ops(work_prep), 2
+    achieved = dom_ops / (dom_ms / 1e3) / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            ent = tj.get(dom, {})
+            if ent.get("source_hash") == kernel_source_hash() and ent.get("workload") == desc["workload"]:
+                traffic = ent.get("bytes_per_step")
+        except (ValueError, OSError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32/fp32 ALU lane-ops)",
+                "frac": achieved / peak_tops, "traffic": traffic, "kernel": dom,
+                "peak_note": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x 2070 MHz (max SM clock of measured peaks)",
+                "achieved_note": "algorithmic ops (strip-edge x 17 + box-edge x 33, counted on device) per step / "
+                                 "phase time (CUDA events)",
+                "work": work_areas if dom != "k_prepare" else work_prep}
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(host[k].numel() * host[k].element_size() for k in host)
+        h_inter = torch.empty(max(cap, 1), dtype=torch.int64).pin_memory()
+        h_uni = torch.empty(max(cap, 1), dtype=torch.int64).pin_memory()
+        d2h = 2 * 8 * n_pairs + 48
+
+        def e2e_step():
+            for k in host:
+                devb[k].copy_(host[k], non_blocking=True)
+            J = step(args.form)
+            h_inter[:n_pairs].copy_(inter[:n_pairs], non_blocking=True)
+            h_uni[:n_pairs].copy_(uni[:n_pairs], non_blocking=True)
+            return J
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        s0, s1 = ev(), ev()
+        s0.record(stream)
+        n_e2e = max(3, args.steps // 2)
+        for _ in range(n_e2e):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = s0.elapsed_time(s1)
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / n_e2e}
+
+    # CPU baseline (rank 0, N=1): the oracle on the host cores, with a parity check on the sample
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        res, tiles, el = oracle_sample(w, target_s=15.0)
+        k = len(res["pa"])
+        cpu = {"value": k / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {tiles} of {w.n_tiles} tiles ({k} candidate pairs, {el:.1f} s): brute-force "
+                         "pixel areas of both sets, candidate pairs, pair areas, Jaccard"}
+        g_pa = pa[:k].cpu().numpy()
+        g_pb = pb[:k].cpu().numpy()
+        g_i = inter[:k].cpu().numpy()
+        g_u = uni[:k].cpu().numpy()
+        parity = {"sample_pairs": k,
+                  "bit_exact": bool(np.array_equal(g_pa, res["pa"]) and np.array_equal(g_pb, res["pb"]) and
+                                    np.array_equal(g_i, res["inter"]) and np.array_equal(g_u, res["uni"]))}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    Jd = main_r["J"]
+    other = "persistent" if args.form == "tiles" else "tiles"
+    o = results[other]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": dict(desc, form=("one kernel launch per tile" if args.form == "tiles" else
+                                   "persistent single launch, device work queue"),
+                       pairs_per_step=n_pairs, polygons=[nA, nB], tiles=w.n_tiles,
+                       l2="inputs larger than L2 (no flush needed)",
+                       input_bytes=sum(devb[k].numel() * devb[k].element_size() for k in devb),
+                       generation_s=round(gen_s, 1), seed=1 + rank),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": main_r["clocks"],
+        "gpu_launches": main_r["launches"],
+        "phases_ms": main_r["phases_ms"],
+        "jaccard": {"J": Jd["J"], "Jprime": Jd["Jprime"], "n_nonzero": Jd["n_nonzero"]},
+        "parity_vs_oracle": parity,
+        other: {"value": total_pairs * args.steps / (o["ms"] / 1e3), "ms_per_step": o["ms"] / args.steps,
+                "phases_ms": o["phases_ms"], "gpu_launches": o["launches"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

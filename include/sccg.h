@@ -114,7 +114,8 @@ int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream);
  * by0 <= ay1), written to pa[k], pb[k] in ascending (a, b) order. Both sets must be prepared.
  *   capacity        entries available in pa/pb
  *   n_pairs         HOST out: total number of pairs (also when it exceeds capacity)
- *   tile_pair_off   device out [n_tiles + 1] (may be NULL): first pair index of each tile, where
+ *   tile_pair_off   out [n_tiles + 1], device or host memory (may be NULL): first pair index of
+ *                   each tile, where
  *                   n_tiles = max(A.n_tiles, B.n_tiles); tile t owns pairs
  *                   tile_pair_off[t] .. tile_pair_off[t+1]-1.
  * SYNCHRONISES the stream once (to return the count). SCCG_ECAPACITY if the pairs do not fit
@@ -140,6 +141,19 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
 int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                     const int32_t* pa, const int32_t* pb, int64_t n_pairs,
                     int64_t* inter, int64_t* uni, int mode, void* stream);
+
+/* The one-launch-per-tile form of the aggregator (Sec. 4.1: a task is one image tile): the same
+ * result as sccg_pair_areas in PLAIN mode, with one kernel launch per tile that has pairs.
+ *   tile_pair_off  HOST [n_tiles + 1]: tile t owns pairs tile_pair_off[t] .. tile_pair_off[t+1]-1
+ *                  (as written by sccg_candidate_pairs); must start at 0 and be non-decreasing.
+ * The launches are spread round-robin over 8 internal streams forked from `stream` (so independent
+ * tiles may run concurrently) and joined back into it before the call returns. Asynchronous. */
+int sccg_pair_areas_tiles(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
+                          const int32_t* pa, const int32_t* pb, const int64_t* tile_pair_off,
+                          int32_t n_tiles, int64_t* inter, int64_t* uni, void* stream);
+
+/* Number of kernels this context has launched so far (all calls). */
+int sccg_launch_count(const sccg_ctx* ctx, uint64_t* out /* host */);
 
 /* Jaccard reductions of Sec. 2.1 over the pairs with inter > 0 (Sec. 4.1: pairs that do not
  * actually intersect are not considered):

@@ -36,6 +36,10 @@ def _ptr(t) -> int | None:
     return None if t is None else t.data_ptr()
 
 
+def _hptr(a) -> int | None:
+    return None if a is None else a.ctypes.data
+
+
 def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -104,11 +108,16 @@ class Context:
         tile = torch.from_numpy(ps.tile).to(dev)
         return self.prepare(off, xy, tile, stream)
 
-    def prepare(self, off, xy, tile=None, stream=None) -> DevicePolySet:
+    def prepare(self, off, xy, tile=None, stream=None, out=None) -> DevicePolySet:
+        """MBRs, validation and pixel areas of a device-resident CSR set (off int64, xy int32 pairs,
+        tile int32 or None). out = (mbr int32 [n,4], area int64 [n]) reuses caller buffers."""
         import torch
         n = off.numel() - 1
-        mbr = torch.empty((max(n, 1), 4), dtype=torch.int32, device=off.device)
-        area = torch.empty(max(n, 1), dtype=torch.int64, device=off.device)
+        if out is None:
+            mbr = torch.empty((max(n, 1), 4), dtype=torch.int32, device=off.device)
+            area = torch.empty(max(n, 1), dtype=torch.int64, device=off.device)
+        else:
+            mbr, area = out
         if xy.numel() == 0:
             xy = torch.zeros(2, dtype=torch.int32, device=off.device)
         c = _native.PolySetC(n=n, off=off.data_ptr(), xy=xy.data_ptr(), tile=_ptr(tile),
@@ -118,23 +127,29 @@ class Context:
 
     # ------------------------------------------------------------------ hot path
     def candidate_pairs(self, A: DevicePolySet, B: DevicePolySet, capacity: int | None = None,
-                        stream=None, with_tile_offsets: bool = False):
-        """(pa, pb[, tile_pair_off]) int32 device tensors of all same-tile MBR-overlapping pairs."""
+                        stream=None, with_tile_offsets: bool = False, out=None):
+        """(pa, pb) int32 device tensors of all same-tile MBR-overlapping pairs; with
+        with_tile_offsets also the host int64 array of per-tile pair offsets [n_tiles + 1]."""
+        import numpy as np
         import torch
         dev = A.off.device
         n = ctypes.c_int64(0)
         n_tiles = max(A.c.n_tiles, B.c.n_tiles, 1)
-        tpo = torch.empty(n_tiles + 1, dtype=torch.int64, device=dev) if with_tile_offsets else None
+        tpo = np.zeros(n_tiles + 1, dtype=np.int64) if with_tile_offsets else None
         if capacity is None:
-            st =self.lib.sccg_candidate_pairs(self.h, ctypes.byref(A.c), ctypes.byref(B.c), None, None, 0,
-                                               ctypes.byref(n), _ptr(tpo), _stream(stream))
+            st = self.lib.sccg_candidate_pairs(self.h, ctypes.byref(A.c), ctypes.byref(B.c), None, None, 0,
+                                               ctypes.byref(n), _hptr(tpo), _stream(stream))
             if st not in (SCCG_OK, SCCG_ECAPACITY):
                 self._check(st, "sccg_candidate_pairs")
             capacity = int(n.value)
-        pa = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
-        pb = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+        if out is None:
+            pa = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+            pb = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+        else:
+            pa, pb = out
+            capacity = min(capacity, pa.numel(), pb.numel())
         self._check(self.lib.sccg_candidate_pairs(self.h, ctypes.byref(A.c), ctypes.byref(B.c), pa.data_ptr(),
-                                                  pb.data_ptr(), capacity, ctypes.byref(n), _ptr(tpo),
+                                                  pb.data_ptr(), capacity, ctypes.byref(n), _hptr(tpo),
                                                   _stream(stream)), "sccg_candidate_pairs")
         k = int(n.value)
         if with_tile_offsets:
@@ -155,6 +170,27 @@ class Context:
                                              pb.data_ptr(), n, inter.data_ptr(), uni.data_ptr(), int(mode),
                                              _stream(stream)), "sccg_pair_areas")
         return inter[:n], uni[:n]
+
+    def pair_areas_tiles(self, A: DevicePolySet, B: DevicePolySet, pa, pb, tile_pair_off, out=None, stream=None):
+        """One kernel launch per tile (tile_pair_off: host int64 [n_tiles + 1])."""
+        import numpy as np
+        import torch
+        n = pa.numel()
+        tpo = np.ascontiguousarray(tile_pair_off, dtype=np.int64)
+        if out is None:
+            inter = torch.empty(max(n, 1), dtype=torch.int64, device=pa.device)
+            uni = torch.empty(max(n, 1), dtype=torch.int64, device=pa.device)
+        else:
+            inter, uni = out
+        self._check(self.lib.sccg_pair_areas_tiles(self.h, ctypes.byref(A.c), ctypes.byref(B.c), pa.data_ptr(),
+                                                   pb.data_ptr(), tpo.ctypes.data, len(tpo) - 1, inter.data_ptr(),
+                                                   uni.data_ptr(), _stream(stream)), "sccg_pair_areas_tiles")
+        return inter[:n], uni[:n]
+
+    def launch_count(self) -> int:
+        c = ctypes.c_uint64(0)
+        self._check(self.lib.sccg_launch_count(self.h, ctypes.byref(c)), "sccg_launch_count")
+        return int(c.value)
 
     def pair_areas_raw(self, A, B, pa_ptr: int, pb_ptr: int, n: int, inter_ptr: int, uni_ptr: int,
                        mode: int = MODE_PLAIN, stream=None):

@@ -24,7 +24,8 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 EXPORTS = [
     "sccg_status_str", "sccg_ctx_create", "sccg_ctx_destroy", "sccg_ctx_set_param",
     "sccg_ctx_get_params", "sccg_last_error", "sccg_prepare", "sccg_candidate_pairs",
-    "sccg_pair_areas", "sccg_jaccard", "sccg_work_counters",
+    "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_launch_count", "sccg_jaccard",
+    "sccg_work_counters",
 ]
 
 _lock = threading.Lock()
@@ -108,6 +109,8 @@ def load(path: str | None = None):
             "sccg_prepare": ([V, PS, V], I),
             "sccg_candidate_pairs": ([V, PS, PS, V, V, I64, ctypes.POINTER(I64), V, V], I),
             "sccg_pair_areas": ([V, PS, PS, V, V, I64, V, V, I, V], I),
+            "sccg_pair_areas_tiles": ([V, PS, PS, V, V, V, ctypes.c_int32, V, V, V], I),
+            "sccg_launch_count": ([V, ctypes.POINTER(ctypes.c_uint64)], I),
             "sccg_jaccard": ([V, V, V, I64, V, V], I),
             "sccg_work_counters": ([V, ctypes.POINTER(ctypes.c_uint64), I], I),
         }

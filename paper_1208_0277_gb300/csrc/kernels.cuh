@@ -304,6 +304,120 @@ __global__ void __launch_bounds__(256) k_pair_areas_plain(const AreasArgs a)
 }
 
 // ----------------------------------------------------------------------------------------------
+// a7: persistent form. Each pair's window is cut into work items of at most side x side pixels
+// (heavy pairs spread over many warps); resident warps pull chunks of items from a device queue.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool pair_window(const AreasArgs& a, long long i, int& ia, int& ib, int& wx0, int& wy0,
+                                            int& wx1, int& wy1)
+{
+    ia = a.pa[i];
+    ib = a.pb[i];
+    if (ia < 0 || ia >= a.nA || ib < 0 || ib >= a.nB) return false;
+    const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
+    wx0 = max(ma.x, mb.x); wy0 = max(ma.y, mb.y);
+    wx1 = min(ma.z, mb.z); wy1 = min(ma.w, mb.w);
+    return true;
+}
+
+// One thread per pair: number of work items; pairs without items get their final values here.
+__global__ void k_plan(const AreasArgs a, int side, long long* nitems)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int ia, ib, wx0, wy0, wx1, wy1;
+    long long k = 0;
+    if (!pair_window(a, i, ia, ib, wx0, wy0, wx1, wy1)) {
+        a.inter[i] = -1;
+        a.uni[i] = -1;
+    } else if (wx1 <= wx0 || wy1 <= wy0) {
+        a.inter[i] = 0;
+        a.uni[i] = a.areaA[ia] + a.areaB[ib];
+    } else {
+        k = (long long)((wx1 - wx0 + side - 1) / side) * ((wy1 - wy0 + side - 1) / side);
+        if (k > 1) a.inter[i] = 0;     // accumulated by atomics
+    }
+    nitems[i] = k;
+}
+
+// Pairs cut into several items: union from the accumulated intersection.
+__global__ void k_union(const AreasArgs a, const long long* nitems)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n || nitems[i] <= 1) return;
+    a.uni[i] = a.areaA[a.pa[i]] + a.areaB[a.pb[i]] - a.inter[i];
+}
+
+// Largest p in [0, n) with ioff[p] <= it (ioff non-decreasing, ioff[0] = 0, it < ioff[n]):
+// 32-ary search, one probe per lane per round. Whole warp, converged.
+__device__ __forceinline__ long long find_pair(const long long* ioff, long long n, long long it, int lane)
+{
+    long long lo = 0, hi = n;   // ioff[lo] <= it, and the answer is < hi
+    while (hi - lo > 1) {
+        const long long step = (hi - lo + 31) / 32;
+        const long long pos = lo + (long long)lane * step;
+        const bool ok = pos < hi && ioff[pos] <= it;
+        const unsigned m = __ballot_sync(kFull, ok);
+        const int L = 31 - __clz(m);          // lane 0 always qualifies (ioff[lo] <= it)
+        lo = lo + (long long)L * step;
+        hi = min(lo + step, hi);
+    }
+    return lo;
+}
+
+constexpr int kItemChunk = 4;
+
+template <int CAP, int STK, bool COUNT>
+__global__ void __launch_bounds__(256) k_pair_areas_persistent(const AreasArgs a, int side, const long long* nitems,
+                                                               const long long* ioff,
+                                                               unsigned long long* head)
+{
+    extern __shared__ int4 smem4[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    WorkCounters wc = {0, 0, 0, 0};
+    const long long total = ioff[a.n];
+    for (;;) {
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(head, (unsigned long long)kItemChunk);
+        first = __shfl_sync(kFull, first, 0);
+        if ((long long)first >= total) break;
+        const long long last = min((long long)first + kItemChunk, total);
+        long long i = find_pair(ioff, a.n, (long long)first, lane);
+        for (long long it = (long long)first; it < last; ++it) {
+            while (ioff[i + 1] <= it) ++i;            // warp-uniform walk to the item's pair
+            const long long sub = it - ioff[i];
+            int ia, ib, wx0, wy0, wx1, wy1;
+            pair_window(a, i, ia, ib, wx0, wy0, wx1, wy1);
+            const int gx = (wx1 - wx0 + side - 1) / side;
+            const int sx = (int)(sub % gx), sy = (int)(sub / gx);
+            const int x0 = wx0 + sx * side, y0 = wy0 + sy * side;
+            const int x1 = min(x0 + side, wx1), y1 = min(y0 + side, wy1);
+            const long long pa0 = a.offA[ia], pa1 = a.offA[ia + 1];
+            const long long qb0 = a.offB[ib], qb1 = a.offB[ib + 1];
+            PolyPair pp;
+            pp.vp = reinterpret_cast<const int2*>(a.xyA) + pa0; pp.np = (int)(pa1 - pa0);
+            pp.vq = reinterpret_cast<const int2*>(a.xyB) + qb0; pp.nq = (int)(qb1 - qb0);
+            pp.rp_res = pp.np <= CAP;
+            pp.rq_res = pp.nq <= CAP;
+            __syncwarp();
+            if (pp.rp_res) stage_edges(pp.vp, pp.np, 0, pp.np, S.ep, S.rp, lane);
+            if (pp.rq_res) stage_edges(pp.vq, pp.nq, 0, pp.nq, S.eq, S.rq, lane);
+            __syncwarp();
+            const uint32_t cnt = pixelbox<true, COUNT>(pp, x0, y0, x1, y1, a.T, S, lane, wc);
+            if (lane == 0) {
+                if (nitems[i] == 1) {
+                    a.inter[i] = (int64_t)cnt;
+                    a.uni[i] = a.areaA[ia] + a.areaB[ib] - (int64_t)cnt;
+                } else {
+                    atomicAdd(reinterpret_cast<unsigned long long*>(a.inter + i), (unsigned long long)cnt);
+                }
+            }
+        }
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
+// ----------------------------------------------------------------------------------------------
 // a6: Jaccard reductions (exact integer sums; ratios summed in 128-bit fixed point, scale 2^100)
 // ----------------------------------------------------------------------------------------------
 struct JPart {

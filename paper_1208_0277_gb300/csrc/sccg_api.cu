@@ -29,6 +29,11 @@ struct sccg_ctx {
     void* pinned = nullptr;         // small host-pinned staging area
     WorkCounters* counters = nullptr;   // device work counters (counting mode)
     int count_work = 0;
+    unsigned long long launches = 0;    // kernels launched by this context (all calls)
+    static constexpr int kTileStreams = 8;
+    cudaStream_t tstream[kTileStreams] = {};
+    cudaEvent_t tevent[kTileStreams + 1] = {};
+    bool tile_streams_ready = false;
     char last_err[256] = {0};
 };
 
@@ -153,6 +158,7 @@ int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
         k_prepare<CAP, kStack, false><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
     }
     SCCG_LAUNCHED(ctx, "k_prepare");
+    ctx->launches += 1;
     return SCCG_OK;
 }
 
@@ -172,6 +178,27 @@ int launch_plain(sccg_ctx* ctx, const AreasArgs& a, cudaStream_t st)
         k_pair_areas_plain<CAP, kStack, false><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
     }
     SCCG_LAUNCHED(ctx, "k_pair_areas_plain");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+template <int CAP>
+int launch_persistent(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
+                      unsigned long long* head, cudaStream_t st)
+{
+    const int wpc = std::max(1, std::min(8, ctx->params.warps_per_cta));
+    const size_t smem = warp_smem<CAP>() * wpc;
+    auto kfn = ctx->count_work ? k_pair_areas_persistent<CAP, kStack, true> : k_pair_areas_persistent<CAP, kStack, false>;
+    int r = set_smem(ctx, kfn, smem);
+    if (r) return r;
+    int per_sm = ctx->params.ctas_per_sm;
+    if (per_sm <= 0) {
+        SCCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpc, smem));
+        per_sm = std::max(per_sm, 1);
+    }
+    kfn<<<(unsigned)(ctx->sm_count * per_sm), 32 * wpc, smem, st>>>(a, side, nitems, ioff, head);
+    SCCG_LAUNCHED(ctx, "k_pair_areas_persistent");
+    ctx->launches += 1;
     return SCCG_OK;
 }
 
@@ -196,6 +223,7 @@ int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* 
     k_scan_top<<<1, kScanBlock, 0, st>>>(bsum, nb);
     k_scan_apply<<<(unsigned)nb, kScanBlock, 0, st>>>(counts, n, bsum, offs);
     SCCG_LAUNCHED(ctx, "device_scan");
+    ctx->launches += 3;
     return SCCG_OK;
 }
 
@@ -291,6 +319,10 @@ int sccg_ctx_destroy(sccg_ctx* ctx)
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->pinned) cudaFreeHost(ctx->pinned);
+        if (ctx->tile_streams_ready) {
+            for (int k = 0; k < sccg_ctx::kTileStreams; ++k) cudaStreamDestroy(ctx->tstream[k]);
+            for (int k = 0; k <= sccg_ctx::kTileStreams; ++k) cudaEventDestroy(ctx->tevent[k]);
+        }
     }
     delete ctx;
     return SCCG_OK;
@@ -385,13 +417,13 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     if (!ctx || !n_pairs || capacity < 0) return SCCG_EINVAL;
     if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
     if (capacity > 0 && (!is_device_ptr(pa) || !is_device_ptr(pb))) return SCCG_EINVAL;
-    if (tile_pair_off && !is_device_ptr(tile_pair_off)) return SCCG_EINVAL;
+    const bool tpo_host = tile_pair_off && !is_device_ptr(tile_pair_off);
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int n_tiles = std::max(std::max(A->n_tiles, B->n_tiles), 1);
     const long long nA = A->n, nB = B->n;
     const long long nb = (nA + kScanBlock - 1) / kScanBlock + 1;
-    const size_t need = carve_size<long long>(n_tiles + 1) * 2 + carve_size<long long>(nA + 1) * 2 +
+    const size_t need = carve_size<long long>(n_tiles + 1) * 3 + carve_size<long long>(nA + 1) * 2 +
                         carve_size<long long>(nb);
     int r = ws_reserve(ctx, need);
     if (r) return r;
@@ -401,16 +433,19 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     long long* counts = cv.take<long long>(nA + 1);
     long long* offs = cv.take<long long>(nA + 1);
     long long* bsum = cv.take<long long>(nb);
+    long long* tpo_dev = cv.take<long long>(n_tiles + 1);
     const unsigned tg = (unsigned)((n_tiles + 1 + 255) / 256);
     k_tile_ranges<<<tg, 256, 0, st>>>(A->tile, nA, n_tiles, astart);
     k_tile_ranges<<<tg, 256, 0, st>>>(B->tile, nB, n_tiles, bstart);
     SCCG_LAUNCHED(ctx, "k_tile_ranges");
+    ctx->launches += 2;
     const int4* mA = reinterpret_cast<const int4*>(A->mbr);
     const int4* mB = reinterpret_cast<const int4*>(B->mbr);
     if (nA > 0) {
         const unsigned ga = (unsigned)((nA + 255) / 256);
         k_pairs<true><<<ga, 256, 0, st>>>(mA, A->tile, nA, mB, bstart, n_tiles, counts, nullptr, nullptr, 0);
         SCCG_LAUNCHED(ctx, "k_pairs(count)");
+        ctx->launches += 1;
     }
     r = device_scan(ctx, counts, nA, offs, bsum, st);
     if (r) return r;
@@ -418,13 +453,19 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
         const unsigned ga = (unsigned)((nA + 255) / 256);
         k_pairs<false><<<ga, 256, 0, st>>>(mA, A->tile, nA, mB, bstart, n_tiles, offs, pa, pb, capacity);
         SCCG_LAUNCHED(ctx, "k_pairs(write)");
+        ctx->launches += 1;
     }
     if (tile_pair_off) {
-        k_gather_tile_offsets<<<tg, 256, 0, st>>>(offs, astart, n_tiles, n_tiles, nA, tile_pair_off);
+        k_gather_tile_offsets<<<tg, 256, 0, st>>>(offs, astart, n_tiles, n_tiles, nA,
+                                                  tpo_host ? reinterpret_cast<int64_t*>(tpo_dev) : tile_pair_off);
         SCCG_LAUNCHED(ctx, "k_gather_tile_offsets");
+        ctx->launches += 1;
     }
     long long* h = static_cast<long long*>(ctx->pinned);
     SCCG_CUDA(ctx, cudaMemcpyAsync(h, offs + nA, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    if (tpo_host)
+        SCCG_CUDA(ctx, cudaMemcpyAsync(tile_pair_off, tpo_dev, sizeof(long long) * (n_tiles + 1),
+                                       cudaMemcpyDeviceToHost, st));
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
     *n_pairs = *h;
     return *h > capacity ? SCCG_ECAPACITY : SCCG_OK;
@@ -446,12 +487,100 @@ int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                 B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
                 inter, uni, ctx->params.T, ctx->counters};
     const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
-    if (mode == SCCG_MODE_PERSISTENT) return SCCG_ENOTSUP;
+    if (mode == SCCG_MODE_PERSISTENT) {
+        int side = 1;
+        while ((long long)(side + 1) * (side + 1) <= ctx->params.split_pixels) ++side;
+        const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
+        int r = ws_reserve(ctx, carve_size<long long>(n_pairs + 1) * 2 + carve_size<long long>(nb) +
+                                    carve_size<unsigned long long>(1));
+        if (r) return r;
+        Carve cv(ctx->ws);
+        long long* nitems = cv.take<long long>(n_pairs + 1);
+        long long* ioff = cv.take<long long>(n_pairs + 1);
+        long long* bsum = cv.take<long long>(nb);
+        unsigned long long* head = cv.take<unsigned long long>(1);
+        const unsigned g = (unsigned)((n_pairs + 255) / 256);
+        k_plan<<<g, 256, 0, st>>>(a, side, nitems);
+        SCCG_LAUNCHED(ctx, "k_plan");
+        ctx->launches += 1;
+        r = device_scan(ctx, nitems, n_pairs, ioff, bsum, st);
+        if (r) return r;
+        SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, sizeof(unsigned long long), st));
+        switch (cap) {
+            case 32: r = launch_persistent<32>(ctx, a, side, nitems, ioff, head, st); break;
+            case 64: r = launch_persistent<64>(ctx, a, side, nitems, ioff, head, st); break;
+            default: r = launch_persistent<128>(ctx, a, side, nitems, ioff, head, st); break;
+        }
+        if (r) return r;
+        k_union<<<g, 256, 0, st>>>(a, nitems);
+        SCCG_LAUNCHED(ctx, "k_union");
+        ctx->launches += 1;
+        return SCCG_OK;
+    }
     switch (cap) {
         case 32: return launch_plain<32>(ctx, a, st);
         case 64: return launch_plain<64>(ctx, a, st);
         default: return launch_plain<128>(ctx, a, st);
     }
+}
+
+int sccg_pair_areas_tiles(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa,
+                          const int32_t* pb, const int64_t* tile_pair_off, int32_t n_tiles, int64_t* inter,
+                          int64_t* uni, void* stream)
+{
+    if (!ctx || !tile_pair_off || n_tiles < 0) return SCCG_EINVAL;
+    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
+    if (is_device_ptr(tile_pair_off)) return SCCG_EINVAL;   // must be host memory
+    if (n_tiles == 0 || tile_pair_off[n_tiles] == 0) return SCCG_OK;
+    if (tile_pair_off[0] != 0) return SCCG_EINVAL;
+    for (int t = 0; t < n_tiles; ++t)
+        if (tile_pair_off[t + 1] < tile_pair_off[t]) return SCCG_EINVAL;
+    if (!is_device_ptr(pa) || !is_device_ptr(pb) || !is_device_ptr(inter) || !is_device_ptr(uni))
+        return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!ctx->tile_streams_ready) {
+        for (int k = 0; k < sccg_ctx::kTileStreams; ++k)
+            SCCG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->tstream[k], cudaStreamNonBlocking));
+        for (int k = 0; k <= sccg_ctx::kTileStreams; ++k)
+            SCCG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->tevent[k], cudaEventDisableTiming));
+        ctx->tile_streams_ready = true;
+    }
+    // fork the tile streams from the caller's stream
+    SCCG_CUDA(ctx, cudaEventRecord(ctx->tevent[sccg_ctx::kTileStreams], st));
+    for (int k = 0; k < sccg_ctx::kTileStreams; ++k)
+        SCCG_CUDA(ctx, cudaStreamWaitEvent(ctx->tstream[k], ctx->tevent[sccg_ctx::kTileStreams], 0));
+    const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
+    int k = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        const long long p0 = tile_pair_off[t], p1 = tile_pair_off[t + 1];
+        if (p1 == p0) continue;
+        AreasArgs a{p1 - p0, A->n, B->n, pa + p0, pb + p0,
+                    A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
+                    B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
+                    inter + p0, uni + p0, ctx->params.T, ctx->counters};
+        int r;
+        switch (cap) {
+            case 32: r = launch_plain<32>(ctx, a, ctx->tstream[k]); break;
+            case 64: r = launch_plain<64>(ctx, a, ctx->tstream[k]); break;
+            default: r = launch_plain<128>(ctx, a, ctx->tstream[k]); break;
+        }
+        if (r) return r;
+        k = (k + 1) % sccg_ctx::kTileStreams;
+    }
+    // join them back into the caller's stream
+    for (int j = 0; j < sccg_ctx::kTileStreams; ++j) {
+        SCCG_CUDA(ctx, cudaEventRecord(ctx->tevent[j], ctx->tstream[j]));
+        SCCG_CUDA(ctx, cudaStreamWaitEvent(st, ctx->tevent[j], 0));
+    }
+    return SCCG_OK;
+}
+
+int sccg_launch_count(const sccg_ctx* ctx, uint64_t* out)
+{
+    if (!ctx || !out) return SCCG_EINVAL;
+    *out = ctx->launches;
+    return SCCG_OK;
 }
 
 int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_t n_pairs,
@@ -472,6 +601,7 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
     k_jaccard_partial<<<nparts, 256, 0, st>>>(inter, uni, n_pairs, parts);
     k_jaccard_final<<<1, 32, 0, st>>>(parts, nparts, n_pairs, res);
     SCCG_LAUNCHED(ctx, "k_jaccard");
+    ctx->launches += 2;
     if (!dev_out) {
         SCCG_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, res, sizeof(JaccardOut), cudaMemcpyDeviceToHost, st));
         SCCG_CUDA(ctx, cudaStreamSynchronize(st));

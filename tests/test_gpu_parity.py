@@ -118,15 +118,37 @@ def test_whole_slide_tiles_sampled(ctx):
     np.testing.assert_array_equal(g["uni"][idx], bu)
 
 
-def test_tile_pair_offsets(ctx):
-    w = W.subset_tiles(W.whole_slide(seed=0), [3, 4, 5])
+def test_tile_pair_offsets_and_one_launch_per_tile(ctx):
+    w = W.subset_tiles(W.whole_slide(seed=0), [3, 4, 5, 30, 31])
     A, B = ctx.upload(w.A), ctx.upload(w.B)
     pa, pb, tpo = ctx.candidate_pairs(A, B, with_tile_offsets=True)
-    tpo = tpo.cpu().numpy()
-    pa = pa.cpu().numpy()
-    assert tpo[0] == 0 and tpo[-1] == len(pa)
-    for t in range(3):
-        assert np.all(w.A.tile[pa[tpo[t]:tpo[t + 1]]] == t)
+    pa_h = pa.cpu().numpy()
+    assert tpo[0] == 0 and tpo[-1] == len(pa_h)
+    for t in range(5):
+        assert np.all(w.A.tile[pa_h[tpo[t]:tpo[t + 1]]] == t)
+    before = ctx.launch_count()
+    inter, uni = ctx.pair_areas_tiles(A, B, pa, pb, tpo)
+    torch.cuda.synchronize()
+    assert ctx.launch_count() - before == int((np.diff(tpo) > 0).sum())
+    i2, u2 = ctx.pair_areas(A, B, pa, pb)
+    np.testing.assert_array_equal(inter.cpu().numpy(), i2.cpu().numpy())
+    np.testing.assert_array_equal(uni.cpu().numpy(), u2.cpu().numpy())
+    ref_i, ref_u = O.pair_areas(w.A, w.B, pa_h, pb.cpu().numpy(), method="rle")
+    np.testing.assert_array_equal(inter.cpu().numpy(), ref_i)
+    np.testing.assert_array_equal(uni.cpu().numpy(), ref_u)
+
+
+@pytest.mark.parametrize("split", [32, 100, 4096])
+def test_persistent_queue_matches_oracle(sccg, split):
+    """Persistent form: one launch, device work queue, windows cut into items of about `split`
+    pixels (many items per pair for small `split`); results identical to the oracle."""
+    c = sccg.Context(0, {"split_pixels": split, "T": 256})
+    w = W.single_tile(seed=5, n=500)
+    assert_same(gpu_run(c, w, mode=1), O.cross_compare(w.A, w.B))
+    A = medium_polygons(12)
+    B = medium_polygons(13, kind="tissue")
+    wm = W.Workload("medium", A, B, 1, 2048, 0)
+    assert_same(gpu_run(c, wm, mode=1), O.cross_compare(A, B, method="rle"))
 
 
 # ------------------------------------------------------------------------------- edge cases
