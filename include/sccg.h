@@ -175,6 +175,24 @@ typedef struct sccg_jaccard_result {
 int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_t n_pairs,
                  sccg_jaccard_result* out, void* stream);
 
+/* Allocation-free variant of sccg_jaccard (the paper has no counterpart; this is a library
+ * service). Same results as sccg_jaccard, but it needs no context and allocates nothing: its scratch
+ * (4096 partial-sum slots, 160 KB) is a fixed array in device memory that every GPU loading this
+ * library keeps until the process exits. It is meant for callers that must not allocate device
+ * memory: code running while a CUDA graph is being captured (allocation calls are not allowed
+ * there), plugins inside a host application that owns all device memory through its own pool, and
+ * latency-critical loops where cudaMalloc/cudaFree would synchronise the device.
+ *   inter, uni  device, [n_pairs] (as written by sccg_pair_areas)
+ *   out         DEVICE pointer to one sccg_jaccard_result, written asynchronously on `stream`
+ *   n_pairs     at most 268,435,456 (4096 slots x 65,536 pairs); larger counts return SCCG_ERANGE
+ * The first call on a device (the current device) looks up the array's device address; make that
+ * first call before any stream capture. All calls share the one array and leave their partial sums
+ * in it; each call writes every slot it reads before reading it, so nothing needs clearing, but two
+ * calls whose work overlaps on the GPU (different streams, or different host threads) race on the
+ * array and must be serialised by the caller. Returns SCCG_EINVAL for host pointers or n_pairs < 0. */
+int sccg_jaccard_static(const int64_t* inter, const int64_t* uni, int64_t n_pairs,
+                        sccg_jaccard_result* out, void* stream);
+
 /* ------------------------------------------------------------------------------------------- */
 /* work accounting                                                                              */
 /* ------------------------------------------------------------------------------------------- */

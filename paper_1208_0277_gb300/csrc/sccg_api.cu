@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "kernels.cuh"
@@ -253,6 +254,91 @@ int validate_params(const sccg_params& p)
     if (p.warps_per_cta < 1 || p.warps_per_cta > 8) return SCCG_EINVAL;
     if (p.split_pixels < 32) return SCCG_EINVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return SCCG_EINVAL;
+    return SCCG_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free Jaccard: the partial sums live in a fixed array in device global memory instead
+// of context scratch, for callers that may not allocate device memory (see include/sccg.h).
+// ------------------------------------------------------------------------------------------------
+constexpr int kStaticParts = 4096;            // partial-sum slots in the fixed array
+constexpr long long kStaticChunk = 65536;     // pairs reduced into one slot
+constexpr long long kStaticMaxPairs = kStaticParts * kStaticChunk;   // 268,435,456 pairs
+constexpr int kStaticMaxDevices = 64;
+
+// One CTA reduces pairs [blockIdx.x * chunk, min(n, (blockIdx.x + 1) * chunk)) into parts[blockIdx.x],
+// exactly as k_jaccard_partial does for its grid-stride share.
+__global__ void __launch_bounds__(256) k_jaccard_partial_chunked(const int64_t* __restrict__ inter,
+                                                                 const int64_t* __restrict__ uni, long long n,
+                                                                 long long chunk, JPart* parts)
+{
+    unsigned long long si = 0, su = 0, nz = 0;
+    unsigned __int128 fx = 0;
+    const long long lo_i = (long long)blockIdx.x * chunk;
+    const long long hi_i = min(n, lo_i + chunk);
+    for (long long i = lo_i + threadIdx.x; i < hi_i; i += blockDim.x) {
+        const long long in = inter[i];
+        if (in > 0) {
+            const long long un = uni[i];
+            si += (unsigned long long)in;
+            su += (unsigned long long)un;
+            nz += 1;
+            fx += ratio_fixed(in, un);
+        }
+    }
+    unsigned long long lo = (unsigned long long)fx, hi = (unsigned long long)(fx >> 64);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        si += shfl_down_u64(si, o);
+        su += shfl_down_u64(su, o);
+        nz += shfl_down_u64(nz, o);
+        const unsigned long long l2 = shfl_down_u64(lo, o), h2 = shfl_down_u64(hi, o);
+        const unsigned long long nl = lo + l2;
+        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+    __shared__ JPart sh[8];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[warp] = JPart{si, su, nz, lo, hi};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        JPart t = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            t.si += sh[w].si; t.su += sh[w].su; t.nz += sh[w].nz;
+            const unsigned long long nl = t.fx_lo + sh[w].fx_lo;
+            t.fx_hi += sh[w].fx_hi + (nl < t.fx_lo ? 1ull : 0ull);
+            t.fx_lo = nl;
+        }
+        parts[blockIdx.x] = t;
+    }
+}
+
+// The fixed scratch array. Every GPU that loads this library holds it until the process exits.
+static __device__ __align__(256) JPart g_jaccard_static_parts[kStaticParts];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of the fixed array on the current device, looked up once per device (the host-side
+// name of a __device__ variable is not a device address and must never be passed to a kernel).
+int static_parts_address(JPart** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+        cudaGetLastError();
+        return SCCG_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_jaccard_static_parts);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SCCG_ECUDA;
+        }
+        g_static_addr[dev] = p;
+    }
+    *out = static_cast<JPart*>(g_static_addr[dev]);
     return SCCG_OK;
 }
 
@@ -607,6 +693,25 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
         SCCG_CUDA(ctx, cudaStreamSynchronize(st));
         memcpy(out, ctx->pinned, sizeof(JaccardOut));
     }
+    return SCCG_OK;
+}
+
+int sccg_jaccard_static(const int64_t* inter, const int64_t* uni, int64_t n_pairs, sccg_jaccard_result* out,
+                        void* stream)
+{
+    static_assert(sizeof(JaccardOut) == sizeof(sccg_jaccard_result), "layout");
+    if (n_pairs < 0 || !out) return SCCG_EINVAL;
+    if (n_pairs > kStaticMaxPairs) return SCCG_ERANGE;
+    if (!is_device_ptr(out)) return SCCG_EINVAL;
+    if (n_pairs > 0 && (!is_device_ptr(inter) || !is_device_ptr(uni))) return SCCG_EINVAL;
+    JPart* parts = nullptr;
+    int r = static_parts_address(&parts);
+    if (r) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nparts = (int)std::max(1LL, (n_pairs + kStaticChunk - 1) / kStaticChunk);
+    k_jaccard_partial_chunked<<<nparts, 256, 0, st>>>(inter, uni, n_pairs, kStaticChunk, parts);
+    k_jaccard_final<<<1, 32, 0, st>>>(parts, nparts, n_pairs, reinterpret_cast<JaccardOut*>(out));
+    if (cudaGetLastError() != cudaSuccess) return SCCG_ECUDA;
     return SCCG_OK;
 }
 
