@@ -5,6 +5,11 @@
 
 #include "pixelbox.cuh"
 
+// Dynamic shared memory of the one-warp-per-item kernels (per-warp WarpSmem slices).
+#ifndef SCCG_DYNAMIC_SMEM
+#define SCCG_DYNAMIC_SMEM(T, name) extern __shared__ T name[]
+#endif
+
 namespace sccg {
 
 constexpr int kCoordLimit = 1 << 28;   // |x|, |y| <= 2^28
@@ -60,7 +65,7 @@ struct PrepArgs {
 template <int CAP, int STK, bool COUNT>
 __global__ void __launch_bounds__(256) k_prepare(const PrepArgs a)
 {
-    extern __shared__ int4 smem4[];
+    SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -140,33 +145,234 @@ __global__ void k_tile_ranges(const int32_t* tile, long long n, int n_tiles, lon
     start[t] = lo;
 }
 
-// One thread per A polygon: scan the B polygons of its tile in ascending order. COUNT_ONLY writes
-// the number of overlapping B polygons; otherwise the pairs are written from offs[a] on.
-template <bool COUNT_ONLY>
-__global__ void __launch_bounds__(256) k_pairs(const int4* __restrict__ mbrA, const int32_t* __restrict__ tileA,
-                                               long long nA, const int4* __restrict__ mbrB,
-                                               const long long* __restrict__ bstart, int n_tiles_b,
-                                               long long* __restrict__ counts_or_offs,
-                                               int32_t* __restrict__ pa, int32_t* __restrict__ pb,
-                                               long long cap)
+// Per-tile uniform grid over the B polygons. Cell size: about one B polygon per cell (a performance
+// choice only; any size gives the same pairs). B polygon b is registered in every cell its closed
+// MBR touches; an A polygon probes every cell its closed MBR touches, and a pair (a, b) is reported
+// only from the cell holding the corner (max(ax0, bx0), max(ay0, by0)) of the MBR intersection,
+// which both MBRs touch: every overlapping pair is found exactly once.
+struct TileGrid {
+    int ox, oy;        // grid origin (min x0, min y0 of the tile's B MBRs)
+    int cell;          // cell size in pixels
+    int gx, gy;        // cells per row / column (0 when the tile has no B polygon)
+};
+
+__device__ __forceinline__ int floor_div(int n, int d) { return n >= 0 ? n / d : -((-n + d - 1) / d); }
+
+// One warp per tile: bounding box of the tile's B MBRs and the grid laid over it.
+__global__ void k_tile_grid(const int4* __restrict__ mbrB, const long long* __restrict__ bstart, int n_tiles,
+                            TileGrid* grid, long long* ncells)
 {
-    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nA) return;
-    const int t = tileA ? tileA[a] : 0;
-    long long cnt = 0;
-    if (t < n_tiles_b) {
-        const int4 A = mbrA[a];
-        const long long b0 = bstart[t], b1 = bstart[t + 1];
-        long long o = COUNT_ONLY ? 0 : counts_or_offs[a];
-        for (long long b = b0; b < b1; ++b) {
-            const int4 B = mbrB[b];
-            if (A.x <= B.z && B.x <= A.z && A.y <= B.w && B.y <= A.w) {
-                if (!COUNT_ONLY && o < cap) { pa[o] = (int32_t)a; pb[o] = (int32_t)b; }
-                ++o; ++cnt;
-            }
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n_tiles) return;
+    const long long b0 = bstart[warp], b1 = bstart[warp + 1];
+    int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -0x7fffffff, y1 = -0x7fffffff;
+    for (long long base = b0; base < b1; base += 32) {
+        const long long b = base + lane;
+        if (b < b1) {
+            const int4 m = mbrB[b];
+            x0 = min(x0, m.x); y0 = min(y0, m.y); x1 = max(x1, m.z); y1 = max(y1, m.w);
         }
     }
-    if (COUNT_ONLY) counts_or_offs[a] = cnt;
+    x0 = warp_min(x0); y0 = warp_min(y0); x1 = warp_max(x1); y1 = warp_max(y1);
+    if (lane != 0) return;
+    TileGrid g{0, 0, 1, 0, 0};
+    if (b1 > b0) {
+        const double area = ((double)(x1 - x0) + 1.0) * ((double)(y1 - y0) + 1.0);
+        int cell = (int)ceil(sqrt(area / (double)(b1 - b0)));
+        cell = max(cell, 8);
+        // at most 4096 cells per axis
+        cell = max(cell, (int)(((long long)max(x1 - x0, y1 - y0) + 4095) / 4096));
+        g = TileGrid{x0, y0, cell, (x1 - x0) / cell + 1, (y1 - y0) / cell + 1};
+    }
+    grid[warp] = g;
+    ncells[warp] = (long long)g.gx * g.gy;
+}
+
+// One thread per B polygon: count its registrations per cell.
+__global__ void __launch_bounds__(256) k_bin_count(const int4* __restrict__ mbrB, const int32_t* __restrict__ tileB,
+                                                   long long nB, const TileGrid* __restrict__ grid,
+                                                   const long long* __restrict__ cellbase,
+                                                   unsigned long long* __restrict__ count)
+{
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nB) return;
+    const int t = tileB ? tileB[b] : 0;
+    const TileGrid g = grid[t];
+    const int4 m = mbrB[b];
+    const int cx0 = (m.x - g.ox) / g.cell, cx1 = (m.z - g.ox) / g.cell;
+    const int cy0 = (m.y - g.oy) / g.cell, cy1 = (m.w - g.oy) / g.cell;
+    const long long base = cellbase[t];
+    for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx) atomicAdd(&count[base + (long long)cy * g.gx + cx], 1ull);
+}
+
+// One thread per B polygon: place its index in every cell it touches (order within a cell unspecified).
+__global__ void __launch_bounds__(256) k_bin_fill(const int4* __restrict__ mbrB, const int32_t* __restrict__ tileB,
+                                                  long long nB, const TileGrid* __restrict__ grid,
+                                                  const long long* __restrict__ cellbase, int* __restrict__ cursor,
+                                                  const long long* __restrict__ cell_off, int* __restrict__ entries)
+{
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nB) return;
+    const int t = tileB ? tileB[b] : 0;
+    const TileGrid g = grid[t];
+    const int4 m = mbrB[b];
+    const int cx0 = (m.x - g.ox) / g.cell, cx1 = (m.z - g.ox) / g.cell;
+    const int cy0 = (m.y - g.oy) / g.cell, cy1 = (m.w - g.oy) / g.cell;
+    const long long base = cellbase[t];
+    for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx) {
+            const long long c = base + (long long)cy * g.gx + cx;
+            entries[cell_off[c] + atomicAdd(&cursor[c], 1)] = (int)b;
+        }
+}
+
+struct ProbeArgs {
+    const int4* mbrA; const int32_t* tileA; long long nA;
+    const int4* mbrB;
+    const TileGrid* grid; const long long* cellbase; const long long* cell_off; const int* entries;
+    int n_tiles;
+};
+
+// The cells an A polygon probes (clamped to its tile's grid); false when there are none.
+__device__ __forceinline__ bool probe_range(const ProbeArgs& p, long long a, int4& A, TileGrid& g, long long& base,
+                                            int& cx0, int& cx1, int& cy0, int& cy1)
+{
+    const int t = p.tileA ? p.tileA[a] : 0;
+    if (t >= p.n_tiles) return false;
+    g = p.grid[t];
+    if (g.gx == 0) return false;
+    A = p.mbrA[a];
+    cx0 = max(0, floor_div(A.x - g.ox, g.cell)); cx1 = min(g.gx - 1, floor_div(A.z - g.ox, g.cell));
+    cy0 = max(0, floor_div(A.y - g.oy, g.cell)); cy1 = min(g.gy - 1, floor_div(A.w - g.oy, g.cell));
+    base = p.cellbase[t];
+    return cx0 <= cx1 && cy0 <= cy1;
+}
+
+// Is b (in cell (cx, cy)) a pair of A reported from this cell?
+__device__ __forceinline__ bool pair_here(const int4& A, const int4& B, const TileGrid& g, int cx, int cy)
+{
+    if (!(A.x <= B.z && B.x <= A.z && A.y <= B.w && B.y <= A.w)) return false;
+    const int rx = max(A.x, B.x), ry = max(A.y, B.y);
+    return (rx - g.ox) / g.cell == cx && (ry - g.oy) / g.cell == cy;
+}
+
+constexpr int kSmallPairs = 32;   // A polygons with at most this many pairs sort them in registers
+
+// One thread per A polygon: number of pairs; A polygons with more than kSmallPairs pairs are
+// listed for the CTA path.
+__global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long long* counts, int* big_list,
+                                                     unsigned* big_n)
+{
+    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= p.nA) return;
+    int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
+    long long cnt = 0;
+    if (probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) {
+        for (int cy = cy0; cy <= cy1; ++cy)
+            for (int cx = cx0; cx <= cx1; ++cx) {
+                const long long c = base + (long long)cy * g.gx + cx;
+                for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e)
+                    cnt += pair_here(A, p.mbrB[p.entries[e]], g, cx, cy);
+            }
+    }
+    counts[a] = cnt;
+    if (cnt > kSmallPairs) big_list[atomicAdd(big_n, 1u)] = (int)a;
+}
+
+// One thread per A polygon with at most kSmallPairs pairs: gather, sort by b, write at offs[a].
+__global__ void __launch_bounds__(256) k_probe_write_small(const ProbeArgs p, const long long* __restrict__ offs,
+                                                           int32_t* pa, int32_t* pb, long long cap)
+{
+    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= p.nA) return;
+    const long long o = offs[a], n = offs[a + 1] - o;
+    if (n == 0 || n > kSmallPairs) return;
+    int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
+    if (!probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) return;
+    int buf[kSmallPairs];
+    int k = 0;
+    for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx) {
+            const long long c = base + (long long)cy * g.gx + cx;
+            for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e) {
+                const int b = p.entries[e];
+                if (pair_here(A, p.mbrB[b], g, cx, cy) && k < kSmallPairs) {
+                    int j = k++;                    // insertion into the sorted prefix
+                    while (j > 0 && buf[j - 1] > b) { buf[j] = buf[j - 1]; --j; }
+                    buf[j] = b;
+                }
+            }
+        }
+    for (int j = 0; j < k; ++j)
+        if (o + j < cap) { pa[o + j] = (int32_t)a; pb[o + j] = buf[j]; }
+}
+
+// One CTA per listed A polygon (more than kSmallPairs pairs): mark its pairs in a shared bitmap
+// over the tile's B range, window by window, and write them in ascending b.
+constexpr int kBitmapWords = 2048;    // 65,536 B polygons per window
+__global__ void __launch_bounds__(256) k_probe_write_big(const ProbeArgs p, const long long* __restrict__ bstart,
+                                                         const long long* __restrict__ offs,
+                                                         const int* __restrict__ big_list,
+                                                         const unsigned* __restrict__ big_n, int32_t* pa,
+                                                         int32_t* pb, long long cap)
+{
+    __shared__ unsigned bits[kBitmapWords];
+    __shared__ int wsum[8];
+    __shared__ long long run;
+    const unsigned nbig = *big_n;
+    for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const long long a = big_list[bi];
+        int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
+        if (!probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) continue;   // uniform per CTA
+        const int t = p.tileA ? p.tileA[a] : 0;
+        const long long b0 = bstart[t], b1 = bstart[t + 1];
+        const int ncx = cx1 - cx0 + 1;
+        const long long ncell = (long long)ncx * (cy1 - cy0 + 1);
+        if (threadIdx.x == 0) run = offs[a];
+        for (long long w0 = b0; w0 < b1; w0 += 32LL * kBitmapWords) {
+            for (int i = threadIdx.x; i < kBitmapWords; i += blockDim.x) bits[i] = 0u;
+            __syncthreads();
+            for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
+                const int cx = cx0 + (int)(q % ncx), cy = cy0 + (int)(q / ncx);
+                const long long c = base + (long long)cy * g.gx + cx;
+                for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e) {
+                    const int b = p.entries[e];
+                    const long long r = (long long)b - w0;
+                    if (r >= 0 && r < 32LL * kBitmapWords && pair_here(A, p.mbrB[b], g, cx, cy))
+                        atomicOr(&bits[r >> 5], 1u << (r & 31));
+                }
+            }
+            __syncthreads();
+            // ordered emission: each thread owns kBitmapWords / blockDim consecutive words
+            const int per = kBitmapWords / (int)blockDim.x;
+            int mine = 0;
+            for (int i = 0; i < per; ++i) mine += __popc(bits[threadIdx.x * per + i]);
+            int incl = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, o);
+                if ((threadIdx.x & 31) >= o) incl += v;
+            }
+            if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = incl;
+            __syncthreads();
+            int before = 0;
+            for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) before += wsum[w];
+            long long o = run + before + incl - mine;
+            for (int i = 0; i < per; ++i) {
+                unsigned m = bits[threadIdx.x * per + i];
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    if (o < cap) { pa[o] = (int32_t)a; pb[o] = (int32_t)(w0 + 32LL * (threadIdx.x * per + i) + bit); }
+                    ++o;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) run = o;
+            __syncthreads();
+        }
+    }
 }
 
 __global__ void k_gather_tile_offsets(const long long* offs, const long long* astart, int n_tiles,
@@ -265,7 +471,7 @@ struct AreasArgs {
 template <int CAP, int STK, bool COUNT>
 __global__ void __launch_bounds__(256) k_pair_areas_plain(const AreasArgs a)
 {
-    extern __shared__ int4 smem4[];
+    SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -371,7 +577,7 @@ __global__ void __launch_bounds__(256) k_pair_areas_persistent(const AreasArgs a
                                                                const long long* ioff,
                                                                unsigned long long* head)
 {
-    extern __shared__ int4 smem4[];
+    SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     WorkCounters wc = {0, 0, 0, 0};
@@ -516,28 +722,51 @@ __device__ __forceinline__ double u128_to_double_scaled(unsigned __int128 s, int
     return (double)m * p2;
 }
 
-__global__ void k_jaccard_final(const JPart* parts, int nparts, long long n_pairs, JaccardOut* out)
+// Combine the partial sums (one CTA of 256 threads) and form J and J'.
+__global__ void __launch_bounds__(256) k_jaccard_final(const JPart* parts, int nparts, long long n_pairs,
+                                                       JaccardOut* out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned long long si = 0, su = 0, nz = 0, lo = 0, hi = 0;
-    for (int i = 0; i < nparts; ++i) {
-        si += parts[i].si; su += parts[i].su; nz += parts[i].nz;
-        const unsigned long long nl = lo + parts[i].fx_lo;
-        hi += parts[i].fx_hi + (nl < lo ? 1ull : 0ull);
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        const JPart p = parts[i];
+        si += p.si; su += p.su; nz += p.nz;
+        const unsigned long long nl = lo + p.fx_lo;
+        hi += p.fx_hi + (nl < lo ? 1ull : 0ull);
         lo = nl;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        si += shfl_down_u64(si, o);
+        su += shfl_down_u64(su, o);
+        nz += shfl_down_u64(nz, o);
+        const unsigned long long l2 = shfl_down_u64(lo, o), h2 = shfl_down_u64(hi, o);
+        const unsigned long long nl = lo + l2;
+        hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+    __shared__ JPart sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = JPart{si, su, nz, lo, hi};
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    JPart t = sh[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        t.si += sh[w].si; t.su += sh[w].su; t.nz += sh[w].nz;
+        const unsigned long long nl = t.fx_lo + sh[w].fx_lo;
+        t.fx_hi += sh[w].fx_hi + (nl < t.fx_lo ? 1ull : 0ull);
+        t.fx_lo = nl;
+    }
     JaccardOut r;
-    r.sum_inter = (long long)si;
-    r.sum_union = (long long)su;
-    r.n_nonzero = (long long)nz;
+    r.sum_inter = (long long)t.si;
+    r.sum_union = (long long)t.su;
+    r.n_nonzero = (long long)t.nz;
     r.n_pairs = n_pairs;
-    if (nz == 0) {
+    if (t.nz == 0) {
         r.J = 0.0; r.Jprime = 0.0;
     } else {
-        r.J = __ddiv_rn(__ll2double_rn((long long)si), __ll2double_rn((long long)su));
-        const unsigned __int128 s = ((unsigned __int128)hi << 64) | lo;
+        r.J = __ddiv_rn(__ll2double_rn((long long)t.si), __ll2double_rn((long long)t.su));
+        const unsigned __int128 s = ((unsigned __int128)t.fx_hi << 64) | t.fx_lo;
         const double sum = u128_to_double_scaled(s, -100);
-        r.Jprime = __ddiv_rn(sum, __ll2double_rn((long long)nz));
+        r.Jprime = __ddiv_rn(sum, __ll2double_rn((long long)t.nz));
     }
     *out = r;
 }

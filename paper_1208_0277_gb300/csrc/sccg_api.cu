@@ -27,6 +27,8 @@ struct sccg_ctx {
     sccg_params params{};
     void* ws = nullptr;             // device scratch
     size_t ws_size = 0;
+    void* aux[2] = {nullptr, nullptr};  // separately growable scratch (candidate-pair grid cells, entries)
+    size_t aux_size[2] = {0, 0};
     void* pinned = nullptr;         // small host-pinned staging area
     WorkCounters* counters = nullptr;   // device work counters (counting mode)
     int count_work = 0;
@@ -101,6 +103,27 @@ int ws_reserve(sccg_ctx* ctx, size_t bytes)
         return SCCG_ENOMEM;
     }
     ctx->ws_size = want;
+    return SCCG_OK;
+}
+
+// Grow auxiliary scratch buffer k to at least `bytes` (its previous contents are not kept).
+int aux_reserve(sccg_ctx* ctx, int k, size_t bytes)
+{
+    if (bytes <= ctx->aux_size[k]) return SCCG_OK;
+    size_t want = std::max(bytes, ctx->aux_size[k] * 3 / 2);
+    want = (want + 0xFFFFF) & ~size_t(0xFFFFF);
+    if (ctx->aux[k]) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->aux[k]);
+        ctx->aux[k] = nullptr;
+        ctx->aux_size[k] = 0;
+    }
+    if (cudaMalloc(&ctx->aux[k], want) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(ctx->last_err, sizeof ctx->last_err, "scratch allocation of %zu bytes failed", want);
+        return SCCG_ENOMEM;
+    }
+    ctx->aux_size[k] = want;
     return SCCG_OK;
 }
 
@@ -373,8 +396,8 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     sccg_ctx* ctx = new (std::nothrow) sccg_ctx();
     if (!ctx) return SCCG_ENOMEM;
     ctx->device = device;
-    ctx->params.T = 1024;
-    ctx->params.warps_per_cta = 8;
+    ctx->params.T = 4096;
+    ctx->params.warps_per_cta = 4;
     ctx->params.split_pixels = 4096;
     ctx->params.ctas_per_sm = 0;
     int r = parse_params(params_json, &ctx->params);
@@ -403,6 +426,8 @@ int sccg_ctx_destroy(sccg_ctx* ctx)
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         if (ctx->ws) cudaFree(ctx->ws);
+        for (int k = 0; k < 2; ++k)
+            if (ctx->aux[k]) cudaFree(ctx->aux[k]);
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->pinned) cudaFreeHost(ctx->pinned);
         if (ctx->tile_streams_ready) {
@@ -508,38 +533,88 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int n_tiles = std::max(std::max(A->n_tiles, B->n_tiles), 1);
     const long long nA = A->n, nB = B->n;
-    const long long nb = (nA + kScanBlock - 1) / kScanBlock + 1;
-    const size_t need = carve_size<long long>(n_tiles + 1) * 3 + carve_size<long long>(nA + 1) * 2 +
-                        carve_size<long long>(nb);
+    const long long nscan = std::max<long long>(std::max(nA, (long long)n_tiles), 1);
+    const long long nb = (nscan + kScanBlock - 1) / kScanBlock + 1;
+    const size_t need = carve_size<long long>(n_tiles + 1) * 5 + carve_size<TileGrid>(n_tiles) +
+                        carve_size<long long>(nA + 1) * 2 + carve_size<long long>(nb) +
+                        carve_size<int>(nA + 1) + carve_size<unsigned long long>(4);
     int r = ws_reserve(ctx, need);
     if (r) return r;
     Carve cv(ctx->ws);
     long long* astart = cv.take<long long>(n_tiles + 1);
     long long* bstart = cv.take<long long>(n_tiles + 1);
+    long long* ncells = cv.take<long long>(n_tiles + 1);
+    long long* cellbase = cv.take<long long>(n_tiles + 1);
+    TileGrid* grid = cv.take<TileGrid>(n_tiles);
+    long long* tpo_dev = cv.take<long long>(n_tiles + 1);
     long long* counts = cv.take<long long>(nA + 1);
     long long* offs = cv.take<long long>(nA + 1);
     long long* bsum = cv.take<long long>(nb);
-    long long* tpo_dev = cv.take<long long>(n_tiles + 1);
+    int* big_list = cv.take<int>(nA + 1);
+    unsigned long long* small = cv.take<unsigned long long>(4);   // [0] big count (as unsigned)
+    long long* h = static_cast<long long*>(ctx->pinned);
+    const int4* mA = reinterpret_cast<const int4*>(A->mbr);
+    const int4* mB = reinterpret_cast<const int4*>(B->mbr);
     const unsigned tg = (unsigned)((n_tiles + 1 + 255) / 256);
     k_tile_ranges<<<tg, 256, 0, st>>>(A->tile, nA, n_tiles, astart);
     k_tile_ranges<<<tg, 256, 0, st>>>(B->tile, nB, n_tiles, bstart);
-    SCCG_LAUNCHED(ctx, "k_tile_ranges");
-    ctx->launches += 2;
-    const int4* mA = reinterpret_cast<const int4*>(A->mbr);
-    const int4* mB = reinterpret_cast<const int4*>(B->mbr);
+    k_tile_grid<<<(unsigned)((32LL * n_tiles + 255) / 256), 256, 0, st>>>(mB, bstart, n_tiles, grid, ncells);
+    SCCG_LAUNCHED(ctx, "k_tile_grid");
+    ctx->launches += 3;
+    r = device_scan(ctx, ncells, n_tiles, cellbase, bsum, st);
+    if (r) return r;
+    // 1st sync: number of grid cells
+    SCCG_CUDA(ctx, cudaMemcpyAsync(h, cellbase + n_tiles, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+    const long long ncell = *h;
+    const long long nbc = (std::max(ncell, 1LL) + kScanBlock - 1) / kScanBlock + 1;
+    r = aux_reserve(ctx, 0, carve_size<unsigned long long>(ncell + 1) + carve_size<long long>(ncell + 1) +
+                                carve_size<int>(ncell + 1) + carve_size<long long>(nbc));
+    if (r) return r;
+    Carve ca(ctx->aux[0]);
+    unsigned long long* ccount = ca.take<unsigned long long>(ncell + 1);
+    long long* cell_off = ca.take<long long>(ncell + 1);
+    int* cursor = ca.take<int>(ncell + 1);
+    long long* bsum2 = ca.take<long long>(nbc);
+    SCCG_CUDA(ctx, cudaMemsetAsync(ccount, 0, sizeof(unsigned long long) * (ncell + 1), st));
+    SCCG_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * (ncell + 1), st));
+    const unsigned gb = (unsigned)((std::max(nB, 1LL) + 255) / 256);
+    if (nB > 0) {
+        k_bin_count<<<gb, 256, 0, st>>>(mB, B->tile, nB, grid, cellbase, ccount);
+        SCCG_LAUNCHED(ctx, "k_bin_count");
+        ctx->launches += 1;
+    }
+    r = device_scan(ctx, reinterpret_cast<const long long*>(ccount), ncell, cell_off, bsum2, st);
+    if (r) return r;
+    // 2nd sync: number of cell registrations
+    SCCG_CUDA(ctx, cudaMemcpyAsync(h, cell_off + ncell, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+    const long long nent = *h;
+    r = aux_reserve(ctx, 1, carve_size<int>(nent + 1));
+    if (r) return r;
+    int* entries = static_cast<int*>(ctx->aux[1]);
+    if (nB > 0) {
+        k_bin_fill<<<gb, 256, 0, st>>>(mB, B->tile, nB, grid, cellbase, cursor, cell_off, entries);
+        SCCG_LAUNCHED(ctx, "k_bin_fill");
+        ctx->launches += 1;
+    }
+    ProbeArgs pr{mA, A->tile, nA, mB, grid, cellbase, cell_off, entries, n_tiles};
+    SCCG_CUDA(ctx, cudaMemsetAsync(small, 0, sizeof(unsigned long long) * 4, st));
+    unsigned* big_n = reinterpret_cast<unsigned*>(small);
+    const unsigned ga = (unsigned)((std::max(nA, 1LL) + 255) / 256);
     if (nA > 0) {
-        const unsigned ga = (unsigned)((nA + 255) / 256);
-        k_pairs<true><<<ga, 256, 0, st>>>(mA, A->tile, nA, mB, bstart, n_tiles, counts, nullptr, nullptr, 0);
-        SCCG_LAUNCHED(ctx, "k_pairs(count)");
+        k_probe_count<<<ga, 256, 0, st>>>(pr, counts, big_list, big_n);
+        SCCG_LAUNCHED(ctx, "k_probe_count");
         ctx->launches += 1;
     }
     r = device_scan(ctx, counts, nA, offs, bsum, st);
     if (r) return r;
     if (nA > 0 && capacity > 0) {
-        const unsigned ga = (unsigned)((nA + 255) / 256);
-        k_pairs<false><<<ga, 256, 0, st>>>(mA, A->tile, nA, mB, bstart, n_tiles, offs, pa, pb, capacity);
-        SCCG_LAUNCHED(ctx, "k_pairs(write)");
-        ctx->launches += 1;
+        k_probe_write_small<<<ga, 256, 0, st>>>(pr, offs, pa, pb, capacity);
+        k_probe_write_big<<<(unsigned)(2 * ctx->sm_count), 256, 0, st>>>(pr, bstart, offs, big_list, big_n, pa, pb,
+                                                                        capacity);
+        SCCG_LAUNCHED(ctx, "k_probe_write");
+        ctx->launches += 2;
     }
     if (tile_pair_off) {
         k_gather_tile_offsets<<<tg, 256, 0, st>>>(offs, astart, n_tiles, n_tiles, nA,
@@ -547,11 +622,11 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
         SCCG_LAUNCHED(ctx, "k_gather_tile_offsets");
         ctx->launches += 1;
     }
-    long long* h = static_cast<long long*>(ctx->pinned);
     SCCG_CUDA(ctx, cudaMemcpyAsync(h, offs + nA, sizeof(long long), cudaMemcpyDeviceToHost, st));
     if (tpo_host)
         SCCG_CUDA(ctx, cudaMemcpyAsync(tile_pair_off, tpo_dev, sizeof(long long) * (n_tiles + 1),
                                        cudaMemcpyDeviceToHost, st));
+    // 3rd sync: number of pairs
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
     *n_pairs = *h;
     return *h > capacity ? SCCG_ECAPACITY : SCCG_OK;
@@ -685,7 +760,7 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
     JPart* parts = cv.take<JPart>(nparts);
     JaccardOut* res = dev_out ? reinterpret_cast<JaccardOut*>(out) : cv.take<JaccardOut>(1);
     k_jaccard_partial<<<nparts, 256, 0, st>>>(inter, uni, n_pairs, parts);
-    k_jaccard_final<<<1, 32, 0, st>>>(parts, nparts, n_pairs, res);
+    k_jaccard_final<<<1, 256, 0, st>>>(parts, nparts, n_pairs, res);
     SCCG_LAUNCHED(ctx, "k_jaccard");
     ctx->launches += 2;
     if (!dev_out) {
@@ -710,7 +785,7 @@ int sccg_jaccard_static(const int64_t* inter, const int64_t* uni, int64_t n_pair
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nparts = (int)std::max(1LL, (n_pairs + kStaticChunk - 1) / kStaticChunk);
     k_jaccard_partial_chunked<<<nparts, 256, 0, st>>>(inter, uni, n_pairs, kStaticChunk, parts);
-    k_jaccard_final<<<1, 32, 0, st>>>(parts, nparts, n_pairs, reinterpret_cast<JaccardOut*>(out));
+    k_jaccard_final<<<1, 256, 0, st>>>(parts, nparts, n_pairs, reinterpret_cast<JaccardOut*>(out));
     if (cudaGetLastError() != cudaSuccess) return SCCG_ECUDA;
     return SCCG_OK;
 }

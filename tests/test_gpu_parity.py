@@ -151,6 +151,23 @@ def test_persistent_queue_matches_oracle(sccg, split):
     assert_same(gpu_run(c, wm, mode=1), O.cross_compare(A, B, method="rle"))
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_heavy_tail_tissue_and_nuclei(sccg, mode):
+    """Tissue polygons (500-2000 vertices, 400-1200 px) among nuclei: large A polygons take the
+    bitmap path of the candidate-pair join, edges are re-staged chunk by chunk, windows are deeply
+    subdivided; the persistent form cuts the big windows into many items."""
+    w = W.heavy_tail(seed=2, n_tiles=2, nuclei_per_tile=1500, tissue_lo=3, tissue_hi=4, tissue_nv_lo=500,
+                     tissue_nv_hi=2000, tissue_s_lo=400.0, tissue_s_hi=1200.0)
+    c = sccg.Context(0, {"split_pixels": 20000})
+    g = gpu_run(c, w, mode=mode)
+    ref = O.cross_compare(w.A, w.B, method="rle")
+    assert_same(g, ref)
+    idx = np.arange(0, len(ref["pa"]), max(1, len(ref["pa"]) // 300))
+    bi, bu = O.pair_areas(w.A, w.B, ref["pa"][idx], ref["pb"][idx], method="brute")
+    np.testing.assert_array_equal(g["inter"][idx], bi)
+    np.testing.assert_array_equal(g["uni"][idx], bu)
+
+
 # ------------------------------------------------------------------------------- edge cases
 
 def rings_workload(rings_a, rings_b):
