@@ -39,6 +39,8 @@ UNIT = "pairs/s"
 # sampling box against one edge.
 OPS_PER_STRIP_EDGE = 17
 OPS_PER_BOX_EDGE = 33
+OPS_PER_ROW_EDGE = 15      # listed straddling edge: the strip test without its straddle check
+OPS_PER_ROW_ENTRY = 11     # building one (edge, row) list entry: count pass + fill pass
 
 
 def parse_args():
@@ -93,7 +95,7 @@ def kernel_source_hash() -> str:
 # ------------------------------------------------------------------------------------------------
 
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -116,7 +118,16 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def wait_ready(self, timeout_s: float = 10.0):
+        """Block until the first sample has arrived (NVML initialised outside the timed region)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout_s:
+            time.sleep(0.05)
+
+    def mark(self, which: str):
+        setattr(self, which, time.time())
 
     def stop(self):
         if self.proc is None:
@@ -130,7 +141,12 @@ class ClockSampler:
             self.thread.join(timeout=5)
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "t_start", 0.0), getattr(self, "t_end", float("inf"))
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1 + 0.25]
+        if not inside and self.lines:
+            # timed region shorter than the sampling period: take the sample nearest to it
+            inside = [min(self.lines, key=lambda x: abs(x[0] - t0))[1]]
+        for ln in inside:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -302,10 +318,15 @@ def main():
     ctx.set_param("count_work", 0)
 
     def ops(wc):
-        return wc["strip_edges"] * OPS_PER_STRIP_EDGE + wc["box_edges"] * OPS_PER_BOX_EDGE
+        return (wc["strip_edges"] * OPS_PER_STRIP_EDGE + wc["box_edges"] * OPS_PER_BOX_EDGE +
+                wc["row_edges"] * OPS_PER_ROW_EDGE + wc["row_entries"] * OPS_PER_ROW_ENTRY)
 
     results = {}
     for form in (args.form, "persistent" if args.form == "tiles" else "tiles"):
+        sampler = ClockSampler(local_rank) if form == args.form else None
+        if sampler:
+            sampler.start()
+            sampler.wait_ready()
         for _ in range(max(args.warmup, 3)):
             step(form)
         torch.cuda.synchronize()
@@ -313,11 +334,9 @@ def main():
             dist.barrier()
         phases = []
         launches0 = ctx.launch_count()
-        sampler = ClockSampler(local_rank) if form == args.form else None
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark("t_start")
         start, end = ev(), ev()
         start.record(stream)
         J = None
@@ -325,6 +344,8 @@ def main():
             J = step(form, phases)
         end.record(stream)
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark("t_end")
         clocks = sampler.stop() if sampler else None
         launches = ctx.launch_count() - launches0
         ms = start.elapsed_time(end)
@@ -365,8 +386,8 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32/fp32 ALU lane-ops)",
                 "frac": achieved / peak_tops, "traffic": traffic, "kernel": dom,
                 "peak_note": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x 2070 MHz (max SM clock of measured peaks)",
-                "achieved_note": "algorithmic ops (strip-edge x 17 + box-edge x 33, counted on device) per step / "
-                                 "phase time (CUDA events)",
+                "achieved_note": "algorithmic ops (strip-edge x 17 + box-edge x 33 + listed row-edge x 15 + "
+                                 "row-list entry x 11, counted on device) per step / phase time (CUDA events)",
                 "work": work_areas if dom != "k_prepare" else work_prep}
 
     # end-to-end through the public API with host buffers

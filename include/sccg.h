@@ -198,10 +198,12 @@ int sccg_jaccard_static(const int64_t* inter, const int64_t* uni, int64_t n_pair
 /* ------------------------------------------------------------------------------------------- */
 /* With sccg_ctx_set_param(ctx, "count_work", 1) the prepare and pair-area kernels run an
  * instrumented build that counts the work the method performs; the counts accumulate in the
- * context until read. out4 (host, 4 entries): [0] (32-pixel row strip, edge) evaluations,
- * [1] (pixel, edge) point-in-polygon tests inside those strips, [2] (sampling box, edge)
- * classifications, [3] sampling boxes classified. Synchronous. reset != 0 zeroes the counters. */
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out4, int reset);
+ * context until read. out6 (host, 6 entries): [0] (32-pixel row strip, edge) evaluations of the
+ * full strip test, [1] (pixel, edge) point-in-polygon tests inside all strips, [2] (sampling box,
+ * edge) classifications, [3] sampling boxes classified, [4] (edge, row) entries of the per-row edge
+ * lists built, [5] (32-pixel row strip, listed straddling edge) evaluations. Synchronous.
+ * reset != 0 zeroes the counters. */
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out6, int reset);
 
 #ifdef __cplusplus
 }

@@ -212,9 +212,10 @@ class Context:
                                           ctypes.c_void_p(out.data_ptr()), _stream(stream)), "sccg_jaccard")
 
     def work_counters(self, reset: bool = True) -> dict:
-        a = (ctypes.c_uint64 * 4)()
+        a = (ctypes.c_uint64 * 6)()
         self._check(self.lib.sccg_work_counters(self.h, a, int(reset)), "sccg_work_counters")
-        return dict(strip_edges=a[0], pixel_edges=a[1], box_edges=a[2], boxes=a[3])
+        return dict(strip_edges=a[0], pixel_edges=a[1], box_edges=a[2], boxes=a[3], row_entries=a[4],
+                    row_edges=a[5])
 
 
 def cross_compare(ctx: Context, A: DevicePolySet, B: DevicePolySet, mode: int = MODE_PLAIN, stream=None):

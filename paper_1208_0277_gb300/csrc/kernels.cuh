@@ -10,6 +10,17 @@
 #define SCCG_DYNAMIC_SMEM(T, name) extern __shared__ T name[]
 #endif
 
+// Minimum resident CTAs per SM requested from the compiler for the one-warp-per-item kernels
+// (0: no request). 4 CTAs of 256 threads cap registers at 64 (32 resident warps per SM).
+#ifndef SCCG_MIN_BLOCKS
+#define SCCG_MIN_BLOCKS 4
+#endif
+#if SCCG_MIN_BLOCKS > 0
+#define SCCG_ITEM_BOUNDS __launch_bounds__(256, SCCG_MIN_BLOCKS)
+#else
+#define SCCG_ITEM_BOUNDS __launch_bounds__(256)
+#endif
+
 namespace sccg {
 
 constexpr int kCoordLimit = 1 << 28;   // |x|, |y| <= 2^28
@@ -31,19 +42,24 @@ struct PrepStats {
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
 {
-    unsigned long long a = wc.strip_edges, b = wc.pixel_edges, c = wc.box_edges, d = wc.boxes;
+    unsigned long long a = wc.strip_edges, b = wc.pixel_edges, c = wc.box_edges, d = wc.boxes,
+                       e = wc.row_entries, f = wc.row_edges;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(kFull, a, o);
         b += __shfl_xor_sync(kFull, b, o);
         c += __shfl_xor_sync(kFull, c, o);
         d += __shfl_xor_sync(kFull, d, o);
+        e += __shfl_xor_sync(kFull, e, o);
+        f += __shfl_xor_sync(kFull, f, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&out->strip_edges, a);
         atomicAdd(&out->pixel_edges, b);
         atomicAdd(&out->box_edges, c);
         atomicAdd(&out->boxes, d);
+        atomicAdd(&out->row_entries, e);
+        atomicAdd(&out->row_edges, f);
     }
 }
 
@@ -63,13 +79,13 @@ struct PrepArgs {
 };
 
 template <int CAP, int STK, bool COUNT>
-__global__ void __launch_bounds__(256) k_prepare(const PrepArgs a)
+__global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0};
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
     long long first_bad = 0x7fffffffffffffffLL;
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
@@ -469,13 +485,13 @@ struct AreasArgs {
 };
 
 template <int CAP, int STK, bool COUNT>
-__global__ void __launch_bounds__(256) k_pair_areas_plain(const AreasArgs a)
+__global__ void SCCG_ITEM_BOUNDS k_pair_areas_plain(const AreasArgs a)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0};
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
         const int ia = a.pa[i], ib = a.pb[i];
         int64_t out_i = -1, out_u = -1;      // invalid pair: flagged, not read
@@ -573,14 +589,14 @@ __device__ __forceinline__ long long find_pair(const long long* ioff, long long 
 constexpr int kItemChunk = 4;
 
 template <int CAP, int STK, bool COUNT>
-__global__ void __launch_bounds__(256) k_pair_areas_persistent(const AreasArgs a, int side, const long long* nitems,
+__global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int side, const long long* nitems,
                                                                const long long* ioff,
                                                                unsigned long long* head)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
-    WorkCounters wc = {0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0};
     const long long total = ioff[a.n];
     for (;;) {
         unsigned long long first = 0;

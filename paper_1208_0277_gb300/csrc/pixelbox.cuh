@@ -27,6 +27,8 @@ struct WorkCounters {          // algorithmic work, accumulated only by the coun
     unsigned long long pixel_edges;   // (valid pixel, edge) point-in-polygon tests inside those
     unsigned long long box_edges;     // (sampling box, edge) classifications
     unsigned long long boxes;         // sampling boxes classified (per polygon)
+    unsigned long long row_entries;   // (edge, row) entries of the per-row edge lists built
+    unsigned long long row_edges;     // (32-pixel row strip, listed straddling edge) evaluations
 };
 
 __device__ __forceinline__ int warp_min(int v)
@@ -185,17 +187,95 @@ __device__ __forceinline__ int poly_box(const int2* v, int nv, bool resident, in
     return meet ? 2 : (int)(par & 1u);
 }
 
-// Per-warp shared memory: edge buffers of the two polygons and the subdivision loop's state.
+// Lists of the staged edges that straddle each row of a band of at most 32 rows: the edges of
+// row r are ent[off[r] .. off[r+1]). An edge contributes to a pixel's crossing count only if it
+// straddles the pixel's row, so evaluating a row against its list alone is exact.
+constexpr int kRowEntries = 512;
+struct RowLists {
+    int cnt[32];
+    int off[33];
+    unsigned short ent[kRowEntries];
+};
+
+// Per-warp shared memory: edge buffers of the two polygons, their row lists and the subdivision
+// loop's state.
 template <int CAP, int STK>
 struct WarpSmem {
     int4 ep[CAP];
     int4 eq[CAP];
     float rp[CAP];
     float rq[CAP];
+    RowLists lp;
+    RowLists lq;
     uint2 stack[STK];     // pending sampling boxes (window-relative, packed with flags)
     uint2 leaf[32];       // boxes to pixelize in the current round, one slot per lane
     int loff[32];         // exclusive prefix of row strips over the leaf slots
 };
+
+// Build the row lists of the `ne` staged edges for rows band0 .. band0 + nrows - 1 (nrows <= 32).
+// Returns false (warp-uniform) when they do not fit in kRowEntries. Whole warp, converged.
+template <bool COUNT>
+__device__ __forceinline__ bool build_rows(const int4* E, int ne, int band0, int nrows, RowLists& L, int lane,
+                                           unsigned long long& cnt_entries)
+{
+    L.cnt[lane] = 0;
+    __syncwarp();
+    for (int base = 0; base < ne; base += 32) {
+        const int i = base + lane;
+        if (i < ne) {
+            const int4 ed = E[i];
+            const int r0 = max(ed.x, band0) - band0, r1 = min(ed.x + ed.y, band0 + nrows) - band0;
+            for (int r = r0; r < r1; ++r) atomicAdd(&L.cnt[r], 1);
+        }
+    }
+    __syncwarp();
+    const int c = L.cnt[lane];
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total > kRowEntries) return false;
+    if (COUNT) cnt_entries += (unsigned long long)c;
+    L.off[lane] = incl - c;
+    if (lane == 31) L.off[32] = total;
+    L.cnt[lane] = 0;              // reused as the fill cursor
+    __syncwarp();
+    for (int base = 0; base < ne; base += 32) {
+        const int i = base + lane;
+        if (i < ne) {
+            const int4 ed = E[i];
+            const int r0 = max(ed.x, band0) - band0, r1 = min(ed.x + ed.y, band0 + nrows) - band0;
+            for (int r = r0; r < r1; ++r) L.ent[L.off[r] + atomicAdd(&L.cnt[r], 1)] = (unsigned short)i;
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// Parity bitmask of the 32 pixels (x0 + k, y) against the edges listed for row r (all of which
+// straddle row y): the same exact test as strip_parity without the straddle check.
+__device__ __forceinline__ uint32_t row_parity(const int4* E, const float* R, const RowLists& L, int r, int y,
+                                               int x0)
+{
+    const int sx = 2 * x0 + 1;
+    uint32_t par = 0;
+    const int k1 = L.off[r + 1];
+    for (int k = L.off[r]; k < k1; ++k) {
+        const int i = L.ent[k];
+        const int4 ed = E[i];
+        const float rc = R[i];
+        const int D = (2 * (y - ed.x) + 1) * ed.z - (sx - 2 * ed.w) * ed.y;
+        const int Dc = min(max(D, 0), ed.y << 6);
+        const float f = __int_as_float(Dc | 0x4B000000) - 8388608.0f;
+        const float q = __fmaf_rn(f, rc, -7.62939453125e-06f);
+        const int cc = __float_as_int(__fadd_ru(q, 12582912.0f)) - 0x4B400000;
+        par ^= __funnelshift_lc(0xffffffffu, 0u, (unsigned)cc);
+    }
+    return par;
+}
 
 // Box packing: window-relative coordinates (< 2^15) in 15 bits each; bit 15 of the low halves
 // carries the "still needs testing against P / Q" flags.
@@ -310,7 +390,43 @@ __device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0
     const int fl0 = TWO ? 3 : 1;
     uint32_t acc = 0;
     int top = 0;
-    if ((long long)W * H < T) {
+    if ((long long)W * H < T && pp.rp_res && (!TWO || pp.rq_res)) {
+        // The whole window is one leaf: pixelize it band by band (32 rows, one lane per row), each
+        // row against the edges that straddle it.
+        const int chunks = (W + 31) >> 5;
+        bool fits = true;
+        for (int b0 = 0; b0 < H && fits; b0 += 32) {
+            const int nrows = min(32, H - b0);
+            unsigned long long ce = 0;
+            fits = build_rows<COUNT>(S.ep, pp.np, wy0 + b0, nrows, S.lp, lane, ce);
+            if (TWO && fits) fits = build_rows<COUNT>(S.eq, pp.nq, wy0 + b0, nrows, S.lq, lane, ce);
+            if (!fits) {
+                // rows too crowded for the lists: this band and the rest go through the leaf path
+                for (int r0 = b0; r0 < H; r0 += 32)
+                    acc += pixelize_leaves<TWO, COUNT>(pp, S, wx0, wy0, lane,
+                                                       pack_box(0, r0, W, min(H, r0 + 32), fl0), lane == 0, wc);
+                break;
+            }
+            if (lane < nrows) {
+                const int y = wy0 + b0 + lane;
+                for (int c = 0; c < chunks; ++c) {
+                    const int xs = wx0 + 32 * c;
+                    uint32_t in = __funnelshift_lc(0xffffffffu, 0u, (unsigned)min(32, W - 32 * c));
+                    in &= row_parity(S.ep, S.rp, S.lp, lane, y, xs);
+                    if (TWO) in &= row_parity(S.eq, S.rq, S.lq, lane, y, xs);
+                    acc += __popc(in);
+                    if (COUNT) {
+                        const int ne = S.lp.off[lane + 1] - S.lp.off[lane] +
+                                       (TWO ? S.lq.off[lane + 1] - S.lq.off[lane] : 0);
+                        wc.row_edges += (unsigned long long)ne;
+                        wc.pixel_edges += (unsigned long long)ne * min(32, W - 32 * c);
+                    }
+                }
+            }
+            if (COUNT) wc.row_entries += ce;
+            __syncwarp();
+        }
+    } else if ((long long)W * H < T) {
         acc += pixelize_leaves<TWO, COUNT>(pp, S, wx0, wy0, lane, pack_box(0, 0, W, H, fl0), lane == 0, wc);
     } else {
         if (lane == 0) S.stack[0] = pack_box(0, 0, W, H, fl0);

@@ -464,13 +464,14 @@ int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out)
 
 const char* sccg_last_error(const sccg_ctx* ctx) { return ctx ? ctx->last_err : ""; }
 
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out4, int reset)
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out6, int reset)
 {
-    if (!ctx || !out4) return SCCG_EINVAL;
+    if (!ctx || !out6) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     WorkCounters h;
     SCCG_CUDA(ctx, cudaMemcpy(&h, ctx->counters, sizeof h, cudaMemcpyDeviceToHost));
-    out4[0] = h.strip_edges; out4[1] = h.pixel_edges; out4[2] = h.box_edges; out4[3] = h.boxes;
+    out6[0] = h.strip_edges; out6[1] = h.pixel_edges; out6[2] = h.box_edges; out6[3] = h.boxes;
+    out6[4] = h.row_entries; out6[5] = h.row_edges;
     if (reset) SCCG_CUDA(ctx, cudaMemset(ctx->counters, 0, sizeof(WorkCounters)));
     return SCCG_OK;
 }

@@ -186,7 +186,11 @@ def test_edge_cases_ties_degenerate_selfintersecting(ctx):
     bowtie = [[0, 0], [8, 8], [8, 0], [0, 8]]             # self-intersecting ring (even-odd)
     spike = [[0, 0], [9, 1], [0, 2], [9, 3], [0, 4], [9, 5], [0, 6]]  # centres on many edges
     rect_stack = [[1, 1], [7, 1], [7, 7], [1, 7]]
-    rings = [tri, tri2, tri3, diamond, collinear, thin, tall, dup, bowtie, spike, rect_stack]
+    # 30 teeth: every row of the 40-row window is crossed 60 times (too many for the per-row edge
+    # lists of one band, so the window falls back to the general leaf path)
+    comb = [[0, 0]] + [p for k in range(30) for p in ([2 * k + 1, 40], [2 * k + 2, 0])] + [[60, -1], [0, -1]]
+    comb_cover = [[-2, -3], [63, -3], [63, 45], [-2, 45]]
+    rings = [tri, tri2, tri3, diamond, collinear, thin, tall, dup, bowtie, spike, rect_stack, comb, comb_cover]
     w = rings_workload(rings, rings[::-1])
     assert_same(gpu_run(ctx, w), O.cross_compare(w.A, w.B))
 
