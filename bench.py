@@ -34,9 +34,10 @@ if ROOT not in sys.path:
 METRIC = "polygon pairs/s (bit-exact inter/union areas) on 1 GB300; % ALU peak; p99 job ms"
 UNIT = "pairs/s"
 
-# Algorithmic int32/fp32 ALU operations per unit of work, counted from the exact tests as
-# formulated ("Roofline"): one 32-pixel row strip against one edge, and one
-# sampling box against one edge.
+# Algorithmic int32/fp32 ALU operations per unit of work, counted from the exact tests as the
+# kernels formulate them: one 32-pixel row strip against one edge (straddle test, crossing count,
+# prefix-mask update), one sampling box against one edge (bounding-box and separating-axis tests,
+# reference-centre crossing), one listed straddling edge, and one (edge, row) list entry.
 OPS_PER_STRIP_EDGE = 17
 OPS_PER_BOX_EDGE = 33
 OPS_PER_ROW_EDGE = 15      # listed straddling edge: the strip test without its straddle check
@@ -49,8 +50,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--form", choices=["tiles", "persistent"], default="tiles")
-    p.add_argument("--config", type=int, default=2, help="1 single tile, 2 whole slide (default)")
+    p.add_argument("--form", choices=["tiles", "persistent", "graph"], default=None,
+                   help="a4 form timed as the headline (default: tiles for configs 1-2, graph for 3)")
+    p.add_argument("--config", type=int, default=2,
+                   help="1 single tile, 2 whole slide (default), 3 batched uneven tiles")
     p.add_argument("--tiles", type=int, default=0, help="restrict to the first N tiles (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -74,6 +77,11 @@ def make_workload(config: int, seed: int, tiles: int):
         desc = {"workload": "whole slide 100,000x100,000 px, 4096x4096 tiles (625), ~1M star nuclei per set "
                             "(8-64 vertices, MBR 10-40 px, 100 per 10^6 px^2); B = A jittered +-3, shifted +-5, "
                             "10% dropped, 10% new"}
+    elif config == 3:
+        w = W.batched_uneven(seed=seed)
+        desc = {"workload": "2,000 tiles of 4096^2 px, polygons per tile log-uniform 50-20,000 (~6.4M per set), "
+                            "MBR lognormal(ln 20, 0.75) clipped to 8-400 px, 4-512 vertices; B = A jittered/"
+                            "shifted, 10% dropped, 10% new"}
     else:
         raise SystemExit(f"--config {config} is not a bench workload here")
     if tiles:
@@ -225,6 +233,8 @@ def reference_arm(args):
 
 def main():
     args = parse_args()
+    if args.form is None:
+        args.form = "graph" if args.config == 3 else "tiles"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -277,6 +287,7 @@ def main():
     inter = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
     uni = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
     del pa0, pb0
+    jres = torch.zeros(48, dtype=torch.uint8, device=dev)    # device Jaccard result of the graph form
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -290,10 +301,12 @@ def main():
         if e: e[2].record(stream)
         if form == "tiles":
             i, u = ctx.pair_areas_tiles(a, b, p_a, p_b, tpo, out=(inter, uni))
-        else:
+        elif form == "persistent":
             i, u = ctx.pair_areas(a, b, p_a, p_b, mode=P.MODE_PERSISTENT, out=(inter, uni))
+        else:
+            i, u = ctx.batch_run(a, b, p_a, p_b, (inter, uni), jres)
         if e: e[3].record(stream)
-        J = ctx.jaccard(i, u)
+        J = ctx.jaccard(i, u) if form != "graph" else ctx.read_jaccard(jres)
         if e:
             e[4].record(stream)
             phases.append(e)
@@ -312,7 +325,10 @@ def main():
     b_ = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
     work_prep = ctx.work_counters(reset=True)
     p_a, p_b, tpo = ctx.candidate_pairs(a_, b_, capacity=cap, with_tile_offsets=True, out=(pa, pb))
-    ctx.pair_areas_tiles(a_, b_, p_a, p_b, tpo, out=(inter, uni))
+    if args.form == "tiles":
+        ctx.pair_areas_tiles(a_, b_, p_a, p_b, tpo, out=(inter, uni))
+    else:
+        ctx.pair_areas(a_, b_, p_a, p_b, mode=P.MODE_PERSISTENT, out=(inter, uni))
     torch.cuda.synchronize()
     work_areas = ctx.work_counters(reset=True)
     ctx.set_param("count_work", 0)
@@ -322,7 +338,7 @@ def main():
                 wc["row_edges"] * OPS_PER_ROW_EDGE + wc["row_entries"] * OPS_PER_ROW_ENTRY)
 
     results = {}
-    for form in (args.form, "persistent" if args.form == "tiles" else "tiles"):
+    for form in [args.form] + [f for f in ("tiles", "persistent", "graph") if f != args.form]:
         sampler = ClockSampler(local_rank) if form == args.form else None
         if sampler:
             sampler.start()
@@ -447,14 +463,14 @@ def main():
             dist.destroy_process_group()
         return
     Jd = main_r["J"]
-    other = "persistent" if args.form == "tiles" else "tiles"
-    o = results[other]
+    form_names = {"tiles": "one kernel launch per tile",
+                  "persistent": "persistent single launch, device work queue",
+                  "graph": "persistent launch + Jaccard replayed as one CUDA graph"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(desc, form=("one kernel launch per tile" if args.form == "tiles" else
-                                   "persistent single launch, device work queue"),
+        "config": dict(desc, form=form_names[args.form],
                        pairs_per_step=n_pairs, polygons=[nA, nB], tiles=w.n_tiles,
                        l2="inputs larger than L2 (no flush needed)",
                        input_bytes=sum(devb[k].numel() * devb[k].element_size() for k in devb),
@@ -467,8 +483,10 @@ def main():
         "phases_ms": main_r["phases_ms"],
         "jaccard": {"J": Jd["J"], "Jprime": Jd["Jprime"], "n_nonzero": Jd["n_nonzero"]},
         "parity_vs_oracle": parity,
-        other: {"value": total_pairs * args.steps / (o["ms"] / 1e3), "ms_per_step": o["ms"] / args.steps,
-                "phases_ms": o["phases_ms"], "gpu_launches": o["launches"]},
+        "other_forms": {f: {"form": form_names[f], "value": total_pairs * args.steps / (o["ms"] / 1e3),
+                            "ms_per_step": o["ms"] / args.steps, "phases_ms": o["phases_ms"],
+                            "gpu_launches": o["launches"]}
+                        for f, o in results.items() if f != args.form},
     }
     print(json.dumps(line), flush=True)
     if dist:

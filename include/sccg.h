@@ -175,6 +175,17 @@ typedef struct sccg_jaccard_result {
 int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_t n_pairs,
                  sccg_jaccard_result* out, void* stream);
 
+/* Batched form (Sec. 4.1: the aggregator groups many tile tasks into one GPU batch; the batched step):
+ * the persistent pair areas and unions of sccg_pair_areas(PERSISTENT) followed by the Jaccard
+ * reductions into the DEVICE result `out`, replayed as one CUDA graph. The graph is captured on the
+ * first call and re-captured only when the pointers, the pair count or the parameters change, so
+ * repeated calls on the same buffers cost one graph launch. Asynchronous. Scratch is sized before
+ * capture; the context must not be used for other calls while the graph may be running. */
+int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
+                   const int32_t* pa, const int32_t* pb, int64_t n_pairs,
+                   int64_t* inter, int64_t* uni, sccg_jaccard_result* out, void* stream);
+
+
 /* Allocation-free variant of sccg_jaccard (the paper has no counterpart; this is a library
  * service). Same results as sccg_jaccard, but it needs no context and allocates nothing: its scratch
  * (4096 partial-sum slots, 160 KB) is a fixed array in device memory that every GPU loading this

@@ -187,6 +187,22 @@ class Context:
                                                    uni.data_ptr(), _stream(stream)), "sccg_pair_areas_tiles")
         return inter[:n], uni[:n]
 
+    def batch_run(self, A: DevicePolySet, B: DevicePolySet, pa, pb, out, result, stream=None):
+        """Persistent pair areas + Jaccard replayed as one CUDA graph. out = (inter, uni) int64 device
+        tensors; result = device uint8 tensor of 48 bytes receiving the Jaccard struct."""
+        inter, uni = out
+        n = pa.numel()
+        self._check(self.lib.sccg_batch_run(self.h, ctypes.byref(A.c), ctypes.byref(B.c), pa.data_ptr(),
+                                            pb.data_ptr(), n, inter.data_ptr(), uni.data_ptr(), result.data_ptr(),
+                                            _stream(stream)), "sccg_batch_run")
+        return inter[:n], uni[:n]
+
+    @staticmethod
+    def read_jaccard(result) -> dict:
+        """Decode the 48-byte device Jaccard struct (copies it to the host)."""
+        r = _native.JaccardC.from_buffer_copy(result.cpu().numpy().tobytes())
+        return {k: getattr(r, k) for k, _ in r._fields_}
+
     def launch_count(self) -> int:
         c = ctypes.c_uint64(0)
         self._check(self.lib.sccg_launch_count(self.h, ctypes.byref(c)), "sccg_launch_count")

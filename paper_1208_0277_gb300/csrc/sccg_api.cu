@@ -37,6 +37,13 @@ struct sccg_ctx {
     cudaStream_t tstream[kTileStreams] = {};
     cudaEvent_t tevent[kTileStreams + 1] = {};
     bool tile_streams_ready = false;
+    // sccg_batch_run: the captured graph and the arguments it was captured for
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    const void* batch_key[9] = {};
+    long long batch_n = -1;
+    sccg_params batch_params{};
+    int batch_count_work = 0;
     char last_err[256] = {0};
 };
 
@@ -251,6 +258,73 @@ int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* 
     return SCCG_OK;
 }
 
+size_t persistent_scratch(long long n_pairs)
+{
+    const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
+    return carve_size<long long>(n_pairs + 1) * 2 + carve_size<long long>(nb) + carve_size<unsigned long long>(1);
+}
+
+int split_side(const sccg_ctx* ctx)
+{
+    int side = 1;
+    while ((long long)(side + 1) * (side + 1) <= ctx->params.split_pixels) ++side;
+    return side;
+}
+
+// Persistent form on already reserved scratch (no validation, no allocation: usable under capture).
+int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t st)
+{
+    const long long n_pairs = a.n;
+    const int side = split_side(ctx);
+    const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
+    Carve cv(ctx->ws);
+    long long* nitems = cv.take<long long>(n_pairs + 1);
+    long long* ioff = cv.take<long long>(n_pairs + 1);
+    long long* bsum = cv.take<long long>(nb);
+    unsigned long long* head = cv.take<unsigned long long>(1);
+    const unsigned g = (unsigned)((n_pairs + 255) / 256);
+    k_plan<<<g, 256, 0, st>>>(a, side, nitems);
+    SCCG_LAUNCHED(ctx, "k_plan");
+    ctx->launches += 1;
+    int r = device_scan(ctx, nitems, n_pairs, ioff, bsum, st);
+    if (r) return r;
+    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, sizeof(unsigned long long), st));
+    switch (cap) {
+        case 32: r = launch_persistent<32>(ctx, a, side, nitems, ioff, head, st); break;
+        case 64: r = launch_persistent<64>(ctx, a, side, nitems, ioff, head, st); break;
+        default: r = launch_persistent<128>(ctx, a, side, nitems, ioff, head, st); break;
+    }
+    if (r) return r;
+    k_union<<<g, 256, 0, st>>>(a, nitems);
+    SCCG_LAUNCHED(ctx, "k_union");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+int jaccard_parts(const sccg_ctx* ctx, long long n_pairs)
+{
+    return (int)std::max(1LL, std::min<long long>((n_pairs + 255) / 256, 4LL * ctx->sm_count));
+}
+
+size_t jaccard_scratch(const sccg_ctx* ctx, long long n_pairs)
+{
+    return carve_size<JPart>(jaccard_parts(ctx, n_pairs)) + carve_size<JaccardOut>(1);
+}
+
+// Jaccard into a device result on already reserved scratch (no validation, no allocation).
+int jaccard_launch(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, long long n_pairs, JaccardOut* res,
+                   cudaStream_t st)
+{
+    const int nparts = jaccard_parts(ctx, n_pairs);
+    Carve cv(ctx->ws);
+    JPart* parts = cv.take<JPart>(nparts);
+    k_jaccard_partial<<<nparts, 256, 0, st>>>(inter, uni, n_pairs, parts);
+    k_jaccard_final<<<1, 256, 0, st>>>(parts, nparts, n_pairs, res);
+    SCCG_LAUNCHED(ctx, "k_jaccard");
+    ctx->launches += 2;
+    return SCCG_OK;
+}
+
 int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
@@ -430,6 +504,8 @@ int sccg_ctx_destroy(sccg_ctx* ctx)
             if (ctx->aux[k]) cudaFree(ctx->aux[k]);
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->pinned) cudaFreeHost(ctx->pinned);
+        if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         if (ctx->tile_streams_ready) {
             for (int k = 0; k < sccg_ctx::kTileStreams; ++k) cudaStreamDestroy(ctx->tstream[k]);
             for (int k = 0; k <= sccg_ctx::kTileStreams; ++k) cudaEventDestroy(ctx->tevent[k]);
@@ -650,34 +726,9 @@ int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                 inter, uni, ctx->params.T, ctx->counters};
     const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
     if (mode == SCCG_MODE_PERSISTENT) {
-        int side = 1;
-        while ((long long)(side + 1) * (side + 1) <= ctx->params.split_pixels) ++side;
-        const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
-        int r = ws_reserve(ctx, carve_size<long long>(n_pairs + 1) * 2 + carve_size<long long>(nb) +
-                                    carve_size<unsigned long long>(1));
+        const int r = ws_reserve(ctx, persistent_scratch(n_pairs));
         if (r) return r;
-        Carve cv(ctx->ws);
-        long long* nitems = cv.take<long long>(n_pairs + 1);
-        long long* ioff = cv.take<long long>(n_pairs + 1);
-        long long* bsum = cv.take<long long>(nb);
-        unsigned long long* head = cv.take<unsigned long long>(1);
-        const unsigned g = (unsigned)((n_pairs + 255) / 256);
-        k_plan<<<g, 256, 0, st>>>(a, side, nitems);
-        SCCG_LAUNCHED(ctx, "k_plan");
-        ctx->launches += 1;
-        r = device_scan(ctx, nitems, n_pairs, ioff, bsum, st);
-        if (r) return r;
-        SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, sizeof(unsigned long long), st));
-        switch (cap) {
-            case 32: r = launch_persistent<32>(ctx, a, side, nitems, ioff, head, st); break;
-            case 64: r = launch_persistent<64>(ctx, a, side, nitems, ioff, head, st); break;
-            default: r = launch_persistent<128>(ctx, a, side, nitems, ioff, head, st); break;
-        }
-        if (r) return r;
-        k_union<<<g, 256, 0, st>>>(a, nitems);
-        SCCG_LAUNCHED(ctx, "k_union");
-        ctx->launches += 1;
-        return SCCG_OK;
+        return persistent_launch(ctx, a, cap, st);
     }
     switch (cap) {
         case 32: return launch_plain<32>(ctx, a, st);
@@ -738,6 +789,62 @@ int sccg_pair_areas_tiles(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polys
     return SCCG_OK;
 }
 
+int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa,
+                   const int32_t* pb, int64_t n_pairs, int64_t* inter, int64_t* uni, sccg_jaccard_result* out,
+                   void* stream)
+{
+    if (!ctx || !out || n_pairs < 0) return SCCG_EINVAL;
+    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
+    if (!is_device_ptr(out)) return SCCG_EINVAL;
+    if (n_pairs > 0 && (!is_device_ptr(pa) || !is_device_ptr(pb) || !is_device_ptr(inter) || !is_device_ptr(uni)))
+        return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int r = ws_reserve(ctx, std::max(persistent_scratch(std::max<long long>(n_pairs, 1)), jaccard_scratch(ctx, n_pairs)));
+    if (r) return r;
+    const void* key[9] = {A->off, A->xy, A->mbr, B->off, B->xy, B->mbr, pa, inter, out};
+    const bool same = ctx->batch_exec && ctx->batch_n == n_pairs && !memcmp(key, ctx->batch_key, sizeof key) &&
+                      !memcmp(&ctx->batch_params, &ctx->params, sizeof(sccg_params)) &&
+                      ctx->batch_count_work == ctx->count_work && ctx->batch_key[0] != nullptr;
+    if (!same) {
+        if (ctx->batch_exec) {
+            cudaGraphExecDestroy(ctx->batch_exec);
+            ctx->batch_exec = nullptr;
+        }
+        if (!ctx->cap_stream) SCCG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        AreasArgs a{n_pairs, A->n, B->n, pa, pb,
+                    A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
+                    B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
+                    inter, uni, ctx->params.T, ctx->counters};
+        const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
+        const unsigned long long launches0 = ctx->launches;
+        SCCG_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        r = n_pairs > 0 ? persistent_launch(ctx, a, cap, ctx->cap_stream) : SCCG_OK;
+        if (!r) r = jaccard_launch(ctx, inter, uni, n_pairs, reinterpret_cast<JaccardOut*>(out), ctx->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        ctx->launches = launches0;
+        if (r) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->batch_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            ctx->batch_exec = nullptr;
+            return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+        }
+        memcpy(ctx->batch_key, key, sizeof key);
+        ctx->batch_n = n_pairs;
+        ctx->batch_params = ctx->params;
+        ctx->batch_count_work = ctx->count_work;
+    }
+    SCCG_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, st));
+    ctx->launches += n_pairs > 0 ? 8 : 2;    // plan, 3 scan passes, persistent, union, 2 Jaccard
+    return SCCG_OK;
+}
+
 int sccg_launch_count(const sccg_ctx* ctx, uint64_t* out)
 {
     if (!ctx || !out) return SCCG_EINVAL;
@@ -754,16 +861,13 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool dev_out = is_device_ptr(out);
-    const int nparts = (int)std::max(1LL, std::min<long long>((n_pairs + 255) / 256, 4LL * ctx->sm_count));
-    int r = ws_reserve(ctx, carve_size<JPart>(nparts) + carve_size<JaccardOut>(1));
+    int r = ws_reserve(ctx, jaccard_scratch(ctx, n_pairs));
     if (r) return r;
     Carve cv(ctx->ws);
-    JPart* parts = cv.take<JPart>(nparts);
+    cv.take<JPart>(jaccard_parts(ctx, n_pairs));
     JaccardOut* res = dev_out ? reinterpret_cast<JaccardOut*>(out) : cv.take<JaccardOut>(1);
-    k_jaccard_partial<<<nparts, 256, 0, st>>>(inter, uni, n_pairs, parts);
-    k_jaccard_final<<<1, 256, 0, st>>>(parts, nparts, n_pairs, res);
-    SCCG_LAUNCHED(ctx, "k_jaccard");
-    ctx->launches += 2;
+    r = jaccard_launch(ctx, inter, uni, n_pairs, res, st);
+    if (r) return r;
     if (!dev_out) {
         SCCG_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, res, sizeof(JaccardOut), cudaMemcpyDeviceToHost, st));
         SCCG_CUDA(ctx, cudaStreamSynchronize(st));

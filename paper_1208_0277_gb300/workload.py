@@ -378,58 +378,89 @@ def _loguniform_int(rng, lo, hi, size):
     return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size))).astype(np.int64)
 
 
-def batched_uneven(seed: int = 1, n_tiles: int = 2000, tile_px: int = 4096,
-                   count_lo: int = 50, count_hi: int = 20_000, tiles_per_row: int = 50) -> Workload:
-    """n_tiles tiles of uneven load: polygons per tile log-uniform [50, 20000]; MBR size
-    s = clip(lognormal(ln 20, 0.75), 8, 400); vertices log-uniform {4..512}, capped at 2*pi*s."""
-    rng = _rng(seed)
-    counts = _loguniform_int(rng, count_lo, count_hi, n_tiles)
-    counts = np.minimum(counts, count_hi)
-    tiles = np.repeat(np.arange(n_tiles, dtype=np.int32), counts)
-    tx = (tiles % tiles_per_row).astype(np.float64) * tile_px
-    ty = (tiles // tiles_per_row).astype(np.float64) * tile_px
+def _concat(parts) -> PolySet:
+    """Concatenate PolySets (tiles already in increasing order across parts)."""
+    offs, xys, tiles, base = [np.zeros(1, dtype=np.int64)], [], [], 0
+    for P in parts:
+        offs.append(P.off[1:] + base)
+        base += P.n_vertices
+        xys.append(P.xy)
+        tiles.append(P.tile)
+    return PolySet(off=np.concatenate(offs), xy=np.concatenate(xys), tile=np.concatenate(tiles).astype(np.int32))
+
+
+def _blocks(fn, seed: int, n_tiles: int, block: int, workers: int | None, **kw):
+    """Draw tile blocks [t0, t0 + block) independently, block k from SeedSequence([seed, k]), in a
+    thread pool (numpy releases the GIL on large array operations). The result does not depend on
+    the number of workers."""
+    import concurrent.futures as cf
+    import os
+    jobs = [(k, t0, min(t0 + block, n_tiles)) for k, t0 in enumerate(range(0, n_tiles, block))]
+    workers = workers or min(len(jobs), max(1, (os.cpu_count() or 1)))
+
+    def run(job):
+        k, t0, t1 = job
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, k])))
+        return fn(rng, t0, t1, **kw)
+    if workers == 1:
+        out = [run(j) for j in jobs]
+    else:
+        with cf.ThreadPoolExecutor(workers) as ex:
+            out = list(ex.map(run, jobs))
+    return _concat([a for a, _ in out]), _concat([b for _, b in out])
+
+
+def _uneven_block(rng, t0, t1, tile_px, count_lo, count_hi, tiles_per_row):
+    counts = np.minimum(_loguniform_int(rng, count_lo, count_hi, t1 - t0), count_hi)
+    tiles = np.repeat(np.arange(t0, t1, dtype=np.int32), counts)
     n = tiles.shape[0]
 
-    def draw(r, m, tx_, ty_):
-        cx = tx_ + r.uniform(0, tile_px, m)
-        cy = ty_ + r.uniform(0, tile_px, m)
+    def draw(r, m, t):
+        tx = (t % tiles_per_row).astype(np.float64) * tile_px
+        ty = (t // tiles_per_row).astype(np.float64) * tile_px
+        cx = tx + r.uniform(0, tile_px, m)
+        cy = ty + r.uniform(0, tile_px, m)
         s = np.clip(r.lognormal(math.log(20.0), 0.75, m), 8.0, 400.0)
         nv = _loguniform_int(r, 4, 512, m)
         nv = np.maximum(4, np.minimum(nv, np.floor(2 * np.pi * s).astype(np.int64)))
         return cx, cy, s, nv
 
-    cx, cy, s, nv = draw(rng, n, tx, ty)
+    cx, cy, s, nv = draw(rng, n, tiles)
     x, y, c = star_rings(rng, cx, cy, s, nv)
     A = _pack(x, y, c, tiles)
 
     def new_fn(r, m):
-        t = r.integers(0, n_tiles, m).astype(np.int32)
-        ntx = (t % tiles_per_row).astype(np.float64) * tile_px
-        nty = (t // tiles_per_row).astype(np.float64) * tile_px
-        ncx, ncy, ns, nnv = draw(r, m, ntx, nty)
+        t = r.integers(t0, t1, m).astype(np.int32)
+        ncx, ncy, ns, nnv = draw(r, m, t)
         a, b, cc = star_rings(r, ncx, ncy, ns, nnv)
         return a, b, cc, t
 
     B = _derive_b(rng, A, np.zeros(n, dtype=np.int8), 5, 8, 3, 0.1, new_fn)
+    return A, B
+
+
+def batched_uneven(seed: int = 1, n_tiles: int = 2000, tile_px: int = 4096,
+                   count_lo: int = 50, count_hi: int = 20_000, tiles_per_row: int = 50,
+                   workers: int | None = None) -> Workload:
+    """n_tiles tiles of uneven load: polygons per tile log-uniform [50, 20000]; MBR size
+    s = clip(lognormal(ln 20, 0.75), 8, 400); vertices log-uniform {4..512}, capped at 2*pi*s.
+    Drawn in independent blocks of 50 tiles (B derived from A within each block)."""
+    A, B = _blocks(_uneven_block, seed, n_tiles, 50, workers, tile_px=tile_px, count_lo=count_lo,
+                   count_hi=count_hi, tiles_per_row=tiles_per_row)
     return Workload(f"batched_uneven_{n_tiles}", A, B, n_tiles, tile_px, seed)
 
 
-def heavy_tail(seed: int = 1, n_tiles: int = 200, tile_px: int = 4096, nuclei_per_tile: int = 20_000,
-               tissue_lo: int = 5, tissue_hi: int = 20, tiles_per_row: int = 20,
-               tissue_nv_lo: int = 2000, tissue_nv_hi: int = 20_000,
-               tissue_s_lo: float = 500.0, tissue_s_hi: float = 4000.0) -> Workload:
-    """n_tiles tiles each holding nuclei_per_tile nuclei (MBR 10..40 px, 8..64 vertices) plus
-    U{5..20} concave tissue-region polygons (2,000..20,000 vertices, MBR log-uniform 500..4,000 px).
-    B: nuclei by the single-tile rule; tissue polygons shifted +-8 px and jittered +-3 px."""
-    rng = _rng(seed)
-    n_tissue = rng.integers(tissue_lo, tissue_hi + 1, n_tiles)
+def _heavy_block(rng, t0, t1, tile_px, nuclei_per_tile, tissue_lo, tissue_hi, tiles_per_row,
+                 tissue_nv_lo, tissue_nv_hi, tissue_s_lo, tissue_s_hi):
+    nt_ = t1 - t0
+    n_tissue = rng.integers(tissue_lo, tissue_hi + 1, nt_)
     per_tile = nuclei_per_tile + n_tissue
-    tiles = np.repeat(np.arange(n_tiles, dtype=np.int32), per_tile)
+    tiles = np.repeat(np.arange(t0, t1, dtype=np.int32), per_tile)
     n = tiles.shape[0]
     kinds = np.zeros(n, dtype=np.int8)
     starts = np.cumsum(per_tile) - per_tile
-    for t in range(n_tiles):
-        kinds[starts[t] + nuclei_per_tile: starts[t] + per_tile[t]] = 1
+    for j in range(nt_):
+        kinds[starts[j] + nuclei_per_tile: starts[j] + per_tile[j]] = 1
     tx = (tiles % tiles_per_row).astype(np.float64) * tile_px
     ty = (tiles // tiles_per_row).astype(np.float64) * tile_px
     cx = tx + rng.uniform(0, tile_px, n)
@@ -437,28 +468,24 @@ def heavy_tail(seed: int = 1, n_tiles: int = 200, tile_px: int = 4096, nuclei_pe
     s = rng.uniform(10.0, 40.0, n)
     nv = rng.integers(8, 65, n)
     tis = kinds == 1
-    nt = int(tis.sum())
-    s[tis] = np.exp(rng.uniform(math.log(tissue_s_lo), math.log(tissue_s_hi), nt))
-    nv[tis] = rng.integers(tissue_nv_lo, tissue_nv_hi + 1, nt)
-    xs, ys, cs = [], [], []
-    # nuclei and tissue rings in polygon order
+    ntis = int(tis.sum())
+    s[tis] = np.exp(rng.uniform(math.log(tissue_s_lo), math.log(tissue_s_hi), ntis))
+    nv[tis] = rng.integers(tissue_nv_lo, tissue_nv_hi + 1, ntis)
     xn, yn, cn = star_rings(rng, cx[~tis], cy[~tis], s[~tis], nv[~tis], "nucleus")
     xt, yt, ct = star_rings(rng, cx[tis], cy[tis], s[tis], nv[tis], "tissue")
     counts = np.zeros(n, dtype=np.int64)
     counts[~tis] = cn
     counts[tis] = ct
-    # interleave the two groups back into polygon order
     x = np.empty(int(counts.sum()), dtype=np.int64)
     y = np.empty_like(x)
-    owner, k = _segment_ids(counts)
+    owner, _ = _segment_ids(counts)
     is_t = tis[owner]
     x[~is_t], y[~is_t] = xn, yn
     x[is_t], y[is_t] = xt, yt
-    del xs, ys, cs
     A = _pack(x, y, counts, tiles)
 
     def new_fn(r, m):
-        t = r.integers(0, n_tiles, m).astype(np.int32)
+        t = r.integers(t0, t1, m).astype(np.int32)
         ntx = (t % tiles_per_row).astype(np.float64) * tile_px
         nty = (t // tiles_per_row).astype(np.float64) * tile_px
         ncx = ntx + r.uniform(0, tile_px, m)
@@ -469,6 +496,21 @@ def heavy_tail(seed: int = 1, n_tiles: int = 200, tile_px: int = 4096, nuclei_pe
         return a, b, cc, t
 
     B = _derive_b(rng, A, kinds, 5, 8, 3, 0.1, new_fn)
+    return A, B
+
+
+def heavy_tail(seed: int = 1, n_tiles: int = 200, tile_px: int = 4096, nuclei_per_tile: int = 20_000,
+               tissue_lo: int = 5, tissue_hi: int = 20, tiles_per_row: int = 20,
+               tissue_nv_lo: int = 2000, tissue_nv_hi: int = 20_000,
+               tissue_s_lo: float = 500.0, tissue_s_hi: float = 4000.0, workers: int | None = None) -> Workload:
+    """n_tiles tiles each holding nuclei_per_tile nuclei (MBR 10..40 px, 8..64 vertices) plus
+    U{5..20} concave tissue-region polygons (2,000..20,000 vertices, MBR log-uniform 500..4,000 px).
+    B: nuclei by the single-tile rule; tissue polygons shifted +-8 px and jittered +-3 px.
+    Drawn in independent blocks of 10 tiles."""
+    A, B = _blocks(_heavy_block, seed, n_tiles, 10, workers, tile_px=tile_px, nuclei_per_tile=nuclei_per_tile,
+                   tissue_lo=tissue_lo, tissue_hi=tissue_hi, tiles_per_row=tiles_per_row,
+                   tissue_nv_lo=tissue_nv_lo, tissue_nv_hi=tissue_nv_hi, tissue_s_lo=tissue_s_lo,
+                   tissue_s_hi=tissue_s_hi)
     return Workload(f"heavy_tail_{n_tiles}", A, B, n_tiles, tile_px, seed)
 
 

@@ -168,6 +168,29 @@ def test_heavy_tail_tissue_and_nuclei(sccg, mode):
     np.testing.assert_array_equal(g["uni"][idx], bu)
 
 
+def test_batch_graph_replay_and_recapture(sccg):
+    """sccg_batch_run: persistent areas + Jaccard captured once as a CUDA graph and replayed; a new
+    pair list (other buffers) triggers a new capture. Results equal the oracle every time."""
+    c = sccg.Context(0, {"split_pixels": 64})
+    for seed in (6, 7):
+        w = W.single_tile(seed=seed, n=500)
+        A, B = c.upload(w.A), c.upload(w.B)
+        pa, pb = c.candidate_pairs(A, B)
+        inter = torch.full((pa.numel(),), -7, dtype=torch.int64, device="cuda")
+        uni = torch.full_like(inter, -7)
+        res = torch.zeros(48, dtype=torch.uint8, device="cuda")
+        ref = O.cross_compare(w.A, w.B)
+        for _ in range(2):
+            inter.fill_(-7)
+            c.batch_run(A, B, pa, pb, (inter, uni), res)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(inter.cpu().numpy(), ref["inter"])
+            np.testing.assert_array_equal(uni.cpu().numpy(), ref["uni"])
+            J = c.read_jaccard(res)
+            for k in ("sum_inter", "sum_union", "n_nonzero", "J", "Jprime"):
+                assert J[k] == ref["jaccard"][k], k
+
+
 # ------------------------------------------------------------------------------- edge cases
 
 def rings_workload(rings_a, rings_b):
