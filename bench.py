@@ -53,7 +53,11 @@ def parse_args():
     p.add_argument("--form", choices=["tiles", "persistent", "graph"], default=None,
                    help="a4 form timed as the headline (default: tiles for configs 1-2, graph for 3)")
     p.add_argument("--config", type=int, default=2,
-                   help="1 single tile, 2 whole slide (default), 3 batched uneven tiles")
+                   help="1 single tile, 2 whole slide (default), 3 batched uneven tiles, 5 serving over 3")
+    p.add_argument("--serve-jobs", type=int, default=0, help="jobs per offered load (default 3000 for config 5, "
+                   "1000 otherwise)")
+    p.add_argument("--serve-loads", type=str, default="", help="comma-separated offered loads (fractions of the "
+                   "measured peak); default 0.5,0.8,0.95 for config 5 and 0.8 otherwise; 'none' to skip")
     p.add_argument("--tiles", type=int, default=0, help="restrict to the first N tiles (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -77,13 +81,16 @@ def make_workload(config: int, seed: int, tiles: int):
         desc = {"workload": "whole slide 100,000x100,000 px, 4096x4096 tiles (625), ~1M star nuclei per set "
                             "(8-64 vertices, MBR 10-40 px, 100 per 10^6 px^2); B = A jittered +-3, shifted +-5, "
                             "10% dropped, 10% new"}
-    elif config == 3:
+    elif config in (3, 5):
         w = W.batched_uneven(seed=seed)
         desc = {"workload": "2,000 tiles of 4096^2 px, polygons per tile log-uniform 50-20,000 (~6.4M per set), "
                             "MBR lognormal(ln 20, 0.75) clipped to 8-400 px, 4-512 vertices; B = A jittered/"
                             "shifted, 10% dropped, 10% new"}
     else:
         raise SystemExit(f"--config {config} is not a bench workload here")
+    if config == 5:
+        desc["workload"] = ("serving: jobs of one tile each, a contiguous slice of log-uniform 100-50,000 candidate "
+                            "pairs, Poisson arrivals, over resident sets of " + desc["workload"])
     if tiles:
         w = W.subset_tiles(w, range(min(tiles, w.n_tiles)))
         desc["workload"] += f" (first {tiles} tiles)"
@@ -228,13 +235,42 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------------------------------------
+# serving (continuous batching): peak, then Poisson loads at fractions of it
+# ------------------------------------------------------------------------------------------------
+
+def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
+    import numpy as np
+    from paper_1208_0277_gb300 import serve
+    rng = np.random.default_rng(seed)
+    srv = serve.Server(A, B, pa, pb, device=device, slots=3, max_batch_pairs=1 << 20, max_batch_jobs=1024)
+    try:
+        warm = serve.draw_jobs(rng, tpo, 64)
+        [f.result() for f in [srv.submit(j) for j in warm]]
+        burst = serve.draw_jobs(rng, tpo, n_jobs)
+        t0 = time.perf_counter()
+        res = [f.result() for f in [srv.submit(j) for j in burst]]
+        peak = serve.latency_summary(res, time.perf_counter() - t0)
+        mean_pairs = peak["pairs"] / peak["jobs"]
+        out = {"peak": dict(peak, note="all jobs submitted at once"), "loads": []}
+        for load in loads:
+            jobs = serve.draw_jobs(rng, tpo, n_jobs)
+            rate = load * peak["pairs_per_s"] / mean_pairs
+            res, wall = serve.run_load(srv, jobs, rate, rng)
+            out["loads"].append(dict(serve.latency_summary(res, wall), offered_load=load,
+                                     offered_jobs_per_s=rate))
+        return out
+    finally:
+        srv.close()
+
+
+# ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
 
 def main():
     args = parse_args()
     if args.form is None:
-        args.form = "graph" if args.config == 3 else "tiles"
+        args.form = "graph" if args.config in (3, 5) else "tiles"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -458,6 +494,15 @@ def main():
                   "bit_exact": bool(np.array_equal(g_pa, res["pa"]) and np.array_equal(g_pb, res["pb"]) and
                                     np.array_equal(g_i, res["inter"]) and np.array_equal(g_u, res["uni"]))}
 
+    serving = None
+    loads_arg = args.serve_loads or ("0.5,0.8,0.95" if args.config == 5 else "0.8")
+    if loads_arg != "none":
+        loads = [float(x) for x in loads_arg.split(",") if x]
+        n_jobs = args.serve_jobs or (3000 if args.config == 5 else 1000)
+        serving = serving_results(A, B, pa[:n_pairs], pb[:n_pairs], tpo0, loads, n_jobs, local_rank)
+        serving["jobs_per_load"] = n_jobs
+        serving["job_pairs"] = "log-uniform 100-50,000, clipped to the tile's candidate pairs"
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -483,6 +528,8 @@ def main():
         "phases_ms": main_r["phases_ms"],
         "jaccard": {"J": Jd["J"], "Jprime": Jd["Jprime"], "n_nonzero": Jd["n_nonzero"]},
         "parity_vs_oracle": parity,
+        "serving": serving,
+        "p99_job_ms": (serving["loads"][-1]["p99_ms"] if serving and serving["loads"] else None),
         "other_forms": {f: {"form": form_names[f], "value": total_pairs * args.steps / (o["ms"] / 1e3),
                             "ms_per_step": o["ms"] / args.steps, "phases_ms": o["phases_ms"],
                             "gpu_launches": o["launches"]}

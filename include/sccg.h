@@ -204,6 +204,21 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
 int sccg_jaccard_static(const int64_t* inter, const int64_t* uni, int64_t n_pairs,
                         sccg_jaccard_result* out, void* stream);
 
+/* Batch assembly for the serving loop (Sec. 4.1: the aggregator groups tasks into GPU batches):
+ * copies n_segments slices of the pair arrays, slice s = src[seg_src[s] .. seg_src[s] + len_s),
+ * len_s = seg_dst[s+1] - seg_dst[s], to dst[seg_dst[s] ..). All pointers are device memory;
+ * seg_dst has n_segments + 1 entries. Asynchronous. */
+int sccg_gather_pairs(sccg_ctx* ctx, const int32_t* src_pa, const int32_t* src_pb,
+                      const int64_t* seg_src, const int64_t* seg_dst, int32_t n_segments,
+                      int32_t* dst_pa, int32_t* dst_pb, void* stream);
+
+/* Per-segment Jaccard reductions (Sec. 2.1, Eq. 1, with the same exact rounding as sccg_jaccard):
+ * segment s covers pairs seg_off[s] .. seg_off[s+1]-1 (one job of a serving batch, or one tile);
+ * out is a DEVICE array of n_segments results. Asynchronous. */
+int sccg_jaccard_segments(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni,
+                          const int64_t* seg_off, int32_t n_segments,
+                          sccg_jaccard_result* out, void* stream);
+
 /* ------------------------------------------------------------------------------------------- */
 /* work accounting                                                                              */
 /* ------------------------------------------------------------------------------------------- */

@@ -203,6 +203,26 @@ class Context:
         r = _native.JaccardC.from_buffer_copy(result.cpu().numpy().tobytes())
         return {k: getattr(r, k) for k, _ in r._fields_}
 
+    def gather_pairs(self, src_pa, src_pb, seg_src, seg_dst, dst_pa, dst_pb, stream=None):
+        """Copy pair slices (segment s: seg_src[s], length seg_dst[s+1]-seg_dst[s]) into dst."""
+        self._check(self.lib.sccg_gather_pairs(self.h, src_pa.data_ptr(), src_pb.data_ptr(), seg_src.data_ptr(),
+                                               seg_dst.data_ptr(), seg_src.numel(), dst_pa.data_ptr(),
+                                               dst_pb.data_ptr(), _stream(stream)), "sccg_gather_pairs")
+
+    def jaccard_segments(self, inter, uni, seg_off, out, stream=None):
+        """Per-segment Jaccard into `out` (device uint8 tensor of 48 * n_segments bytes)."""
+        self._check(self.lib.sccg_jaccard_segments(self.h, inter.data_ptr(), uni.data_ptr(), seg_off.data_ptr(),
+                                                   seg_off.numel() - 1, out.data_ptr(), _stream(stream)),
+                    "sccg_jaccard_segments")
+
+    @staticmethod
+    def decode_jaccard_array(raw) -> list:
+        """Decode a host bytes/uint8 array of 48-byte Jaccard structs."""
+        import numpy as np
+        buf = np.asarray(raw, dtype=np.uint8).tobytes()
+        return [{k: getattr(r, k) for k, _ in r._fields_}
+                for r in (_native.JaccardC.from_buffer_copy(buf, 48 * i) for i in range(len(buf) // 48))]
+
     def launch_count(self) -> int:
         c = ctypes.c_uint64(0)
         self._check(self.lib.sccg_launch_count(self.h, ctypes.byref(c)), "sccg_launch_count")

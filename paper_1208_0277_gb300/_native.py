@@ -25,7 +25,7 @@ EXPORTS = [
     "sccg_status_str", "sccg_ctx_create", "sccg_ctx_destroy", "sccg_ctx_set_param",
     "sccg_ctx_get_params", "sccg_last_error", "sccg_prepare", "sccg_candidate_pairs",
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
-    "sccg_jaccard_static", "sccg_work_counters",
+    "sccg_jaccard_static", "sccg_work_counters", "sccg_gather_pairs", "sccg_jaccard_segments",
 ]
 
 _lock = threading.Lock()
@@ -111,6 +111,8 @@ def load(path: str | None = None):
             "sccg_pair_areas": ([V, PS, PS, V, V, I64, V, V, I, V], I),
             "sccg_pair_areas_tiles": ([V, PS, PS, V, V, V, ctypes.c_int32, V, V, V], I),
             "sccg_batch_run": ([V, PS, PS, V, V, I64, V, V, V, V], I),
+            "sccg_gather_pairs": ([V, V, V, V, V, ctypes.c_int32, V, V, V], I),
+            "sccg_jaccard_segments": ([V, V, V, V, ctypes.c_int32, V, V], I),
             "sccg_launch_count": ([V, ctypes.POINTER(ctypes.c_uint64)], I),
             "sccg_jaccard": ([V, V, V, I64, V, V], I),
             "sccg_jaccard_static": ([V, V, I64, V, V], I),

@@ -787,4 +787,86 @@ __global__ void __launch_bounds__(256) k_jaccard_final(const JPart* parts, int n
     *out = r;
 }
 
+// ----------------------------------------------------------------------------------------------
+// Segmented helpers: batch assembly and per-segment Jaccard (jobs of a serving batch, tiles)
+// ----------------------------------------------------------------------------------------------
+
+// One CTA per segment s: copies src[seg_src[s] .. seg_src[s] + len) to dst[seg_dst[s] ..), where
+// len = seg_dst[s+1] - seg_dst[s].
+__global__ void __launch_bounds__(256) k_gather_pairs(const int32_t* __restrict__ src_a,
+                                                      const int32_t* __restrict__ src_b,
+                                                      const int64_t* __restrict__ seg_src,
+                                                      const int64_t* __restrict__ seg_dst, int nseg,
+                                                      int32_t* __restrict__ dst_a, int32_t* __restrict__ dst_b)
+{
+    for (int sgm = blockIdx.x; sgm < nseg; sgm += gridDim.x) {
+        const long long s0 = seg_src[sgm], d0 = seg_dst[sgm], len = seg_dst[sgm + 1] - d0;
+        for (long long i = threadIdx.x; i < len; i += blockDim.x) {
+            dst_a[d0 + i] = src_a[s0 + i];
+            dst_b[d0 + i] = src_b[s0 + i];
+        }
+    }
+}
+
+// One CTA (256 threads) per segment: the Jaccard reductions of pairs seg_off[s] .. seg_off[s+1]-1,
+// with the same exact sums as k_jaccard_partial / k_jaccard_final.
+__global__ void __launch_bounds__(256) k_jaccard_segments(const int64_t* __restrict__ inter,
+                                                          const int64_t* __restrict__ uni,
+                                                          const int64_t* __restrict__ seg_off, int nseg,
+                                                          JaccardOut* out)
+{
+    __shared__ JPart sh[8];
+    for (int sgm = blockIdx.x; sgm < nseg; sgm += gridDim.x) {
+        const long long lo_i = seg_off[sgm], hi_i = seg_off[sgm + 1];
+        unsigned long long si = 0, su = 0, nz = 0;
+        unsigned __int128 fx = 0;
+        for (long long i = lo_i + threadIdx.x; i < hi_i; i += blockDim.x) {
+            const long long in = inter[i];
+            if (in > 0) {
+                const long long un = uni[i];
+                si += (unsigned long long)in;
+                su += (unsigned long long)un;
+                nz += 1;
+                fx += ratio_fixed(in, un);
+            }
+        }
+        unsigned long long lo = (unsigned long long)fx, hi = (unsigned long long)(fx >> 64);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            si += shfl_down_u64(si, o);
+            su += shfl_down_u64(su, o);
+            nz += shfl_down_u64(nz, o);
+            const unsigned long long l2 = shfl_down_u64(lo, o), h2 = shfl_down_u64(hi, o);
+            const unsigned long long nl = lo + l2;
+            hi = hi + h2 + (nl < lo ? 1ull : 0ull);
+            lo = nl;
+        }
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = JPart{si, su, nz, lo, hi};
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            JPart t = sh[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                t.si += sh[w].si; t.su += sh[w].su; t.nz += sh[w].nz;
+                const unsigned long long nl = t.fx_lo + sh[w].fx_lo;
+                t.fx_hi += sh[w].fx_hi + (nl < t.fx_lo ? 1ull : 0ull);
+                t.fx_lo = nl;
+            }
+            JaccardOut r;
+            r.sum_inter = (long long)t.si;
+            r.sum_union = (long long)t.su;
+            r.n_nonzero = (long long)t.nz;
+            r.n_pairs = hi_i - lo_i;
+            if (t.nz == 0) {
+                r.J = 0.0; r.Jprime = 0.0;
+            } else {
+                r.J = __ddiv_rn(__ll2double_rn((long long)t.si), __ll2double_rn((long long)t.su));
+                const unsigned __int128 s = ((unsigned __int128)t.fx_hi << 64) | t.fx_lo;
+                r.Jprime = __ddiv_rn(u128_to_double_scaled(s, -100), __ll2double_rn((long long)t.nz));
+            }
+            out[sgm] = r;
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace sccg

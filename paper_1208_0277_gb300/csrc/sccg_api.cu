@@ -845,6 +845,40 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
     return SCCG_OK;
 }
 
+int sccg_gather_pairs(sccg_ctx* ctx, const int32_t* src_pa, const int32_t* src_pb, const int64_t* seg_src,
+                      const int64_t* seg_dst, int32_t n_segments, int32_t* dst_pa, int32_t* dst_pb, void* stream)
+{
+    if (!ctx || n_segments < 0) return SCCG_EINVAL;
+    if (n_segments == 0) return SCCG_OK;
+    if (!is_device_ptr(src_pa) || !is_device_ptr(src_pb) || !is_device_ptr(seg_src) || !is_device_ptr(seg_dst) ||
+        !is_device_ptr(dst_pa) || !is_device_ptr(dst_pb))
+        return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = (unsigned)std::min<long long>(n_segments, 8LL * ctx->sm_count);
+    k_gather_pairs<<<grid, 256, 0, st>>>(src_pa, src_pb, seg_src, seg_dst, n_segments, dst_pa, dst_pb);
+    SCCG_LAUNCHED(ctx, "k_gather_pairs");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+int sccg_jaccard_segments(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, const int64_t* seg_off,
+                          int32_t n_segments, sccg_jaccard_result* out, void* stream)
+{
+    static_assert(sizeof(JaccardOut) == sizeof(sccg_jaccard_result), "layout");
+    if (!ctx || !out || n_segments < 0) return SCCG_EINVAL;
+    if (n_segments == 0) return SCCG_OK;
+    if (!is_device_ptr(inter) || !is_device_ptr(uni) || !is_device_ptr(seg_off) || !is_device_ptr(out))
+        return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = (unsigned)std::min<long long>(n_segments, 8LL * ctx->sm_count);
+    k_jaccard_segments<<<grid, 256, 0, st>>>(inter, uni, seg_off, n_segments, reinterpret_cast<JaccardOut*>(out));
+    SCCG_LAUNCHED(ctx, "k_jaccard_segments");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
 int sccg_launch_count(const sccg_ctx* ctx, uint64_t* out)
 {
     if (!ctx || !out) return SCCG_EINVAL;

@@ -1,0 +1,71 @@
+"""Serving loop: every job's result is the same alone and in a mixed stream of batched jobs, and
+equals the oracle on its pair slice (tolerance 0: integer areas, correctly rounded Jaccard)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1208_0277_gb300 import workload as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def resident():
+    import paper_1208_0277_gb300 as P
+    P.build()
+    w = W.batched_uneven(seed=4, n_tiles=24, count_lo=50, count_hi=3000)
+    ctx = P.Context(0)
+    A, B = ctx.upload(w.A), ctx.upload(w.B)
+    pa, pb, tpo = ctx.candidate_pairs(A, B, with_tile_offsets=True)
+    return P, w, ctx, A, B, pa, pb, tpo
+
+
+def same(r1, r2):
+    np.testing.assert_array_equal(r1.inter, r2.inter)
+    np.testing.assert_array_equal(r1.uni, r2.uni)
+    for k in ("sum_inter", "sum_union", "n_nonzero", "n_pairs", "J", "Jprime"):
+        assert r1.jaccard[k] == r2.jaccard[k], k
+
+
+def test_results_alone_equal_results_in_the_mix(resident):
+    P, w, ctx, A, B, pa, pb, tpo = resident
+    from paper_1208_0277_gb300 import serve
+    srv = serve.Server(A, B, pa, pb, slots=3, max_batch_pairs=40_000, max_batch_jobs=64)
+    try:
+        rng = np.random.default_rng(0)
+        jobs = serve.draw_jobs(rng, tpo, 300, lo=20, hi=5000)
+        futs = [srv.submit(serve.Job(j.p0, j.p1, j.tile)) for j in jobs]     # a burst: batched together
+        mixed = [f.result(timeout=120) for f in futs]
+        assert srv.batches < len(jobs)                                      # jobs really were batched
+        assert max(r.batch_jobs for r in mixed) > 1
+        for i in rng.choice(len(jobs), 25, replace=False):
+            alone = srv.submit(serve.Job(jobs[i].p0, jobs[i].p1, jobs[i].tile)).result(timeout=60)
+            assert alone.batch_jobs == 1
+            same(alone, mixed[i])
+        pa_h, pb_h = pa.cpu().numpy().astype(np.int64), pb.cpu().numpy().astype(np.int64)
+        for i in rng.choice(len(jobs), 10, replace=False):
+            j = jobs[i]
+            ri, ru = O.pair_areas(w.A, w.B, pa_h[j.p0:j.p1], pb_h[j.p0:j.p1], method="rle")
+            np.testing.assert_array_equal(mixed[i].inter, ri)
+            np.testing.assert_array_equal(mixed[i].uni, ru)
+            ref = O.jaccard(ri, ru)
+            for k in ("sum_inter", "sum_union", "n_nonzero", "J", "Jprime"):
+                assert mixed[i].jaccard[k] == ref[k], k
+    finally:
+        srv.close()
+
+
+def test_oversized_job_is_refused(resident):
+    P, w, ctx, A, B, pa, pb, tpo = resident
+    from paper_1208_0277_gb300 import serve
+    srv = serve.Server(A, B, pa, pb, slots=1, max_batch_pairs=1000, max_batch_jobs=8)
+    try:
+        with pytest.raises(ValueError):
+            srv.submit(serve.Job(0, 1001))
+        r = srv.submit(serve.Job(0, 1000)).result(timeout=60)
+        assert len(r.inter) == 1000
+    finally:
+        srv.close()
+    with pytest.raises(ValueError):
+        serve.Server(A, B, pa, pb, slots=4, max_batch_pairs=1 << 20, mem_budget_bytes=1 << 20)
