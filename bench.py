@@ -42,6 +42,8 @@ OPS_PER_STRIP_EDGE = 17
 OPS_PER_BOX_EDGE = 33
 OPS_PER_ROW_EDGE = 15      # listed straddling edge: the strip test without its straddle check
 OPS_PER_ROW_ENTRY = 11     # building one (edge, row) list entry: count pass + fill pass
+OPS_PER_SCAN_ENTRY = 14    # one (edge, row) crossing value of the by-rows area: count, N, ceil-divide, store
+OPS_PER_SCAN_PAIR = 4      # one comparison while ranking a row's crossing values
 
 
 def parse_args():
@@ -51,9 +53,10 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--form", choices=["tiles", "persistent", "graph"], default=None,
-                   help="a4 form timed as the headline (default: tiles for configs 1-2, graph for 3)")
+                   help="a4 form timed as the headline (default: tiles for configs 1-2, graph for 3-5)")
     p.add_argument("--config", type=int, default=2,
-                   help="1 single tile, 2 whole slide (default), 3 batched uneven tiles, 5 serving over 3")
+                   help="1 single tile, 2 whole slide (default), 3 batched uneven tiles, 4 heavy tail, "
+                   "5 serving over 3")
     p.add_argument("--serve-jobs", type=int, default=0, help="jobs per offered load (default 3000 for config 5, "
                    "1000 otherwise)")
     p.add_argument("--serve-loads", type=str, default="", help="comma-separated offered loads (fractions of the "
@@ -81,6 +84,11 @@ def make_workload(config: int, seed: int, tiles: int):
         desc = {"workload": "whole slide 100,000x100,000 px, 4096x4096 tiles (625), ~1M star nuclei per set "
                             "(8-64 vertices, MBR 10-40 px, 100 per 10^6 px^2); B = A jittered +-3, shifted +-5, "
                             "10% dropped, 10% new"}
+    elif config == 4:
+        w = W.heavy_tail(seed=seed)
+        desc = {"workload": "heavy tail: 200 tiles of 4096^2 px, 20,000 star nuclei per tile (8-64 vertices, MBR "
+                            "10-40 px) + 5-20 concave tissue regions per tile (2,000-20,000 vertices, MBR "
+                            "log-uniform 500-4,000 px); B = A jittered/shifted, nuclei 10% dropped, 10% new"}
     elif config in (3, 5):
         w = W.batched_uneven(seed=seed)
         desc = {"workload": "2,000 tiles of 4096^2 px, polygons per tile log-uniform 50-20,000 (~6.4M per set), "
@@ -201,6 +209,30 @@ def oracle_sample(w, target_s: float):
         tiles = min(w.n_tiles, int(tiles * grow) + 1)
 
 
+def oracle_sample_pairs(w, target_s: float, seed: int = 7):
+    """For workloads whose single tile is already beyond a bounded oracle run (config 4: tissue
+    windows up to 4000^2 px against 20,000-edge rings): the oracle's candidate pairs of tile 0, then
+    its exact pair areas (row-interval method) on a seeded uniform sample of them, grown until one
+    run costs at least target_s / 2. Returns (tile-0 pairs (pa, pb), sample indices, (inter, uni),
+    seconds)."""
+    import numpy as np
+    import oracle as O
+    from paper_1208_0277_gb300 import workload as W
+    sub = W.subset_tiles(w, range(1))
+    pa, pb = O.candidate_pairs(sub.A, sub.B)
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(pa))
+    m = 64
+    while True:
+        idx = np.sort(order[:m])
+        t0 = time.perf_counter()
+        res = O.pair_areas(sub.A, sub.B, pa[idx], pb[idx], method="rle")
+        el = time.perf_counter() - t0
+        if el >= target_s / 2 or m >= len(pa):
+            return (pa, pb), idx, res, el
+        m = min(len(pa), int(m * max(2.0, min(8.0, target_s / max(el, 1e-3)))) + 1)
+
+
 def reference_arm(args):
     """The CPU oracle as the reference arm: each step is a bounded sample of the same workload."""
     import oracle as O
@@ -208,16 +240,28 @@ def reference_arm(args):
     w, desc = make_workload(args.config, 1, args.tiles)
     O.build()
     # size one step so that warm-up plus timed steps take about two minutes
-    res, tiles, el = oracle_sample(w, target_s=max(1.0, 120.0 / (args.steps + args.warmup)))
-    sub = W.subset_tiles(w, range(tiles)) if tiles < w.n_tiles else w
+    target = max(1.0, 120.0 / (args.steps + args.warmup))
+    if args.config == 4:
+        (o_pa, o_pb), idx, _, _ = oracle_sample_pairs(w, target_s=target)
+        sub = W.subset_tiles(w, range(1))
+        step = lambda: O.pair_areas(sub.A, sub.B, o_pa[idx], o_pb[idx], method="rle")  # noqa: E731
+        pairs_of = lambda r: len(idx)                                                   # noqa: E731
+        sample = (f"uniform sample of {len(idx)} of the {len(o_pa)} candidate pairs of tile 0 per step: the "
+                  "oracle's exact row-interval pair areas; extrapolated per pair")
+    else:
+        res, tiles, el = oracle_sample(w, target_s=target)
+        sub = W.subset_tiles(w, range(tiles)) if tiles < w.n_tiles else w
+        step = lambda: O.cross_compare(sub.A, sub.B)                                    # noqa: E731
+        pairs_of = lambda r: len(r["pa"])                                               # noqa: E731
+        sample = None
     for _ in range(args.warmup):
-        O.cross_compare(sub.A, sub.B)
+        step()
     times, pairs = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = O.cross_compare(sub.A, sub.B)
+        r = step()
         times.append(time.perf_counter() - t0)
-        pairs = len(r["pa"])
+        pairs = pairs_of(r)
     tot = sum(times)
     value = pairs * args.steps / tot
     cores = os.cpu_count()
@@ -227,8 +271,8 @@ def reference_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic", "config": desc,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"first {tiles} of {w.n_tiles} tiles per step ({pairs} candidate pairs; "
-                                   "brute-force pixel areas, candidate pairs and Jaccard)"},
+                         "sample": sample or (f"first {tiles} of {w.n_tiles} tiles per step ({pairs} candidate "
+                                              "pairs; brute-force pixel areas, candidate pairs and Jaccard)")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -270,7 +314,7 @@ def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
 def main():
     args = parse_args()
     if args.form is None:
-        args.form = "graph" if args.config in (3, 5) else "tiles"
+        args.form = "graph" if args.config in (3, 4, 5) else "tiles"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -371,7 +415,8 @@ def main():
 
     def ops(wc):
         return (wc["strip_edges"] * OPS_PER_STRIP_EDGE + wc["box_edges"] * OPS_PER_BOX_EDGE +
-                wc["row_edges"] * OPS_PER_ROW_EDGE + wc["row_entries"] * OPS_PER_ROW_ENTRY)
+                wc["row_edges"] * OPS_PER_ROW_EDGE + wc["row_entries"] * OPS_PER_ROW_ENTRY +
+                wc["scan_entries"] * OPS_PER_SCAN_ENTRY + wc["scan_pairs"] * OPS_PER_SCAN_PAIR)
 
     results = {}
     for form in [args.form] + [f for f in ("tiles", "persistent", "graph") if f != args.form]:
@@ -478,7 +523,21 @@ def main():
     # CPU baseline (rank 0, N=1): the oracle on the host cores, with a parity check on the sample
     cpu = None
     parity = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == 4:
+        import oracle as O
+        O.build()
+        (o_pa, o_pb), idx, (o_i, o_u), el = oracle_sample_pairs(w, target_s=15.0)
+        k0 = len(o_pa)
+        cpu = {"value": len(idx) / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"uniform sample of {len(idx)} of the {k0} candidate pairs of tile 0 ({el:.1f} s): the "
+                         "oracle's exact row-interval pair areas (its brute force would take hours on the "
+                         "4000^2-px tissue windows); extrapolated per pair"}
+        parity = {"sample_pairs": int(len(idx)), "tile0_pairs": k0,
+                  "bit_exact": bool(np.array_equal(pa[:k0].cpu().numpy(), o_pa) and
+                                    np.array_equal(pb[:k0].cpu().numpy(), o_pb) and
+                                    np.array_equal(inter[:k0].cpu().numpy()[idx], o_i) and
+                                    np.array_equal(uni[:k0].cpu().numpy()[idx], o_u))}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
         res, tiles, el = oracle_sample(w, target_s=15.0)
@@ -519,7 +578,7 @@ def main():
                        pairs_per_step=n_pairs, polygons=[nA, nB], tiles=w.n_tiles,
                        l2="inputs larger than L2 (no flush needed)",
                        input_bytes=sum(devb[k].numel() * devb[k].element_size() for k in devb),
-                       generation_s=round(gen_s, 1), seed=1 + rank),
+                       generation_s=round(gen_s, 1), seed=1 + rank, params=ctx.params()),
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

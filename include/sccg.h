@@ -65,7 +65,15 @@ typedef struct sccg_params {
     int32_t split_pixels;    /* persistent form: a pair's window is cut into work items of at
                                 most about this many pixels (heavy pairs spread across warps) */
     int32_t ctas_per_sm;     /* persistent form: resident CTAs per SM (0 = occupancy maximum) */
+    int32_t area_method;     /* how sccg_prepare counts ||p||: SCCG_AREA_ROWS (default) or
+                                SCCG_AREA_PIXELBOX; both give the same exact pixel count */
 } sccg_params;
+
+/* sccg_prepare's method for ||p||. ROWS: per pixel row, the crossing positions of the edges that
+ * straddle it (sorted) delimit the inside pixels, so cost follows the edges per row (the exact
+ * pixel-count counterpart of the shoelace area the paper uses, Sec. 3.2). PIXELBOX: Algorithm 1
+ * applied to the polygon alone. */
+enum { SCCG_AREA_ROWS = 0, SCCG_AREA_PIXELBOX = 1 };
 
 /* Create a context on CUDA device `device`. params_json may be NULL or a flat JSON object with any
  * of the sccg_params field names, e.g. {"T": 1024, "warps_per_cta": 8}. */
@@ -94,6 +102,10 @@ typedef struct sccg_polyset {
     int32_t max_extent;     /* largest bounding-box width or height */
     int32_t n_tiles;        /* largest tile id + 1 */
     int32_t reserved;       /* set by sccg_prepare once the set is valid; do not modify */
+    int64_t band_bytes;     /* written by sccg_prepare: device bytes sccg_build_bands needs for the
+                               set's band index (0: no polygon has 1024 or more vertices) */
+    const void* bands;      /* device, optional: the band index written by sccg_build_bands, or
+                               NULL (then every work item reads its polygons' whole rings) */
 } sccg_polyset;
 
 /* Step 1 of the path: per-polygon bounding box (MBR) and pixel area ||p|| (Sec. 3.2 computes ||p||
@@ -104,6 +116,17 @@ typedef struct sccg_polyset {
  * fields; SYNCHRONISES the stream once to read the validation result back.
  * Returns SCCG_EINVAL or SCCG_ERANGE for invalid sets (mbr/area contents then unspecified). */
 int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream);
+
+/* Band index of the set's polygons with 1024 or more vertices (large tissue regions): each such
+ * polygon's rows are cut into 32-row bands and every band lists the edges whose y-range meets it,
+ * so a pair-area work item reads only the edges near its window instead of the whole ring (the
+ * sampling boxes of Sec. 3.2 only ever test edges that can meet them; this finds those edges
+ * without scanning every vertex). Optional: results are identical with and without it.
+ * buf: caller-owned device memory of at least s->band_bytes bytes, 16-byte aligned, kept alive and
+ * unmodified while the set is used; on success s->bands = buf. s must have been prepared.
+ * Asynchronous on `stream`. Returns SCCG_ECAPACITY when bytes < s->band_bytes (s->bands unchanged);
+ * with s->band_bytes == 0 it sets s->bands = NULL and launches nothing. */
+int sccg_build_bands(sccg_ctx* ctx, sccg_polyset* s, void* buf, int64_t bytes, void* stream);
 
 /* ------------------------------------------------------------------------------------------- */
 /* the hot path                                                                                 */
@@ -224,12 +247,13 @@ int sccg_jaccard_segments(sccg_ctx* ctx, const int64_t* inter, const int64_t* un
 /* ------------------------------------------------------------------------------------------- */
 /* With sccg_ctx_set_param(ctx, "count_work", 1) the prepare and pair-area kernels run an
  * instrumented build that counts the work the method performs; the counts accumulate in the
- * context until read. out6 (host, 6 entries): [0] (32-pixel row strip, edge) evaluations of the
+ * context until read. out8 (host, 8 entries): [0] (32-pixel row strip, edge) evaluations of the
  * full strip test, [1] (pixel, edge) point-in-polygon tests inside all strips, [2] (sampling box,
  * edge) classifications, [3] sampling boxes classified, [4] (edge, row) entries of the per-row edge
- * lists built, [5] (32-pixel row strip, listed straddling edge) evaluations. Synchronous.
+ * lists built, [5] (32-pixel row strip, listed straddling edge) evaluations, [6] (edge, row)
+ * crossing values of the by-rows area, [7] crossing-value comparisons ranking them. Synchronous.
  * reset != 0 zeroes the counters. */
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out6, int reset);
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out8, int reset);
 
 #ifdef __cplusplus
 }

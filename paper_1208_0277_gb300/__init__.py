@@ -22,6 +22,8 @@ SCCG_OK = 0
 SCCG_ECAPACITY = 3
 MODE_PLAIN = 0
 MODE_PERSISTENT = 1
+AREA_ROWS = 0          # sccg_prepare counts ||p|| row by row (default)
+AREA_PIXELBOX = 1      # ... or by PixelBox on the polygon alone
 
 
 class SccgError(RuntimeError):
@@ -55,6 +57,7 @@ class DevicePolySet:
     mbr: object
     area: object
     c: _native.PolySetC
+    bands: object = None        # uint8 device tensor holding the band index, if the set has one
 
     @property
     def n(self) -> int:
@@ -99,18 +102,19 @@ class Context:
         return {k: getattr(p, k) for k, _ in p._fields_}
 
     # ------------------------------------------------------------------ sets
-    def upload(self, ps, stream=None) -> DevicePolySet:
+    def upload(self, ps, stream=None, bands: bool = True) -> DevicePolySet:
         """Copy a host PolySet (workload.PolySet) to the device and prepare it (MBRs, areas)."""
         import torch
         dev = torch.device("cuda", self.device)
         off = torch.from_numpy(ps.off).to(dev)
         xy = torch.from_numpy(ps.xy).to(dev)
         tile = torch.from_numpy(ps.tile).to(dev)
-        return self.prepare(off, xy, tile, stream)
+        return self.prepare(off, xy, tile, stream, bands=bands)
 
-    def prepare(self, off, xy, tile=None, stream=None, out=None) -> DevicePolySet:
+    def prepare(self, off, xy, tile=None, stream=None, out=None, bands: bool = True) -> DevicePolySet:
         """MBRs, validation and pixel areas of a device-resident CSR set (off int64, xy int32 pairs,
-        tile int32 or None). out = (mbr int32 [n,4], area int64 [n]) reuses caller buffers."""
+        tile int32 or None). out = (mbr int32 [n,4], area int64 [n]) reuses caller buffers. With
+        bands (default) the band index of polygons with >= 1024 vertices is built when there are any."""
         import torch
         n = off.numel() - 1
         if out is None:
@@ -123,7 +127,18 @@ class Context:
         c = _native.PolySetC(n=n, off=off.data_ptr(), xy=xy.data_ptr(), tile=_ptr(tile),
                              mbr=mbr.data_ptr(), area=area.data_ptr())
         self._check(self.lib.sccg_prepare(self.h, ctypes.byref(c), _stream(stream)), "sccg_prepare")
-        return DevicePolySet(off, xy, tile, mbr, area, c)
+        d = DevicePolySet(off, xy, tile, mbr, area, c)
+        if bands and c.band_bytes > 0:
+            self.build_bands(d, stream=stream)
+        return d
+
+    def build_bands(self, d: DevicePolySet, stream=None):
+        """Build (or rebuild) the band index of a prepared set into a new device buffer."""
+        import torch
+        buf = torch.empty(max(int(d.c.band_bytes), 16), dtype=torch.uint8, device=d.off.device)
+        self._check(self.lib.sccg_build_bands(self.h, ctypes.byref(d.c), ctypes.c_void_p(buf.data_ptr()),
+                                              buf.numel(), _stream(stream)), "sccg_build_bands")
+        d.bands = buf if d.c.bands else None
 
     # ------------------------------------------------------------------ hot path
     def candidate_pairs(self, A: DevicePolySet, B: DevicePolySet, capacity: int | None = None,
@@ -248,10 +263,10 @@ class Context:
                                           ctypes.c_void_p(out.data_ptr()), _stream(stream)), "sccg_jaccard")
 
     def work_counters(self, reset: bool = True) -> dict:
-        a = (ctypes.c_uint64 * 6)()
+        a = (ctypes.c_uint64 * 8)()
         self._check(self.lib.sccg_work_counters(self.h, a, int(reset)), "sccg_work_counters")
         return dict(strip_edges=a[0], pixel_edges=a[1], box_edges=a[2], boxes=a[3], row_entries=a[4],
-                    row_edges=a[5])
+                    row_edges=a[5], scan_entries=a[6], scan_pairs=a[7])
 
 
 def cross_compare(ctx: Context, A: DevicePolySet, B: DevicePolySet, mode: int = MODE_PLAIN, stream=None):

@@ -25,7 +25,8 @@ EXPORTS = [
     "sccg_status_str", "sccg_ctx_create", "sccg_ctx_destroy", "sccg_ctx_set_param",
     "sccg_ctx_get_params", "sccg_last_error", "sccg_prepare", "sccg_candidate_pairs",
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
-    "sccg_jaccard_static", "sccg_work_counters", "sccg_gather_pairs", "sccg_jaccard_segments",
+    "sccg_jaccard_static", "sccg_work_counters", "sccg_build_bands", "sccg_gather_pairs",
+    "sccg_jaccard_segments",
 ]
 
 _lock = threading.Lock()
@@ -72,12 +73,15 @@ class PolySetC(ctypes.Structure):
         ("max_extent", ctypes.c_int32),
         ("n_tiles", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("band_bytes", ctypes.c_int64),
+        ("bands", ctypes.c_void_p),
     ]
 
 
 class ParamsC(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("split_pixels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("split_pixels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("area_method", ctypes.c_int32)]
 
 
 class JaccardC(ctypes.Structure):
@@ -116,6 +120,7 @@ def load(path: str | None = None):
             "sccg_launch_count": ([V, ctypes.POINTER(ctypes.c_uint64)], I),
             "sccg_jaccard": ([V, V, V, I64, V, V], I),
             "sccg_jaccard_static": ([V, V, I64, V, V], I),
+            "sccg_build_bands": ([V, PS, V, I64, V], I),
             "sccg_work_counters": ([V, ctypes.POINTER(ctypes.c_uint64), I], I),
         }
         for name, (args, res) in sig.items():

@@ -4,6 +4,7 @@
 #include <cstdint>
 
 #include "pixelbox.cuh"
+#include "scanline.cuh"
 
 // Dynamic shared memory of the one-warp-per-item kernels (per-warp WarpSmem slices).
 #ifndef SCCG_DYNAMIC_SMEM
@@ -38,12 +39,13 @@ struct PrepStats {
     int max_extent;
     int n_tiles;
     long long first_bad;
+    unsigned long long band_bytes;    // sum of the band index block sizes
 };
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
 {
     unsigned long long a = wc.strip_edges, b = wc.pixel_edges, c = wc.box_edges, d = wc.boxes,
-                       e = wc.row_entries, f = wc.row_edges;
+                       e = wc.row_entries, f = wc.row_edges, g = wc.scan_entries, h = wc.scan_pairs;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(kFull, a, o);
@@ -52,6 +54,8 @@ __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCoun
         d += __shfl_xor_sync(kFull, d, o);
         e += __shfl_xor_sync(kFull, e, o);
         f += __shfl_xor_sync(kFull, f, o);
+        g += __shfl_xor_sync(kFull, g, o);
+        h += __shfl_xor_sync(kFull, h, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&out->strip_edges, a);
@@ -60,7 +64,62 @@ __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCoun
         atomicAdd(&out->boxes, d);
         atomicAdd(&out->row_entries, e);
         atomicAdd(&out->row_edges, f);
+        atomicAdd(&out->scan_entries, g);
+        atomicAdd(&out->scan_pairs, h);
     }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Band index of the polygons with many vertices. A polygon's pixel rows are cut into bands of
+// 2^kBandShift rows counted from its minimum y; band b lists the edge record {ylo, dy, dx, xl} of
+// every edge whose closed y-range [ylo, ylo + dy] meets the band's rows. A work item then stages
+// only the records of the bands its window's rows fall in (stage_banded) instead of reading the
+// whole ring.
+//
+// Blob (16-byte aligned): BandHead; int64 tab[n] (byte offset of polygon i's block, -1 = none);
+// the blocks. Block: int nb and 3 pad ints; int boff[nb + 1] (exclusive offsets of the bands'
+// lists) and int cur[nb] (fill cursors), padded to 16 bytes; int4 ent[boff[nb]].
+// ----------------------------------------------------------------------------------------------
+constexpr int kBandShift = 5;
+#ifndef SCCG_BAND_MIN_VERTICES
+#define SCCG_BAND_MIN_VERTICES 1024
+#endif
+constexpr int kBandMinVertices = SCCG_BAND_MIN_VERTICES;
+constexpr long long kBandMaxEntries = 1LL << 30;
+
+struct BandHead {
+    long long n;
+    long long bytes;
+    int shift;
+    int pad[3];
+};
+
+__host__ __device__ inline long long band_head_bytes(long long n)
+{
+    return (long long)sizeof(BandHead) + ((8 * n + 15) & ~15LL);
+}
+__host__ __device__ inline long long band_block_bytes(int nb, long long entries)
+{
+    return 16 + ((4LL * (2 * nb + 1) + 15) & ~15LL) + 16 * entries;
+}
+
+// Block size of polygon i (0 when it gets no index). Whole warp, converged.
+__device__ __forceinline__ long long band_block_size(const int2* v, int nv, int miny, int maxy, int lane)
+{
+    if (nv < kBandMinVertices) return 0;
+    const int nb = ((maxy - miny) >> kBandShift) + 1;
+    long long entries = 0;
+    for (int base = 0; base < nv; base += 32) {
+        const int e = base + lane;
+        if (e < nv) {
+            const int f = (e + 1 == nv) ? 0 : e + 1;
+            const int ya = v[e].y, yb = v[f].y;
+            entries += (long long)(((max(ya, yb) - miny) >> kBandShift) - ((min(ya, yb) - miny) >> kBandShift) + 1);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) entries += __shfl_xor_sync(kFull, entries, o);
+    return entries > kBandMaxEntries ? 0 : band_block_bytes(nb, entries);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -76,18 +135,36 @@ struct PrepArgs {
     PrepStats* stats;
     int T;
     WorkCounters* counters;
+    int defer_above;        // > 0: polygons with more vertices are listed for k_prepare_big
+    int* big_list;
+    unsigned* big_n;
 };
 
-template <int CAP, int STK, bool COUNT>
+// Per-warp shared memory slice of k_prepare: the PixelBox buffers and, with SCAN, the by-rows
+// buffers in the same bytes.
+template <int CAP, int STK, bool SCAN>
+__host__ __device__ constexpr size_t prep_slice()
+{
+    return (SCAN && sizeof(ScanSmem) > sizeof(WarpSmem<CAP, STK>)) ? sizeof(ScanSmem) : sizeof(WarpSmem<CAP, STK>);
+}
+
+// SCAN: ||p|| by rows (area_scan), except that a polygon whose window holds fewer than T pixels
+// and whose edges fit the buffer is pixelized directly (PixelBox's one-leaf case, cheaper for
+// small windows). Otherwise by PixelBox on the polygon alone, deferring polygons with more than
+// defer_above vertices to k_prepare_big.
+template <int CAP, int STK, bool COUNT, bool SCAN>
 __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    char* slice = reinterpret_cast<char*>(smem4) + (size_t)warp * prep_slice<CAP, STK, SCAN>();
+    WarpSmem<CAP, STK>& S = *reinterpret_cast<WarpSmem<CAP, STK>*>(slice);
+    ScanSmem& SS = *reinterpret_cast<ScanSmem*>(slice);
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
     long long first_bad = 0x7fffffffffffffffLL;
+    unsigned long long band_bytes = 0;
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
         const long long o0 = a.off[i], o1 = a.off[i + 1];
         const long long nvl = o1 - o0;
@@ -113,7 +190,13 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
                 e = kErrRange;
         }
         uint32_t area = 0;
-        if (e == 0 && x1 > x0 && y1 > y0) {
+        const bool defer = !SCAN && e == 0 && a.defer_above > 0 && nvl > a.defer_above;
+        if (defer && lane == 0) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
+        const bool by_rows = SCAN && ((long long)(x1 - x0) * (y1 - y0) >= a.T || nvl > CAP);
+        if (by_rows && e == 0 && x1 > x0 && y1 > y0) {
+            __syncwarp();
+            area = area_scan<COUNT>(v, (int)nvl, x0, y0, x1, y1, SS, lane, wc);
+        } else if (e == 0 && !defer && x1 > x0 && y1 > y0) {
             const int nv = (int)nvl;
             const bool res = nv <= CAP;
             __syncwarp();
@@ -129,8 +212,9 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
         }
         if (lane == 0) {
             a.mbr[i] = make_int4(x0, y0, x1, y1);
-            a.area[i] = (int64_t)area;
+            if (!defer) a.area[i] = (int64_t)area;
         }
+        if (e == 0) band_bytes += (unsigned long long)band_block_size(v, (int)nvl, y0, y1, lane);
         if (e) { err |= e; first_bad = min(first_bad, i); }
         max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
         if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
@@ -141,8 +225,165 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
         atomicMax(&a.stats->max_nv, max_nv);
         atomicMax(&a.stats->max_extent, max_ext);
         atomicMax(&a.stats->n_tiles, max_tile + 1);
+        if (band_bytes) atomicAdd(&a.stats->band_bytes, band_bytes);
     }
     if (COUNT) flush_counters(a.counters, wc);
+}
+
+// Areas of the polygons k_prepare listed (more than defer_above vertices), with larger edge
+// buffers; their MBRs were written and validated by k_prepare.
+template <int CAP, int STK, bool COUNT>
+__global__ void SCCG_ITEM_BOUNDS k_prepare_big(const PrepArgs a)
+{
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long nbig = *a.big_n;
+    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + warp; j < nbig; j += nwarps) {
+        const long long i = a.big_list[j];
+        const long long o0 = a.off[i];
+        const int nv = (int)(a.off[i + 1] - o0);
+        const int2* v = reinterpret_cast<const int2*>(a.xy) + o0;
+        const int4 m = a.mbr[i];
+        uint32_t area = 0;
+        if (m.z > m.x && m.w > m.y) {
+            const bool res = nv <= CAP;
+            __syncwarp();
+            if (res) stage_edges(v, nv, 0, nv, S.ep, S.rp, lane);
+            __syncwarp();
+            const PolyPair pp{v, nv, res, v, nv, res};
+            area = pixelbox<false, COUNT>(pp, m.x, m.y, m.z, m.w, a.T, S, lane, wc);
+        }
+        if (lane == 0) a.area[i] = (int64_t)area;
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
+__global__ void k_band_sizes(long long n, const int64_t* off, const int32_t* xy, const int4* mbr, long long* size)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps) {
+        const long long o0 = off[i];
+        const int nv = (int)(off[i + 1] - o0);
+        const int4 m = mbr[i];
+        const long long s = band_block_size(reinterpret_cast<const int2*>(xy) + o0, nv, m.y, m.w, lane);
+        if (lane == 0) size[i] = s;
+    }
+}
+
+// tab[i] from the scanned block sizes; the header from one thread.
+__global__ void k_band_tab(long long n, const long long* size, const long long* boffs, char* blob, long long bytes)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long* tab = reinterpret_cast<long long*>(blob + sizeof(BandHead));
+    if (i == 0) {
+        BandHead* h = reinterpret_cast<BandHead*>(blob);
+        h->n = n;
+        h->bytes = bytes;
+        h->shift = kBandShift;
+    }
+    if (i < n) tab[i] = size[i] > 0 ? band_head_bytes(n) + boffs[i] : -1;
+}
+
+__global__ void k_band_fill(long long n, const int64_t* off, const int32_t* xy, const int4* mbr, char* blob)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long* tab = reinterpret_cast<const long long*>(blob + sizeof(BandHead));
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps) {
+        const long long at = tab[i];
+        if (at < 0) continue;                       // warp-uniform
+        const long long o0 = off[i];
+        const int nv = (int)(off[i + 1] - o0);
+        const int2* v = reinterpret_cast<const int2*>(xy) + o0;
+        const int4 m = mbr[i];
+        const int nb = ((m.w - m.y) >> kBandShift) + 1;
+        int* head = reinterpret_cast<int*>(blob + at);
+        int* boff = head + 4;
+        int* cur = boff + nb + 1;
+        int4* ent = reinterpret_cast<int4*>(blob + at + 16 + ((4LL * (2 * nb + 1) + 15) & ~15LL));
+        if (lane == 0) head[0] = nb;
+        for (int b = lane; b <= nb; b += 32) boff[b] = 0;
+        __syncwarp();
+        for (int base = 0; base < nv; base += 32) {
+            const int e = base + lane;
+            if (e < nv) {
+                const int f = (e + 1 == nv) ? 0 : e + 1;
+                const int ya = v[e].y, yb = v[f].y;
+                const int b0 = (min(ya, yb) - m.y) >> kBandShift, b1 = (max(ya, yb) - m.y) >> kBandShift;
+                for (int b = b0; b <= b1; ++b) atomicAdd(&boff[b], 1);
+            }
+        }
+        __syncwarp();
+        int carry = 0;
+        for (int base = 0; base <= nb; base += 32) {       // exclusive scan, 32 bands at a time
+            const int b = base + lane;
+            const int c = b <= nb ? boff[b] : 0;
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (b <= nb) boff[b] = carry + incl - c;
+            if (b < nb) cur[b] = 0;
+            carry += __shfl_sync(kFull, incl, 31);
+        }
+        __syncwarp();
+        for (int base = 0; base < nv; base += 32) {
+            const int e = base + lane;
+            if (e < nv) {
+                const int f = (e + 1 == nv) ? 0 : e + 1;
+                int2 a = v[e];
+                int2 b = v[f];
+                if (b.y < a.y) { const int2 t = a; a = b; b = t; }
+                const int4 rec = make_int4(a.y, b.y - a.y, b.x - a.x, a.x);
+                const int b0 = (a.y - m.y) >> kBandShift, b1 = (b.y - m.y) >> kBandShift;
+                for (int bb = b0; bb <= b1; ++bb) ent[boff[bb] + atomicAdd(&cur[bb], 1)] = rec;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// The records of polygon block `blk` (polygon min y `miny`) that stage_culled would keep for the
+// window [x0, x1) x [y0, y1), read from the bands covering rows y0 .. y1 - 1 only. An edge listed
+// in several of those bands is taken from the first of them. Same return convention as
+// stage_culled. Whole warp, converged.
+__device__ __forceinline__ int stage_banded(const char* blk, int miny, int x0, int y0, int x1, int y1, int4* E,
+                                            float* R, int cap, int lane)
+{
+    const int* head = reinterpret_cast<const int*>(blk);
+    const int nb = head[0];
+    const int* boff = head + 4;
+    const int4* ent = reinterpret_cast<const int4*>(blk + 16 + ((4LL * (2 * nb + 1) + 15) & ~15LL));
+    const int b0 = min(max((y0 - miny) >> kBandShift, 0), nb - 1);
+    const int b1 = min(max((y1 - 1 - miny) >> kBandShift, 0), nb - 1);
+    int cnt = 0;
+    for (int b = b0; b <= b1; ++b) {
+        const int e0 = boff[b], e1 = boff[b + 1];
+        for (int base = e0; base < e1; base += 32) {
+            const int k = base + lane;
+            bool keep = false;
+            int4 rec = make_int4(0, 0, 0, 0);
+            if (k < e1) {
+                rec = ent[k];
+                const int first = max(b0, (rec.x - miny) >> kBandShift);
+                keep = (first == b) & (rec.x < y1) & (rec.x + rec.y > y0) & (max(rec.w, rec.w + rec.z) > x0);
+            }
+            const unsigned msk = __ballot_sync(kFull, keep);
+            const int pos = cnt + __popc(msk & ((1u << lane) - 1u));
+            if (keep && pos < cap) {
+                E[pos] = rec;
+                R[pos] = rec.y > 0 ? __frcp_rn((float)(2 * rec.y)) : 0.0f;
+            }
+            cnt += __popc(msk);
+        }
+    }
+    return cnt;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -482,7 +723,34 @@ struct AreasArgs {
     int64_t* uni;
     int T;
     WorkCounters* counters;
+    const char* bandsA;     // band index blobs (nullptr = none)
+    const char* bandsB;
 };
+
+// Block of polygon i in a band index blob (nullptr: no blob, or no block for this polygon).
+__device__ __forceinline__ const char* band_block(const char* blob, long long i)
+{
+    if (!blob) return nullptr;
+    const long long at = reinterpret_cast<const long long*>(blob + sizeof(BandHead))[i];
+    return at < 0 ? nullptr : blob + at;
+}
+
+// Stage both polygons of a pair for the window [x0, x1) x [y0, y1): each keeps only the edges
+// that can matter there (from its band block bp / bq when it has one, else from its ring) and is
+// resident when those fit the buffer; otherwise it is read chunk by chunk from its whole ring.
+template <int CAP, int STK>
+__device__ __forceinline__ void stage_pair(PolyPair& pp, const char* bp, int minyp, const char* bq, int minyq,
+                                           int x0, int y0, int x1, int y1, WarpSmem<CAP, STK>& S, int lane)
+{
+    const int cp = bp ? stage_banded(bp, minyp, x0, y0, x1, y1, S.ep, S.rp, CAP, lane)
+                      : stage_culled(pp.vp, pp.np, x0, y0, x1, y1, S.ep, S.rp, CAP, lane);
+    const int cq = bq ? stage_banded(bq, minyq, x0, y0, x1, y1, S.eq, S.rq, CAP, lane)
+                      : stage_culled(pp.vq, pp.nq, x0, y0, x1, y1, S.eq, S.rq, CAP, lane);
+    pp.rp_res = cp <= CAP;
+    pp.rq_res = cq <= CAP;
+    if (pp.rp_res) pp.np = cp;
+    if (pp.rq_res) pp.nq = cq;
+}
 
 template <int CAP, int STK, bool COUNT>
 __global__ void SCCG_ITEM_BOUNDS k_pair_areas_plain(const AreasArgs a)
@@ -491,7 +759,7 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_plain(const AreasArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
         const int ia = a.pa[i], ib = a.pb[i];
         int64_t out_i = -1, out_u = -1;      // invalid pair: flagged, not read
@@ -506,11 +774,10 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_plain(const AreasArgs a)
                 PolyPair pp;
                 pp.vp = reinterpret_cast<const int2*>(a.xyA) + pa0; pp.np = (int)(pa1 - pa0);
                 pp.vq = reinterpret_cast<const int2*>(a.xyB) + qb0; pp.nq = (int)(qb1 - qb0);
-                pp.rp_res = pp.np <= CAP;
-                pp.rq_res = pp.nq <= CAP;
                 __syncwarp();
-                if (pp.rp_res) stage_edges(pp.vp, pp.np, 0, pp.np, S.ep, S.rp, lane);
-                if (pp.rq_res) stage_edges(pp.vq, pp.nq, 0, pp.nq, S.eq, S.rq, lane);
+                const char* bp = band_block(a.bandsA, ia);
+                const char* bq = band_block(a.bandsB, ib);
+                stage_pair(pp, bp, ma.y, bq, mb.y, wx0, wy0, wx1, wy1, S, lane);
                 __syncwarp();
                 inter = pixelbox<true, COUNT>(pp, wx0, wy0, wx1, wy1, a.T, S, lane, wc);
             }
@@ -542,12 +809,13 @@ __device__ __forceinline__ bool pair_window(const AreasArgs& a, long long i, int
 }
 
 // One thread per pair: number of work items; pairs without items get their final values here.
-__global__ void k_plan(const AreasArgs a, int side, long long* nitems)
+__global__ void k_plan(const AreasArgs a, int side, int cap_small, long long* nitems_s, long long* nitems_b)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int ia, ib, wx0, wy0, wx1, wy1;
     long long k = 0;
+    bool big = false;
     if (!pair_window(a, i, ia, ib, wx0, wy0, wx1, wy1)) {
         a.inter[i] = -1;
         a.uni[i] = -1;
@@ -557,15 +825,17 @@ __global__ void k_plan(const AreasArgs a, int side, long long* nitems)
     } else {
         k = (long long)((wx1 - wx0 + side - 1) / side) * ((wy1 - wy0 + side - 1) / side);
         if (k > 1) a.inter[i] = 0;     // accumulated by atomics
+        big = a.offA[ia + 1] - a.offA[ia] > cap_small || a.offB[ib + 1] - a.offB[ib] > cap_small;
     }
-    nitems[i] = k;
+    nitems_s[i] = big ? 0 : k;
+    nitems_b[i] = big ? k : 0;
 }
 
 // Pairs cut into several items: union from the accumulated intersection.
-__global__ void k_union(const AreasArgs a, const long long* nitems)
+__global__ void k_union(const AreasArgs a, const long long* nitems_s, const long long* nitems_b)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n || nitems[i] <= 1) return;
+    if (i >= a.n || nitems_s[i] + nitems_b[i] <= 1) return;
     a.uni[i] = a.areaA[a.pa[i]] + a.areaB[a.pb[i]] - a.inter[i];
 }
 
@@ -596,7 +866,7 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int 
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
-    WorkCounters wc = {0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
     const long long total = ioff[a.n];
     for (;;) {
         unsigned long long first = 0;
@@ -606,7 +876,10 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int 
         const long long last = min((long long)first + kItemChunk, total);
         long long i = find_pair(ioff, a.n, (long long)first, lane);
         for (long long it = (long long)first; it < last; ++it) {
-            while (ioff[i + 1] <= it) ++i;            // warp-uniform walk to the item's pair
+            if (ioff[i + 1] <= it) {                  // warp-uniform: next pair, else search again
+                ++i;
+                if (ioff[i + 1] <= it) i = find_pair(ioff, a.n, it, lane);
+            }
             const long long sub = it - ioff[i];
             int ia, ib, wx0, wy0, wx1, wy1;
             pair_window(a, i, ia, ib, wx0, wy0, wx1, wy1);
@@ -619,11 +892,10 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int 
             PolyPair pp;
             pp.vp = reinterpret_cast<const int2*>(a.xyA) + pa0; pp.np = (int)(pa1 - pa0);
             pp.vq = reinterpret_cast<const int2*>(a.xyB) + qb0; pp.nq = (int)(qb1 - qb0);
-            pp.rp_res = pp.np <= CAP;
-            pp.rq_res = pp.nq <= CAP;
             __syncwarp();
-            if (pp.rp_res) stage_edges(pp.vp, pp.np, 0, pp.np, S.ep, S.rp, lane);
-            if (pp.rq_res) stage_edges(pp.vq, pp.nq, 0, pp.nq, S.eq, S.rq, lane);
+            const char* bp = band_block(a.bandsA, ia);
+            const char* bq = band_block(a.bandsB, ib);
+            stage_pair(pp, bp, a.mbrA[ia].y, bq, a.mbrB[ib].y, x0, y0, x1, y1, S, lane);
             __syncwarp();
             const uint32_t cnt = pixelbox<true, COUNT>(pp, x0, y0, x1, y1, a.T, S, lane, wc);
             if (lane == 0) {

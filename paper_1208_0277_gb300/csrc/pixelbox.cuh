@@ -29,6 +29,8 @@ struct WorkCounters {          // algorithmic work, accumulated only by the coun
     unsigned long long boxes;         // sampling boxes classified (per polygon)
     unsigned long long row_entries;   // (edge, row) entries of the per-row edge lists built
     unsigned long long row_edges;     // (32-pixel row strip, listed straddling edge) evaluations
+    unsigned long long scan_entries;  // (edge, row) crossing values of the by-rows area
+    unsigned long long scan_pairs;    // crossing-value comparisons ranking them
 };
 
 __device__ __forceinline__ int warp_min(int v)
@@ -69,6 +71,44 @@ __device__ __forceinline__ void stage_edges(const int2* v, int nv, int e0, int c
             R[i] = dy > 0 ? __frcp_rn((float)(2 * dy)) : 0.0f;
         }
     }
+}
+
+// Stage, from the ring v[0..nv), only the edges that can affect a pixel of the window
+// [x0, x1) x [y0, y1): those with ylo < y1, yhi > y0 and max x > x0. Any other edge lies wholly on
+// or below the line y = y0, on or above y = y1, or on or left of x = x0, while every pixel centre
+// of the window, and every centre rectangle R of a box inside it, lies strictly inside those three
+// lines: such an edge straddles no row of the window, is never right of a centre in it and meets
+// no R. Dropping it changes no crossing parity and no box position, so every count over the
+// window is unchanged. Returns the number of kept edges (warp-uniform); only the first `cap` are
+// stored, so a return value above `cap` means the caller must use the whole ring instead.
+__device__ __forceinline__ int stage_culled(const int2* v, int nv, int x0, int y0, int x1, int y1, int4* E,
+                                            float* R, int cap, int lane)
+{
+    int cnt = 0;
+    for (int base = 0; base < nv; base += 32) {
+        const int e = base + lane;
+        bool keep = false;
+        int4 rec = make_int4(0, 0, 0, 0);
+        float rc = 0.0f;
+        if (e < nv) {
+            const int f = (e + 1 == nv) ? 0 : e + 1;
+            int2 a = v[e];
+            int2 b = v[f];
+            if (b.y < a.y) { const int2 t = a; a = b; b = t; }
+            const int dy = b.y - a.y;
+            keep = (a.y < y1) & (b.y > y0) & (max(a.x, b.x) > x0);
+            rec = make_int4(a.y, dy, b.x - a.x, a.x);
+            rc = dy > 0 ? __frcp_rn((float)(2 * dy)) : 0.0f;
+        }
+        const unsigned m = __ballot_sync(kFull, keep);
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        if (keep && pos < cap) {
+            E[pos] = rec;
+            R[pos] = rc;
+        }
+        cnt += __popc(m);
+    }
+    return cnt;
 }
 
 // Parity bitmask of the 32 pixels (x0 + k, y), k = 0..31, against `cnt` staged edges.

@@ -40,7 +40,7 @@ struct sccg_ctx {
     // sccg_batch_run: the captured graph and the arguments it was captured for
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t batch_exec = nullptr;
-    const void* batch_key[9] = {};
+    const void* batch_key[11] = {};
     long long batch_n = -1;
     sccg_params batch_params{};
     int batch_count_work = 0;
@@ -151,7 +151,15 @@ struct Carve {
 template <class T>
 size_t carve_size(size_t count) { return ((count * sizeof(T) + 255) & ~size_t(255)) + 256; }
 
-int edge_cap_for(int max_nv) { return max_nv <= 32 ? 32 : (max_nv <= 64 ? 64 : 128); }
+constexpr int kCapSmall = 64;     // edge buffer of the one-warp-per-item kernels (4 warps per CTA)
+constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices (2 warps per CTA)
+
+int edge_cap_for(int max_nv) { return max_nv <= kCapSmall ? kCapSmall : kCapBig; }
+int warps_for(const sccg_ctx* ctx, int cap)
+{
+    const int w = std::max(1, std::min(8, ctx->params.warps_per_cta));
+    return cap > kCapSmall ? std::min(w, 2) : w;
+}
 
 template <int CAP>
 size_t warp_smem() { return sizeof(WarpSmem<CAP, kStack>); }
@@ -173,22 +181,31 @@ long long grid_for(const sccg_ctx* ctx, long long items, int per_block, int max_
     return g;
 }
 
-template <int CAP>
+template <int CAP, bool SCAN>
 int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
 {
-    const int wpc = std::max(1, std::min(8, ctx->params.warps_per_cta));
-    const size_t smem = warp_smem<CAP>() * wpc;
+    const int wpc = warps_for(ctx, CAP);
+    const size_t smem = prep_slice<CAP, kStack, SCAN>() * wpc;
     const long long grid = grid_for(ctx, a.n, wpc, 64);
-    if (ctx->count_work) {
-        int r = set_smem(ctx, k_prepare<CAP, kStack, true>, smem);
-        if (r) return r;
-        k_prepare<CAP, kStack, true><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
-    } else {
-        int r = set_smem(ctx, k_prepare<CAP, kStack, false>, smem);
-        if (r) return r;
-        k_prepare<CAP, kStack, false><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
-    }
+    auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN> : k_prepare<CAP, kStack, false, SCAN>;
+    int r = set_smem(ctx, kfn, smem);
+    if (r) return r;
+    kfn<<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
     SCCG_LAUNCHED(ctx, "k_prepare");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+template <int CAP>
+int launch_prepare_big(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
+{
+    const int wpc = warps_for(ctx, CAP);
+    const size_t smem = warp_smem<CAP>() * wpc;
+    auto kfn = ctx->count_work ? k_prepare_big<CAP, kStack, true> : k_prepare_big<CAP, kStack, false>;
+    int r = set_smem(ctx, kfn, smem);
+    if (r) return r;
+    kfn<<<(unsigned)(2 * ctx->sm_count), 32 * wpc, smem, st>>>(a);
+    SCCG_LAUNCHED(ctx, "k_prepare_big");
     ctx->launches += 1;
     return SCCG_OK;
 }
@@ -196,7 +213,7 @@ int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
 template <int CAP>
 int launch_plain(sccg_ctx* ctx, const AreasArgs& a, cudaStream_t st)
 {
-    const int wpc = std::max(1, std::min(8, ctx->params.warps_per_cta));
+    const int wpc = warps_for(ctx, CAP);
     const size_t smem = warp_smem<CAP>() * wpc;
     const long long grid = grid_for(ctx, a.n, wpc, 64);
     if (ctx->count_work) {
@@ -217,7 +234,7 @@ template <int CAP>
 int launch_persistent(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
                       unsigned long long* head, cudaStream_t st)
 {
-    const int wpc = std::max(1, std::min(8, ctx->params.warps_per_cta));
+    const int wpc = warps_for(ctx, CAP);
     const size_t smem = warp_smem<CAP>() * wpc;
     auto kfn = ctx->count_work ? k_pair_areas_persistent<CAP, kStack, true> : k_pair_areas_persistent<CAP, kStack, false>;
     int r = set_smem(ctx, kfn, smem);
@@ -261,7 +278,7 @@ int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* 
 size_t persistent_scratch(long long n_pairs)
 {
     const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
-    return carve_size<long long>(n_pairs + 1) * 2 + carve_size<long long>(nb) + carve_size<unsigned long long>(1);
+    return carve_size<long long>(n_pairs + 1) * 4 + carve_size<long long>(nb) + carve_size<unsigned long long>(2);
 }
 
 int split_side(const sccg_ctx* ctx)
@@ -278,24 +295,25 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     const int side = split_side(ctx);
     const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
     Carve cv(ctx->ws);
-    long long* nitems = cv.take<long long>(n_pairs + 1);
-    long long* ioff = cv.take<long long>(n_pairs + 1);
+    long long* nitems_s = cv.take<long long>(n_pairs + 1);
+    long long* nitems_b = cv.take<long long>(n_pairs + 1);
+    long long* ioff_s = cv.take<long long>(n_pairs + 1);
+    long long* ioff_b = cv.take<long long>(n_pairs + 1);
     long long* bsum = cv.take<long long>(nb);
-    unsigned long long* head = cv.take<unsigned long long>(1);
+    unsigned long long* head = cv.take<unsigned long long>(2);
     const unsigned g = (unsigned)((n_pairs + 255) / 256);
-    k_plan<<<g, 256, 0, st>>>(a, side, nitems);
+    // pairs whose polygons all fit the small edge buffers go to one queue, the rest to another
+    k_plan<<<g, 256, 0, st>>>(a, side, kCapSmall, nitems_s, nitems_b);
     SCCG_LAUNCHED(ctx, "k_plan");
     ctx->launches += 1;
-    int r = device_scan(ctx, nitems, n_pairs, ioff, bsum, st);
+    int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
+    if (!r && cap > kCapSmall) r = device_scan(ctx, nitems_b, n_pairs, ioff_b, bsum, st);
     if (r) return r;
-    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, sizeof(unsigned long long), st));
-    switch (cap) {
-        case 32: r = launch_persistent<32>(ctx, a, side, nitems, ioff, head, st); break;
-        case 64: r = launch_persistent<64>(ctx, a, side, nitems, ioff, head, st); break;
-        default: r = launch_persistent<128>(ctx, a, side, nitems, ioff, head, st); break;
-    }
+    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, 2 * sizeof(unsigned long long), st));
+    r = launch_persistent<kCapSmall>(ctx, a, side, nitems_s, ioff_s, head, st);
+    if (!r && cap > kCapSmall) r = launch_persistent<kCapBig>(ctx, a, side, nitems_b, ioff_b, head + 1, st);
     if (r) return r;
-    k_union<<<g, 256, 0, st>>>(a, nitems);
+    k_union<<<g, 256, 0, st>>>(a, nitems_s, nitems_b);
     SCCG_LAUNCHED(ctx, "k_union");
     ctx->launches += 1;
     return SCCG_OK;
@@ -328,9 +346,9 @@ int jaccard_launch(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, long
 int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
-    static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm"};
-    int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm};
-    for (int k = 0; k < 4; ++k) {
+    static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method"};
+    int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm, &p->area_method};
+    for (int k = 0; k < 5; ++k) {
         char key[64];
         snprintf(key, sizeof key, "\"%s\"", names[k]);
         const char* at = strstr(js, key);
@@ -351,6 +369,7 @@ int validate_params(const sccg_params& p)
     if (p.warps_per_cta < 1 || p.warps_per_cta > 8) return SCCG_EINVAL;
     if (p.split_pixels < 32) return SCCG_EINVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return SCCG_EINVAL;
+    if (p.area_method != SCCG_AREA_ROWS && p.area_method != SCCG_AREA_PIXELBOX) return SCCG_EINVAL;
     return SCCG_OK;
 }
 
@@ -470,10 +489,11 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     sccg_ctx* ctx = new (std::nothrow) sccg_ctx();
     if (!ctx) return SCCG_ENOMEM;
     ctx->device = device;
-    ctx->params.T = 4096;
+    ctx->params.T = 8192;
     ctx->params.warps_per_cta = 4;
     ctx->params.split_pixels = 4096;
     ctx->params.ctas_per_sm = 0;
+    ctx->params.area_method = SCCG_AREA_ROWS;
     int r = parse_params(params_json, &ctx->params);
     if (!r) r = validate_params(ctx->params);
     if (r) { delete ctx; return r; }
@@ -523,6 +543,7 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     else if (!strcmp(name, "warps_per_cta")) p.warps_per_cta = (int32_t)value;
     else if (!strcmp(name, "split_pixels")) p.split_pixels = (int32_t)value;
     else if (!strcmp(name, "ctas_per_sm")) p.ctas_per_sm = (int32_t)value;
+    else if (!strcmp(name, "area_method")) p.area_method = (int32_t)value;
     else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
     else return SCCG_EINVAL;
     const int r = validate_params(p);
@@ -540,14 +561,14 @@ int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out)
 
 const char* sccg_last_error(const sccg_ctx* ctx) { return ctx ? ctx->last_err : ""; }
 
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out6, int reset)
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out8, int reset)
 {
-    if (!ctx || !out6) return SCCG_EINVAL;
+    if (!ctx || !out8) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     WorkCounters h;
     SCCG_CUDA(ctx, cudaMemcpy(&h, ctx->counters, sizeof h, cudaMemcpyDeviceToHost));
-    out6[0] = h.strip_edges; out6[1] = h.pixel_edges; out6[2] = h.box_edges; out6[3] = h.boxes;
-    out6[4] = h.row_entries; out6[5] = h.row_edges;
+    out8[0] = h.strip_edges; out8[1] = h.pixel_edges; out8[2] = h.box_edges; out8[3] = h.boxes;
+    out8[4] = h.row_entries; out8[5] = h.row_edges; out8[6] = h.scan_entries; out8[7] = h.scan_pairs;
     if (reset) SCCG_CUDA(ctx, cudaMemset(ctx->counters, 0, sizeof(WorkCounters)));
     return SCCG_OK;
 }
@@ -562,20 +583,30 @@ int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
     if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
     if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
     if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
-    int r = ws_reserve(ctx, carve_size<PrepStats>(1));
+    int r = ws_reserve(ctx, carve_size<PrepStats>(1) + carve_size<int>(s->n + 1) + carve_size<unsigned>(1));
     if (r) return r;
     Carve cv(ctx->ws);
     PrepStats* stats = cv.take<PrepStats>(1);
-    PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL};
+    int* big_list = cv.take<int>(s->n + 1);
+    unsigned* big_n = cv.take<unsigned>(1);
+    PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0};
     // the initial stats are written by a copy from pinned memory, kept ordered on the stream
     PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
     *hstats = init;
     SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, sizeof init, cudaMemcpyHostToDevice, st));
-    if (s->n > 0) {
+    if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
         PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats,
-                   ctx->params.T, ctx->counters};
-        // the largest vertex count is not known yet: use the chunked 64-edge buffers
-        r = launch_prepare<64>(ctx, a, st);
+                   ctx->params.T, ctx->counters, 0, big_list, big_n};
+        r = launch_prepare<kCapSmall, true>(ctx, a, st);
+        if (r) return r;
+    } else if (s->n > 0) {
+        SCCG_CUDA(ctx, cudaMemsetAsync(big_n, 0, sizeof(unsigned), st));
+        PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats,
+                   ctx->params.T, ctx->counters, kCapSmall, big_list, big_n};
+        // polygons with more than kCapSmall vertices are listed and done with the larger buffers
+        r = launch_prepare<kCapSmall, false>(ctx, a, st);
+        if (r) return r;
+        r = launch_prepare_big<kCapBig>(ctx, a, st);
         if (r) return r;
     }
     SCCG_CUDA(ctx, cudaMemcpyAsync(hstats, stats, sizeof init, cudaMemcpyDeviceToHost, st));
@@ -584,6 +615,8 @@ int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
     s->max_nv = res.max_nv;
     s->max_extent = res.max_extent;
     s->n_tiles = std::max(res.n_tiles, s->n > 0 ? 1 : 0);
+    s->band_bytes = res.band_bytes ? band_head_bytes(s->n) + (long long)res.band_bytes : 0;
+    s->bands = nullptr;
     if (res.err & (kErrFewVertices | kErrTiles)) {
         snprintf(ctx->last_err, sizeof ctx->last_err, "invalid polygon set (flags %d, first bad polygon %lld)",
                  res.err, res.first_bad);
@@ -595,6 +628,41 @@ int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
         return SCCG_ERANGE;
     }
     s->reserved = (int32_t)kPreparedMagic;
+    return SCCG_OK;
+}
+
+int sccg_build_bands(sccg_ctx* ctx, sccg_polyset* s, void* buf, int64_t bytes, void* stream)
+{
+    if (!ctx || check_prepared(s)) return SCCG_EINVAL;
+    if (s->band_bytes == 0) {
+        s->bands = nullptr;
+        return SCCG_OK;
+    }
+    if (bytes < s->band_bytes) return SCCG_ECAPACITY;
+    if (!buf || !is_device_ptr(buf) || reinterpret_cast<uintptr_t>(buf) % 16) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long n = s->n;
+    const long long nb = (n + kScanBlock - 1) / kScanBlock + 1;
+    int r = ws_reserve(ctx, carve_size<long long>(n + 1) * 2 + carve_size<long long>(nb));
+    if (r) return r;
+    Carve cv(ctx->ws);
+    long long* size = cv.take<long long>(n + 1);
+    long long* boffs = cv.take<long long>(n + 1);
+    long long* bsum = cv.take<long long>(nb);
+    const int4* mbr = reinterpret_cast<const int4*>(s->mbr);
+    char* blob = static_cast<char*>(buf);
+    const unsigned gw = (unsigned)grid_for(ctx, n, 8, 16);      // 8 warps per CTA, one polygon per warp
+    k_band_sizes<<<gw, 256, 0, st>>>(n, s->off, s->xy, mbr, size);
+    SCCG_LAUNCHED(ctx, "k_band_sizes");
+    r = device_scan(ctx, size, n, boffs, bsum, st);
+    if (r) return r;
+    k_band_tab<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, size, boffs, blob, s->band_bytes);
+    SCCG_LAUNCHED(ctx, "k_band_tab");
+    k_band_fill<<<gw, 256, 0, st>>>(n, s->off, s->xy, mbr, blob);
+    SCCG_LAUNCHED(ctx, "k_band_fill");
+    ctx->launches += 3;
+    s->bands = buf;
     return SCCG_OK;
 }
 
@@ -723,18 +791,15 @@ int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
     AreasArgs a{n_pairs, A->n, B->n, pa, pb,
                 A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
                 B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
-                inter, uni, ctx->params.T, ctx->counters};
+                inter, uni, ctx->params.T, ctx->counters,
+                static_cast<const char*>(A->bands), static_cast<const char*>(B->bands)};
     const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
     if (mode == SCCG_MODE_PERSISTENT) {
         const int r = ws_reserve(ctx, persistent_scratch(n_pairs));
         if (r) return r;
         return persistent_launch(ctx, a, cap, st);
     }
-    switch (cap) {
-        case 32: return launch_plain<32>(ctx, a, st);
-        case 64: return launch_plain<64>(ctx, a, st);
-        default: return launch_plain<128>(ctx, a, st);
-    }
+    return cap == kCapSmall ? launch_plain<kCapSmall>(ctx, a, st) : launch_plain<kCapBig>(ctx, a, st);
 }
 
 int sccg_pair_areas_tiles(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa,
@@ -771,13 +836,11 @@ int sccg_pair_areas_tiles(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polys
         AreasArgs a{p1 - p0, A->n, B->n, pa + p0, pb + p0,
                     A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
                     B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
-                    inter + p0, uni + p0, ctx->params.T, ctx->counters};
+                    inter + p0, uni + p0, ctx->params.T, ctx->counters,
+                    static_cast<const char*>(A->bands), static_cast<const char*>(B->bands)};
         int r;
-        switch (cap) {
-            case 32: r = launch_plain<32>(ctx, a, ctx->tstream[k]); break;
-            case 64: r = launch_plain<64>(ctx, a, ctx->tstream[k]); break;
-            default: r = launch_plain<128>(ctx, a, ctx->tstream[k]); break;
-        }
+        r = cap == kCapSmall ? launch_plain<kCapSmall>(ctx, a, ctx->tstream[k])
+                             : launch_plain<kCapBig>(ctx, a, ctx->tstream[k]);
         if (r) return r;
         k = (k + 1) % sccg_ctx::kTileStreams;
     }
@@ -802,7 +865,7 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int r = ws_reserve(ctx, std::max(persistent_scratch(std::max<long long>(n_pairs, 1)), jaccard_scratch(ctx, n_pairs)));
     if (r) return r;
-    const void* key[9] = {A->off, A->xy, A->mbr, B->off, B->xy, B->mbr, pa, inter, out};
+    const void* key[11] = {A->off, A->xy, A->mbr, A->bands, B->off, B->xy, B->mbr, B->bands, pa, inter, out};
     const bool same = ctx->batch_exec && ctx->batch_n == n_pairs && !memcmp(key, ctx->batch_key, sizeof key) &&
                       !memcmp(&ctx->batch_params, &ctx->params, sizeof(sccg_params)) &&
                       ctx->batch_count_work == ctx->count_work && ctx->batch_key[0] != nullptr;
@@ -815,7 +878,8 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
         AreasArgs a{n_pairs, A->n, B->n, pa, pb,
                     A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
                     B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
-                    inter, uni, ctx->params.T, ctx->counters};
+                    inter, uni, ctx->params.T, ctx->counters,
+                static_cast<const char*>(A->bands), static_cast<const char*>(B->bands)};
         const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
         const unsigned long long launches0 = ctx->launches;
         SCCG_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -841,7 +905,8 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
         ctx->batch_count_work = ctx->count_work;
     }
     SCCG_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, st));
-    ctx->launches += n_pairs > 0 ? 8 : 2;    // plan, 3 scan passes, persistent, union, 2 Jaccard
+    // plan, 3 scan passes and one persistent launch per queue, union, 2 Jaccard
+    ctx->launches += n_pairs > 0 ? (edge_cap_for(std::max(A->max_nv, B->max_nv)) > kCapSmall ? 12 : 8) : 2;
     return SCCG_OK;
 }
 

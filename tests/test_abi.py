@@ -41,10 +41,31 @@ def test_status_strings(lib):
     assert f(99) == b"unknown status"
 
 
-def test_struct_sizes_match_header():
-    assert ctypes.sizeof(_native.PolySetC) == 8 * 6 + 4 * 4
-    assert ctypes.sizeof(_native.JaccardC) == 48
-    assert ctypes.sizeof(_native.ParamsC) == 16
+def test_struct_sizes_match_header(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler gives the header's structs."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"sccg_polyset": _native.PolySetC, "sccg_params": _native.ParamsC,
+               "sccg_jaccard_result": _native.JaccardC}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sccg.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
 
 
 def test_ctx_create_without_gpu_reports_not_supported(lib):

@@ -168,6 +168,33 @@ def test_heavy_tail_tissue_and_nuclei(sccg, mode):
     np.testing.assert_array_equal(g["uni"][idx], bu)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_band_index_gives_the_same_results(sccg, mode):
+    """Polygons with >= 1024 vertices get a band index; items then stage only their bands' edges.
+    Concave tissue rings and rectilinear staircases (horizontal edges on band boundaries) against
+    nuclei, with small work items in the persistent form so item windows start at many offsets
+    relative to the bands: identical to the run without the index and to the oracle."""
+    w = W.heavy_tail(seed=3, n_tiles=1, nuclei_per_tile=800, tissue_lo=3, tissue_hi=3, tissue_nv_lo=1024,
+                     tissue_nv_hi=3000, tissue_s_lo=200.0, tissue_s_hi=600.0)
+    rng = np.random.Generator(np.random.PCG64(21))
+    stairs, _ = W.staircase_rings(rng, 4, max_cols=700, max_h=60, origin_span=300)
+    small, _ = W.staircase_rings(rng, 300, max_cols=12, max_h=15, origin_span=600)
+    ws = rings_workload([np.asarray(r) for r in stairs] + [np.asarray(r) for r in small],
+                        [np.asarray(r) for r in small] + [np.asarray(r) for r in stairs])
+    c = sccg.Context(0, {"split_pixels": 400, "T": 64})
+    for wk in (w, ws):
+        with_bands = gpu_run(c, wk, mode=mode)
+        A, B = c.upload(wk.A, bands=False), c.upload(wk.B, bands=False)
+        assert A.bands is None
+        import paper_1208_0277_gb300 as P
+        r = P.cross_compare(c, A, B, mode=mode)
+        np.testing.assert_array_equal(with_bands["inter"], r["inter"].cpu().numpy())
+        np.testing.assert_array_equal(with_bands["uni"], r["uni"].cpu().numpy())
+        ref = O.cross_compare(wk.A, wk.B, method="rle")
+        assert_same(with_bands, ref)
+    assert c.upload(w.A).bands is not None
+
+
 def test_batch_graph_replay_and_recapture(sccg):
     """sccg_batch_run: persistent areas + Jaccard captured once as a CUDA graph and replayed; a new
     pair list (other buffers) triggers a new capture. Results equal the oracle every time."""
@@ -216,6 +243,33 @@ def test_edge_cases_ties_degenerate_selfintersecting(ctx):
     rings = [tri, tri2, tri3, diamond, collinear, thin, tall, dup, bowtie, spike, rect_stack, comb, comb_cover]
     w = rings_workload(rings, rings[::-1])
     assert_same(gpu_run(ctx, w), O.cross_compare(w.A, w.B))
+
+
+def comb_ring(teeth, h=40):
+    """A bar with `teeth` one-pixel teeth: each row through the teeth is crossed 2 * teeth times."""
+    pts = [[0, 0], [2 * teeth, 0]]
+    for k in range(teeth - 1, -1, -1):
+        pts += [[2 * k + 1, 3], [2 * k + 1, h], [2 * k, h]] + ([[2 * k, 3]] if k else [])
+    return pts
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_polygon_area_methods_match_oracle(sccg, method):
+    """||p|| by rows (default) and by PixelBox on the polygon alone, on shapes that stress each:
+    rows crossed by more edges than one pass holds (combs of 520 and 700 teeth), self-intersecting
+    random rings, concave tissue polygons, staircases and ties."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    stairs, _ = W.staircase_rings(rng, 80, max_cols=40, max_h=30)
+    selfx = [rng.integers(0, 60, size=(int(rng.integers(3, 300)), 2)).tolist() for _ in range(40)]
+    ties = [[[0, 0], [4, 2], [0, 4]], [[0, 0], [2, 2], [4, 0]], [[0, 0], [4, 4], [0, 8], [-4, 4]]]
+    rings = [comb_ring(700), comb_ring(520, 9), comb_ring(30)] + selfx + ties + [np.asarray(r).tolist() for r in stairs]
+    sets = [W.from_rings(rings), medium_polygons(12, n=40, kind="tissue"), W.single_tile(seed=5, n=400).A]
+    ctx = sccg.Context(0, {"area_method": method})
+    for P in sets:
+        d = ctx.upload(P)
+        torch.cuda.synchronize()
+        ref, _ = O.polygon_areas(P.off, P.xy, method="rle")
+        np.testing.assert_array_equal(d.area.cpu().numpy()[: P.n], ref)
 
 
 def test_rectilinear_staircases_match_shoelace(ctx):
