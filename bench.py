@@ -191,6 +191,19 @@ class ClockSampler:
 # CPU oracle (baseline and reference arm)
 # ------------------------------------------------------------------------------------------------
 
+def whole_job(ms: float, pairs: int, dist, device):
+    """Whole-job figures of a timed region under weak scaling (every rank compares its own slide):
+    the slowest rank's duration and the pairs of all ranks. dist = torch.distributed or None."""
+    if not dist:
+        return ms, pairs
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([pairs], dtype=torch.int64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(p.item())
+
+
 def oracle_sample(w, target_s: float):
     """Run the CPU oracle (brute force, all host cores) on the first tiles of the workload, growing
     the sample geometrically until one run costs at least target_s / 2 (or the whole workload is
@@ -219,7 +232,9 @@ def oracle_sample_pairs(w, target_s: float, seed: int = 7):
     import oracle as O
     from paper_1208_0277_gb300 import workload as W
     sub = W.subset_tiles(w, range(1))
-    pa, pb = O.candidate_pairs(sub.A, sub.B)
+    _, mbr_a = O.polygon_areas(sub.A.off, sub.A.xy, method="rle")
+    _, mbr_b = O.polygon_areas(sub.B.off, sub.B.xy, method="rle")
+    pa, pb = O.candidate_pairs(mbr_a, sub.A.tile, mbr_b, sub.B.tile)
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(pa))
     m = 64
@@ -445,11 +460,7 @@ def main():
             sampler.mark("t_end")
         clocks = sampler.stop() if sampler else None
         launches = ctx.launch_count() - launches0
-        ms = start.elapsed_time(end)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms, _ = whole_job(start.elapsed_time(end), n_pairs, dist, dev)
         ph = np.array([[p[k].elapsed_time(p[k + 1]) for k in range(4)] for p in phases])
         results[form] = dict(ms=ms, J=J, launches=launches, clocks=clocks,
                              phases_ms=dict(zip(["prepare", "candidate_pairs", "pair_areas", "jaccard"],
@@ -457,7 +468,7 @@ def main():
 
     main_r = results[args.form]
     ms_per_step = main_r["ms"] / args.steps
-    total_pairs = n_pairs * world
+    _, total_pairs = whole_job(0.0, n_pairs, dist, dev)       # every rank compares its own slide
     value = total_pairs * args.steps / (main_r["ms"] / 1e3)
 
     # roofline of the dominant kernel (average over the timed steps, CUDA events on its stream)
@@ -512,11 +523,7 @@ def main():
             e2e_step()
         s1.record(stream)
         torch.cuda.synchronize()
-        e_ms = s0.elapsed_time(s1)
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms, _ = whole_job(s0.elapsed_time(s1), n_pairs, dist, dev)
         e2e = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / n_e2e}
 

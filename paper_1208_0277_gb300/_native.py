@@ -17,7 +17,7 @@ INCLUDE = os.path.join(_ROOT, "include")
 BUILD_DIR = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsccg.so")
 SOURCES = ["sccg_api.cu"]
-HEADERS = ["pixelbox.cuh", "kernels.cuh"]
+HEADERS = ["pixelbox.cuh", "scanline.cuh", "kernels.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 # Every symbol include/sccg.h declares (checked by the CPU test suite).

@@ -858,10 +858,58 @@ __device__ __forceinline__ long long find_pair(const long long* ioff, long long 
 
 constexpr int kItemChunk = 4;
 
-template <int CAP, int STK, bool COUNT>
+// One work item: sub-window `sub` of pair i's window, cut into side x side items. With OVF, an item
+// whose window-culled edges do not fit the buffers is appended to the overflow list (for a kernel
+// with larger buffers) instead of being read chunk by chunk from the whole rings; when the list is
+// full the item is done here anyway. Whole warp, converged.
+template <int CAP, int STK, bool COUNT, bool OVF>
+__device__ __forceinline__ void do_item(const AreasArgs a, int side, const long long* nitems, long long i, long long it,
+                                        long long sub, long long* ovf_list, unsigned long long* ovf_n,
+                                        long long ovf_cap, WarpSmem<CAP, STK>& S, int lane, WorkCounters& wc)
+{
+    const int ia = a.pa[i], ib = a.pb[i];
+    const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
+    const int wx0 = max(ma.x, mb.x), wy0 = max(ma.y, mb.y);
+    const int wx1 = min(ma.z, mb.z), wy1 = min(ma.w, mb.w);
+    const int gx = (wx1 - wx0 + side - 1) / side;
+    const int sx = (int)(sub % gx), sy = (int)(sub / gx);
+    const int x0 = wx0 + sx * side, y0 = wy0 + sy * side;
+    const int x1 = min(x0 + side, wx1), y1 = min(y0 + side, wy1);
+    const long long pa0 = a.offA[ia], pa1 = a.offA[ia + 1];
+    const long long qb0 = a.offB[ib], qb1 = a.offB[ib + 1];
+    PolyPair pp;
+    pp.vp = reinterpret_cast<const int2*>(a.xyA) + pa0; pp.np = (int)(pa1 - pa0);
+    pp.vq = reinterpret_cast<const int2*>(a.xyB) + qb0; pp.nq = (int)(qb1 - qb0);
+    __syncwarp();
+    stage_pair(pp, band_block(a.bandsA, ia), ma.y, band_block(a.bandsB, ib), mb.y, x0, y0, x1, y1, S, lane);
+    __syncwarp();
+    if (OVF && !(pp.rp_res && pp.rq_res)) {
+        unsigned long long slot = 0;
+        if (lane == 0) slot = atomicAdd(ovf_n, 1ull);
+        slot = __shfl_sync(kFull, slot, 0);
+        if ((long long)slot < ovf_cap) {
+            if (lane == 0) ovf_list[slot] = it;
+            return;
+        }
+    }
+    const uint32_t cnt = pixelbox<true, COUNT>(pp, x0, y0, x1, y1, a.T, S, lane, wc);
+    if (lane == 0) {
+        if (nitems[i] == 1) {
+            a.inter[i] = (int64_t)cnt;
+            a.uni[i] = a.areaA[ia] + a.areaB[ib] - (int64_t)cnt;
+        } else {
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.inter + i), (unsigned long long)cnt);
+        }
+    }
+}
+
+// Persistent pair areas over one item queue (items of pair i: ioff[i] .. ioff[i+1]-1): resident
+// warps take kItemChunk items at a time from the queue head.
+template <int CAP, int STK, bool COUNT, bool OVF>
 __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int side, const long long* nitems,
-                                                               const long long* ioff,
-                                                               unsigned long long* head)
+                                                               const long long* ioff, unsigned long long* head,
+                                                               long long* ovf_list, unsigned long long* ovf_n,
+                                                               long long ovf_cap)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -880,33 +928,34 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int 
                 ++i;
                 if (ioff[i + 1] <= it) i = find_pair(ioff, a.n, it, lane);
             }
-            const long long sub = it - ioff[i];
-            int ia, ib, wx0, wy0, wx1, wy1;
-            pair_window(a, i, ia, ib, wx0, wy0, wx1, wy1);
-            const int gx = (wx1 - wx0 + side - 1) / side;
-            const int sx = (int)(sub % gx), sy = (int)(sub / gx);
-            const int x0 = wx0 + sx * side, y0 = wy0 + sy * side;
-            const int x1 = min(x0 + side, wx1), y1 = min(y0 + side, wy1);
-            const long long pa0 = a.offA[ia], pa1 = a.offA[ia + 1];
-            const long long qb0 = a.offB[ib], qb1 = a.offB[ib + 1];
-            PolyPair pp;
-            pp.vp = reinterpret_cast<const int2*>(a.xyA) + pa0; pp.np = (int)(pa1 - pa0);
-            pp.vq = reinterpret_cast<const int2*>(a.xyB) + qb0; pp.nq = (int)(qb1 - qb0);
-            __syncwarp();
-            const char* bp = band_block(a.bandsA, ia);
-            const char* bq = band_block(a.bandsB, ib);
-            stage_pair(pp, bp, a.mbrA[ia].y, bq, a.mbrB[ib].y, x0, y0, x1, y1, S, lane);
-            __syncwarp();
-            const uint32_t cnt = pixelbox<true, COUNT>(pp, x0, y0, x1, y1, a.T, S, lane, wc);
-            if (lane == 0) {
-                if (nitems[i] == 1) {
-                    a.inter[i] = (int64_t)cnt;
-                    a.uni[i] = a.areaA[ia] + a.areaB[ib] - (int64_t)cnt;
-                } else {
-                    atomicAdd(reinterpret_cast<unsigned long long*>(a.inter + i), (unsigned long long)cnt);
-                }
-            }
+            do_item<CAP, STK, COUNT, OVF>(a, side, nitems, i, it, it - ioff[i], ovf_list, ovf_n, ovf_cap, S, lane,
+                                          wc);
         }
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
+// The items another persistent launch appended to its overflow list (its queue's ioff), one at a
+// time from a second queue head.
+template <int CAP, int STK, bool COUNT>
+__global__ void SCCG_ITEM_BOUNDS k_pair_areas_overflow(const AreasArgs a, int side, const long long* nitems,
+                                                             const long long* ioff, const long long* ovf_list,
+                                                             const unsigned long long* ovf_n, long long ovf_cap,
+                                                             unsigned long long* head)
+{
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long n = min((long long)*ovf_n, ovf_cap);
+    for (;;) {
+        unsigned long long j = 0;
+        if (lane == 0) j = atomicAdd(head, 1ull);
+        j = __shfl_sync(kFull, j, 0);
+        if ((long long)j >= n) break;
+        const long long it = ovf_list[j];
+        const long long i = find_pair(ioff, a.n, it, lane);
+        do_item<CAP, STK, COUNT, false>(a, side, nitems, i, it, it - ioff[i], nullptr, nullptr, 0, S, lane, wc);
     }
     if (COUNT) flush_counters(a.counters, wc);
 }

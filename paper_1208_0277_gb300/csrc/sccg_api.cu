@@ -37,6 +37,9 @@ struct sccg_ctx {
     cudaStream_t tstream[kTileStreams] = {};
     cudaEvent_t tevent[kTileStreams + 1] = {};
     bool tile_streams_ready = false;
+    // second stream of the persistent form (the big-polygon queue runs beside the small one)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t fork_event = nullptr, join_event = nullptr;
     // sccg_batch_run: the captured graph and the arguments it was captured for
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t batch_exec = nullptr;
@@ -151,14 +154,18 @@ struct Carve {
 template <class T>
 size_t carve_size(size_t count) { return ((count * sizeof(T) + 255) & ~size_t(255)) + 256; }
 
+#ifndef SCCG_CAP_MID
+#define SCCG_CAP_MID 128
+#endif
 constexpr int kCapSmall = 64;     // edge buffer of the one-warp-per-item kernels (4 warps per CTA)
+constexpr int kCapMid = SCCG_CAP_MID;   // persistent form, pairs with a polygon over kCapSmall vertices
 constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices (2 warps per CTA)
 
 int edge_cap_for(int max_nv) { return max_nv <= kCapSmall ? kCapSmall : kCapBig; }
 int warps_for(const sccg_ctx* ctx, int cap)
 {
     const int w = std::max(1, std::min(8, ctx->params.warps_per_cta));
-    return cap > kCapSmall ? std::min(w, 2) : w;
+    return cap > kCapMid ? std::min(w, 2) : w;
 }
 
 template <int CAP>
@@ -230,22 +237,51 @@ int launch_plain(sccg_ctx* ctx, const AreasArgs& a, cudaStream_t st)
     return SCCG_OK;
 }
 
-template <int CAP>
-int launch_persistent(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
-                      unsigned long long* head, cudaStream_t st)
+template <class K>
+int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
 {
-    const int wpc = warps_for(ctx, CAP);
-    const size_t smem = warp_smem<CAP>() * wpc;
-    auto kfn = ctx->count_work ? k_pair_areas_persistent<CAP, kStack, true> : k_pair_areas_persistent<CAP, kStack, false>;
-    int r = set_smem(ctx, kfn, smem);
-    if (r) return r;
     int per_sm = ctx->params.ctas_per_sm;
     if (per_sm <= 0) {
         SCCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpc, smem));
         per_sm = std::max(per_sm, 1);
     }
-    kfn<<<(unsigned)(ctx->sm_count * per_sm), 32 * wpc, smem, st>>>(a, side, nitems, ioff, head);
+    *grid = (unsigned)(ctx->sm_count * per_sm);
+    return SCCG_OK;
+}
+
+template <int CAP, bool OVF>
+int launch_persistent(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
+                      unsigned long long* head, long long* ovf_list, unsigned long long* ovf_n, long long ovf_cap,
+                      cudaStream_t st)
+{
+    const int wpc = warps_for(ctx, CAP);
+    const size_t smem = warp_smem<CAP>() * wpc;
+    auto kfn = ctx->count_work ? k_pair_areas_persistent<CAP, kStack, true, OVF>
+                               : k_pair_areas_persistent<CAP, kStack, false, OVF>;
+    int r = set_smem(ctx, kfn, smem);
+    unsigned grid = 0;
+    if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &grid);
+    if (r) return r;
+    kfn<<<grid, 32 * wpc, smem, st>>>(a, side, nitems, ioff, head, ovf_list, ovf_n, ovf_cap);
     SCCG_LAUNCHED(ctx, "k_pair_areas_persistent");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+template <int CAP>
+int launch_overflow(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
+                    const long long* ovf_list, const unsigned long long* ovf_n, long long ovf_cap,
+                    unsigned long long* head, cudaStream_t st)
+{
+    const int wpc = warps_for(ctx, CAP);
+    const size_t smem = warp_smem<CAP>() * wpc;
+    auto kfn = ctx->count_work ? k_pair_areas_overflow<CAP, kStack, true> : k_pair_areas_overflow<CAP, kStack, false>;
+    int r = set_smem(ctx, kfn, smem);
+    unsigned grid = 0;
+    if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &grid);
+    if (r) return r;
+    kfn<<<grid, 32 * wpc, smem, st>>>(a, side, nitems, ioff, ovf_list, ovf_n, ovf_cap, head);
+    SCCG_LAUNCHED(ctx, "k_pair_areas_overflow");
     ctx->launches += 1;
     return SCCG_OK;
 }
@@ -275,10 +311,14 @@ int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* 
     return SCCG_OK;
 }
 
+// overflow list capacity of the persistent form (items beyond it are done in place, chunked)
+long long overflow_cap(long long n_pairs) { return n_pairs + 65536; }
+
 size_t persistent_scratch(long long n_pairs)
 {
     const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
-    return carve_size<long long>(n_pairs + 1) * 4 + carve_size<long long>(nb) + carve_size<unsigned long long>(2);
+    return carve_size<long long>(n_pairs + 1) * 4 + carve_size<long long>(nb) + carve_size<unsigned long long>(4) +
+           carve_size<long long>(overflow_cap(n_pairs));
 }
 
 int split_side(const sccg_ctx* ctx)
@@ -300,7 +340,9 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     long long* ioff_s = cv.take<long long>(n_pairs + 1);
     long long* ioff_b = cv.take<long long>(n_pairs + 1);
     long long* bsum = cv.take<long long>(nb);
-    unsigned long long* head = cv.take<unsigned long long>(2);
+    unsigned long long* head = cv.take<unsigned long long>(4);   // 3 queue heads + overflow count
+    const long long ovf_cap = overflow_cap(n_pairs);
+    long long* ovf_list = cv.take<long long>(ovf_cap);
     const unsigned g = (unsigned)((n_pairs + 255) / 256);
     // pairs whose polygons all fit the small edge buffers go to one queue, the rest to another
     k_plan<<<g, 256, 0, st>>>(a, side, kCapSmall, nitems_s, nitems_b);
@@ -309,10 +351,22 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
     if (!r && cap > kCapSmall) r = device_scan(ctx, nitems_b, n_pairs, ioff_b, bsum, st);
     if (r) return r;
-    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, 2 * sizeof(unsigned long long), st));
-    r = launch_persistent<kCapSmall>(ctx, a, side, nitems_s, ioff_s, head, st);
-    if (!r && cap > kCapSmall) r = launch_persistent<kCapBig>(ctx, a, side, nitems_b, ioff_b, head + 1, st);
+    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, 4 * sizeof(unsigned long long), st));
+    if (cap > kCapSmall) {
+        // the big-polygon queue on the side stream, beside the small one: mid-size buffers, and the
+        // items whose culled edges still do not fit go to the largest buffers afterwards
+        SCCG_CUDA(ctx, cudaEventRecord(ctx->fork_event, st));
+        SCCG_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->fork_event, 0));
+        r = launch_persistent<kCapMid, true>(ctx, a, side, nitems_b, ioff_b, head + 1, ovf_list, head + 3, ovf_cap,
+                                             ctx->side_stream);
+        if (!r) r = launch_overflow<kCapBig>(ctx, a, side, nitems_b, ioff_b, ovf_list, head + 3, ovf_cap, head + 2,
+                                             ctx->side_stream);
+        if (r) return r;
+        SCCG_CUDA(ctx, cudaEventRecord(ctx->join_event, ctx->side_stream));
+    }
+    r = launch_persistent<kCapSmall, false>(ctx, a, side, nitems_s, ioff_s, head, nullptr, nullptr, 0, st);
     if (r) return r;
+    if (cap > kCapSmall) SCCG_CUDA(ctx, cudaStreamWaitEvent(st, ctx->join_event, 0));
     k_union<<<g, 256, 0, st>>>(a, nitems_s, nitems_b);
     SCCG_LAUNCHED(ctx, "k_union");
     ctx->launches += 1;
@@ -509,6 +563,13 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
         delete ctx;
         return SCCG_ENOMEM;
     }
+    if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork_event, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->join_event, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        sccg_ctx_destroy(ctx);
+        return SCCG_ECUDA;
+    }
     *out = ctx;
     return SCCG_OK;
 }
@@ -525,6 +586,9 @@ int sccg_ctx_destroy(sccg_ctx* ctx)
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->pinned) cudaFreeHost(ctx->pinned);
         if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+        if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+        if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
+        if (ctx->join_event) cudaEventDestroy(ctx->join_event);
         if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         if (ctx->tile_streams_ready) {
             for (int k = 0; k < sccg_ctx::kTileStreams; ++k) cudaStreamDestroy(ctx->tstream[k]);
@@ -906,7 +970,7 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
     }
     SCCG_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, st));
     // plan, 3 scan passes and one persistent launch per queue, union, 2 Jaccard
-    ctx->launches += n_pairs > 0 ? (edge_cap_for(std::max(A->max_nv, B->max_nv)) > kCapSmall ? 12 : 8) : 2;
+    ctx->launches += n_pairs > 0 ? (edge_cap_for(std::max(A->max_nv, B->max_nv)) > kCapSmall ? 13 : 8) : 2;
     return SCCG_OK;
 }
 

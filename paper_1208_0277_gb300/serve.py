@@ -88,8 +88,9 @@ class Server:
         self.A, self.B, self.pa, self.pb = A, B, pa, pb
         self.cap_pairs, self.cap_jobs = int(max_batch_pairs), int(max_batch_jobs)
         self.slots = [_Slot(device, params, self.cap_pairs, self.cap_jobs) for _ in range(slots)]
-        # per-slot context scratch of the persistent form (two item queues) is ~40 bytes per pair
-        need = sum(s.device_bytes() + 40 * self.cap_pairs for s in self.slots)
+        # per-slot context scratch of the persistent form (two item queues, overflow list) is ~48 bytes
+        # per pair
+        need = sum(s.device_bytes() + 48 * self.cap_pairs for s in self.slots)
         if need > mem_budget_bytes:
             raise ValueError(f"{slots} slots of {max_batch_pairs} pairs need {need} bytes > budget {mem_budget_bytes}")
         self.free = collections.deque(range(slots))

@@ -195,6 +195,41 @@ def test_band_index_gives_the_same_results(sccg, mode):
     assert c.upload(w.A).bands is not None
 
 
+def test_heavy_tail_full_size_tissue(sccg):
+    """One tile of the heavy-tail workload at full tissue size (2,000-20,000 vertices, MBR up to
+    4,000 px, with band indexes) among 3,000 nuclei: areas and candidate pairs against the oracle in
+    full, pair areas (persistent form) on every tissue-tissue pair and a seeded sample of the
+    others (the oracle's row-interval method; its brute force would take hours here)."""
+    w = W.heavy_tail(seed=4, n_tiles=1, nuclei_per_tile=3000, tissue_lo=4, tissue_hi=5)
+    c = sccg.Context(0)
+    A, B = c.upload(w.A), c.upload(w.B)
+    assert A.bands is not None and B.bands is not None
+    mbrs = []
+    for P_, d in ((w.A, A), (w.B, B)):
+        ref_area, ref_mbr = O.polygon_areas(P_.off, P_.xy, method="rle")
+        np.testing.assert_array_equal(d.area.cpu().numpy()[: P_.n], ref_area)
+        np.testing.assert_array_equal(d.mbr.cpu().numpy()[: P_.n], ref_mbr)
+        mbrs.append(ref_mbr)
+    pa, pb = c.candidate_pairs(A, B)
+    opa, opb = O.candidate_pairs(mbrs[0], w.A.tile, mbrs[1], w.B.tile)
+    np.testing.assert_array_equal(pa.cpu().numpy(), opa)
+    np.testing.assert_array_equal(pb.cpu().numpy(), opb)
+    inter, uni = c.pair_areas(A, B, pa, pb, mode=1)
+    torch.cuda.synchronize()
+    big_a = np.diff(w.A.off)[opa] >= 1000
+    big_b = np.diff(w.B.off)[opb] >= 1000
+    rng = np.random.Generator(np.random.PCG64(9))
+    both = np.nonzero(big_a & big_b)[0]
+    one = np.nonzero(big_a ^ big_b)[0]
+    none = np.nonzero(~big_a & ~big_b)[0]
+    idx = np.sort(np.concatenate([both, rng.choice(one, min(150, len(one)), replace=False),
+                                  rng.choice(none, min(3000, len(none)), replace=False)]))
+    assert len(both) > 0 and len(one) > 0
+    ri, ru = O.pair_areas(w.A, w.B, opa[idx], opb[idx], method="rle")
+    np.testing.assert_array_equal(inter.cpu().numpy()[idx], ri)
+    np.testing.assert_array_equal(uni.cpu().numpy()[idx], ru)
+
+
 def test_batch_graph_replay_and_recapture(sccg):
     """sccg_batch_run: persistent areas + Jaccard captured once as a CUDA graph and replayed; a new
     pair list (other buffers) triggers a new capture. Results equal the oracle every time."""
