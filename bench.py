@@ -40,8 +40,8 @@ UNIT = "pairs/s"
 # reference-centre crossing), one listed straddling edge, and one (edge, row) list entry.
 OPS_PER_STRIP_EDGE = 17
 OPS_PER_BOX_EDGE = 33
-OPS_PER_ROW_EDGE = 15      # listed straddling edge: the strip test without its straddle check
-OPS_PER_ROW_ENTRY = 11     # building one (edge, row) list entry: count pass + fill pass
+OPS_PER_ROW_WORD = 10      # one (row, 32-pixel word) of a leaf window: parity of both polygons, combine, count
+OPS_PER_ROW_ENTRY = 16     # one (edge, row) crossing of a leaf window: exact crossing count, two XOR flips
 OPS_PER_SCAN_ENTRY = 14    # one (edge, row) crossing value of the by-rows area: count, N, ceil-divide, store
 OPS_PER_SCAN_PAIR = 4      # one comparison while ranking a row's crossing values
 
@@ -65,6 +65,12 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--params", type=str, default="", help="JSON tunables for the context")
+    p.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
+                   help="time T / split_pixels / warps_per_cta on the workload before the run (untimed); "
+                   "auto = on for configs 3-5")
+    p.add_argument("--ablation", action="store_true",
+                   help="Fig. 8 of the paper: PixelOnly / PixelBox-NoSep / PixelBox pair-area times on the "
+                   "first 9 whole-slide tiles with coordinates scaled x1..x5 (prints one JSON line)")
     p.add_argument("--profile-once", action="store_true",
                    help="run a single step of --form and exit (for ncu captures; prints no bench line)")
     return p.parse_args()
@@ -248,6 +254,81 @@ def oracle_sample_pairs(w, target_s: float, seed: int = 7):
         m = min(len(pa), int(m * max(2.0, min(8.0, target_s / max(el, 1e-3)))) + 1)
 
 
+def ablation(args):
+    """PixelOnly (pixelize every window: T above any window), PixelBox-NoSep (union counted directly
+    by subdivision) and PixelBox (union from the areas) on the same candidate pairs, coordinates
+    scaled x1..x5 (Sec. 5.2, Fig. 8); T tuned per variant and scale over a sweep (Fig. 10), as the
+    paper tunes it. Pair-area phase only, one launch, CUDA events; every result checked against the
+    oracle's row-interval method."""
+    import numpy as np
+    import torch
+    import oracle as O
+    import paper_1208_0277_gb300 as P
+    from paper_1208_0277_gb300 import workload as W
+    P.build()
+    O.build()
+    base = W.subset_tiles(W.whole_slide(seed=1), range(9))
+    ctx = P.Context(0)
+    dev = torch.device("cuda", 0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)      # noqa: E731
+    t_sweep = [256, 1024, 4096, 16384, 65536]
+
+    def timed(fn, reps=7, warm=2):
+        ts = []
+        for r in range(warm + reps):
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if r >= warm:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    rows = []
+    n_ref = None
+    for s in range(1, 6):
+        w = W.scaled(base, s)
+        A, B = ctx.upload(w.A), ctx.upload(w.B)
+        pa, pb = ctx.candidate_pairs(A, B)
+        n = pa.numel()
+        n_ref = n_ref or n
+        ri, ru = O.pair_areas(w.A, w.B, pa.cpu().numpy().astype(np.int64), pb.cpu().numpy().astype(np.int64),
+                              method="rle")
+        inter = torch.empty(n, dtype=torch.int64, device=dev)
+        uni = torch.empty_like(inter)
+        row = {"scale": s, "pairs": n, "mean_window_px": None, "parity": True}
+        mbr_a, mbr_b = A.mbr[pa.long()].cpu().numpy(), B.mbr[pb.long()].cpu().numpy()
+        ww = np.maximum(0, np.minimum(mbr_a[:, 2], mbr_b[:, 2]) - np.maximum(mbr_a[:, 0], mbr_b[:, 0]))
+        wh = np.maximum(0, np.minimum(mbr_a[:, 3], mbr_b[:, 3]) - np.maximum(mbr_a[:, 1], mbr_b[:, 1]))
+        row["mean_window_px"] = float((ww * wh).mean())
+        for name, mode, words, ts in (("PixelOnly", P.MODE_PLAIN, 0, [1 << 28]),
+                                      ("PixelBox-NoSep", P.MODE_NOSEP, 0, t_sweep),
+                                      ("PixelBox", P.MODE_PLAIN, 0, t_sweep),
+                                      ("PixelOnly+words", P.MODE_PLAIN, 1, [1 << 28]),
+                                      ("PixelBox+words", P.MODE_PLAIN, 1, t_sweep)):
+            ctx.set_param("leaf_words", words)
+            best = None
+            for T in ts:
+                ctx.set_param("T", T)
+                inter.fill_(-7)
+                ms = timed(lambda: ctx.pair_areas(A, B, pa, pb, mode=mode, out=(inter, uni)))
+                ok = bool(np.array_equal(inter.cpu().numpy(), ri) and np.array_equal(uni.cpu().numpy(), ru))
+                row["parity"] = row["parity"] and ok
+                row.setdefault("T_sweep_ms", {}).setdefault(name, {})[str(T)] = round(ms, 4)
+                if best is None or ms < best[0]:
+                    best = (ms, T)
+            row[name] = {"ms": round(best[0], 4), "T": best[1]}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    line = {"ablation": "Sec. 5.2 Fig. 8: PixelOnly vs PixelBox-NoSep vs PixelBox, coordinates scaled x1..x5; "
+                        "leaves as 32-pixel strips tested against every edge (the paper's per-pixel test), and "
+                        "'+words': leaves from per-row parity words (this build's default)",
+            "workload": "first 9 tiles of the whole slide (seed 1), same candidate pairs at every scale",
+            "pairs": n_ref, "unit": "ms per pair-area launch (median of 7, CUDA events)", "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def reference_arm(args):
     """The CPU oracle as the reference arm: each step is a bounded sample of the same workload."""
     import oracle as O
@@ -333,6 +414,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.ablation:
+        ablation(args)
+        return
     if args.impl == "reference":
         if rank == 0:
             reference_arm(args)
@@ -376,6 +460,11 @@ def main():
     B = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
     pa0, pb0, tpo0 = ctx.candidate_pairs(A, B, with_tile_offsets=True)
     n_pairs = int(pa0.numel())
+    tuned = None
+    if args.autotune == "on" or (args.autotune == "auto" and args.config in (3, 4, 5)):
+        from paper_1208_0277_gb300 import tune
+        tuned = tune.tune(ctx, A, B, pa0, pb0, mode=P.MODE_PLAIN if args.form == "tiles" else P.MODE_PERSISTENT)
+        print(f"autotune: {tuned['params']} ({len(tuned['table'])} trials, {tuned['ms']} ms)", file=sys.stderr)
     cap = n_pairs
     pa = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     pb = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
@@ -430,7 +519,7 @@ def main():
 
     def ops(wc):
         return (wc["strip_edges"] * OPS_PER_STRIP_EDGE + wc["box_edges"] * OPS_PER_BOX_EDGE +
-                wc["row_edges"] * OPS_PER_ROW_EDGE + wc["row_entries"] * OPS_PER_ROW_ENTRY +
+                wc["row_edges"] * OPS_PER_ROW_WORD + wc["row_entries"] * OPS_PER_ROW_ENTRY +
                 wc["scan_entries"] * OPS_PER_SCAN_ENTRY + wc["scan_pairs"] * OPS_PER_SCAN_PAIR)
 
     results = {}
@@ -499,9 +588,9 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32/fp32 ALU lane-ops)",
                 "frac": achieved / peak_tops, "traffic": traffic, "kernel": dom,
                 "peak_note": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x 2070 MHz (max SM clock of measured peaks)",
-                "achieved_note": "algorithmic ops (strip-edge x 17 + box-edge x 33 + listed row-edge x 15 + "
-                                 "row-list entry x 11 + crossing value x 14 + crossing comparison x 4, counted "
-                                 "on device) per step / phase time (CUDA events)",
+                "achieved_note": "algorithmic ops (strip-edge x 17 + box-edge x 33 + leaf (edge, row) crossing x "
+                                 "16 + leaf (row, word) x 10 + area crossing value x 14 + area comparison x 4, "
+                                 "counted on device) per step / phase time (CUDA events)",
                 "work": work_areas if dom != "k_prepare" else work_prep}
 
     # end-to-end through the public API with host buffers
@@ -591,8 +680,15 @@ def main():
                        pairs_per_step=n_pairs, polygons=[nA, nB], tiles=w.n_tiles,
                        l2="inputs larger than L2 (no flush needed)",
                        input_bytes=sum(devb[k].numel() * devb[k].element_size() for k in devb),
-                       generation_s=round(gen_s, 1), seed=1 + rank, params=ctx.params()),
+                       generation_s=round(gen_s, 1), seed=1 + rank, params=ctx.params(),
+                       autotune=({"params": tuned["params"], "trials": len(tuned["table"]), "mode": tuned["mode"],
+                                  "best_ms": tuned["ms"]} if tuned else None)),
         "roofline": roofline,
+        # secondary rates of the pair-area phase (counts from the counting step, time from the timed steps)
+        "rates": {"pixel_tests_per_s": work_areas["leaf_pixels"] / (ph["pair_areas"] / 1e3),
+                  "window_pixels_per_s": work_areas["window_pixels"] / (ph["pair_areas"] / 1e3),
+                  "note": "pixel tests = (pixel, polygon) memberships decided one pixel at a time in leaves; "
+                          "window pixels = pixels of the pair windows (or work items) resolved"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": main_r["clocks"],

@@ -67,6 +67,10 @@ typedef struct sccg_params {
     int32_t ctas_per_sm;     /* persistent form: resident CTAs per SM (0 = occupancy maximum) */
     int32_t area_method;     /* how sccg_prepare counts ||p||: SCCG_AREA_ROWS (default) or
                                 SCCG_AREA_PIXELBOX; both give the same exact pixel count */
+    int32_t leaf_words;      /* 1 (default): a leaf window (fewer than T pixels) is pixelized from
+                                per-row parity words, each edge flipping the pixels left of its
+                                crossing; 0: as 32-pixel row strips tested against every edge (the
+                                per-pixel test of Sec. 3.1). Same results. */
 } sccg_params;
 
 /* sccg_prepare's method for ||p||. ROWS: per pixel row, the crossing positions of the edges that
@@ -158,9 +162,15 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
  *                              launches once per tile for the one-launch-per-tile form)
  *   mode SCCG_MODE_PERSISTENT  resident CTAs pull work items from a device queue; pairs with large
  *                              windows are cut into several items whose partial counts are added
- *                              with 64-bit atomics (Sec. 4.1's batching, on the device) */
+ *                              with 64-bit atomics (Sec. 4.1's batching, on the device)
+ *   mode SCCG_MODE_NOSEP       the PixelBox-NoSep variant of Sec. 5.2 (Fig. 8), for comparison: as
+ *                              PLAIN, but uni[k] is counted directly by subdivision of the bounding
+ *                              box of MBR(p) u MBR(q) instead of from the areas. Same results.
+ *                              SCCG_ERANGE if either set has a polygon wider or taller than 8192 px.
+ * A pixelization-only run (PixelOnly of Sec. 5.2) is PLAIN with T above every window (T = 2^28). */
 #define SCCG_MODE_PLAIN 0
 #define SCCG_MODE_PERSISTENT 1
+#define SCCG_MODE_NOSEP 2
 int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                     const int32_t* pa, const int32_t* pb, int64_t n_pairs,
                     int64_t* inter, int64_t* uni, int mode, void* stream);
@@ -247,13 +257,14 @@ int sccg_jaccard_segments(sccg_ctx* ctx, const int64_t* inter, const int64_t* un
 /* ------------------------------------------------------------------------------------------- */
 /* With sccg_ctx_set_param(ctx, "count_work", 1) the prepare and pair-area kernels run an
  * instrumented build that counts the work the method performs; the counts accumulate in the
- * context until read. out8 (host, 8 entries): [0] (32-pixel row strip, edge) evaluations of the
- * full strip test, [1] (pixel, edge) point-in-polygon tests inside all strips, [2] (sampling box,
- * edge) classifications, [3] sampling boxes classified, [4] (edge, row) entries of the per-row edge
- * lists built, [5] (32-pixel row strip, listed straddling edge) evaluations, [6] (edge, row)
- * crossing values of the by-rows area, [7] crossing-value comparisons ranking them. Synchronous.
+ * context until read. out10 (host, 10 entries): [0] (32-pixel row strip, edge) evaluations of the
+ * full strip test, [1] (pixel, edge) point-in-polygon tests inside those strips, [2] (sampling box,
+ * edge) classifications, [3] sampling boxes classified, [4] (edge, row) crossings XORed into leaf
+ * parity words, [5] (row, 32-pixel word) parity words reduced, [6] (edge, row) crossing values of
+ * the by-rows area, [7] crossing-value comparisons ranking them, [8] (pixel, polygon) memberships
+ * decided one pixel at a time (leaves), [9] pixels of the windows counted. Synchronous.
  * reset != 0 zeroes the counters. */
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out8, int reset);
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out10, int reset);
 
 #ifdef __cplusplus
 }

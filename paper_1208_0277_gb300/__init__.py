@@ -22,6 +22,7 @@ SCCG_OK = 0
 SCCG_ECAPACITY = 3
 MODE_PLAIN = 0
 MODE_PERSISTENT = 1
+MODE_NOSEP = 2         # PixelBox-NoSep (Sec. 5.2): union counted directly, for comparison
 AREA_ROWS = 0          # sccg_prepare counts ||p|| row by row (default)
 AREA_PIXELBOX = 1      # ... or by PixelBox on the polygon alone
 
@@ -263,10 +264,10 @@ class Context:
                                           ctypes.c_void_p(out.data_ptr()), _stream(stream)), "sccg_jaccard")
 
     def work_counters(self, reset: bool = True) -> dict:
-        a = (ctypes.c_uint64 * 8)()
+        a = (ctypes.c_uint64 * 10)()
         self._check(self.lib.sccg_work_counters(self.h, a, int(reset)), "sccg_work_counters")
         return dict(strip_edges=a[0], pixel_edges=a[1], box_edges=a[2], boxes=a[3], row_entries=a[4],
-                    row_edges=a[5], scan_entries=a[6], scan_pairs=a[7])
+                    row_edges=a[5], scan_entries=a[6], scan_pairs=a[7], leaf_pixels=a[8], window_pixels=a[9])
 
 
 def cross_compare(ctx: Context, A: DevicePolySet, B: DevicePolySet, mode: int = MODE_PLAIN, stream=None):

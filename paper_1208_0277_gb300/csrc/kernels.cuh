@@ -44,28 +44,15 @@ struct PrepStats {
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
 {
-    unsigned long long a = wc.strip_edges, b = wc.pixel_edges, c = wc.box_edges, d = wc.boxes,
-                       e = wc.row_entries, f = wc.row_edges, g = wc.scan_entries, h = wc.scan_pairs;
+    const unsigned long long* in = &wc.strip_edges;
+    unsigned long long* dst = &out->strip_edges;
+    constexpr int kFields = sizeof(WorkCounters) / sizeof(unsigned long long);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(kFull, a, o);
-        b += __shfl_xor_sync(kFull, b, o);
-        c += __shfl_xor_sync(kFull, c, o);
-        d += __shfl_xor_sync(kFull, d, o);
-        e += __shfl_xor_sync(kFull, e, o);
-        f += __shfl_xor_sync(kFull, f, o);
-        g += __shfl_xor_sync(kFull, g, o);
-        h += __shfl_xor_sync(kFull, h, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&out->strip_edges, a);
-        atomicAdd(&out->pixel_edges, b);
-        atomicAdd(&out->box_edges, c);
-        atomicAdd(&out->boxes, d);
-        atomicAdd(&out->row_entries, e);
-        atomicAdd(&out->row_edges, f);
-        atomicAdd(&out->scan_entries, g);
-        atomicAdd(&out->scan_pairs, h);
+    for (int k = 0; k < kFields; ++k) {
+        unsigned long long v = in[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(dst + k, v);
     }
 }
 
@@ -138,6 +125,7 @@ struct PrepArgs {
     int defer_above;        // > 0: polygons with more vertices are listed for k_prepare_big
     int* big_list;
     unsigned* big_n;
+    int words;              // as AreasArgs::words
 };
 
 // Per-warp shared memory slice of k_prepare: the PixelBox buffers and, with SCAN, the by-rows
@@ -161,7 +149,7 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
     WarpSmem<CAP, STK>& S = *reinterpret_cast<WarpSmem<CAP, STK>*>(slice);
     ScanSmem& SS = *reinterpret_cast<ScanSmem*>(slice);
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
     long long first_bad = 0x7fffffffffffffffLL;
     unsigned long long band_bytes = 0;
@@ -203,7 +191,7 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
             if (res) stage_edges(v, nv, 0, nv, S.ep, S.rp, lane);
             __syncwarp();
             const PolyPair pp{v, nv, res, v, nv, res};
-            area = pixelbox<false, COUNT>(pp, x0, y0, x1, y1, a.T, S, lane, wc);
+            area = pixelbox<false, COUNT>(pp, x0, y0, x1, y1, a.T, a.words, S, lane, wc);
         }
         int t = 0;
         if (a.tile) {
@@ -239,7 +227,7 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare_big(const PrepArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const long long nbig = *a.big_n;
     for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + warp; j < nbig; j += nwarps) {
         const long long i = a.big_list[j];
@@ -254,7 +242,7 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare_big(const PrepArgs a)
             if (res) stage_edges(v, nv, 0, nv, S.ep, S.rp, lane);
             __syncwarp();
             const PolyPair pp{v, nv, res, v, nv, res};
-            area = pixelbox<false, COUNT>(pp, m.x, m.y, m.z, m.w, a.T, S, lane, wc);
+            area = pixelbox<false, COUNT>(pp, m.x, m.y, m.z, m.w, a.T, a.words, S, lane, wc);
         }
         if (lane == 0) a.area[i] = (int64_t)area;
     }
@@ -725,6 +713,7 @@ struct AreasArgs {
     WorkCounters* counters;
     const char* bandsA;     // band index blobs (nullptr = none)
     const char* bandsB;
+    int words;              // leaf windows from parity words (1) or as strips against every edge (0)
 };
 
 // Block of polygon i in a band index blob (nullptr: no blob, or no block for this polygon).
@@ -759,7 +748,7 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_plain(const AreasArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
         const int ia = a.pa[i], ib = a.pb[i];
         int64_t out_i = -1, out_u = -1;      // invalid pair: flagged, not read
@@ -779,10 +768,59 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_plain(const AreasArgs a)
                 const char* bq = band_block(a.bandsB, ib);
                 stage_pair(pp, bp, ma.y, bq, mb.y, wx0, wy0, wx1, wy1, S, lane);
                 __syncwarp();
-                inter = pixelbox<true, COUNT>(pp, wx0, wy0, wx1, wy1, a.T, S, lane, wc);
+                inter = pixelbox<true, COUNT>(pp, wx0, wy0, wx1, wy1, a.T, a.words, S, lane, wc);
             }
             out_i = (int64_t)inter;
             out_u = a.areaA[ia] + a.areaB[ib] - (int64_t)inter;
+        }
+        if (lane == 0) {
+            a.inter[i] = out_i;
+            a.uni[i] = out_u;
+        }
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
+// PixelBox-NoSep (Sec. 5.2, Fig. 8): the intersection by PixelBox over MBR(p) n MBR(q) and the union
+// counted directly, by the same subdivision over the bounding box of MBR(p) u MBR(q), instead of
+// ||p|| + ||q|| - ||p n q||. One warp per pair. Kept for the comparison; requires polygon extents
+// of at most kNoSepExtent so that the union window keeps every product in int32.
+constexpr int kNoSepExtent = 8192;
+
+template <int CAP, int STK, bool COUNT>
+__global__ void SCCG_ITEM_BOUNDS k_pair_areas_nosep(const AreasArgs a)
+{
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
+        const int ia = a.pa[i], ib = a.pb[i];
+        int64_t out_i = -1, out_u = -1;
+        if (ia >= 0 && ia < a.nA && ib >= 0 && ib < a.nB) {
+            const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
+            const long long pa0 = a.offA[ia], pa1 = a.offA[ia + 1];
+            const long long qb0 = a.offB[ib], qb1 = a.offB[ib + 1];
+            const char* bp = band_block(a.bandsA, ia);
+            const char* bq = band_block(a.bandsB, ib);
+            uint32_t cnt[2] = {0, 0};
+            for (int u = 0; u < 2; ++u) {
+                const int wx0 = u ? min(ma.x, mb.x) : max(ma.x, mb.x), wy0 = u ? min(ma.y, mb.y) : max(ma.y, mb.y);
+                const int wx1 = u ? max(ma.z, mb.z) : min(ma.z, mb.z), wy1 = u ? max(ma.w, mb.w) : min(ma.w, mb.w);
+                if (wx1 > wx0 && wy1 > wy0) {
+                    PolyPair pp;
+                    pp.vp = reinterpret_cast<const int2*>(a.xyA) + pa0; pp.np = (int)(pa1 - pa0);
+                    pp.vq = reinterpret_cast<const int2*>(a.xyB) + qb0; pp.nq = (int)(qb1 - qb0);
+                    __syncwarp();
+                    stage_pair(pp, bp, ma.y, bq, mb.y, wx0, wy0, wx1, wy1, S, lane);
+                    __syncwarp();
+                    cnt[u] = u ? pixelbox<true, COUNT, CAP, STK, true>(pp, wx0, wy0, wx1, wy1, a.T, a.words, S, lane, wc)
+                               : pixelbox<true, COUNT>(pp, wx0, wy0, wx1, wy1, a.T, a.words, S, lane, wc);
+                }
+            }
+            out_i = (int64_t)cnt[0];
+            out_u = (int64_t)cnt[1];
         }
         if (lane == 0) {
             a.inter[i] = out_i;
@@ -892,7 +930,7 @@ __device__ __forceinline__ void do_item(const AreasArgs a, int side, const long 
             return;
         }
     }
-    const uint32_t cnt = pixelbox<true, COUNT>(pp, x0, y0, x1, y1, a.T, S, lane, wc);
+    const uint32_t cnt = pixelbox<true, COUNT>(pp, x0, y0, x1, y1, a.T, a.words, S, lane, wc);
     if (lane == 0) {
         if (nitems[i] == 1) {
             a.inter[i] = (int64_t)cnt;
@@ -914,7 +952,7 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int 
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
-    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const long long total = ioff[a.n];
     for (;;) {
         unsigned long long first = 0;
@@ -946,7 +984,7 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_overflow(const AreasArgs a, int si
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
-    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0};
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const long long n = min((long long)*ovf_n, ovf_cap);
     for (;;) {
         unsigned long long j = 0;

@@ -27,10 +27,12 @@ struct WorkCounters {          // algorithmic work, accumulated only by the coun
     unsigned long long pixel_edges;   // (valid pixel, edge) point-in-polygon tests inside those
     unsigned long long box_edges;     // (sampling box, edge) classifications
     unsigned long long boxes;         // sampling boxes classified (per polygon)
-    unsigned long long row_entries;   // (edge, row) entries of the per-row edge lists built
-    unsigned long long row_edges;     // (32-pixel row strip, listed straddling edge) evaluations
+    unsigned long long row_entries;   // (edge, row) crossings XORed into leaf parity words
+    unsigned long long row_edges;     // (row, 32-pixel word) parity words of leaf windows reduced
     unsigned long long scan_entries;  // (edge, row) crossing values of the by-rows area
     unsigned long long scan_pairs;    // crossing-value comparisons ranking them
+    unsigned long long leaf_pixels;   // (pixel, polygon) memberships decided one pixel at a time
+    unsigned long long window_pixels; // pixels of the windows counted (pairs' windows or items)
 };
 
 __device__ __forceinline__ int warp_min(int v)
@@ -227,94 +229,80 @@ __device__ __forceinline__ int poly_box(const int2* v, int nv, bool resident, in
     return meet ? 2 : (int)(par & 1u);
 }
 
-// Lists of the staged edges that straddle each row of a band of at most 32 rows: the edges of
-// row r are ent[off[r] .. off[r+1]). An edge contributes to a pixel's crossing count only if it
-// straddles the pixel's row, so evaluating a row against its list alone is exact.
-constexpr int kRowEntries = 512;
-struct RowLists {
-    int cnt[32];
-    int off[33];
-    unsigned short ent[kRowEntries];
+// c = ceil(N / (2 dy)) for N > 0, else 0: the number of pixels xb, xb + 1, ... of row y crossed by
+// an edge that straddles the row, with N = (2 (y - ylo) + 1) dx - (2 (xb - xl) + 1) dy (pixel xb + t is
+// crossed iff 2 t dy < N, the rule of strip_parity). N / (2 dy) is the crossing's distance right of
+// xb in pixels, at most 2^15 whenever xb is at or right of the polygon's minimum x minus its
+// extent. The quotient is estimated in fp32 (relative error below 2^-22, absolute below 2^-7 at
+// 2^15, so the estimate's ceiling is off by at most one) and corrected with exact integer products
+// (< 2^31).
+__device__ __forceinline__ int crossing_count(int ylo, int dy, int dx, int xl, int y, int xb)
+{
+    const int N = (2 * (y - ylo) + 1) * dx - (2 * (xb - xl) + 1) * dy;
+    const int d2 = 2 * dy;
+    int c = (int)ceilf(__fmul_rn((float)N, __frcp_rn((float)d2)));
+    c += (c * d2 < N) ? 1 : 0;
+    c -= ((c - 1) * d2 >= N) ? 1 : 0;
+    return N <= 0 ? 0 : c;
+}
+
+// Parity words of a leaf window, one pass of up to 64 rows (pixelization in edge-major order).
+// An edge that straddles row y crosses exactly the first c pixels of the row right of the window's
+// left column x0 (c = crossing_count clamped to the window width W), so it flips those pixels'
+// parity: words 0 .. c/32 - 1 entirely and the first c mod 32 pixels of word c/32. The whole-word
+// flips are recorded as bit c/32 of F[r], the partial one XORed into P[r * nw + c/32]; the parity
+// of pixel x0 + 32 j + k of row r is then bit k of
+//   P[r * nw + j] ^ (all ones if F[r] has an odd number of bits above bit j).
+// Windows are handled in pieces of at most kXorMaxWords words (992 px) so that c/32 fits F's bits.
+constexpr int kXorWords = 256;
+constexpr int kXorMaxWords = 31;
+struct XorRows {
+    unsigned F[64];
+    unsigned P[kXorWords];
 };
 
-// Per-warp shared memory: edge buffers of the two polygons, their row lists and the subdivision
-// loop's state.
+// Per-warp shared memory: edge buffers of the two polygons, their leaf parity words and the
+// subdivision loop's state.
 template <int CAP, int STK>
 struct WarpSmem {
     int4 ep[CAP];
     int4 eq[CAP];
     float rp[CAP];
     float rq[CAP];
-    RowLists lp;
-    RowLists lq;
+    XorRows xp;
+    XorRows xq;
     uint2 stack[STK];     // pending sampling boxes (window-relative, packed with flags)
     uint2 leaf[32];       // boxes to pixelize in the current round, one slot per lane
     int loff[32];         // exclusive prefix of row strips over the leaf slots
 };
 
-// Build the row lists of the `ne` staged edges for rows band0 .. band0 + nrows - 1 (nrows <= 32).
-// Returns false (warp-uniform) when they do not fit in kRowEntries. Whole warp, converged.
+// XOR the crossings of the `ne` staged edges with rows y0 .. y0 + nr - 1 into X (cleared), for
+// columns x0 .. x0 + W - 1 (W <= 32 nw, nw <= kXorMaxWords). Whole warp, converged.
 template <bool COUNT>
-__device__ __forceinline__ bool build_rows(const int4* E, int ne, int band0, int nrows, RowLists& L, int lane,
-                                           unsigned long long& cnt_entries)
+__device__ __forceinline__ void xor_rows(const int4* E, int ne, int x0, int y0, int nr, int W, int nw, XorRows& X,
+                                         int lane, unsigned long long& entries)
 {
-    L.cnt[lane] = 0;
-    __syncwarp();
     for (int base = 0; base < ne; base += 32) {
         const int i = base + lane;
         if (i < ne) {
             const int4 ed = E[i];
-            const int r0 = max(ed.x, band0) - band0, r1 = min(ed.x + ed.y, band0 + nrows) - band0;
-            for (int r = r0; r < r1; ++r) atomicAdd(&L.cnt[r], 1);
+            const int r1 = min(ed.x + ed.y, y0 + nr);
+            for (int y = max(ed.x, y0); y < r1; ++y) {
+                const int c = min(crossing_count(ed.x, ed.y, ed.z, ed.w, y, x0), W);
+                const int q = c >> 5, rem = c & 31;
+                const int r = y - y0;
+                if (q) atomicXor(&X.F[r], 1u << q);
+                if (rem) atomicXor(&X.P[r * nw + q], (1u << rem) - 1u);
+                if (COUNT) ++entries;
+            }
         }
     }
-    __syncwarp();
-    const int c = L.cnt[lane];
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (total > kRowEntries) return false;
-    if (COUNT) cnt_entries += (unsigned long long)c;
-    L.off[lane] = incl - c;
-    if (lane == 31) L.off[32] = total;
-    L.cnt[lane] = 0;              // reused as the fill cursor
-    __syncwarp();
-    for (int base = 0; base < ne; base += 32) {
-        const int i = base + lane;
-        if (i < ne) {
-            const int4 ed = E[i];
-            const int r0 = max(ed.x, band0) - band0, r1 = min(ed.x + ed.y, band0 + nrows) - band0;
-            for (int r = r0; r < r1; ++r) L.ent[L.off[r] + atomicAdd(&L.cnt[r], 1)] = (unsigned short)i;
-        }
-    }
-    __syncwarp();
-    return true;
 }
 
-// Parity bitmask of the 32 pixels (x0 + k, y) against the edges listed for row r (all of which
-// straddle row y): the same exact test as strip_parity without the straddle check.
-__device__ __forceinline__ uint32_t row_parity(const int4* E, const float* R, const RowLists& L, int r, int y,
-                                               int x0)
+// Parity word j of row r (see XorRows).
+__device__ __forceinline__ uint32_t xor_word(const XorRows& X, int r, int nw, int j)
 {
-    const int sx = 2 * x0 + 1;
-    uint32_t par = 0;
-    const int k1 = L.off[r + 1];
-    for (int k = L.off[r]; k < k1; ++k) {
-        const int i = L.ent[k];
-        const int4 ed = E[i];
-        const float rc = R[i];
-        const int D = (2 * (y - ed.x) + 1) * ed.z - (sx - 2 * ed.w) * ed.y;
-        const int Dc = min(max(D, 0), ed.y << 6);
-        const float f = __int_as_float(Dc | 0x4B000000) - 8388608.0f;
-        const float q = __fmaf_rn(f, rc, -7.62939453125e-06f);
-        const int cc = __float_as_int(__fadd_ru(q, 12582912.0f)) - 0x4B400000;
-        par ^= __funnelshift_lc(0xffffffffu, 0u, (unsigned)cc);
-    }
-    return par;
+    return X.P[r * nw + j] ^ ((__popc(X.F[r] >> (j + 1)) & 1) ? 0xffffffffu : 0u);
 }
 
 // Box packing: window-relative coordinates (< 2^15) in 15 bits each; bit 15 of the low halves
@@ -356,8 +344,8 @@ struct PolyPair {
 
 // Pixelize the leaf boxes held in the lanes' slots (Algorithm 1's pixelization branch, done as
 // 32-pixel row strips spread over the warp). Returns this lane's count of pixels inside every
-// polygon its box still needs. Whole warp, converged.
-template <bool TWO, bool COUNT, int CAP, int STK>
+// polygon its box still needs (UNION: inside any of them). Whole warp, converged.
+template <bool TWO, bool COUNT, int CAP, int STK, bool UNION = false>
 __device__ __forceinline__ uint32_t pixelize_leaves(const PolyPair pp, WarpSmem<CAP, STK>& S, int wx0, int wy0,
                                                     int lane, uint2 myleaf, bool have, WorkCounters& wc)
 {
@@ -395,21 +383,25 @@ __device__ __forceinline__ uint32_t pixelize_leaves(const PolyPair pp, WarpSmem<
         const uint32_t vmask = act ? __funnelshift_lc(0xffffffffu, 0u, (unsigned)max(valid, 0)) : 0u;
         const bool needP = act && (fl & 1);
         const bool needQ = TWO && act && (fl & 2);
-        uint32_t in = vmask;
+        uint32_t in = UNION ? 0u : vmask;
         unsigned long long ce = 0;
         if (__any_sync(kFull, needP)) {
             const uint32_t par = poly_strip<COUNT>(pp.vp, pp.np, pp.rp_res, S.ep, S.rp, CAP, y, xs, lane, ce);
-            if (needP) in &= par;
+            if (needP) in = UNION ? (in | par) : (in & par);
             if (COUNT && needP) wc.pixel_edges += (unsigned long long)pp.np * valid;
         }
         if (TWO) {
             if (__any_sync(kFull, needQ)) {
                 const uint32_t par = poly_strip<COUNT>(pp.vq, pp.nq, pp.rq_res, S.eq, S.rq, CAP, y, xs, lane, ce);
-                if (needQ) in &= par;
+                if (needQ) in = UNION ? (in | par) : (in & par);
                 if (COUNT && needQ) wc.pixel_edges += (unsigned long long)pp.nq * valid;
             }
         }
-        if (COUNT) wc.strip_edges += ce;
+        if (UNION) in &= vmask;
+        if (COUNT) {
+            wc.strip_edges += ce;
+            wc.leaf_pixels += (unsigned long long)(needP ? valid : 0) + (needQ ? valid : 0);
+        }
         acc += __popc(in);
     }
     __syncwarp();
@@ -421,53 +413,66 @@ __device__ __forceinline__ uint32_t pixelize_leaves(const PolyPair pp, WarpSmem<
 // lane; each lane classifies its sub-box against the polygons the box still needs (a box inside P
 // no longer needs P). Sub-boxes inside every needed polygon add their pixel count, sub-boxes
 // outside any add nothing, mixed ones are pushed (>= T pixels) or pixelized (< T pixels).
+// UNION (with TWO): count the pixels inside P or Q instead (the direct union of the PixelBox-NoSep
+// variant, Sec. 5.2): a sub-box inside either polygon adds its pixels, one outside both adds
+// nothing, and a polygon found outside a box is no longer tested on it.
+// A window of fewer than T pixels is one leaf; with `words` it is pixelized from parity words
+// (xor_rows) when both polygons are resident, otherwise as row strips against every edge.
 // Returns the warp-wide count (the same in every lane). Whole warp, converged.
-template <bool TWO, bool COUNT, int CAP, int STK>
-__device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0, int wx1, int wy1, int T,
+template <bool TWO, bool COUNT, int CAP, int STK, bool UNION = false>
+__device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0, int wx1, int wy1, int T, int words,
                                              WarpSmem<CAP, STK>& S, int lane, WorkCounters& wc)
 {
     const int W = wx1 - wx0, H = wy1 - wy0;
     const int fl0 = TWO ? 3 : 1;
     uint32_t acc = 0;
     int top = 0;
-    if ((long long)W * H < T && pp.rp_res && (!TWO || pp.rq_res)) {
-        // The whole window is one leaf: pixelize it band by band (32 rows, one lane per row), each
-        // row against the edges that straddle it.
-        const int chunks = (W + 31) >> 5;
-        bool fits = true;
-        for (int b0 = 0; b0 < H && fits; b0 += 32) {
-            const int nrows = min(32, H - b0);
-            unsigned long long ce = 0;
-            fits = build_rows<COUNT>(S.ep, pp.np, wy0 + b0, nrows, S.lp, lane, ce);
-            if (TWO && fits) fits = build_rows<COUNT>(S.eq, pp.nq, wy0 + b0, nrows, S.lq, lane, ce);
-            if (!fits) {
-                // rows too crowded for the lists: this band and the rest go through the leaf path
-                for (int r0 = b0; r0 < H; r0 += 32)
-                    acc += pixelize_leaves<TWO, COUNT>(pp, S, wx0, wy0, lane,
-                                                       pack_box(0, r0, W, min(H, r0 + 32), fl0), lane == 0, wc);
-                break;
-            }
-            if (lane < nrows) {
-                const int y = wy0 + b0 + lane;
-                for (int c = 0; c < chunks; ++c) {
-                    const int xs = wx0 + 32 * c;
-                    uint32_t in = __funnelshift_lc(0xffffffffu, 0u, (unsigned)min(32, W - 32 * c));
-                    in &= row_parity(S.ep, S.rp, S.lp, lane, y, xs);
-                    if (TWO) in &= row_parity(S.eq, S.rq, S.lq, lane, y, xs);
-                    acc += __popc(in);
+    if (COUNT && lane == 0) wc.window_pixels += (unsigned long long)W * H;
+    if (words && (long long)W * H < T && pp.rp_res && (!TWO || pp.rq_res)) {
+        // The whole window is one leaf: pixelize it from the parity words (xor_rows), in pieces of
+        // up to 992 columns and passes of up to 64 rows, one lane per row in the reduction.
+        for (int cx = 0; cx < W; cx += 32 * kXorMaxWords) {
+            const int Wp = min(32 * kXorMaxWords, W - cx), nw = (Wp + 31) >> 5;
+            const int nr = min(64, kXorWords / nw);
+            for (int r0 = 0; r0 < H; r0 += nr) {
+                const int nrr = min(nr, H - r0);
+                for (int k = lane; k < nrr; k += 32) {
+                    S.xp.F[k] = 0;
+                    if (TWO) S.xq.F[k] = 0;
+                }
+                for (int k = lane; k < nrr * nw; k += 32) {
+                    S.xp.P[k] = 0;
+                    if (TWO) S.xq.P[k] = 0;
+                }
+                __syncwarp();
+                unsigned long long ce = 0;
+                xor_rows<COUNT>(S.ep, pp.np, wx0 + cx, wy0 + r0, nrr, Wp, nw, S.xp, lane, ce);
+                if (TWO) xor_rows<COUNT>(S.eq, pp.nq, wx0 + cx, wy0 + r0, nrr, Wp, nw, S.xq, lane, ce);
+                __syncwarp();
+                for (int k = lane; k < nrr; k += 32) {
+                    for (int j = 0; j < nw; ++j) {
+                        uint32_t in = __funnelshift_lc(0xffffffffu, 0u, (unsigned)min(32, Wp - 32 * j));
+                        const uint32_t wp = xor_word(S.xp, k, nw, j);
+                        if (TWO) {
+                            const uint32_t wq = xor_word(S.xq, k, nw, j);
+                            in &= UNION ? (wp | wq) : (wp & wq);
+                        } else {
+                            in &= wp;
+                        }
+                        acc += __popc(in);
+                    }
                     if (COUNT) {
-                        const int ne = S.lp.off[lane + 1] - S.lp.off[lane] +
-                                       (TWO ? S.lq.off[lane + 1] - S.lq.off[lane] : 0);
-                        wc.row_edges += (unsigned long long)ne;
-                        wc.pixel_edges += (unsigned long long)ne * min(32, W - 32 * c);
+                        wc.row_edges += (unsigned long long)nw;
+                        wc.leaf_pixels += (unsigned long long)Wp * (TWO ? 2 : 1);
                     }
                 }
+                if (COUNT) wc.row_entries += ce;
+                __syncwarp();
             }
-            if (COUNT) wc.row_entries += ce;
-            __syncwarp();
         }
     } else if ((long long)W * H < T) {
-        acc += pixelize_leaves<TWO, COUNT>(pp, S, wx0, wy0, lane, pack_box(0, 0, W, H, fl0), lane == 0, wc);
+        acc += pixelize_leaves<TWO, COUNT, CAP, STK, UNION>(pp, S, wx0, wy0, lane, pack_box(0, 0, W, H, fl0),
+                                                            lane == 0, wc);
     } else {
         if (lane == 0) S.stack[0] = pack_box(0, 0, W, H, fl0);
         top = 1;
@@ -487,7 +492,9 @@ __device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0
         const int sx0 = x0 + (ix * w) / gx, sx1 = x0 + ((ix + 1) * w) / gx;
         const int sy0 = y0 + (iy * h) / gy, sy1 = y0 + ((iy + 1) * h) / gy;
         const int ax0 = wx0 + sx0, ay0 = wy0 + sy0, ax1 = wx0 + sx1, ay1 = wy0 + sy1;
-        int posP = 1, posQ = 1;   // 0 outside, 1 inside, 2 hover
+        // 0 outside, 1 inside, 2 hover; a polygon the box no longer needs is inside it for the
+        // intersection and outside it for the union
+        int posP = UNION ? 0 : 1, posQ = UNION ? 0 : 1;
         unsigned long long ce = 0;
         if (fl & 1) {
             posP = poly_box<COUNT>(pp.vp, pp.np, pp.rp_res, S.ep, S.rp, CAP, ax0, ay0, ax1, ay1, lane, ce);
@@ -498,8 +505,8 @@ __device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0
             if (COUNT && mine) wc.boxes += 1;
         }
         if (COUNT && mine) wc.box_edges += ce;
-        const bool out = mine && (posP == 0 || posQ == 0);
-        const bool allin = mine && !out && posP == 1 && posQ == 1;
+        const bool out = mine && (UNION ? (posP == 0 && posQ == 0) : (posP == 0 || posQ == 0));
+        const bool allin = mine && !out && (UNION ? (posP == 1 || posQ == 1) : (posP == 1 && posQ == 1));
         const int size = (sx1 - sx0) * (sy1 - sy0);
         if (allin) acc += (uint32_t)size;
         const bool cont = mine && !out && !allin;
@@ -516,7 +523,8 @@ __device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0
         __syncwarp();
         const bool anyleaf = __any_sync(kFull, leaf);
         if (anyleaf)
-            acc += pixelize_leaves<TWO, COUNT>(pp, S, wx0, wy0, lane, pack_box(sx0, sy0, sx1, sy1, nfl), leaf, wc);
+            acc += pixelize_leaves<TWO, COUNT, CAP, STK, UNION>(pp, S, wx0, wy0, lane,
+                                                                pack_box(sx0, sy0, sx1, sy1, nfl), leaf, wc);
     }
     return warp_sum(acc);
 }

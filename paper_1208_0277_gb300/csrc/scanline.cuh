@@ -29,21 +29,6 @@ struct alignas(16) ScanSmem {
     int val[kScanEntries];       // crossing values c, grouped by row
 };
 
-// c = ceil(N / (2 dy)) for N > 0, else 0. Whenever the edge straddles the row, N / (2 dy) is the
-// crossing's distance right of xb in pixels, so c <= 2^15 under the set limits. The quotient is
-// estimated in fp32 (relative error below 2^-22, i.e. absolute error below 2^-7 at c <= 2^15, so
-// the estimate's ceiling is off by at most one) and then corrected exactly with integer products
-// (< 2^31).
-__device__ __forceinline__ int crossing_count(int ylo, int dy, int dx, int xl, int y, int xb)
-{
-    const int N = (2 * (y - ylo) + 1) * dx - (2 * (xb - xl) + 1) * dy;
-    const int d2 = 2 * dy;
-    int c = (int)ceilf(__fmul_rn((float)N, __frcp_rn((float)d2)));
-    c += (c * d2 < N) ? 1 : 0;
-    c -= ((c - 1) * d2 >= N) ? 1 : 0;
-    return N <= 0 ? 0 : c;
-}
-
 // Inside pixels of one row from its k crossing values (one lane).
 __device__ __forceinline__ uint32_t row_inside(const int* val, int k)
 {

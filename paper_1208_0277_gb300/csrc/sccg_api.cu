@@ -217,22 +217,18 @@ int launch_prepare_big(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
     return SCCG_OK;
 }
 
-template <int CAP>
+template <int CAP, bool NOSEP = false>
 int launch_plain(sccg_ctx* ctx, const AreasArgs& a, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
     const size_t smem = warp_smem<CAP>() * wpc;
     const long long grid = grid_for(ctx, a.n, wpc, 64);
-    if (ctx->count_work) {
-        int r = set_smem(ctx, k_pair_areas_plain<CAP, kStack, true>, smem);
-        if (r) return r;
-        k_pair_areas_plain<CAP, kStack, true><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
-    } else {
-        int r = set_smem(ctx, k_pair_areas_plain<CAP, kStack, false>, smem);
-        if (r) return r;
-        k_pair_areas_plain<CAP, kStack, false><<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
-    }
-    SCCG_LAUNCHED(ctx, "k_pair_areas_plain");
+    auto kfn = NOSEP ? (ctx->count_work ? k_pair_areas_nosep<CAP, kStack, true> : k_pair_areas_nosep<CAP, kStack, false>)
+                     : (ctx->count_work ? k_pair_areas_plain<CAP, kStack, true> : k_pair_areas_plain<CAP, kStack, false>);
+    int r = set_smem(ctx, kfn, smem);
+    if (r) return r;
+    kfn<<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
+    SCCG_LAUNCHED(ctx, NOSEP ? "k_pair_areas_nosep" : "k_pair_areas_plain");
     ctx->launches += 1;
     return SCCG_OK;
 }
@@ -400,9 +396,10 @@ int jaccard_launch(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, long
 int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
-    static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method"};
-    int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm, &p->area_method};
-    for (int k = 0; k < 5; ++k) {
+    static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method", "leaf_words"};
+    int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm, &p->area_method,
+                         &p->leaf_words};
+    for (int k = 0; k < 6; ++k) {
         char key[64];
         snprintf(key, sizeof key, "\"%s\"", names[k]);
         const char* at = strstr(js, key);
@@ -424,6 +421,7 @@ int validate_params(const sccg_params& p)
     if (p.split_pixels < 32) return SCCG_EINVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return SCCG_EINVAL;
     if (p.area_method != SCCG_AREA_ROWS && p.area_method != SCCG_AREA_PIXELBOX) return SCCG_EINVAL;
+    if (p.leaf_words != 0 && p.leaf_words != 1) return SCCG_EINVAL;
     return SCCG_OK;
 }
 
@@ -548,6 +546,7 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     ctx->params.split_pixels = 4096;
     ctx->params.ctas_per_sm = 0;
     ctx->params.area_method = SCCG_AREA_ROWS;
+    ctx->params.leaf_words = 1;
     int r = parse_params(params_json, &ctx->params);
     if (!r) r = validate_params(ctx->params);
     if (r) { delete ctx; return r; }
@@ -608,6 +607,7 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     else if (!strcmp(name, "split_pixels")) p.split_pixels = (int32_t)value;
     else if (!strcmp(name, "ctas_per_sm")) p.ctas_per_sm = (int32_t)value;
     else if (!strcmp(name, "area_method")) p.area_method = (int32_t)value;
+    else if (!strcmp(name, "leaf_words")) p.leaf_words = (int32_t)value;
     else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
     else return SCCG_EINVAL;
     const int r = validate_params(p);
@@ -625,14 +625,15 @@ int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out)
 
 const char* sccg_last_error(const sccg_ctx* ctx) { return ctx ? ctx->last_err : ""; }
 
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out8, int reset)
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out10, int reset)
 {
-    if (!ctx || !out8) return SCCG_EINVAL;
+    if (!ctx || !out10) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     WorkCounters h;
     SCCG_CUDA(ctx, cudaMemcpy(&h, ctx->counters, sizeof h, cudaMemcpyDeviceToHost));
-    out8[0] = h.strip_edges; out8[1] = h.pixel_edges; out8[2] = h.box_edges; out8[3] = h.boxes;
-    out8[4] = h.row_entries; out8[5] = h.row_edges; out8[6] = h.scan_entries; out8[7] = h.scan_pairs;
+    out10[0] = h.strip_edges; out10[1] = h.pixel_edges; out10[2] = h.box_edges; out10[3] = h.boxes;
+    out10[4] = h.row_entries; out10[5] = h.row_edges; out10[6] = h.scan_entries; out10[7] = h.scan_pairs;
+    out10[8] = h.leaf_pixels; out10[9] = h.window_pixels;
     if (reset) SCCG_CUDA(ctx, cudaMemset(ctx->counters, 0, sizeof(WorkCounters)));
     return SCCG_OK;
 }
@@ -660,13 +661,13 @@ int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
     SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, sizeof init, cudaMemcpyHostToDevice, st));
     if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
         PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats,
-                   ctx->params.T, ctx->counters, 0, big_list, big_n};
+                   ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
         r = launch_prepare<kCapSmall, true>(ctx, a, st);
         if (r) return r;
     } else if (s->n > 0) {
         SCCG_CUDA(ctx, cudaMemsetAsync(big_n, 0, sizeof(unsigned), st));
         PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats,
-                   ctx->params.T, ctx->counters, kCapSmall, big_list, big_n};
+                   ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words};
         // polygons with more than kCapSmall vertices are listed and done with the larger buffers
         r = launch_prepare<kCapSmall, false>(ctx, a, st);
         if (r) return r;
@@ -846,7 +847,8 @@ int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
 {
     if (!ctx || n_pairs < 0) return SCCG_EINVAL;
     if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
-    if (mode != SCCG_MODE_PLAIN && mode != SCCG_MODE_PERSISTENT) return SCCG_EINVAL;
+    if (mode != SCCG_MODE_PLAIN && mode != SCCG_MODE_PERSISTENT && mode != SCCG_MODE_NOSEP) return SCCG_EINVAL;
+    if (mode == SCCG_MODE_NOSEP && std::max(A->max_extent, B->max_extent) > kNoSepExtent) return SCCG_ERANGE;
     if (n_pairs == 0) return SCCG_OK;
     if (!is_device_ptr(pa) || !is_device_ptr(pb) || !is_device_ptr(inter) || !is_device_ptr(uni))
         return SCCG_EINVAL;
@@ -856,13 +858,16 @@ int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                 A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
                 B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
                 inter, uni, ctx->params.T, ctx->counters,
-                static_cast<const char*>(A->bands), static_cast<const char*>(B->bands)};
+                static_cast<const char*>(A->bands), static_cast<const char*>(B->bands),
+                ctx->params.leaf_words};
     const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
     if (mode == SCCG_MODE_PERSISTENT) {
         const int r = ws_reserve(ctx, persistent_scratch(n_pairs));
         if (r) return r;
         return persistent_launch(ctx, a, cap, st);
     }
+    if (mode == SCCG_MODE_NOSEP)
+        return cap == kCapSmall ? launch_plain<kCapSmall, true>(ctx, a, st) : launch_plain<kCapBig, true>(ctx, a, st);
     return cap == kCapSmall ? launch_plain<kCapSmall>(ctx, a, st) : launch_plain<kCapBig>(ctx, a, st);
 }
 
@@ -901,7 +906,8 @@ int sccg_pair_areas_tiles(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polys
                     A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
                     B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
                     inter + p0, uni + p0, ctx->params.T, ctx->counters,
-                    static_cast<const char*>(A->bands), static_cast<const char*>(B->bands)};
+                    static_cast<const char*>(A->bands), static_cast<const char*>(B->bands),
+                    ctx->params.leaf_words};
         int r;
         r = cap == kCapSmall ? launch_plain<kCapSmall>(ctx, a, ctx->tstream[k])
                              : launch_plain<kCapBig>(ctx, a, ctx->tstream[k]);
@@ -943,7 +949,8 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
                     A->off, A->xy, reinterpret_cast<const int4*>(A->mbr), A->area,
                     B->off, B->xy, reinterpret_cast<const int4*>(B->mbr), B->area,
                     inter, uni, ctx->params.T, ctx->counters,
-                static_cast<const char*>(A->bands), static_cast<const char*>(B->bands)};
+                static_cast<const char*>(A->bands), static_cast<const char*>(B->bands),
+                ctx->params.leaf_words};
         const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
         const unsigned long long launches0 = ctx->launches;
         SCCG_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));

@@ -1,0 +1,110 @@
+"""Autotuner for the pair-area launch parameters.
+
+Picks, by timing on the resident sets and candidate pairs it is given, the sampling-box threshold T
+(Sec. 3.4: where subdivision stops and a box is pixelized), the work-item size of the persistent
+form (split_pixels: how many warps a large pair is spread over) and the warps per CTA (how many
+pairs or items share an SM slot). Every candidate runs the real kernels through the library (CUDA
+events on the launching stream, median of a few launches after warm-up); results are identical for
+every setting, so the tuner only compares times. The search is a small coordinate descent: T first
+over a log grid, then split_pixels, then warps per CTA, each with the others fixed at their best so
+far, which covers the parameters that interact (T and the item size) without timing the full grid.
+
+`tune(ctx, A, B, pa, pb)` returns the best parameters and the timing table; `load`/`save` keep
+results in a JSON file keyed by a workload signature, so that a serving process or a benchmark can
+reuse them.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+from . import MODE_PERSISTENT, MODE_PLAIN
+
+T_GRID = (2048, 4096, 8192, 16384, 65536)
+SPLIT_GRID = (1024, 2048, 4096, 16384)
+WPC_GRID = (2, 4, 8)
+
+
+def _time(ctx, fn, reps: int, warm: int) -> float:
+    import torch
+    ts = []
+    for r in range(warm + reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        if r >= warm:
+            ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: int = 1,
+         t_grid=T_GRID, split_grid=SPLIT_GRID, wpc_grid=WPC_GRID) -> dict:
+    """Coordinate descent over T, split_pixels (persistent form only) and warps_per_cta for the
+    pair areas of (pa, pb). Leaves ctx set to the best parameters. Returns
+    {"params": {...}, "ms": best, "table": [(params, ms), ...]}."""
+    import torch
+    n = pa.numel()
+    inter = torch.empty(max(n, 1), dtype=torch.int64, device=pa.device)
+    uni = torch.empty_like(inter)
+    best = dict(ctx.params())
+    table = []
+
+    def run(params):
+        for k, v in params.items():
+            ctx.set_param(k, v)
+        ms = _time(ctx, lambda: ctx.pair_areas(A, B, pa, pb, mode=mode, out=(inter, uni)), reps, warm)
+        table.append((dict(params), round(ms, 4)))
+        return ms
+
+    best_ms = run({k: best[k] for k in ("T", "split_pixels", "warps_per_cta")})
+    axes = [("T", t_grid)]
+    if mode == MODE_PERSISTENT:
+        axes.append(("split_pixels", split_grid))
+    axes.append(("warps_per_cta", wpc_grid))
+    for name, grid in axes:
+        for v in grid:
+            if v == best[name]:
+                continue
+            trial = {k: best[k] for k in ("T", "split_pixels", "warps_per_cta")}
+            trial[name] = v
+            ms = run(trial)
+            if ms < best_ms:
+                best_ms, best = ms, dict(best, **trial)
+    for k in ("T", "split_pixels", "warps_per_cta"):
+        ctx.set_param(k, best[k])
+    return {"params": {k: best[k] for k in ("T", "split_pixels", "warps_per_cta")}, "ms": round(best_ms, 4),
+            "mode": "persistent" if mode == MODE_PERSISTENT else ("plain" if mode == MODE_PLAIN else str(mode)),
+            "table": table}
+
+
+def signature(A, B, n_pairs: int) -> str:
+    """A workload key: set sizes, vertex counts, largest polygon and extent, pair count."""
+    return (f"nA={A.c.n},nB={B.c.n},vA={A.xy.numel() // 2},vB={B.xy.numel() // 2},"
+            f"maxnv={max(A.c.max_nv, B.c.max_nv)},maxext={max(A.c.max_extent, B.c.max_extent)},np={n_pairs}")
+
+
+def load(path: str, key: str) -> dict | None:
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def save(path: str, key: str, result: dict) -> None:
+    data = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            data = {}
+    data[key] = {"params": result["params"], "ms": result["ms"], "mode": result["mode"]}
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)

@@ -532,6 +532,18 @@ def subset_tiles(w: Workload, tiles) -> Workload:
     return Workload(w.name + f"_sub{len(tiles)}", sub(w.A), sub(w.B), len(tiles), w.tile_px, w.seed)
 
 
+def scaled(w: Workload, factor: int) -> Workload:
+    """Every vertex coordinate multiplied by an integer factor (the scale-factor experiment of
+    Sec. 5.2, Fig. 8: polygons factor^2 times larger, same vertices, same MBR overlaps)."""
+    def sc(P: PolySet) -> PolySet:
+        xy = P.xy.astype(np.int64) * int(factor)
+        if xy.size and np.abs(xy).max() > (1 << 28):
+            raise ValueError("scaled coordinates exceed the +-2^28 limit")
+        return PolySet(off=P.off.copy(), xy=xy.astype(np.int32), tile=P.tile.copy())
+
+    return Workload(f"{w.name}_x{factor}", sc(w.A), sc(w.B), w.n_tiles, w.tile_px * int(factor), w.seed)
+
+
 CONFIGS = {
     1: single_tile,
     2: whole_slide,

@@ -58,11 +58,13 @@ def test_single_tile_bit_exact(ctx):
     assert_same(gpu_run(ctx, w), O.cross_compare(w.A, w.B))
 
 
-@pytest.mark.parametrize("T", [2, 33, 200, 1024, 4096, 1 << 22])
-def test_threshold_does_not_change_results(sccg, T):
-    """T only decides where subdivision stops (Sec. 3.4); results must be identical for every T."""
+@pytest.mark.parametrize("words", [1, 0])
+@pytest.mark.parametrize("T", [2, 33, 200, 1024, 4096, 8192, 1 << 22])
+def test_threshold_does_not_change_results(sccg, T, words):
+    """T only decides where subdivision stops (Sec. 3.4) and leaf_words how a leaf is pixelized;
+    results must be identical for every setting."""
     w = W.single_tile(seed=3, n=400)
-    c = sccg.Context(0, {"T": T})
+    c = sccg.Context(0, {"T": T, "leaf_words": words})
     assert_same(gpu_run(c, w), O.cross_compare(w.A, w.B))
 
 
@@ -94,10 +96,11 @@ def test_medium_and_large_polygons_subdivision_and_chunked_edges(sccg, T):
     A = medium_polygons(10)
     B = medium_polygons(11, kind="tissue")
     w = W.Workload("medium", A, B, 1, 2048, 0)
-    c = sccg.Context(0, {"T": T})
-    g = gpu_run(c, w)
-    ref = O.cross_compare(A, B, method="rle")
-    assert_same(g, ref)
+    for words in (1, 0):
+        c = sccg.Context(0, {"T": T, "leaf_words": words})
+        g = gpu_run(c, w)
+        ref = O.cross_compare(A, B, method="rle")
+        assert_same(g, ref)
     idx = np.arange(0, len(ref["pa"]), max(1, len(ref["pa"]) // 25))
     bi, bu = O.pair_areas(A, B, ref["pa"][idx], ref["pb"][idx], method="brute")
     np.testing.assert_array_equal(g["inter"][idx], bi)
@@ -228,6 +231,31 @@ def test_heavy_tail_full_size_tissue(sccg):
     ri, ru = O.pair_areas(w.A, w.B, opa[idx], opb[idx], method="rle")
     np.testing.assert_array_equal(inter.cpu().numpy()[idx], ri)
     np.testing.assert_array_equal(uni.cpu().numpy()[idx], ru)
+
+
+@pytest.mark.parametrize("T", [2, 256, 8192, 1 << 28])
+def test_nosep_variant_counts_the_union_directly(sccg, T):
+    """PixelBox-NoSep (Sec. 5.2): the union counted by subdivision of the union window equals the
+    oracle's directly counted union; T = 2^28 is PixelOnly. Nuclei, concave polygons, staircases."""
+    c = sccg.Context(0, {"T": T})
+    rng = np.random.Generator(np.random.PCG64(8))
+    ra, _ = W.staircase_rings(rng, 60, max_cols=30, max_h=30, origin_span=60)
+    rb, _ = W.staircase_rings(rng, 60, max_cols=30, max_h=30, origin_span=60)
+    for wk, meth in ((W.single_tile(seed=3, n=400), "brute"),
+                     (W.Workload("medium", medium_polygons(14, n=40), medium_polygons(15, n=40, kind="tissue"),
+                                 1, 2048, 0), "rle"),
+                     (rings_workload([np.asarray(r) for r in ra], [np.asarray(r) for r in rb]), "brute")):
+        assert_same(gpu_run(c, wk, mode=sccg.MODE_NOSEP), O.cross_compare(wk.A, wk.B, method=meth))
+
+
+def test_nosep_refuses_wide_polygons(sccg):
+    c = sccg.Context(0)
+    w = rings_workload([[[0, 0], [9000, 0], [0, 40]]], [[[0, 0], [50, 0], [0, 50]]])
+    A, B = c.upload(w.A), c.upload(w.B)
+    pa, pb = c.candidate_pairs(A, B)
+    with pytest.raises(sccg.SccgError) as e:
+        c.pair_areas(A, B, pa, pb, mode=sccg.MODE_NOSEP)
+    assert e.value.status == 2
 
 
 def test_batch_graph_replay_and_recapture(sccg):
