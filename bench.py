@@ -64,6 +64,7 @@ def parse_args():
     p.add_argument("--tiles", type=int, default=0, help="restrict to the first N tiles (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-chunks", type=int, default=4, help="tile chunks of the end-to-end pipeline")
     p.add_argument("--params", type=str, default="", help="JSON tunables for the context")
     p.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
                    help="time T / split_pixels / warps_per_cta on the workload before the run (untimed); "
@@ -478,8 +479,8 @@ def main():
     def step(form: str, phases=None):
         e = [ev() for _ in range(5)] if phases is not None else None
         if e: e[0].record(stream)
-        a = ctx.prepare(devb["Aoff"], devb["Axy"], devb["Atile"], out=(outs["Ambr"], outs["Aarea"]))
-        b = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
+        a, b = ctx.prepare_sets([(devb["Aoff"], devb["Axy"], devb["Atile"], (outs["Ambr"], outs["Aarea"])),
+                                 (devb["Boff"], devb["Bxy"], devb["Btile"], (outs["Bmbr"], outs["Barea"]))])
         if e: e[1].record(stream)
         p_a, p_b, tpo = ctx.candidate_pairs(a, b, capacity=cap, with_tile_offsets=True, out=(pa, pb))
         if e: e[2].record(stream)
@@ -593,34 +594,33 @@ def main():
                                  "counted on device) per step / phase time (CUDA events)",
                 "work": work_areas if dom != "k_prepare" else work_prep}
 
-    # end-to-end through the public API with host buffers
+    # end-to-end through the public API with host buffers: the copy-overlapped pipeline over pinned
+    # host sets (H2D of every input byte and D2H of every pair's indices and areas plus J each step)
     e2e = None
     if not args.no_e2e:
-        h2d = sum(host[k].numel() * host[k].element_size() for k in host)
-        h_inter = torch.empty(max(cap, 1), dtype=torch.int64).pin_memory()
-        h_uni = torch.empty(max(cap, 1), dtype=torch.int64).pin_memory()
-        d2h = 2 * 8 * n_pairs + 48
-
-        def e2e_step():
-            for k in host:
-                devb[k].copy_(host[k], non_blocking=True)
-            J = step(args.form)
-            h_inter[:n_pairs].copy_(inter[:n_pairs], non_blocking=True)
-            h_uni[:n_pairs].copy_(uni[:n_pairs], non_blocking=True)
-            return J
-        for _ in range(2):
-            e2e_step()
+        from paper_1208_0277_gb300.pipeline import HostSet, Pipeline
+        pipe = Pipeline(ctx, HostSet(host["Aoff"], host["Axy"], host["Atile"]),
+                        HostSet(host["Boff"], host["Bxy"], host["Btile"]), w.n_tiles, chunks=args.e2e_chunks,
+                        initial_pairs=n_pairs + 1024)
+        e_pa, _, e_inter, _, e_J = pipe.run()               # warm-up, and the same results as the device run
+        e2e_same = bool(len(e_pa) == n_pairs and e_J["J"] == main_r["J"]["J"] and
+                        e_J["Jprime"] == main_r["J"]["Jprime"])
+        pipe.run()
         torch.cuda.synchronize()
-        s0, s1 = ev(), ev()
-        s0.record(stream)
+        if dist:
+            dist.barrier()
         n_e2e = max(3, args.steps // 2)
+        t0 = time.perf_counter()
         for _ in range(n_e2e):
-            e2e_step()
-        s1.record(stream)
+            pipe.run()
         torch.cuda.synchronize()
-        e_ms, _ = whole_job(s0.elapsed_time(s1), n_pairs, dist, dev)
-        e2e = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / n_e2e}
+        e_ms, _ = whole_job(1e3 * (time.perf_counter() - t0), n_pairs, dist, dev)
+        e2e = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pipe.h2d_bytes,
+               "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
+               "chunks": len(pipe.chunks), "same_results_as_device_run": e2e_same,
+               "how": "paper_1208_0277_gb300.pipeline: tiles in chunks, H2D of chunk k+1 overlapped with chunk k "
+                      "(prepare, candidate pairs, persistent pair areas), results D2H as they finish, one Jaccard; "
+                      "host wall clock"}
 
     # CPU baseline (rank 0, N=1): the oracle on the host cores, with a parity check on the sample
     cpu = None

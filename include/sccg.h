@@ -121,6 +121,11 @@ typedef struct sccg_polyset {
  * Returns SCCG_EINVAL or SCCG_ERANGE for invalid sets (mbr/area contents then unspecified). */
 int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream);
 
+/* sccg_prepare for n_sets sets (1..64) at once: their kernels are launched back to back and the
+ * stream is synchronised once. Every set's summary is filled in; a set that fails validation is not
+ * marked prepared, and the call returns the first failure's status (SCCG_OK if none). */
+int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* stream);
+
 /* Band index of the set's polygons with 1024 or more vertices (large tissue regions): each such
  * polygon's rows are cut into 32-row bands and every band lists the edges whose y-range meets it,
  * so a pair-area work item reads only the edges near its window instead of the whole ring (the
@@ -218,6 +223,13 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                    const int32_t* pa, const int32_t* pb, int64_t n_pairs,
                    int64_t* inter, int64_t* uni, sccg_jaccard_result* out, void* stream);
 
+
+/* Add base_a to pa[k] and base_b to pb[k] for k < n_pairs: turns the candidate pairs of a chunk of
+ * tiles (polygon indices local to the chunk's sub-sets) into indices of the whole sets, for a
+ * pipelined front end that copies and compares chunks in turn (Sec. 4.1, Fig. 6; the paper has no
+ * such call). Bases in [0, 2^31); the caller keeps base + local index below 2^31. Asynchronous. */
+int sccg_rebase_pairs(sccg_ctx* ctx, int32_t* pa, int32_t* pb, int64_t n_pairs, int64_t base_a, int64_t base_b,
+                      void* stream);
 
 /* Allocation-free variant of sccg_jaccard (the paper has no counterpart; this is a library
  * service). Same results as sccg_jaccard, but it needs no context and allocates nothing: its scratch

@@ -133,6 +133,36 @@ class Context:
             self.build_bands(d, stream=stream)
         return d
 
+    def prepare_sets(self, specs, stream=None, bands: bool = True) -> list:
+        """prepare() for several sets with one synchronisation: specs = [(off, xy, tile, out), ...]
+        (tile and out may be None)."""
+        import torch
+        k = len(specs)
+        arr = (_native.PolySetC * k)()
+        keep = []
+        for j, (off, xy, tile, out) in enumerate(specs):
+            n = off.numel() - 1
+            if out is None:
+                mbr = torch.empty((max(n, 1), 4), dtype=torch.int32, device=off.device)
+                area = torch.empty(max(n, 1), dtype=torch.int64, device=off.device)
+            else:
+                mbr, area = out
+            if xy.numel() == 0:
+                xy = torch.zeros(2, dtype=torch.int32, device=off.device)
+            arr[j] = _native.PolySetC(n=n, off=off.data_ptr(), xy=xy.data_ptr(), tile=_ptr(tile),
+                                      mbr=mbr.data_ptr(), area=area.data_ptr())
+            keep.append((off, xy, tile, mbr, area))
+        self._check(self.lib.sccg_prepare_sets(self.h, arr, k, _stream(stream)), "sccg_prepare_sets")
+        out = []
+        for j, (off, xy, tile, mbr, area) in enumerate(keep):
+            c = _native.PolySetC()
+            ctypes.pointer(c)[0] = arr[j]
+            d = DevicePolySet(off, xy, tile, mbr, area, c)
+            if bands and c.band_bytes > 0:
+                self.build_bands(d, stream=stream)
+            out.append(d)
+        return out
+
     def build_bands(self, d: DevicePolySet, stream=None):
         """Build (or rebuild) the band index of a prepared set into a new device buffer."""
         import torch
@@ -262,6 +292,12 @@ class Context:
         n = inter.numel()
         self._check(self.lib.sccg_jaccard(self.h, _ptr(inter) if n else None, _ptr(uni) if n else None, n,
                                           ctypes.c_void_p(out.data_ptr()), _stream(stream)), "sccg_jaccard")
+
+    def rebase_pairs(self, pa, pb, base_a: int, base_b: int, stream=None):
+        """In place on the device: pa += base_a, pb += base_b."""
+        n = pa.numel()
+        self._check(self.lib.sccg_rebase_pairs(self.h, _ptr(pa) if n else None, _ptr(pb) if n else None, n,
+                                               int(base_a), int(base_b), _stream(stream)), "sccg_rebase_pairs")
 
     def work_counters(self, reset: bool = True) -> dict:
         a = (ctypes.c_uint64 * 10)()

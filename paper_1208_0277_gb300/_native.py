@@ -26,7 +26,7 @@ EXPORTS = [
     "sccg_ctx_get_params", "sccg_last_error", "sccg_prepare", "sccg_candidate_pairs",
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
     "sccg_jaccard_static", "sccg_work_counters", "sccg_build_bands", "sccg_gather_pairs",
-    "sccg_jaccard_segments",
+    "sccg_jaccard_segments", "sccg_rebase_pairs", "sccg_prepare_sets",
 ]
 
 _lock = threading.Lock()
@@ -111,6 +111,7 @@ def load(path: str | None = None):
             "sccg_ctx_get_params": ([V, ctypes.POINTER(ParamsC)], I),
             "sccg_last_error": ([V], ctypes.c_char_p),
             "sccg_prepare": ([V, PS, V], I),
+            "sccg_prepare_sets": ([V, PS, I, V], I),
             "sccg_candidate_pairs": ([V, PS, PS, V, V, I64, ctypes.POINTER(I64), V, V], I),
             "sccg_pair_areas": ([V, PS, PS, V, V, I64, V, V, I, V], I),
             "sccg_pair_areas_tiles": ([V, PS, PS, V, V, V, ctypes.c_int32, V, V, V], I),
@@ -121,6 +122,7 @@ def load(path: str | None = None):
             "sccg_jaccard": ([V, V, V, I64, V, V], I),
             "sccg_jaccard_static": ([V, V, I64, V, V], I),
             "sccg_build_bands": ([V, PS, V, I64, V], I),
+            "sccg_rebase_pairs": ([V, V, V, I64, I64, I64, V], I),
             "sccg_work_counters": ([V, ctypes.POINTER(ctypes.c_uint64), I], I),
         }
         for name, (args, res) in sig.items():

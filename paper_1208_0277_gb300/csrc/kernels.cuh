@@ -998,6 +998,15 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_overflow(const AreasArgs a, int si
     if (COUNT) flush_counters(a.counters, wc);
 }
 
+// Chunk-local candidate pairs to indices into the whole sets (pipelined front end).
+__global__ void k_rebase_pairs(int32_t* pa, int32_t* pb, long long n, int base_a, int base_b)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        pa[i] += base_a;
+        pb[i] += base_b;
+    }
+}
+
 // ----------------------------------------------------------------------------------------------
 // a6: Jaccard reductions (exact integer sums; ratios summed in 128-bit fixed point, scale 2^100)
 // ----------------------------------------------------------------------------------------------

@@ -236,14 +236,20 @@ __device__ __forceinline__ int poly_box(const int2* v, int nv, bool resident, in
 // extent. The quotient is estimated in fp32 (relative error below 2^-22, absolute below 2^-7 at
 // 2^15, so the estimate's ceiling is off by at most one) and corrected with exact integer products
 // (< 2^31).
-__device__ __forceinline__ int crossing_count(int ylo, int dy, int dx, int xl, int y, int xb)
+// r2 = RN(1 / (2 dy)) (the staged reciprocal).
+__device__ __forceinline__ int crossing_count_r(int ylo, int dy, int dx, int xl, int y, int xb, float r2)
 {
     const int N = (2 * (y - ylo) + 1) * dx - (2 * (xb - xl) + 1) * dy;
     const int d2 = 2 * dy;
-    int c = (int)ceilf(__fmul_rn((float)N, __frcp_rn((float)d2)));
+    int c = (int)ceilf(__fmul_rn((float)N, r2));
     c += (c * d2 < N) ? 1 : 0;
     c -= ((c - 1) * d2 >= N) ? 1 : 0;
     return N <= 0 ? 0 : c;
+}
+
+__device__ __forceinline__ int crossing_count(int ylo, int dy, int dx, int xl, int y, int xb)
+{
+    return crossing_count_r(ylo, dy, dx, xl, y, xb, __frcp_rn((float)(2 * dy)));
 }
 
 // Parity words of a leaf window, one pass of up to 64 rows (pixelization in edge-major order).
@@ -276,26 +282,67 @@ struct WarpSmem {
     int loff[32];         // exclusive prefix of row strips over the leaf slots
 };
 
+// Flattened (edge, row) work: lane L holds an edge with cnt_L rows to visit and excl = the exclusive
+// prefix sum of cnt over the lanes; entry t (0 <= t < total) belongs to the last lane whose excl is
+// <= t (a lane with no rows never is: the next lane has the same offset). Binary search over the
+// lanes by shuffles. Whole warp, converged.
+__device__ __forceinline__ int flat_owner(int excl, int t)
+{
+    int own = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int e = __shfl_sync(kFull, excl, own + s);   // own + s <= 31 throughout
+        if (e <= t) own += s;
+    }
+    return own;
+}
+
+// Exclusive and total of cnt over the warp.
+__device__ __forceinline__ int warp_excl(int cnt, int lane, int& total)
+{
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    total = __shfl_sync(kFull, incl, 31);
+    return incl - cnt;
+}
+
 // XOR the crossings of the `ne` staged edges with rows y0 .. y0 + nr - 1 into X (cleared), for
-// columns x0 .. x0 + W - 1 (W <= 32 nw, nw <= kXorMaxWords). Whole warp, converged.
+// columns x0 .. x0 + W - 1 (W <= 32 nw, nw <= kXorMaxWords). The (edge, row) crossings of each
+// group of 32 edges are spread evenly over the lanes (warp prefix sum of the edges' row counts; each
+// lane finds its crossing's edge by a binary search over the lanes' offsets), so a steep edge does
+// not hold the warp. Whole warp, converged.
 template <bool COUNT>
-__device__ __forceinline__ void xor_rows(const int4* E, int ne, int x0, int y0, int nr, int W, int nw, XorRows& X,
-                                         int lane, unsigned long long& entries)
+__device__ __forceinline__ void xor_rows(const int4* E, const float* R, int ne, int x0, int y0, int nr, int W, int nw,
+                                         XorRows& X, int lane, unsigned long long& entries)
 {
     for (int base = 0; base < ne; base += 32) {
         const int i = base + lane;
+        int cnt = 0;
         if (i < ne) {
             const int4 ed = E[i];
-            const int r1 = min(ed.x + ed.y, y0 + nr);
-            for (int y = max(ed.x, y0); y < r1; ++y) {
-                const int c = min(crossing_count(ed.x, ed.y, ed.z, ed.w, y, x0), W);
+            cnt = max(0, min(ed.x + ed.y, y0 + nr) - max(ed.x, y0));
+        }
+        int total;
+        const int excl = warp_excl(cnt, lane, total);
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            const int own = flat_owner(excl, t);
+            const int eo = __shfl_sync(kFull, excl, own);
+            if (t < total) {
+                const int4 ed = E[base + own];
+                const int y = max(ed.x, y0) + (t - eo);
+                const int c = min(crossing_count_r(ed.x, ed.y, ed.z, ed.w, y, x0, R[base + own]), W);
                 const int q = c >> 5, rem = c & 31;
                 const int r = y - y0;
                 if (q) atomicXor(&X.F[r], 1u << q);
                 if (rem) atomicXor(&X.P[r * nw + q], (1u << rem) - 1u);
-                if (COUNT) ++entries;
             }
         }
+        if (COUNT) entries += (unsigned long long)cnt;
     }
 }
 
@@ -446,8 +493,8 @@ __device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0
                 }
                 __syncwarp();
                 unsigned long long ce = 0;
-                xor_rows<COUNT>(S.ep, pp.np, wx0 + cx, wy0 + r0, nrr, Wp, nw, S.xp, lane, ce);
-                if (TWO) xor_rows<COUNT>(S.eq, pp.nq, wx0 + cx, wy0 + r0, nrr, Wp, nw, S.xq, lane, ce);
+                xor_rows<COUNT>(S.ep, S.rp, pp.np, wx0 + cx, wy0 + r0, nrr, Wp, nw, S.xp, lane, ce);
+                if (TWO) xor_rows<COUNT>(S.eq, S.rq, pp.nq, wx0 + cx, wy0 + r0, nrr, Wp, nw, S.xq, lane, ce);
                 __syncwarp();
                 for (int k = lane; k < nrr; k += 32) {
                     for (int j = 0; j < nw; ++j) {

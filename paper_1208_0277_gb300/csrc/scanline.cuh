@@ -85,13 +85,22 @@ __device__ __forceinline__ uint32_t area_scan(const int2* v, int nv, int x0, int
         const int nrows = min(32, y1 - b0);
         S.cnt[lane] = 0;
         __syncwarp();
-        for (int base = 0; base < nv; base += 32) {
+        for (int base = 0; base < nv; base += 32) {          // per-row counts, (edge, row) flattened
             const int e = base + lane;
+            int r0 = 0, cnt = 0;
             if (e < nv) {
                 const int f = (e + 1 == nv) ? 0 : e + 1;
                 const int ya = v[e].y, yb = v[f].y;
-                const int r0 = max(min(ya, yb), b0) - b0, r1 = min(max(ya, yb), b0 + nrows) - b0;
-                for (int r = r0; r < r1; ++r) atomicAdd(&S.cnt[r], 1);
+                r0 = max(min(ya, yb), b0) - b0;
+                cnt = max(0, min(max(ya, yb), b0 + nrows) - b0 - r0);
+            }
+            int total;
+            const int excl = warp_excl(cnt, lane, total);
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int t = t0 + lane;
+                const int own = flat_owner(excl, t);
+                const int ro = __shfl_sync(kFull, r0, own) + (t - __shfl_sync(kFull, excl, own));
+                if (t < total) atomicAdd(&S.cnt[ro], 1);
             }
         }
         __syncwarp();
@@ -118,17 +127,27 @@ __device__ __forceinline__ uint32_t area_scan(const int2* v, int nv, int x0, int
             S.off[lane] = incl - cm;
             S.cnt[lane] = 0;          // fill cursor
             __syncwarp();
-            for (int base = 0; base < nv; base += 32) {
+            for (int base = 0; base < nv; base += 32) {      // crossing values, (edge, row) flattened
                 const int e = base + lane;
+                int2 a = make_int2(0, 0), b = make_int2(0, 0);
+                int q0 = 0, cnt = 0;
                 if (e < nv) {
                     const int f = (e + 1 == nv) ? 0 : e + 1;
-                    int2 a = v[e];
-                    int2 b = v[f];
+                    a = v[e];
+                    b = v[f];
                     if (b.y < a.y) { const int2 t = a; a = b; b = t; }
-                    const int dy = b.y - a.y, dx = b.x - a.x;
-                    const int q0 = max(a.y, b0 + r) - b0, q1 = min(b.y, b0 + r2) - b0;
-                    for (int q = q0; q < q1; ++q)
-                        S.val[S.off[q] + atomicAdd(&S.cnt[q], 1)] = crossing_count(a.y, dy, dx, a.x, b0 + q, x0);
+                    q0 = max(a.y, b0 + r) - b0;
+                    cnt = max(0, min(b.y, b0 + r2) - b0 - q0);
+                }
+                int total;
+                const int excl = warp_excl(cnt, lane, total);
+                for (int t0 = 0; t0 < total; t0 += 32) {
+                    const int t = t0 + lane;
+                    const int own = flat_owner(excl, t);
+                    const int q = __shfl_sync(kFull, q0, own) + (t - __shfl_sync(kFull, excl, own));
+                    const int ay = __shfl_sync(kFull, a.y, own), ax = __shfl_sync(kFull, a.x, own);
+                    const int dy = __shfl_sync(kFull, b.y, own) - ay, dx = __shfl_sync(kFull, b.x, own) - ax;
+                    if (t < total) S.val[S.off[q] + atomicAdd(&S.cnt[q], 1)] = crossing_count(ay, dy, dx, ax, b0 + q, x0);
                 }
             }
             __syncwarp();

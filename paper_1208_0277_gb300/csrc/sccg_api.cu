@@ -157,6 +157,8 @@ size_t carve_size(size_t count) { return ((count * sizeof(T) + 255) & ~size_t(25
 #ifndef SCCG_CAP_MID
 #define SCCG_CAP_MID 128
 #endif
+constexpr int kMaxPrepSets = 64;  // sets per sccg_prepare_sets call (their stats share the pinned page)
+static_assert(kMaxPrepSets * sizeof(PrepStats) <= 4096, "prepare stats must fit the pinned staging page");
 constexpr int kCapSmall = 64;     // edge buffer of the one-warp-per-item kernels (4 warps per CTA)
 constexpr int kCapMid = SCCG_CAP_MID;   // persistent form, pairs with a polygon over kCapSmall vertices
 constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices (2 warps per CTA)
@@ -638,62 +640,81 @@ int sccg_work_counters(sccg_ctx* ctx, uint64_t* out10, int reset)
     return SCCG_OK;
 }
 
-int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
+int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* stream)
 {
-    if (!ctx || !s || s->n < 0 || s->n > 0x7fffffffLL) return SCCG_EINVAL;
+    if (!ctx || !sets || n_sets < 1 || n_sets > kMaxPrepSets) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    s->reserved = 0;
-    if (!is_device_ptr(s->off) || !is_device_ptr(s->mbr) || !is_device_ptr(s->area)) return SCCG_EINVAL;
-    if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
-    if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
-    if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
-    int r = ws_reserve(ctx, carve_size<PrepStats>(1) + carve_size<int>(s->n + 1) + carve_size<unsigned>(1));
+    size_t need = carve_size<PrepStats>(n_sets) + carve_size<unsigned>(1);
+    for (int k = 0; k < n_sets; ++k) {
+        sccg_polyset* s = sets + k;
+        if (s->n < 0 || s->n > 0x7fffffffLL) return SCCG_EINVAL;
+        s->reserved = 0;
+        if (!is_device_ptr(s->off) || !is_device_ptr(s->mbr) || !is_device_ptr(s->area)) return SCCG_EINVAL;
+        if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
+        if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
+        if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
+        need += carve_size<int>(s->n + 1);
+    }
+    int r = ws_reserve(ctx, need);
     if (r) return r;
     Carve cv(ctx->ws);
-    PrepStats* stats = cv.take<PrepStats>(1);
-    int* big_list = cv.take<int>(s->n + 1);
+    PrepStats* stats = cv.take<PrepStats>(n_sets);
     unsigned* big_n = cv.take<unsigned>(1);
-    PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0};
+    const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0};
     // the initial stats are written by a copy from pinned memory, kept ordered on the stream
     PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
-    *hstats = init;
-    SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, sizeof init, cudaMemcpyHostToDevice, st));
-    if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
-        PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats,
-                   ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
-        r = launch_prepare<kCapSmall, true>(ctx, a, st);
-        if (r) return r;
-    } else if (s->n > 0) {
-        SCCG_CUDA(ctx, cudaMemsetAsync(big_n, 0, sizeof(unsigned), st));
-        PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats,
-                   ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words};
-        // polygons with more than kCapSmall vertices are listed and done with the larger buffers
-        r = launch_prepare<kCapSmall, false>(ctx, a, st);
-        if (r) return r;
-        r = launch_prepare_big<kCapBig>(ctx, a, st);
-        if (r) return r;
+    for (int k = 0; k < n_sets; ++k) hstats[k] = init;
+    SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, n_sets * sizeof init, cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < n_sets; ++k) {
+        const sccg_polyset* s = sets + k;
+        int* big_list = cv.take<int>(s->n + 1);
+        if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
+            PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
+                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
+            r = launch_prepare<kCapSmall, true>(ctx, a, st);
+            if (r) return r;
+        } else if (s->n > 0) {
+            SCCG_CUDA(ctx, cudaMemsetAsync(big_n, 0, sizeof(unsigned), st));
+            PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
+                       ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words};
+            // polygons with more than kCapSmall vertices are listed and done with the larger buffers
+            r = launch_prepare<kCapSmall, false>(ctx, a, st);
+            if (r) return r;
+            r = launch_prepare_big<kCapBig>(ctx, a, st);
+            if (r) return r;
+        }
     }
-    SCCG_CUDA(ctx, cudaMemcpyAsync(hstats, stats, sizeof init, cudaMemcpyDeviceToHost, st));
+    SCCG_CUDA(ctx, cudaMemcpyAsync(hstats, stats, n_sets * sizeof init, cudaMemcpyDeviceToHost, st));
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
-    const PrepStats res = *hstats;
-    s->max_nv = res.max_nv;
-    s->max_extent = res.max_extent;
-    s->n_tiles = std::max(res.n_tiles, s->n > 0 ? 1 : 0);
-    s->band_bytes = res.band_bytes ? band_head_bytes(s->n) + (long long)res.band_bytes : 0;
-    s->bands = nullptr;
-    if (res.err & (kErrFewVertices | kErrTiles)) {
-        snprintf(ctx->last_err, sizeof ctx->last_err, "invalid polygon set (flags %d, first bad polygon %lld)",
-                 res.err, res.first_bad);
-        return SCCG_EINVAL;
+    int status = SCCG_OK;
+    for (int k = 0; k < n_sets; ++k) {
+        sccg_polyset* s = sets + k;
+        const PrepStats res = hstats[k];
+        s->max_nv = res.max_nv;
+        s->max_extent = res.max_extent;
+        s->n_tiles = std::max(res.n_tiles, s->n > 0 ? 1 : 0);
+        s->band_bytes = res.band_bytes ? band_head_bytes(s->n) + (long long)res.band_bytes : 0;
+        s->bands = nullptr;
+        if (res.err & (kErrFewVertices | kErrTiles)) {
+            snprintf(ctx->last_err, sizeof ctx->last_err,
+                     "invalid polygon set %d (flags %d, first bad polygon %lld)", k, res.err, res.first_bad);
+            if (!status) status = SCCG_EINVAL;
+        } else if (res.err & kErrRange) {
+            snprintf(ctx->last_err, sizeof ctx->last_err, "set %d: coordinate/extent out of range at polygon %lld",
+                     k, res.first_bad);
+            if (!status) status = SCCG_ERANGE;
+        } else {
+            s->reserved = (int32_t)kPreparedMagic;
+        }
     }
-    if (res.err & kErrRange) {
-        snprintf(ctx->last_err, sizeof ctx->last_err, "coordinate/extent out of range at polygon %lld",
-                 res.first_bad);
-        return SCCG_ERANGE;
-    }
-    s->reserved = (int32_t)kPreparedMagic;
-    return SCCG_OK;
+    return status;
+}
+
+int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
+{
+    if (!ctx || !s) return SCCG_EINVAL;
+    return sccg_prepare_sets(ctx, s, 1, stream);
 }
 
 int sccg_build_bands(sccg_ctx* ctx, sccg_polyset* s, void* buf, int64_t bytes, void* stream)
@@ -978,6 +999,22 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
     SCCG_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, st));
     // plan, 3 scan passes and one persistent launch per queue, union, 2 Jaccard
     ctx->launches += n_pairs > 0 ? (edge_cap_for(std::max(A->max_nv, B->max_nv)) > kCapSmall ? 13 : 8) : 2;
+    return SCCG_OK;
+}
+
+int sccg_rebase_pairs(sccg_ctx* ctx, int32_t* pa, int32_t* pb, int64_t n_pairs, int64_t base_a, int64_t base_b,
+                      void* stream)
+{
+    if (!ctx || n_pairs < 0 || base_a < 0 || base_b < 0 || base_a > 0x7fffffffLL || base_b > 0x7fffffffLL)
+        return SCCG_EINVAL;
+    if (n_pairs == 0) return SCCG_OK;
+    if (!is_device_ptr(pa) || !is_device_ptr(pb)) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = (unsigned)std::min<long long>((n_pairs + 255) / 256, 8LL * ctx->sm_count);
+    k_rebase_pairs<<<grid, 256, 0, st>>>(pa, pb, n_pairs, (int)base_a, (int)base_b);
+    SCCG_LAUNCHED(ctx, "k_rebase_pairs");
+    ctx->launches += 1;
     return SCCG_OK;
 }
 

@@ -1,0 +1,165 @@
+"""Host-to-host cross-comparison with the copies overlapped (the pipelined front end of Sec. 4.1,
+Fig. 6: while the GPU works on one batch of tiles, the next batch is being moved to it).
+
+The two polygon sets live in pinned host memory, grouped by tile. They are cut into chunks of
+consecutive tiles; chunk k+1 is copied host -> device on a copy stream while chunk k is prepared,
+filtered and compared on the compute stream, into two alternating device buffers. Each chunk's
+candidate pairs and areas land in one device result array (and are copied back to pinned host memory
+as they finish); the Jaccard reduction runs once over all pairs at the end, so J and J' are the same
+bits as for one call over the whole sets. Every step runs in the library's kernels (chunk-local pair
+indices are rebased on the device by sccg_rebase_pairs); the host only rebases the chunks' vertex
+offset arrays before copying them.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import MODE_PERSISTENT, SccgError, SCCG_ECAPACITY
+
+
+def _pin(a, dtype):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=dtype))
+    return t.pin_memory()
+
+
+class HostSet:
+    """A polygon set in pinned host memory (CSR, tiles non-decreasing), ready for chunked copies."""
+
+    def __init__(self, off, xy, tile):
+        self.off = _pin(off, np.int64)
+        self.xy = _pin(xy, np.int32)
+        self.tile = _pin(tile, np.int32)
+        self.n = self.off.numel() - 1
+        self.off_np = self.off.numpy()
+        self.tile_np = self.tile.numpy()
+
+    @classmethod
+    def from_polyset(cls, ps):
+        return cls(ps.off, ps.xy, ps.tile)
+
+    def range_of_tiles(self, t0: int, t1: int):
+        """Polygons [i0, i1) of tiles [t0, t1)."""
+        return (int(np.searchsorted(self.tile_np, t0, "left")), int(np.searchsorted(self.tile_np, t1, "left")))
+
+    def bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.off, self.xy, self.tile))
+
+
+class _Side:
+    """Device and staging buffers of one set for one of the two alternating chunk slots."""
+
+    def __init__(self, dev, max_n: int, max_v: int):
+        import torch
+        self.off = torch.empty(max_n + 1, dtype=torch.int64, device=dev)
+        self.xy = torch.empty(max(2 * max_v, 2), dtype=torch.int32, device=dev)
+        self.tile = torch.empty(max(max_n, 1), dtype=torch.int32, device=dev)
+        self.mbr = torch.empty((max(max_n, 1), 4), dtype=torch.int32, device=dev)
+        self.area = torch.empty(max(max_n, 1), dtype=torch.int64, device=dev)
+        self.h_off = torch.empty(max_n + 1, dtype=torch.int64).pin_memory()
+        self.h_tile = torch.empty(max(max_n, 1), dtype=torch.int32).pin_memory()
+
+
+class Pipeline:
+    """Chunked, copy-overlapped cross comparison of two HostSets on one device.
+
+    chunks: number of tile chunks (the copy of chunk k+1 overlaps the work on chunk k)."""
+
+    def __init__(self, ctx, A: HostSet, B: HostSet, n_tiles: int, chunks: int = 4, mode: int = MODE_PERSISTENT,
+                 initial_pairs: int | None = None):
+        import torch
+        self.ctx, self.A, self.B, self.mode = ctx, A, B, mode
+        self.dev = torch.device("cuda", ctx.device)
+        k = max(1, min(chunks, n_tiles))
+        edges = np.linspace(0, n_tiles, k + 1).round().astype(np.int64)
+        self.chunks = [(int(edges[i]), int(edges[i + 1])) for i in range(k) if edges[i + 1] > edges[i]]
+        self.ranges = [(A.range_of_tiles(t0, t1), B.range_of_tiles(t0, t1)) for t0, t1 in self.chunks]
+        max_na = max(a1 - a0 for (a0, a1), _ in self.ranges)
+        max_nb = max(b1 - b0 for _, (b0, b1) in self.ranges)
+        max_va = max(int(A.off_np[a1] - A.off_np[a0]) for (a0, a1), _ in self.ranges)
+        max_vb = max(int(B.off_np[b1] - B.off_np[b0]) for _, (b0, b1) in self.ranges)
+        self.slots = [(_Side(self.dev, max_na, max_va), _Side(self.dev, max_nb, max_vb)) for _ in range(2)]
+        self.copy_stream = torch.cuda.Stream(device=self.dev)
+        self.compute_stream = torch.cuda.Stream(device=self.dev)
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.freed = [torch.cuda.Event() for _ in range(2)]
+        self._alloc_results(initial_pairs if initial_pairs else max(A.n + B.n, 1 << 16))
+        self.h2d_bytes = A.bytes() + B.bytes()
+
+    def _alloc_results(self, cap: int, keep: int = 0):
+        import torch
+        old = getattr(self, "res", None)
+        res = {"pa": torch.empty(cap, dtype=torch.int32, device=self.dev),
+               "pb": torch.empty(cap, dtype=torch.int32, device=self.dev),
+               "inter": torch.empty(cap, dtype=torch.int64, device=self.dev),
+               "uni": torch.empty(cap, dtype=torch.int64, device=self.dev)}
+        host = {k: torch.empty(cap, dtype=v.dtype).pin_memory() for k, v in res.items()}
+        if old is not None and keep:
+            for k in res:
+                res[k][:keep].copy_(old[k][:keep])
+                host[k][:keep].copy_(self.host[k][:keep])
+        self.res, self.host, self.cap = res, host, cap
+
+    def _copy_in(self, slot: int, k: int):
+        """Host -> device copies of chunk k into `slot` on the copy stream."""
+        import torch
+        (a0, a1), (b0, b1) = self.ranges[k]
+        t0 = self.chunks[k][0]
+        self.copied[slot].synchronize()     # the slot's pinned staging buffers are free again
+        with torch.cuda.stream(self.copy_stream):
+            self.copy_stream.wait_event(self.freed[slot])
+            for side, S, i0, i1 in ((self.slots[slot][0], self.A, a0, a1), (self.slots[slot][1], self.B, b0, b1)):
+                n = i1 - i0
+                v0, v1 = int(S.off_np[i0]), int(S.off_np[i1])
+                np.subtract(S.off_np[i0:i1 + 1], v0, out=side.h_off.numpy()[:n + 1])
+                np.subtract(S.tile_np[i0:i1], t0, out=side.h_tile.numpy()[:n])
+                side.off[:n + 1].copy_(side.h_off[:n + 1], non_blocking=True)
+                side.tile[:n].copy_(side.h_tile[:n], non_blocking=True)
+                side.xy[:2 * (v1 - v0)].copy_(S.xy[2 * v0:2 * v1], non_blocking=True)
+            self.copied[slot].record(self.copy_stream)
+
+    def run(self):
+        """All candidate pairs (indices into the whole sets), their areas and the Jaccard result, in
+        host memory: (pa, pb, inter, uni) numpy views of pinned buffers that the next run overwrites
+        (copy them to keep them), and the Jaccard dict."""
+        import torch
+        ctx = self.ctx
+        cs = self.compute_stream
+        P = 0
+        self._copy_in(0, 0)
+        for k in range(len(self.chunks)):
+            slot = k % 2
+            if k + 1 < len(self.chunks):
+                self._copy_in(1 - slot, k + 1)
+            cs.wait_event(self.copied[slot])
+            sa, sb = self.slots[slot]
+            (a0, a1), (b0, b1) = self.ranges[k]
+            with torch.cuda.stream(cs):
+                A, B = ctx.prepare_sets([(sa.off[:a1 - a0 + 1], sa.xy, sa.tile[:a1 - a0], (sa.mbr, sa.area)),
+                                         (sb.off[:b1 - b0 + 1], sb.xy, sb.tile[:b1 - b0], (sb.mbr, sb.area))],
+                                        stream=cs)
+                while True:
+                    try:
+                        pa, pb = ctx.candidate_pairs(A, B, capacity=self.cap - P, stream=cs,
+                                                     out=(self.res["pa"][P:], self.res["pb"][P:]))
+                        break
+                    except SccgError as e:
+                        if e.status != SCCG_ECAPACITY:
+                            raise
+                        need = ctx.candidate_pairs(A, B, stream=cs)[0].numel()
+                        self._alloc_results(int((P + need) * 1.5) + 1, keep=P)
+                n = pa.numel()
+                if n:
+                    ctx.pair_areas(A, B, pa, pb, mode=self.mode, stream=cs,
+                                   out=(self.res["inter"][P:P + n], self.res["uni"][P:P + n]))
+                    ctx.rebase_pairs(pa, pb, a0, b0, stream=cs)
+                self.freed[slot].record(cs)
+                for key in ("pa", "pb", "inter", "uni"):
+                    self.host[key][P:P + n].copy_(self.res[key][P:P + n], non_blocking=True)
+            P += n
+        with torch.cuda.stream(cs):
+            J = ctx.jaccard(self.res["inter"][:P], self.res["uni"][:P], stream=cs)
+        cs.synchronize()
+        self.d2h_bytes = P * (4 + 4 + 8 + 8) + 48
+        return (self.host["pa"][:P].numpy(), self.host["pb"][:P].numpy(), self.host["inter"][:P].numpy(),
+                self.host["uni"][:P].numpy(), J)

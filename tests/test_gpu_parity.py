@@ -368,6 +368,28 @@ def test_empty_sets_and_no_pairs(ctx):
     assert P.cross_compare(ctx, E, E)["jaccard"]["n_pairs"] == 0
 
 
+def test_prepare_sets_matches_single_prepares(ctx, sccg):
+    """sccg_prepare_sets: several sets with one synchronisation, the same MBRs, areas and summaries
+    as one call per set; a set that fails validation is reported and left unprepared."""
+    w = W.single_tile(seed=4, n=300)
+    dev = torch.device("cuda")
+    specs = [(torch.from_numpy(P_.off).to(dev), torch.from_numpy(P_.xy).to(dev), torch.from_numpy(P_.tile).to(dev),
+              None) for P_ in (w.A, w.B, w.A)]
+    many = ctx.prepare_sets(specs)
+    for d, P_ in zip(many, (w.A, w.B, w.A)):
+        one = ctx.upload(P_)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(d.area.cpu().numpy(), one.area.cpu().numpy())
+        np.testing.assert_array_equal(d.mbr.cpu().numpy(), one.mbr.cpu().numpy())
+        assert (d.c.max_nv, d.c.max_extent, d.c.n_tiles) == (one.c.max_nv, one.c.max_extent, one.c.n_tiles)
+        assert d.c.reserved == one.c.reserved
+    bad = W.from_rings([[[0, 0], [1, 1]]])
+    specs.insert(1, (torch.from_numpy(bad.off).to(dev), torch.from_numpy(bad.xy).to(dev), None, None))
+    with pytest.raises(sccg.SccgError) as e:
+        ctx.prepare_sets(specs)
+    assert e.value.status == 1
+
+
 # ------------------------------------------------------------------------------- errors
 
 def test_invalid_inputs_rejected_on_the_host(ctx, sccg):
