@@ -70,6 +70,8 @@ def _load():
             lib.oracle_polygon_areas.restype = None
             lib.oracle_candidate_pairs.argtypes = [P, P, I64, P, P, I64, P, P, I64]
             lib.oracle_candidate_pairs.restype = I64
+            lib.oracle_touches.argtypes = [P, I64, P, I64]
+            lib.oracle_touches.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -205,3 +207,30 @@ def cross_compare(A, B, method: str = "brute", nthreads: int | None = None):
     inter, uni = pair_areas(A, B, pa, pb, method, nthreads)
     return dict(area_a=area_a, area_b=area_b, mbr_a=mbr_a, mbr_b=mbr_b, pa=pa, pb=pb,
                 inter=inter, uni=uni, jaccard=jaccard(inter, uni))
+
+
+# ---------------------------------------------------------------------------- other operators
+
+def touches(ring_p, ring_q) -> bool:
+    """ST_Touches by the rule given with the other operators of Sec. 5: no edge crossing, no vertex
+    of one strictly within the other, some vertex of one on an edge of the other."""
+    a, b = _ring(ring_p), _ring(ring_q)
+    return bool(_load().oracle_touches(_ptr(a), a.size // 2, _ptr(b), b.size // 2))
+
+
+def touches_pairs(A, B, pa, pb):
+    """touches() for every pair (A polygon pa[k], B polygon pb[k]) -> uint8 [n]."""
+    out = np.zeros(len(pa), dtype=np.uint8)
+    for k, (i, j) in enumerate(zip(np.asarray(pa), np.asarray(pb))):
+        ra = A.xy[2 * A.off[i]: 2 * A.off[i + 1]]
+        rb = B.xy[2 * B.off[j]: 2 * B.off[j + 1]]
+        out[k] = touches(ra, rb)
+    return out
+
+
+def contains_flags(area_a, area_b, pa, pb, inter):
+    """ST_Contains as Sec. 5 states it, on pixel areas: bit 0 = the A polygon contains the B polygon
+    (||p n q|| = ||q|| > 0), bit 1 = the B polygon contains the A polygon (||p n q|| = ||p|| > 0)."""
+    pa, pb, inter = (np.asarray(x, dtype=np.int64) for x in (pa, pb, inter))
+    aa, ab = np.asarray(area_a)[pa], np.asarray(area_b)[pb]
+    return (((inter == ab) & (ab > 0)).astype(np.uint8) | (((inter == aa) & (aa > 0)).astype(np.uint8) << 1))

@@ -294,3 +294,78 @@ i64 oracle_candidate_pairs(const int32_t* mbr_a, const int32_t* tile_a, i64 na,
     }
     return cnt;
 }
+
+/* ------------------------------------------------------------------------------------------- */
+/* ST_Touches by the rule stated with the other operators of Sec. 5 ("Implications of PixelBox    */
+/* to other spatial operators"): two polygons touch when no edge of one crosses an edge of the    */
+/* other, no vertex of one lies within the other, and at least one vertex of one lies on an edge  */
+/* of the other. Read exactly, with integer orientation tests (|coordinates| <= 2^28, products    */
+/* below 2^62): "crosses" = the two segments' interiors cross at one point (each segment's        */
+/* endpoints strictly on opposite sides of the other's line); "lies within" = strictly inside by  */
+/* the even-odd rule and on no edge; "lies on an edge" = on the closed segment.                   */
+/* ------------------------------------------------------------------------------------------- */
+static int orient_sign(i64 ax, i64 ay, i64 bx, i64 by, i64 cx, i64 cy)
+{
+    const i64 v = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    return (v > 0) - (v < 0);
+}
+
+static int on_segment(i64 ax, i64 ay, i64 bx, i64 by, i64 px, i64 py)
+{
+    if (orient_sign(ax, ay, bx, by, px, py) != 0) return 0;
+    return px >= (ax < bx ? ax : bx) && px <= (ax < bx ? bx : ax) && py >= (ay < by ? ay : by) &&
+           py <= (ay < by ? by : ay);
+}
+
+/* 1 if (px, py) is on the boundary of the ring, else 0. */
+static int on_boundary(const int32_t* xy, i64 nv, i64 px, i64 py)
+{
+    for (i64 e = 0; e < nv; ++e) {
+        const i64 f = (e + 1 == nv) ? 0 : e + 1;
+        if (on_segment(xy[2 * e], xy[2 * e + 1], xy[2 * f], xy[2 * f + 1], px, py)) return 1;
+    }
+    return 0;
+}
+
+/* Even-odd parity of a point not on the boundary: count edges whose half-open y-range
+ * [min y, max y) contains py and whose x at height py is greater than px. */
+static int point_inside(const int32_t* xy, i64 nv, i64 px, i64 py)
+{
+    int par = 0;
+    for (i64 e = 0; e < nv; ++e) {
+        const i64 f = (e + 1 == nv) ? 0 : e + 1;
+        i64 ax = xy[2 * e], ay = xy[2 * e + 1], bx = xy[2 * f], by = xy[2 * f + 1];
+        if (ay > by) { i64 t = ax; ax = bx; bx = t; t = ay; ay = by; by = t; }
+        if (!(ay <= py && py < by)) continue;
+        /* the edge's x at height py, ax + (py - ay)(bx - ax)/(by - ay), exceeds px; by > ay here */
+        if ((px - ax) * (by - ay) < (py - ay) * (bx - ax)) par ^= 1;
+    }
+    return par;
+}
+
+int oracle_touches(const int32_t* xp, i64 np, const int32_t* xq, i64 nq)
+{
+    int vertex_on_edge = 0;
+    for (i64 e = 0; e < np; ++e) {
+        const i64 f = (e + 1 == np) ? 0 : e + 1;
+        const i64 ax = xp[2 * e], ay = xp[2 * e + 1], bx = xp[2 * f], by = xp[2 * f + 1];
+        for (i64 g = 0; g < nq; ++g) {
+            const i64 h = (g + 1 == nq) ? 0 : g + 1;
+            const i64 cx = xq[2 * g], cy = xq[2 * g + 1], dx = xq[2 * h], dy = xq[2 * h + 1];
+            const int o1 = orient_sign(ax, ay, bx, by, cx, cy), o2 = orient_sign(ax, ay, bx, by, dx, dy);
+            const int o3 = orient_sign(cx, cy, dx, dy, ax, ay), o4 = orient_sign(cx, cy, dx, dy, bx, by);
+            if (o1 * o2 < 0 && o3 * o4 < 0) return 0;            /* edges cross */
+        }
+    }
+    for (int side = 0; side < 2; ++side) {
+        const int32_t* u = side ? xq : xp;
+        const int32_t* w = side ? xp : xq;
+        const i64 nu = side ? nq : np, nw = side ? np : nq;
+        for (i64 k = 0; k < nu; ++k) {
+            const i64 px = u[2 * k], py = u[2 * k + 1];
+            if (on_boundary(w, nw, px, py)) { vertex_on_edge = 1; continue; }
+            if (point_inside(w, nw, px, py)) return 0;           /* a vertex within the other */
+        }
+    }
+    return vertex_on_edge;
+}

@@ -255,3 +255,71 @@ def test_jaccard_pairs_with_zero_intersection_are_excluded():
     assert J["n_nonzero"] == 2 and J["sum_inter"] == 8 and J["sum_union"] == 16
     assert J["J"] == 0.5 and J["Jprime"] == 0.5
     assert O.jaccard(np.zeros(3, np.int64), np.ones(3, np.int64))["J"] == 0.0
+
+
+# ------------------------------------------------------------------ other operators (Sec. 5)
+
+SQ = [[0, 0], [4, 0], [4, 4], [0, 4]]
+
+
+@pytest.mark.parametrize("other,expect", [
+    ([[4, 0], [8, 0], [8, 4], [4, 4]], True),      # shared edge
+    ([[4, 4], [8, 4], [8, 8], [4, 8]], True),      # shared corner only
+    ([[4, 2], [7, 0], [7, 4]], True),              # a vertex on an edge
+    ([[2, 2], [6, 2], [6, 6], [2, 6]], False),     # overlap: edges cross
+    ([[1, 1], [2, 1], [2, 2], [1, 2]], False),     # inside: vertices within
+    ([[5, 0], [8, 0], [8, 4], [5, 4]], False),     # disjoint
+    ([[2, -1], [3, -1], [3, 5], [2, 5]], False),   # a strip through: edges cross
+])
+def test_touches_hand_cases(other, expect):
+    assert O.touches(SQ, other) is expect
+    assert O.touches(other, SQ) is expect
+
+
+def test_touches_rectangles_closed_form():
+    """Axis-aligned rectangles, closed form of the stated rule. Geometrically they touch when their
+    closed boxes meet and their interiors do not (overlaps in x and y >= 0, one of them 0). The rule
+    as stated also reports a touch when the interiors overlap but no corner of either lies strictly
+    inside the other and no edges cross properly, which for rectangles happens exactly when their
+    x-ranges or their y-ranges are equal (e.g. one inside the other along two shared edges)."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    for _ in range(600):
+        a = np.sort(rng.integers(0, 12, 2)); b = np.sort(rng.integers(0, 12, 2))
+        c = np.sort(rng.integers(0, 12, 2)); d = np.sort(rng.integers(0, 12, 2))
+        if a[0] == a[1] or b[0] == b[1] or c[0] == c[1] or d[0] == d[1]:
+            continue
+        p = [[a[0], b[0]], [a[1], b[0]], [a[1], b[1]], [a[0], b[1]]]
+        q = [[c[0], d[0]], [c[1], d[0]], [c[1], d[1]], [c[0], d[1]]]
+        ox = min(a[1], c[1]) - max(a[0], c[0])
+        oy = min(b[1], d[1]) - max(b[0], d[0])
+        geometric = ox >= 0 and oy >= 0 and (ox == 0 or oy == 0)
+        same_range = (a[0] == c[0] and a[1] == c[1]) or (b[0] == d[0] and b[1] == d[1])
+        expect = geometric or (ox > 0 and oy > 0 and same_range)
+        assert O.touches(p, q) is bool(expect), (p, q)
+
+
+def test_touches_symmetric_and_translation_invariant():
+    rng = np.random.Generator(np.random.PCG64(32))
+    x, y, c = W.star_rings(rng, rng.uniform(0, 60, 40), rng.uniform(0, 60, 40), rng.uniform(8, 30, 40),
+                           rng.integers(3, 12, 40))
+    off = np.concatenate([[0], np.cumsum(c)])
+    rings = [np.stack([x[off[i]:off[i + 1]], y[off[i]:off[i + 1]]], 1) for i in range(40)]
+    for i in range(0, 40, 2):
+        p, q = rings[i], rings[i + 1]
+        t = O.touches(p, q)
+        assert O.touches(q, p) == t
+        assert O.touches(p + [17, -5], q + [17, -5]) == t
+
+
+def test_contains_flags_rectangles():
+    """ST_Contains from areas: rectangle q inside rectangle p (closed form) <=> ||p n q|| = ||q||."""
+    ra = [[[0, 0], [10, 0], [10, 10], [0, 10]], [[20, 0], [24, 0], [24, 4], [20, 4]]]
+    rb = [[[2, 2], [5, 2], [5, 7], [2, 7]], [[8, 8], [12, 8], [12, 12], [8, 12]], [[20, 0], [24, 0], [24, 4], [20, 4]],
+          [[-5, -5], [30, -5], [30, 30], [-5, 30]]]
+    A, B = W.from_rings(ra), W.from_rings(rb)
+    area_a, _ = O.polygon_areas(A.off, A.xy)
+    area_b, _ = O.polygon_areas(B.off, B.xy)
+    pa = np.array([0, 0, 1, 0, 1]); pb = np.array([0, 1, 2, 3, 3])
+    inter, _ = O.pair_areas(A, B, pa, pb)
+    f = O.contains_flags(area_a, area_b, pa, pb, inter)
+    assert list(f) == [1, 0, 3, 2, 2]
