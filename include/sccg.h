@@ -117,7 +117,10 @@ typedef struct sccg_polyset {
  * itself, which equals the shoelace area on pixel-aligned rectilinear polygons and is the value
  * that makes ||p u q|| = ||p|| + ||q|| - ||p n q|| exact for every polygon).
  * Validates the set (>= 3 vertices, coordinate bounds, tile order) and fills the host summary
- * fields; SYNCHRONISES the stream once to read the validation result back.
+ * fields; SYNCHRONISES the stream once to read the validation result back. With the default
+ * area method, polygons of 1024 or more vertices get their areas after that synchronisation, from a
+ * temporary band index in context scratch (kernels queued on the stream; the areas are ready when
+ * the stream reaches them).
  * Returns SCCG_EINVAL or SCCG_ERANGE for invalid sets (mbr/area contents then unspecified). */
 int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream);
 
@@ -223,6 +226,22 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                    const int32_t* pa, const int32_t* pb, int64_t n_pairs,
                    int64_t* inter, int64_t* uni, sccg_jaccard_result* out, void* stream);
 
+
+/* Other spatial operators through the same machinery (Sec. 5, "Implications of PixelBox to other
+ * spatial operators"; device arrays, asynchronous, both sets prepared):
+ * sccg_contains: ST_Contains from the pixel areas, as the paper states it: out[k] bit 0 is set when
+ *   the A polygon contains the B polygon (inter[k] = ||q|| > 0), bit 1 when the B polygon contains
+ *   the A polygon (inter[k] = ||p|| > 0); inter from sccg_pair_areas. 0xff for invalid pairs.
+ * sccg_touches: ST_Touches by the paper's rule, in exact integer geometry on the vertex rings: 1 when
+ *   no edge of one crosses an edge of the other (segment interiors crossing at one point), no vertex
+ *   of one lies strictly within the other (even-odd, not on its boundary) and some vertex of one lies
+ *   on an edge of the other; else 0 (0xff for invalid pairs). The rule also reports a touch for
+ *   polygons whose interiors overlap without any vertex strictly inside or any proper crossing
+ *   (e.g. one inside the other along shared edges). O(n_p n_q) per pair, one warp per pair. */
+int sccg_contains(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa, const int32_t* pb,
+                  const int64_t* inter, int64_t n_pairs, uint8_t* out, void* stream);
+int sccg_touches(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa, const int32_t* pb,
+                 int64_t n_pairs, uint8_t* out, void* stream);
 
 /* Add base_a to pa[k] and base_b to pb[k] for k < n_pairs: turns the candidate pairs of a chunk of
  * tiles (polygon indices local to the chunk's sub-sets) into indices of the whole sets, for a

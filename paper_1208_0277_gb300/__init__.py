@@ -293,6 +293,24 @@ class Context:
         self._check(self.lib.sccg_jaccard(self.h, _ptr(inter) if n else None, _ptr(uni) if n else None, n,
                                           ctypes.c_void_p(out.data_ptr()), _stream(stream)), "sccg_jaccard")
 
+    def contains(self, A: DevicePolySet, B: DevicePolySet, pa, pb, inter, stream=None):
+        """ST_Contains flags (uint8 device tensor): bit 0 A contains B, bit 1 B contains A."""
+        import torch
+        n = pa.numel()
+        out = torch.empty(max(n, 1), dtype=torch.uint8, device=pa.device)
+        self._check(self.lib.sccg_contains(self.h, ctypes.byref(A.c), ctypes.byref(B.c), _ptr(pa), _ptr(pb),
+                                           _ptr(inter), n, _ptr(out), _stream(stream)), "sccg_contains")
+        return out[:n]
+
+    def touches(self, A: DevicePolySet, B: DevicePolySet, pa, pb, stream=None):
+        """ST_Touches (uint8 device tensor, 1 = touch) by the rule of Sec. 5."""
+        import torch
+        n = pa.numel()
+        out = torch.empty(max(n, 1), dtype=torch.uint8, device=pa.device)
+        self._check(self.lib.sccg_touches(self.h, ctypes.byref(A.c), ctypes.byref(B.c), _ptr(pa), _ptr(pb), n,
+                                          _ptr(out), _stream(stream)), "sccg_touches")
+        return out[:n]
+
     def rebase_pairs(self, pa, pb, base_a: int, base_b: int, stream=None):
         """In place on the device: pa += base_a, pb += base_b."""
         n = pa.numel()

@@ -26,7 +26,7 @@ EXPORTS = [
     "sccg_ctx_get_params", "sccg_last_error", "sccg_prepare", "sccg_candidate_pairs",
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
     "sccg_jaccard_static", "sccg_work_counters", "sccg_build_bands", "sccg_gather_pairs",
-    "sccg_jaccard_segments", "sccg_rebase_pairs", "sccg_prepare_sets",
+    "sccg_jaccard_segments", "sccg_rebase_pairs", "sccg_prepare_sets", "sccg_contains", "sccg_touches",
 ]
 
 _lock = threading.Lock()
@@ -123,6 +123,8 @@ def load(path: str | None = None):
             "sccg_jaccard_static": ([V, V, I64, V, V], I),
             "sccg_build_bands": ([V, PS, V, I64, V], I),
             "sccg_rebase_pairs": ([V, V, V, I64, I64, I64, V], I),
+            "sccg_contains": ([V, PS, PS, V, V, V, I64, V, V], I),
+            "sccg_touches": ([V, PS, PS, V, V, I64, V, V], I),
             "sccg_work_counters": ([V, ctypes.POINTER(ctypes.c_uint64), I], I),
         }
         for name, (args, res) in sig.items():

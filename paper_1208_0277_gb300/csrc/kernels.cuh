@@ -40,6 +40,8 @@ struct PrepStats {
     int n_tiles;
     long long first_bad;
     unsigned long long band_bytes;    // sum of the band index block sizes
+    unsigned deferred;                // polygons listed for a second kernel (area not yet written)
+    unsigned pad;
 };
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
@@ -68,6 +70,7 @@ __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCoun
 // lists) and int cur[nb] (fill cursors), padded to 16 bytes; int4 ent[boff[nb]].
 // ----------------------------------------------------------------------------------------------
 constexpr int kBandShift = 5;
+static_assert((1 << kBandShift) <= 32, "a band's rows are counted one lane per row");
 #ifndef SCCG_BAND_MIN_VERTICES
 #define SCCG_BAND_MIN_VERTICES 1024
 #endif
@@ -128,26 +131,16 @@ struct PrepArgs {
     int words;              // as AreasArgs::words
 };
 
-// Per-warp shared memory slice of k_prepare: the PixelBox buffers and, with SCAN, the by-rows
-// buffers in the same bytes.
-template <int CAP, int STK, bool SCAN>
-__host__ __device__ constexpr size_t prep_slice()
-{
-    return (SCAN && sizeof(ScanSmem) > sizeof(WarpSmem<CAP, STK>)) ? sizeof(ScanSmem) : sizeof(WarpSmem<CAP, STK>);
-}
-
-// SCAN: ||p|| by rows (area_scan), except that a polygon whose window holds fewer than T pixels
-// and whose edges fit the buffer is pixelized directly (PixelBox's one-leaf case, cheaper for
-// small windows). Otherwise by PixelBox on the polygon alone, deferring polygons with more than
-// defer_above vertices to k_prepare_big.
+// SCAN: a polygon whose window holds fewer than T pixels and whose edges fit the buffer is pixelized
+// here (PixelBox's one-leaf case, cheapest for small windows); every other one is listed for
+// k_area_bands (by rows). Otherwise by PixelBox on the polygon alone, deferring polygons with more
+// than defer_above vertices to k_prepare_big.
 template <int CAP, int STK, bool COUNT, bool SCAN>
 __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    char* slice = reinterpret_cast<char*>(smem4) + (size_t)warp * prep_slice<CAP, STK, SCAN>();
-    WarpSmem<CAP, STK>& S = *reinterpret_cast<WarpSmem<CAP, STK>*>(slice);
-    ScanSmem& SS = *reinterpret_cast<ScanSmem*>(slice);
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
@@ -178,13 +171,11 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
                 e = kErrRange;
         }
         uint32_t area = 0;
-        const bool defer = !SCAN && e == 0 && a.defer_above > 0 && nvl > a.defer_above;
-        if (defer && lane == 0) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
+        // SCAN: every polygon counted by rows is deferred to k_area_bands; otherwise the large ones
         const bool by_rows = SCAN && ((long long)(x1 - x0) * (y1 - y0) >= a.T || nvl > CAP);
-        if (by_rows && e == 0 && x1 > x0 && y1 > y0) {
-            __syncwarp();
-            area = area_scan<COUNT>(v, (int)nvl, x0, y0, x1, y1, SS, lane, wc);
-        } else if (e == 0 && !defer && x1 > x0 && y1 > y0) {
+        const bool defer = e == 0 && (by_rows || (a.defer_above > 0 && nvl > a.defer_above));
+        if (defer && lane == 0) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
+        if (e == 0 && !defer && x1 > x0 && y1 > y0) {
             const int nv = (int)nvl;
             const bool res = nv <= CAP;
             __syncwarp();
@@ -337,13 +328,61 @@ __global__ void k_band_fill(long long n, const int64_t* off, const int32_t* xy, 
     }
 }
 
+// ||p|| of the polygons k_prepare deferred (list[0 .. *n_list)), by rows: one warp per polygon,
+// band by band. A polygon with a block in the band index (blob may be null) takes each band's rows
+// from the edges listed for that band (band_rows), so no band rescans the whole ring; the others
+// are counted from their rings (area_scan).
+template <bool COUNT>
+__global__ void SCCG_ITEM_BOUNDS k_area_bands(const int64_t* off, const int32_t* xy, const int4* mbr, const char* blob,
+                                              const int* list, const unsigned* n_list, int64_t* area,
+                                              WorkCounters* counters)
+{
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ScanSmem& S = reinterpret_cast<ScanSmem*>(smem4)[warp];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const long long nl = *n_list;
+    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + warp; j < nl; j += nwarps) {
+        const long long i = list[j];
+        const long long o0 = off[i];
+        const int nv = (int)(off[i + 1] - o0);
+        const int2* v = reinterpret_cast<const int2*>(xy) + o0;
+        const int4 m = mbr[i];
+        uint32_t acc = 0;
+        if (m.z > m.x && m.w > m.y) {
+            const long long at = blob ? reinterpret_cast<const long long*>(blob + sizeof(BandHead))[i] : -1;
+            if (at >= 0) {
+                const char* blk = blob + at;
+                const int nb = reinterpret_cast<const int*>(blk)[0];
+                const int* boff = reinterpret_cast<const int*>(blk) + 4;
+                const int4* ent = reinterpret_cast<const int4*>(blk + 16 + ((4LL * (2 * nb + 1) + 15) & ~15LL));
+                for (int b = 0; b < nb; ++b) {
+                    const int b0 = m.y + (b << kBandShift);
+                    const int nrows = min(1 << kBandShift, m.w - b0);
+                    if (nrows <= 0) break;
+                    acc += band_rows<COUNT>(RecordEdges{ent + boff[b], boff[b + 1] - boff[b]}, b0, nrows, m.x, m.z,
+                                            v, nv, S, lane, wc);
+                }
+                acc = warp_sum(acc);
+            } else {
+                acc = area_scan<COUNT>(v, nv, m.x, m.y, m.z, m.w, S, lane, wc);
+            }
+        }
+        if (lane == 0) area[i] = (int64_t)acc;
+    }
+    if (COUNT) flush_counters(counters, wc);
+}
+
 // The records of polygon block `blk` (polygon min y `miny`) that stage_culled would keep for the
 // window [x0, x1) x [y0, y1), read from the bands covering rows y0 .. y1 - 1 only. An edge listed
 // in several of those bands is taken from the first of them. Same return convention as
 // stage_culled. Whole warp, converged.
 __device__ __forceinline__ int stage_banded(const char* blk, int miny, int x0, int y0, int x1, int y1, int4* E,
-                                            float* R, int cap, int lane)
+                                            float* R, int cap, int lane, bool right, unsigned long long& flip)
 {
+    const bool rows64 = right && y1 - y0 <= 64;
+    unsigned long long fl = 0;
     const int* head = reinterpret_cast<const int*>(blk);
     const int nb = head[0];
     const int* boff = head + 4;
@@ -361,6 +400,10 @@ __device__ __forceinline__ int stage_banded(const char* blk, int miny, int x0, i
                 rec = ent[k];
                 const int first = max(b0, (rec.x - miny) >> kBandShift);
                 keep = (first == b) & (rec.x < y1) & (rec.x + rec.y > y0) & (max(rec.w, rec.w + rec.z) > x0);
+                if (keep && rows64 && min(rec.w, rec.w + rec.z) >= x1) {      // see stage_culled
+                    keep = false;
+                    fl ^= row_span_mask(max(rec.x, y0) - y0, min(rec.x + rec.y, y1) - y0);
+                }
             }
             const unsigned msk = __ballot_sync(kFull, keep);
             const int pos = cnt + __popc(msk & ((1u << lane) - 1u));
@@ -371,6 +414,11 @@ __device__ __forceinline__ int stage_banded(const char* blk, int miny, int x0, i
             cnt += __popc(msk);
         }
     }
+    if (right) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fl ^= __shfl_xor_sync(kFull, fl, o);
+    }
+    flip = fl;
     return cnt;
 }
 
@@ -503,9 +551,11 @@ __device__ __forceinline__ bool pair_here(const int4& A, const int4& B, const Ti
 }
 
 constexpr int kSmallPairs = 32;   // A polygons with at most this many pairs sort them in registers
+constexpr int kSerialCells = 64;  // A polygons probing more cells are counted by a whole CTA
 
-// One thread per A polygon: number of pairs; A polygons with more than kSmallPairs pairs are
-// listed for the CTA path.
+// One thread per A polygon: number of pairs. A polygons with more than kSmallPairs pairs, or whose
+// MBR covers more than kSerialCells cells (counted afterwards by k_probe_count_big), are listed for
+// the CTA paths.
 __global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long long* counts, int* big_list,
                                                      unsigned* big_n)
 {
@@ -514,6 +564,11 @@ __global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long lon
     int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
     long long cnt = 0;
     if (probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) {
+        if ((long long)(cx1 - cx0 + 1) * (cy1 - cy0 + 1) > kSerialCells) {
+            counts[a] = 0;
+            big_list[atomicAdd(big_n, 1u)] = (int)a;
+            return;
+        }
         for (int cy = cy0; cy <= cy1; ++cy)
             for (int cx = cx0; cx <= cx1; ++cx) {
                 const long long c = base + (long long)cy * g.gx + cx;
@@ -523,6 +578,40 @@ __global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long lon
     }
     counts[a] = cnt;
     if (cnt > kSmallPairs) big_list[atomicAdd(big_n, 1u)] = (int)a;
+}
+
+// One CTA per listed A polygon that covers more than kSerialCells cells: its pair count, cells
+// spread over the threads.
+__global__ void __launch_bounds__(256) k_probe_count_big(const ProbeArgs p, const int* __restrict__ big_list,
+                                                         const unsigned* __restrict__ big_n, long long* counts)
+{
+    __shared__ long long wsum[8];
+    const unsigned nbig = *big_n;
+    for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const long long a = big_list[bi];
+        int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
+        if (!probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) continue;    // uniform per CTA
+        const int ncx = cx1 - cx0 + 1;
+        const long long ncell = (long long)ncx * (cy1 - cy0 + 1);
+        if (ncell <= kSerialCells) continue;                                  // counted by k_probe_count
+        long long cnt = 0;
+        for (long long q = threadIdx.x; q < ncell; q += blockDim.x) {
+            const int cx = cx0 + (int)(q % ncx), cy = cy0 + (int)(q / ncx);
+            const long long c = base + (long long)cy * g.gx + cx;
+            for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e)
+                cnt += pair_here(A, p.mbrB[p.entries[e]], g, cx, cy);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long s = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wsum[w];
+            counts[a] = s;
+        }
+        __syncthreads();
+    }
 }
 
 // One thread per A polygon with at most kSmallPairs pairs: gather, sort by b, write at offs[a].
@@ -535,6 +624,7 @@ __global__ void __launch_bounds__(256) k_probe_write_small(const ProbeArgs p, co
     if (n == 0 || n > kSmallPairs) return;
     int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
     if (!probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) return;
+    if ((long long)(cx1 - cx0 + 1) * (cy1 - cy0 + 1) > kSerialCells) return;     // the CTA path writes it
     int buf[kSmallPairs];
     int k = 0;
     for (int cy = cy0; cy <= cy1; ++cy)
@@ -731,14 +821,18 @@ template <int CAP, int STK>
 __device__ __forceinline__ void stage_pair(PolyPair& pp, const char* bp, int minyp, const char* bq, int minyq,
                                            int x0, int y0, int x1, int y1, WarpSmem<CAP, STK>& S, int lane)
 {
-    const int cp = bp ? stage_banded(bp, minyp, x0, y0, x1, y1, S.ep, S.rp, CAP, lane)
-                      : stage_culled(pp.vp, pp.np, x0, y0, x1, y1, S.ep, S.rp, CAP, lane);
-    const int cq = bq ? stage_banded(bq, minyq, x0, y0, x1, y1, S.eq, S.rq, CAP, lane)
-                      : stage_culled(pp.vq, pp.nq, x0, y0, x1, y1, S.eq, S.rq, CAP, lane);
+    constexpr bool right = CAP > 64;     // see flip_of
+    unsigned long long fp = 0, fq = 0;
+    const int cp = bp ? stage_banded(bp, minyp, x0, y0, x1, y1, S.ep, S.rp, CAP, lane, right, fp)
+                      : stage_culled(pp.vp, pp.np, x0, y0, x1, y1, S.ep, S.rp, CAP, lane, right, fp);
+    const int cq = bq ? stage_banded(bq, minyq, x0, y0, x1, y1, S.eq, S.rq, CAP, lane, right, fq)
+                      : stage_culled(pp.vq, pp.nq, x0, y0, x1, y1, S.eq, S.rq, CAP, lane, right, fq);
     pp.rp_res = cp <= CAP;
     pp.rq_res = cq <= CAP;
     if (pp.rp_res) pp.np = cp;
     if (pp.rq_res) pp.nq = cq;
+    pp.fp = pp.rp_res ? fp : 0;   // a polygon read from its whole ring keeps every edge
+    pp.fq = pp.rq_res ? fq : 0;
 }
 
 template <int CAP, int STK, bool COUNT>
@@ -1004,6 +1098,94 @@ __global__ void k_rebase_pairs(int32_t* pa, int32_t* pb, long long n, int base_a
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         pa[i] += base_a;
         pb[i] += base_b;
+    }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Other operators through the same results (Sec. 5, implications of PixelBox for other spatial
+// operators): ST_Contains from the areas, ST_Touches from edge and vertex tests.
+// ----------------------------------------------------------------------------------------------
+// bit 0: the A polygon contains the B polygon (||p n q|| = ||q|| > 0); bit 1: the B polygon contains
+// the A polygon (||p n q|| = ||p|| > 0); 0xff for a pair whose indices or intersection are invalid.
+__global__ void k_contains(const int32_t* pa, const int32_t* pb, const int64_t* inter, const int64_t* areaA,
+                           const int64_t* areaB, long long nA, long long nB, long long n, uint8_t* out)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int ia = pa[k], ib = pb[k];
+        if (ia < 0 || ia >= nA || ib < 0 || ib >= nB || inter[k] < 0) { out[k] = 0xff; continue; }
+        const int64_t ap = areaA[ia], aq = areaB[ib], x = inter[k];
+        out[k] = (uint8_t)(((x == aq && aq > 0) ? 1 : 0) | ((x == ap && ap > 0) ? 2 : 0));
+    }
+}
+
+__device__ __forceinline__ int orient_sign64(long long ax, long long ay, long long bx, long long by, long long cx,
+                                             long long cy)
+{
+    const long long v = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+    return (v > 0) - (v < 0);
+}
+
+// One polygon's vertices (lane k: vertex base + k) against the other polygon's edges: whether an
+// edge of `w` crosses the edge starting at the lane's vertex properly, whether the vertex lies on an
+// edge of `w`, and its even-odd parity against `w` (half-open y-ranges). Whole warp (uniform nw).
+__device__ __forceinline__ void vertex_vs_ring(const int2* u, int nu, int k, const int2* w, int nw, bool& cross,
+                                               bool& on, int& par)
+{
+    const bool have = k < nu;
+    const int2 a = have ? u[k] : make_int2(0, 0);
+    const int2 b = have ? u[k + 1 == nu ? 0 : k + 1] : make_int2(0, 0);
+    for (int g = 0; g < nw; ++g) {
+        const int2 c = w[g];
+        const int2 d = w[g + 1 == nw ? 0 : g + 1];
+        if (!have) continue;
+        const int o1 = orient_sign64(a.x, a.y, b.x, b.y, c.x, c.y), o2 = orient_sign64(a.x, a.y, b.x, b.y, d.x, d.y);
+        const int o3 = orient_sign64(c.x, c.y, d.x, d.y, a.x, a.y), o4 = orient_sign64(c.x, c.y, d.x, d.y, b.x, b.y);
+        cross |= (o1 * o2 < 0) & (o3 * o4 < 0);
+        on |= (o3 == 0) & (a.x >= min(c.x, d.x)) & (a.x <= max(c.x, d.x)) & (a.y >= min(c.y, d.y)) &
+              (a.y <= max(c.y, d.y));
+        const int lo_y = min(c.y, d.y), hi_y = max(c.y, d.y);
+        if (lo_y <= a.y && a.y < hi_y) {
+            const int2 l = c.y < d.y ? c : d, h = c.y < d.y ? d : c;
+            par ^= ((long long)(a.x - l.x) * (h.y - l.y) < (long long)(a.y - l.y) * (h.x - l.x)) ? 1 : 0;
+        }
+    }
+}
+
+// ST_Touches by the stated rule: no proper edge crossing, no vertex of one strictly within the
+// other (even-odd, off its boundary), some vertex of one on an edge of the other. One warp per pair;
+// 1 / 0, 0xff for invalid indices. O(n_p n_q) per pair.
+__global__ void __launch_bounds__(256) k_touches(const int32_t* pa, const int32_t* pb, long long n, long long nA,
+                                                 long long nB, const int64_t* offA, const int32_t* xyA,
+                                                 const int64_t* offB, const int32_t* xyB, uint8_t* out)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nwarps) {
+        const int ia = pa[i], ib = pb[i];
+        if (ia < 0 || ia >= nA || ib < 0 || ib >= nB) {
+            if (lane == 0) out[i] = 0xff;
+            continue;
+        }
+        const int2* p = reinterpret_cast<const int2*>(xyA) + offA[ia];
+        const int2* q = reinterpret_cast<const int2*>(xyB) + offB[ib];
+        const int np = (int)(offA[ia + 1] - offA[ia]), nq = (int)(offB[ib + 1] - offB[ib]);
+        bool cross = false, inside = false, on_any = false;
+        for (int side = 0; side < 2 && !cross && !inside; ++side) {       // warp-uniform conditions
+            const int2* u = side ? q : p;
+            const int2* w = side ? p : q;
+            const int nu = side ? nq : np, nw = side ? np : nq;
+            for (int base = 0; base < nu; base += 32) {
+                bool cr = false, on = false;
+                int par = 0;
+                vertex_vs_ring(u, nu, base + lane, w, nw, cr, on, par);
+                const bool have = base + lane < nu;
+                cross |= __any_sync(kFull, have && cr);
+                inside |= __any_sync(kFull, have && !on && par);
+                on_any |= __any_sync(kFull, have && on);
+                if (cross || inside) break;
+            }
+        }
+        if (lane == 0) out[i] = (uint8_t)((!cross && !inside && on_any) ? 1 : 0);
     }
 }
 

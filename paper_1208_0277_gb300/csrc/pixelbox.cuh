@@ -83,10 +83,25 @@ __device__ __forceinline__ void stage_edges(const int2* v, int nv, int e0, int c
 // no R. Dropping it changes no crossing parity and no box position, so every count over the
 // window is unchanged. Returns the number of kept edges (warp-uniform); only the first `cap` are
 // stored, so a return value above `cap` means the caller must use the whole ring instead.
-__device__ __forceinline__ int stage_culled(const int2* v, int nv, int x0, int y0, int x1, int y1, int4* E,
-                                            float* R, int cap, int lane)
+//
+// Windows of at most 64 rows also drop the edges lying wholly on or right of x = x1: every pixel
+// centre of the window is strictly left of such an edge, so it crosses all of them in each row it
+// straddles and meets no box. Its effect is recorded instead in `flip` (bit r: the edges dropped
+// this way flip every pixel of row y0 + r an odd number of times), which the pixelization and the
+// box positions add back (row_flip).
+__device__ __forceinline__ unsigned long long row_span_mask(int r0, int r1)    // bits r0 .. r1-1, 0 <= r0 <= r1 <= 64
 {
+    const unsigned long long hi = r1 >= 64 ? ~0ull : ((1ull << r1) - 1ull);
+    const unsigned long long lo = (1ull << r0) - 1ull;
+    return hi & ~lo;
+}
+
+__device__ __forceinline__ int stage_culled(const int2* v, int nv, int x0, int y0, int x1, int y1, int4* E,
+                                            float* R, int cap, int lane, bool right, unsigned long long& flip)
+{
+    const bool rows64 = right && y1 - y0 <= 64;
     int cnt = 0;
+    unsigned long long fl = 0;
     for (int base = 0; base < nv; base += 32) {
         const int e = base + lane;
         bool keep = false;
@@ -99,6 +114,10 @@ __device__ __forceinline__ int stage_culled(const int2* v, int nv, int x0, int y
             if (b.y < a.y) { const int2 t = a; a = b; b = t; }
             const int dy = b.y - a.y;
             keep = (a.y < y1) & (b.y > y0) & (max(a.x, b.x) > x0);
+            if (keep && rows64 && min(a.x, b.x) >= x1) {
+                keep = false;
+                fl ^= row_span_mask(max(a.y, y0) - y0, min(b.y, y1) - y0);
+            }
             rec = make_int4(a.y, dy, b.x - a.x, a.x);
             rc = dy > 0 ? __frcp_rn((float)(2 * dy)) : 0.0f;
         }
@@ -110,7 +129,19 @@ __device__ __forceinline__ int stage_culled(const int2* v, int nv, int x0, int y
         }
         cnt += __popc(m);
     }
+    if (right) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fl ^= __shfl_xor_sync(kFull, fl, o);
+    }
+    flip = fl;
     return cnt;
+}
+
+// All ones when the dropped right-side edges flip row y of a window starting at row wy0.
+__device__ __forceinline__ uint32_t row_flip(unsigned long long flip, int y, int wy0)
+{
+    const int r = y - wy0;
+    return (r >= 0 && r < 64 && ((flip >> r) & 1ull)) ? 0xffffffffu : 0u;
 }
 
 // Parity bitmask of the 32 pixels (x0 + k, y), k = 0..31, against `cnt` staged edges.
@@ -183,13 +214,14 @@ __device__ __forceinline__ void box_scan(const int4* E, int cnt, int bx0, int by
 
 // Strip parity against a whole polygon: its staged edges when resident (nv <= cap), else chunk by
 // chunk re-staged into E/R. Whole warp, converged; `resident` is warp-uniform.
+// `flip`: the resident polygon's row flip (row_flip) for row y.
 template <bool COUNT>
 __device__ __forceinline__ uint32_t poly_strip(const int2* v, int nv, bool resident, int4* E, float* R, int cap,
-                                               int y, int x0, int lane, unsigned long long& cnt_edges)
+                                               int y, int x0, uint32_t flip, int lane, unsigned long long& cnt_edges)
 {
     if (resident) {
         if (COUNT) cnt_edges += (unsigned long long)nv;
-        return strip_parity(E, R, nv, y, x0);
+        return strip_parity(E, R, nv, y, x0) ^ flip;
     }
     uint32_t par = 0;
     for (int e0 = 0; e0 < nv; e0 += cap) {
@@ -205,14 +237,16 @@ __device__ __forceinline__ uint32_t poly_strip(const int2* v, int nv, bool resid
 }
 
 // Box position against a whole polygon (resident or chunked, as above): 0 outside, 1 inside, 2 hover.
+// `flip`: the resident polygon's row flip for row by0 (the reference centre's row).
 template <bool COUNT>
 __device__ __forceinline__ int poly_box(const int2* v, int nv, bool resident, int4* E, float* R, int cap,
-                                        int bx0, int by0, int bx1, int by1, int lane,
+                                        int bx0, int by0, int bx1, int by1, uint32_t flip, int lane,
                                         unsigned long long& cnt_edges)
 {
     bool meet = false;
     uint32_t par = 0;
     if (resident) {
+        par = flip & 1u;
         box_scan(E, nv, bx0, by0, bx1, by1, meet, par);
         if (COUNT) cnt_edges += (unsigned long long)nv;
     } else {
@@ -387,7 +421,17 @@ __device__ __forceinline__ void choose_split(int w, int h, int& gx, int& gy)
 struct PolyPair {
     const int2* vp; int np; bool rp_res;
     const int2* vq; int nq; bool rq_res;
+    unsigned long long fp, fq;   // row flips of the edges dropped right of the window (buffers > 64 edges)
 };
+
+// Right-side culling (stage_culled) is used by the kernels whose buffers hold more than 64 edges,
+// where large polygons' items carry many such edges; the 64-edge kernels keep them staged.
+template <int CAP>
+__device__ __forceinline__ uint32_t flip_of(unsigned long long f, int y, int wy0)
+{
+    if constexpr (CAP > 64) return row_flip(f, y, wy0);
+    else return 0u;
+}
 
 // Pixelize the leaf boxes held in the lanes' slots (Algorithm 1's pixelization branch, done as
 // 32-pixel row strips spread over the warp). Returns this lane's count of pixels inside every
@@ -433,13 +477,15 @@ __device__ __forceinline__ uint32_t pixelize_leaves(const PolyPair pp, WarpSmem<
         uint32_t in = UNION ? 0u : vmask;
         unsigned long long ce = 0;
         if (__any_sync(kFull, needP)) {
-            const uint32_t par = poly_strip<COUNT>(pp.vp, pp.np, pp.rp_res, S.ep, S.rp, CAP, y, xs, lane, ce);
+            const uint32_t par = poly_strip<COUNT>(pp.vp, pp.np, pp.rp_res, S.ep, S.rp, CAP, y, xs,
+                                                   flip_of<CAP>(pp.fp, y, wy0), lane, ce);
             if (needP) in = UNION ? (in | par) : (in & par);
             if (COUNT && needP) wc.pixel_edges += (unsigned long long)pp.np * valid;
         }
         if (TWO) {
             if (__any_sync(kFull, needQ)) {
-                const uint32_t par = poly_strip<COUNT>(pp.vq, pp.nq, pp.rq_res, S.eq, S.rq, CAP, y, xs, lane, ce);
+                const uint32_t par = poly_strip<COUNT>(pp.vq, pp.nq, pp.rq_res, S.eq, S.rq, CAP, y, xs,
+                                                       flip_of<CAP>(pp.fq, y, wy0), lane, ce);
                 if (needQ) in = UNION ? (in | par) : (in & par);
                 if (COUNT && needQ) wc.pixel_edges += (unsigned long long)pp.nq * valid;
             }
@@ -499,9 +545,9 @@ __device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0
                 for (int k = lane; k < nrr; k += 32) {
                     for (int j = 0; j < nw; ++j) {
                         uint32_t in = __funnelshift_lc(0xffffffffu, 0u, (unsigned)min(32, Wp - 32 * j));
-                        const uint32_t wp = xor_word(S.xp, k, nw, j);
+                        const uint32_t wp = xor_word(S.xp, k, nw, j) ^ flip_of<CAP>(pp.fp, r0 + k, 0);
                         if (TWO) {
-                            const uint32_t wq = xor_word(S.xq, k, nw, j);
+                            const uint32_t wq = xor_word(S.xq, k, nw, j) ^ flip_of<CAP>(pp.fq, r0 + k, 0);
                             in &= UNION ? (wp | wq) : (wp & wq);
                         } else {
                             in &= wp;
@@ -544,11 +590,13 @@ __device__ __forceinline__ uint32_t pixelbox(const PolyPair pp, int wx0, int wy0
         int posP = UNION ? 0 : 1, posQ = UNION ? 0 : 1;
         unsigned long long ce = 0;
         if (fl & 1) {
-            posP = poly_box<COUNT>(pp.vp, pp.np, pp.rp_res, S.ep, S.rp, CAP, ax0, ay0, ax1, ay1, lane, ce);
+            posP = poly_box<COUNT>(pp.vp, pp.np, pp.rp_res, S.ep, S.rp, CAP, ax0, ay0, ax1, ay1,
+                                   flip_of<CAP>(pp.fp, ay0, wy0), lane, ce);
             if (COUNT && mine) wc.boxes += 1;
         }
         if (TWO && (fl & 2)) {
-            posQ = poly_box<COUNT>(pp.vq, pp.nq, pp.rq_res, S.eq, S.rq, CAP, ax0, ay0, ax1, ay1, lane, ce);
+            posQ = poly_box<COUNT>(pp.vq, pp.nq, pp.rq_res, S.eq, S.rq, CAP, ax0, ay0, ax1, ay1,
+                                   flip_of<CAP>(pp.fq, ay0, wy0), lane, ce);
             if (COUNT && mine) wc.boxes += 1;
         }
         if (COUNT && mine) wc.box_edges += ce;

@@ -73,6 +73,99 @@ __device__ __forceinline__ uint32_t row_direct(const int2* v, int nv, int y, int
     return total;
 }
 
+// Edge sources for the row counting: the edges of a ring (closing edge included), or edge records
+// {ylo, dy, dx, xl} (a band of a band index). get() returns edge k with its lower endpoint first.
+struct RingEdges {
+    const int2* v;
+    int n;
+    __device__ __forceinline__ void get(int k, int& ylo, int& dy, int& dx, int& xl) const
+    {
+        const int f = (k + 1 == n) ? 0 : k + 1;
+        int2 a = v[k];
+        int2 b = v[f];
+        if (b.y < a.y) { const int2 t = a; a = b; b = t; }
+        ylo = a.y; dy = b.y - a.y; dx = b.x - a.x; xl = a.x;
+    }
+};
+
+struct RecordEdges {
+    const int4* e;
+    int n;
+    __device__ __forceinline__ void get(int k, int& ylo, int& dy, int& dx, int& xl) const
+    {
+        const int4 r = e[k];
+        ylo = r.x; dy = r.y; dx = r.z; xl = r.w;
+    }
+};
+
+// This lane's share of the inside pixels of rows b0 .. b0 + nrows - 1 (nrows <= 32), over columns
+// [x0, x1), from the edges of `src`, which must include every edge of the ring that straddles one of
+// those rows (more edges are harmless). A row crossed by more edges than one pass holds is counted
+// from the whole ring (row_direct). Whole warp, converged.
+template <bool COUNT, class Edges>
+__device__ __forceinline__ uint32_t band_rows(const Edges src, int b0, int nrows, int x0, int x1, const int2* ring,
+                                              int nring, ScanSmem& S, int lane, WorkCounters& wc)
+{
+    uint32_t acc = 0;
+    S.cnt[lane] = 0;
+    __syncwarp();
+    for (int base = 0; base < src.n; base += 32) {          // per-row counts, one edge per lane
+        const int e = base + lane;
+        if (e < src.n) {
+            int ylo, dy, dx, xl;
+            src.get(e, ylo, dy, dx, xl);
+            const int r1 = min(ylo + dy, b0 + nrows) - b0;
+            for (int q = max(ylo, b0) - b0; q < r1; ++q) atomicAdd(&S.cnt[q], 1);
+        }
+    }
+    __syncwarp();
+    const int c = S.cnt[lane];
+    int r = 0;
+    while (r < nrows) {
+        // the longest run of rows from r whose crossing values fit one pass
+        const int cm = (lane >= r && lane < nrows) ? c : 0;
+        int incl = cm;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const unsigned fit = __ballot_sync(kFull, lane >= r && lane < nrows && incl <= kScanEntries);
+        const int r2 = fit ? 32 - __clz(fit) : r;
+        if (r2 == r) {
+            // a single row with more crossings than a pass holds
+            const uint32_t t = row_direct(ring, nring, b0 + r, x0, x1, lane);
+            if (lane == 0) acc += t;
+            r += 1;
+            continue;
+        }
+        S.off[lane] = incl - cm;
+        S.cnt[lane] = 0;          // fill cursor
+        __syncwarp();
+        for (int base = 0; base < src.n; base += 32) {      // crossing values, one edge per lane
+            const int e = base + lane;
+            if (e < src.n) {
+                int ylo, dy, dx, xl;
+                src.get(e, ylo, dy, dx, xl);
+                const int q1 = min(ylo + dy, b0 + r2) - b0;
+                for (int q = max(ylo, b0 + r) - b0; q < q1; ++q)
+                    S.val[S.off[q] + atomicAdd(&S.cnt[q], 1)] = crossing_count(ylo, dy, dx, xl, b0 + q, x0);
+            }
+        }
+        __syncwarp();
+        if (lane >= r && lane < r2) {
+            acc += row_inside(S.val + S.off[lane], c);
+            if (COUNT) {
+                wc.scan_entries += (unsigned long long)c;
+                wc.scan_pairs += (unsigned long long)c * c;
+            }
+        }
+        __syncwarp();
+        r = r2;
+    }
+    return acc;
+}
+
 // ||p|| over the pixel window [x0, x1) x [y0, y1) (x0 at or left of every vertex), band by band
 // of 32 rows, one lane per row. Returns the warp-wide count (same in every lane). Whole warp,
 // converged; every loop before a collective has a warp-uniform trip count.
@@ -81,87 +174,8 @@ __device__ __forceinline__ uint32_t area_scan(const int2* v, int nv, int x0, int
                                               int lane, WorkCounters& wc)
 {
     uint32_t acc = 0;
-    for (int b0 = y0; b0 < y1; b0 += 32) {
-        const int nrows = min(32, y1 - b0);
-        S.cnt[lane] = 0;
-        __syncwarp();
-        for (int base = 0; base < nv; base += 32) {          // per-row counts, (edge, row) flattened
-            const int e = base + lane;
-            int r0 = 0, cnt = 0;
-            if (e < nv) {
-                const int f = (e + 1 == nv) ? 0 : e + 1;
-                const int ya = v[e].y, yb = v[f].y;
-                r0 = max(min(ya, yb), b0) - b0;
-                cnt = max(0, min(max(ya, yb), b0 + nrows) - b0 - r0);
-            }
-            int total;
-            const int excl = warp_excl(cnt, lane, total);
-            for (int t0 = 0; t0 < total; t0 += 32) {
-                const int t = t0 + lane;
-                const int own = flat_owner(excl, t);
-                const int ro = __shfl_sync(kFull, r0, own) + (t - __shfl_sync(kFull, excl, own));
-                if (t < total) atomicAdd(&S.cnt[ro], 1);
-            }
-        }
-        __syncwarp();
-        const int c = S.cnt[lane];
-        int r = 0;
-        while (r < nrows) {
-            // the longest run of rows from r whose crossing values fit one pass
-            const int cm = (lane >= r && lane < nrows) ? c : 0;
-            int incl = cm;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const unsigned fit = __ballot_sync(kFull, lane >= r && lane < nrows && incl <= kScanEntries);
-            const int r2 = fit ? 32 - __clz(fit) : r;
-            if (r2 == r) {
-                // a single row with more crossings than a pass holds
-                const uint32_t t = row_direct(v, nv, b0 + r, x0, x1, lane);
-                if (lane == 0) acc += t;
-                r += 1;
-                continue;
-            }
-            S.off[lane] = incl - cm;
-            S.cnt[lane] = 0;          // fill cursor
-            __syncwarp();
-            for (int base = 0; base < nv; base += 32) {      // crossing values, (edge, row) flattened
-                const int e = base + lane;
-                int2 a = make_int2(0, 0), b = make_int2(0, 0);
-                int q0 = 0, cnt = 0;
-                if (e < nv) {
-                    const int f = (e + 1 == nv) ? 0 : e + 1;
-                    a = v[e];
-                    b = v[f];
-                    if (b.y < a.y) { const int2 t = a; a = b; b = t; }
-                    q0 = max(a.y, b0 + r) - b0;
-                    cnt = max(0, min(b.y, b0 + r2) - b0 - q0);
-                }
-                int total;
-                const int excl = warp_excl(cnt, lane, total);
-                for (int t0 = 0; t0 < total; t0 += 32) {
-                    const int t = t0 + lane;
-                    const int own = flat_owner(excl, t);
-                    const int q = __shfl_sync(kFull, q0, own) + (t - __shfl_sync(kFull, excl, own));
-                    const int ay = __shfl_sync(kFull, a.y, own), ax = __shfl_sync(kFull, a.x, own);
-                    const int dy = __shfl_sync(kFull, b.y, own) - ay, dx = __shfl_sync(kFull, b.x, own) - ax;
-                    if (t < total) S.val[S.off[q] + atomicAdd(&S.cnt[q], 1)] = crossing_count(ay, dy, dx, ax, b0 + q, x0);
-                }
-            }
-            __syncwarp();
-            if (lane >= r && lane < r2) {
-                acc += row_inside(S.val + S.off[lane], c);
-                if (COUNT) {
-                    wc.scan_entries += (unsigned long long)c;
-                    wc.scan_pairs += (unsigned long long)c * c;
-                }
-            }
-            __syncwarp();
-            r = r2;
-        }
-    }
+    for (int b0 = y0; b0 < y1; b0 += 32)
+        acc += band_rows<COUNT>(RingEdges{v, nv}, b0, min(32, y1 - b0), x0, x1, v, nv, S, lane, wc);
     return warp_sum(acc);
 }
 

@@ -27,8 +27,9 @@ struct sccg_ctx {
     sccg_params params{};
     void* ws = nullptr;             // device scratch
     size_t ws_size = 0;
-    void* aux[2] = {nullptr, nullptr};  // separately growable scratch (candidate-pair grid cells, entries)
-    size_t aux_size[2] = {0, 0};
+    void* aux[3] = {nullptr, nullptr, nullptr};  // separately growable scratch (candidate-pair grid cells,
+                                                 // entries; prepare's temporary band index)
+    size_t aux_size[3] = {0, 0, 0};
     void* pinned = nullptr;         // small host-pinned staging area
     WorkCounters* counters = nullptr;   // device work counters (counting mode)
     int count_work = 0;
@@ -194,7 +195,7 @@ template <int CAP, bool SCAN>
 int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
-    const size_t smem = prep_slice<CAP, kStack, SCAN>() * wpc;
+    const size_t smem = warp_smem<CAP>() * wpc;
     const long long grid = grid_for(ctx, a.n, wpc, 64);
     auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN> : k_prepare<CAP, kStack, false, SCAN>;
     int r = set_smem(ctx, kfn, smem);
@@ -395,6 +396,33 @@ int jaccard_launch(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, long
     return SCCG_OK;
 }
 
+// Band index of set s into blob (at least band_bytes(s) bytes), scratch from `cv`. Asynchronous.
+int build_bands_into(sccg_ctx* ctx, const sccg_polyset* s, char* blob, long long bytes, Carve& cv, cudaStream_t st)
+{
+    const long long n = s->n;
+    const long long nb = (n + kScanBlock - 1) / kScanBlock + 1;
+    long long* size = cv.take<long long>(n + 1);
+    long long* boffs = cv.take<long long>(n + 1);
+    long long* bsum = cv.take<long long>(nb);
+    const int4* mbr = reinterpret_cast<const int4*>(s->mbr);
+    const unsigned gw = (unsigned)grid_for(ctx, n, 8, 16);      // 8 warps per CTA, one polygon per warp
+    k_band_sizes<<<gw, 256, 0, st>>>(n, s->off, s->xy, mbr, size);
+    SCCG_LAUNCHED(ctx, "k_band_sizes");
+    const int r = device_scan(ctx, size, n, boffs, bsum, st);
+    if (r) return r;
+    k_band_tab<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, size, boffs, blob, bytes);
+    SCCG_LAUNCHED(ctx, "k_band_tab");
+    k_band_fill<<<gw, 256, 0, st>>>(n, s->off, s->xy, mbr, blob);
+    SCCG_LAUNCHED(ctx, "k_band_fill");
+    ctx->launches += 3;
+    return SCCG_OK;
+}
+
+size_t band_build_scratch(long long n)
+{
+    return carve_size<long long>(n + 1) * 2 + carve_size<long long>((n + kScanBlock - 1) / kScanBlock + 1);
+}
+
 int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
@@ -582,7 +610,7 @@ int sccg_ctx_destroy(sccg_ctx* ctx)
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         if (ctx->ws) cudaFree(ctx->ws);
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 3; ++k)
             if (ctx->aux[k]) cudaFree(ctx->aux[k]);
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -645,7 +673,8 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
     if (!ctx || !sets || n_sets < 1 || n_sets > kMaxPrepSets) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    size_t need = carve_size<PrepStats>(n_sets) + carve_size<unsigned>(1);
+    size_t need = carve_size<PrepStats>(n_sets);
+    long long max_n = 0;
     for (int k = 0; k < n_sets; ++k) {
         sccg_polyset* s = sets + k;
         if (s->n < 0 || s->n > 0x7fffffffLL) return SCCG_EINVAL;
@@ -655,27 +684,30 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
         if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
         need += carve_size<int>(s->n + 1);
+        max_n = std::max<long long>(max_n, s->n);
     }
+    need += band_build_scratch(max_n);     // for the band index of deferred polygons, after the sync
     int r = ws_reserve(ctx, need);
     if (r) return r;
     Carve cv(ctx->ws);
     PrepStats* stats = cv.take<PrepStats>(n_sets);
-    unsigned* big_n = cv.take<unsigned>(1);
-    const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0};
+    int* big_lists[kMaxPrepSets];
+    const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0, 0};
     // the initial stats are written by a copy from pinned memory, kept ordered on the stream
     PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
     for (int k = 0; k < n_sets; ++k) hstats[k] = init;
     SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, n_sets * sizeof init, cudaMemcpyHostToDevice, st));
     for (int k = 0; k < n_sets; ++k) {
         const sccg_polyset* s = sets + k;
-        int* big_list = cv.take<int>(s->n + 1);
+        int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
+        unsigned* big_n = &stats[k].deferred;
         if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
+            // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
             r = launch_prepare<kCapSmall, true>(ctx, a, st);
             if (r) return r;
         } else if (s->n > 0) {
-            SCCG_CUDA(ctx, cudaMemsetAsync(big_n, 0, sizeof(unsigned), st));
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words};
             // polygons with more than kCapSmall vertices are listed and done with the larger buffers
@@ -685,6 +717,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
             if (r) return r;
         }
     }
+    const Carve after_lists = cv;        // scratch of the band builds below starts here
     SCCG_CUDA(ctx, cudaMemcpyAsync(hstats, stats, n_sets * sizeof init, cudaMemcpyDeviceToHost, st));
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
     int status = SCCG_OK;
@@ -696,6 +729,29 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         s->n_tiles = std::max(res.n_tiles, s->n > 0 ? 1 : 0);
         s->band_bytes = res.band_bytes ? band_head_bytes(s->n) + (long long)res.band_bytes : 0;
         s->bands = nullptr;
+        if (!res.err && res.deferred && ctx->params.area_method == SCCG_AREA_ROWS) {
+            // areas of the deferred polygons by rows; those with 1024 or more vertices from a
+            // temporary band index
+            int rr = SCCG_OK;
+            const char* blob = nullptr;
+            if (s->band_bytes) {
+                rr = aux_reserve(ctx, 2, (size_t)s->band_bytes);
+                Carve bcv = after_lists;
+                if (!rr) rr = build_bands_into(ctx, s, static_cast<char*>(ctx->aux[2]), s->band_bytes, bcv, st);
+                blob = static_cast<const char*>(ctx->aux[2]);
+            }
+            if (!rr) {
+                const int wpc = 4;
+                const size_t smem = sizeof(ScanSmem) * wpc;
+                auto kfn = ctx->count_work ? k_area_bands<true> : k_area_bands<false>;
+                const unsigned grid = (unsigned)((res.deferred + wpc - 1) / wpc);
+                kfn<<<grid, 32 * wpc, smem, st>>>(s->off, s->xy, reinterpret_cast<const int4*>(s->mbr), blob,
+                                                  big_lists[k], &stats[k].deferred, s->area, ctx->counters);
+                SCCG_LAUNCHED(ctx, "k_area_bands");
+                ctx->launches += 1;
+            }
+            if (rr && !status) status = rr;
+        }
         if (res.err & (kErrFewVertices | kErrTiles)) {
             snprintf(ctx->last_err, sizeof ctx->last_err,
                      "invalid polygon set %d (flags %d, first bad polygon %lld)", k, res.err, res.first_bad);
@@ -728,26 +784,11 @@ int sccg_build_bands(sccg_ctx* ctx, sccg_polyset* s, void* buf, int64_t bytes, v
     if (!buf || !is_device_ptr(buf) || reinterpret_cast<uintptr_t>(buf) % 16) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const long long n = s->n;
-    const long long nb = (n + kScanBlock - 1) / kScanBlock + 1;
-    int r = ws_reserve(ctx, carve_size<long long>(n + 1) * 2 + carve_size<long long>(nb));
+    int r = ws_reserve(ctx, band_build_scratch(s->n));
     if (r) return r;
     Carve cv(ctx->ws);
-    long long* size = cv.take<long long>(n + 1);
-    long long* boffs = cv.take<long long>(n + 1);
-    long long* bsum = cv.take<long long>(nb);
-    const int4* mbr = reinterpret_cast<const int4*>(s->mbr);
-    char* blob = static_cast<char*>(buf);
-    const unsigned gw = (unsigned)grid_for(ctx, n, 8, 16);      // 8 warps per CTA, one polygon per warp
-    k_band_sizes<<<gw, 256, 0, st>>>(n, s->off, s->xy, mbr, size);
-    SCCG_LAUNCHED(ctx, "k_band_sizes");
-    r = device_scan(ctx, size, n, boffs, bsum, st);
+    r = build_bands_into(ctx, s, static_cast<char*>(buf), s->band_bytes, cv, st);
     if (r) return r;
-    k_band_tab<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, size, boffs, blob, s->band_bytes);
-    SCCG_LAUNCHED(ctx, "k_band_tab");
-    k_band_fill<<<gw, 256, 0, st>>>(n, s->off, s->xy, mbr, blob);
-    SCCG_LAUNCHED(ctx, "k_band_fill");
-    ctx->launches += 3;
     s->bands = buf;
     return SCCG_OK;
 }
@@ -835,8 +876,9 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     const unsigned ga = (unsigned)((std::max(nA, 1LL) + 255) / 256);
     if (nA > 0) {
         k_probe_count<<<ga, 256, 0, st>>>(pr, counts, big_list, big_n);
+        k_probe_count_big<<<(unsigned)(2 * ctx->sm_count), 256, 0, st>>>(pr, big_list, big_n, counts);
         SCCG_LAUNCHED(ctx, "k_probe_count");
-        ctx->launches += 1;
+        ctx->launches += 2;
     }
     r = device_scan(ctx, counts, nA, offs, bsum, st);
     if (r) return r;
@@ -1014,6 +1056,38 @@ int sccg_rebase_pairs(sccg_ctx* ctx, int32_t* pa, int32_t* pb, int64_t n_pairs, 
     const unsigned grid = (unsigned)std::min<long long>((n_pairs + 255) / 256, 8LL * ctx->sm_count);
     k_rebase_pairs<<<grid, 256, 0, st>>>(pa, pb, n_pairs, (int)base_a, (int)base_b);
     SCCG_LAUNCHED(ctx, "k_rebase_pairs");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+int sccg_contains(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa, const int32_t* pb,
+                  const int64_t* inter, int64_t n_pairs, uint8_t* out, void* stream)
+{
+    if (!ctx || n_pairs < 0) return SCCG_EINVAL;
+    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
+    if (n_pairs == 0) return SCCG_OK;
+    if (!is_device_ptr(pa) || !is_device_ptr(pb) || !is_device_ptr(inter) || !is_device_ptr(out)) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = (unsigned)std::min<long long>((n_pairs + 255) / 256, 8LL * ctx->sm_count);
+    k_contains<<<grid, 256, 0, st>>>(pa, pb, inter, A->area, B->area, A->n, B->n, n_pairs, out);
+    SCCG_LAUNCHED(ctx, "k_contains");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+int sccg_touches(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa, const int32_t* pb,
+                 int64_t n_pairs, uint8_t* out, void* stream)
+{
+    if (!ctx || n_pairs < 0) return SCCG_EINVAL;
+    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
+    if (n_pairs == 0) return SCCG_OK;
+    if (!is_device_ptr(pa) || !is_device_ptr(pb) || !is_device_ptr(out)) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned grid = (unsigned)grid_for(ctx, n_pairs, 8, 16);
+    k_touches<<<grid, 256, 0, st>>>(pa, pb, n_pairs, A->n, B->n, A->off, A->xy, B->off, B->xy, out);
+    SCCG_LAUNCHED(ctx, "k_touches");
     ctx->launches += 1;
     return SCCG_OK;
 }
