@@ -19,7 +19,8 @@ A completer thread waits for each batch's event in order and resolves the jobs' 
 
 Admission: memory is bounded by construction (``slots`` x the slot buffers, checked against
 ``mem_budget_bytes`` when the server is built); a job larger than a slot is refused with
-``ValueError`` at submit time; otherwise jobs wait in the queue until a slot frees up.
+``ValueError`` at submit time; otherwise jobs wait in the queue until a slot frees up. A job whose
+future the client cancels before it is admitted to a batch is dropped.
 """
 from __future__ import annotations
 
@@ -136,7 +137,6 @@ class Server:
                     self.cv.wait(timeout=0.01)
                 if self.stop:
                     return
-                slot_id = self.free.popleft()
                 jobs, npairs = [], 0
                 while self.pending and len(jobs) < self.cap_jobs:
                     job, fut = self.pending[0]
@@ -144,8 +144,13 @@ class Server:
                     if npairs + n > self.cap_pairs:
                         break
                     self.pending.popleft()
+                    if not fut.set_running_or_notify_cancel():
+                        continue                     # cancelled by the client before admission
                     jobs.append((job, fut))
                     npairs += n
+                if not jobs:
+                    continue
+                slot_id = self.free.popleft()
             slot = self.slots[slot_id]
             k = len(jobs)
             src = np.array([j.p0 for j, _ in jobs], dtype=np.int64)

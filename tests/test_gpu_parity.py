@@ -258,6 +258,26 @@ def test_nosep_refuses_wide_polygons(sccg):
     assert e.value.status == 2
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_a_20000_vertex_polygon(sccg, mode):
+    """A rectilinear staircase of about 24,000 vertices (6,600 one-pixel columns) against small
+    polygons along it and against a shifted copy of itself: area, pairs and areas by the band index,
+    right-side culling and the overflow path, against the oracle's row-interval method."""
+    rng = np.random.Generator(np.random.PCG64(41))
+    big, heights = W.staircase_rings(rng, 1, max_cols=10_000, max_h=6, origin_span=1)
+    big = np.asarray(big[0])
+    assert len(big) >= 15_000
+    small, _ = W.staircase_rings(rng, 300, max_cols=12, max_h=12, origin_span=1)
+    shift = rng.integers(0, 9_000, 300)
+    small = [np.asarray(r) + [int(s), 0] for r, s in zip(small, shift)]
+    w = rings_workload([big] + small[:150], [big + [3, 1]] + small[150:])
+    c = sccg.Context(0, {"split_pixels": 1024})
+    g = gpu_run(c, w, mode=mode)
+    ref = O.cross_compare(w.A, w.B, method="rle")
+    assert_same(g, ref)
+    assert g["area_a"][0] == int(heights[0].sum())
+
+
 def test_batch_graph_replay_and_recapture(sccg):
     """sccg_batch_run: persistent areas + Jaccard captured once as a CUDA graph and replayed; a new
     pair list (other buffers) triggers a new capture. Results equal the oracle every time."""
@@ -279,6 +299,28 @@ def test_batch_graph_replay_and_recapture(sccg):
             J = c.read_jaccard(res)
             for k in ("sum_inter", "sum_union", "n_nonzero", "J", "Jprime"):
                 assert J[k] == ref["jaccard"][k], k
+
+
+def test_batch_graph_with_large_polygons(sccg):
+    """The graph form when polygons exceed 64 vertices: the big queue runs on the side stream (fork and
+    join inside the captured graph) with 128-edge buffers and the overflow kernel; replayed twice."""
+    c = sccg.Context(0, {"split_pixels": 256})
+    A_, B_ = medium_polygons(16, n=50), medium_polygons(17, n=50, kind="tissue")
+    A, B = c.upload(A_), c.upload(B_)
+    pa, pb = c.candidate_pairs(A, B)
+    inter = torch.full((pa.numel(),), -7, dtype=torch.int64, device="cuda")
+    uni = torch.full_like(inter, -7)
+    res = torch.zeros(48, dtype=torch.uint8, device="cuda")
+    ref = O.cross_compare(A_, B_, method="rle")
+    for _ in range(2):
+        inter.fill_(-7)
+        c.batch_run(A, B, pa, pb, (inter, uni), res)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(inter.cpu().numpy(), ref["inter"])
+        np.testing.assert_array_equal(uni.cpu().numpy(), ref["uni"])
+        J = c.read_jaccard(res)
+        for k in ("sum_inter", "sum_union", "n_nonzero", "J", "Jprime"):
+            assert J[k] == ref["jaccard"][k], k
 
 
 # ------------------------------------------------------------------------------- edge cases

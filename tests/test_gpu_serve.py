@@ -69,3 +69,24 @@ def test_oversized_job_is_refused(resident):
         srv.close()
     with pytest.raises(ValueError):
         serve.Server(A, B, pa, pb, slots=4, max_batch_pairs=1 << 20, mem_budget_bytes=1 << 20)
+
+
+def test_cancelled_jobs_are_dropped_and_the_server_keeps_serving(resident):
+    P, w, ctx, A, B, pa, pb, tpo = resident
+    from paper_1208_0277_gb300 import serve
+    srv = serve.Server(A, B, pa, pb, slots=1, max_batch_pairs=20_000, max_batch_jobs=16)
+    try:
+        rng = np.random.default_rng(3)
+        jobs = serve.draw_jobs(rng, tpo, 200, lo=20, hi=5000)
+        futs = [srv.submit(serve.Job(j.p0, j.p1, j.tile)) for j in jobs]
+        cancelled = [f.cancel() for f in futs[::2]]          # those still queued are cancelled
+        done = [f.result(timeout=120) for f in futs[1::2]]
+        assert any(cancelled)
+        pa_h, pb_h = pa.cpu().numpy().astype(np.int64), pb.cpu().numpy().astype(np.int64)
+        j = jobs[1]
+        ri, ru = O.pair_areas(w.A, w.B, pa_h[j.p0:j.p1], pb_h[j.p0:j.p1], method="rle")
+        np.testing.assert_array_equal(done[0].inter, ri)
+        again = srv.submit(serve.Job(jobs[0].p0, jobs[0].p1)).result(timeout=60)
+        assert len(again.inter) == jobs[0].p1 - jobs[0].p0
+    finally:
+        srv.close()
