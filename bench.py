@@ -113,8 +113,9 @@ def make_workload(config: int, seed: int, tiles: int):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the device code (the kernels whose DRAM traffic profiles/traffic.json records)."""
     h = hashlib.sha256()
-    for f in ("pixelbox.cuh", "scanline.cuh", "kernels.cuh", "sccg_api.cu"):
+    for f in ("pixelbox.cuh", "scanline.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_1208_0277_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

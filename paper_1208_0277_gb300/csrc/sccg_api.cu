@@ -697,25 +697,36 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
     PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
     for (int k = 0; k < n_sets; ++k) hstats[k] = init;
     SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, n_sets * sizeof init, cudaMemcpyHostToDevice, st));
+    // odd-numbered sets run on the side stream, beside the even ones (one fork, one join)
+    const bool two_streams = n_sets > 1;
+    if (two_streams) {
+        SCCG_CUDA(ctx, cudaEventRecord(ctx->fork_event, st));
+        SCCG_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->fork_event, 0));
+    }
     for (int k = 0; k < n_sets; ++k) {
         const sccg_polyset* s = sets + k;
         int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
         unsigned* big_n = &stats[k].deferred;
+        cudaStream_t sk = (two_streams && (k & 1)) ? ctx->side_stream : st;
         if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
-            r = launch_prepare<kCapSmall, true>(ctx, a, st);
+            r = launch_prepare<kCapSmall, true>(ctx, a, sk);
             if (r) return r;
         } else if (s->n > 0) {
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words};
             // polygons with more than kCapSmall vertices are listed and done with the larger buffers
-            r = launch_prepare<kCapSmall, false>(ctx, a, st);
+            r = launch_prepare<kCapSmall, false>(ctx, a, sk);
             if (r) return r;
-            r = launch_prepare_big<kCapBig>(ctx, a, st);
+            r = launch_prepare_big<kCapBig>(ctx, a, sk);
             if (r) return r;
         }
+    }
+    if (two_streams) {
+        SCCG_CUDA(ctx, cudaEventRecord(ctx->join_event, ctx->side_stream));
+        SCCG_CUDA(ctx, cudaStreamWaitEvent(st, ctx->join_event, 0));
     }
     const Carve after_lists = cv;        // scratch of the band builds below starts here
     SCCG_CUDA(ctx, cudaMemcpyAsync(hstats, stats, n_sets * sizeof init, cudaMemcpyDeviceToHost, st));
