@@ -41,7 +41,7 @@ struct PrepStats {
     long long first_bad;
     unsigned long long band_bytes;    // sum of the band index block sizes
     unsigned deferred;                // polygons listed for a second kernel (area not yet written)
-    unsigned pad;
+    unsigned deferred_mid;            // ... for the one-leaf pass with mid-size buffers
 };
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
@@ -129,6 +129,9 @@ struct PrepArgs {
     int* big_list;
     unsigned* big_n;
     int words;              // as AreasArgs::words
+    int mid_cap;            // SCAN: small-window polygons with CAP < nv <= mid_cap are listed in mid_list
+    int* mid_list;
+    unsigned* mid_n;
 };
 
 // SCAN: a polygon whose window holds fewer than T pixels and whose edges fit the buffer is pixelized
@@ -171,10 +174,17 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
                 e = kErrRange;
         }
         uint32_t area = 0;
-        // SCAN: every polygon counted by rows is deferred to k_area_bands; otherwise the large ones
-        const bool by_rows = SCAN && ((long long)(x1 - x0) * (y1 - y0) >= a.T || nvl > CAP);
-        const bool defer = e == 0 && (by_rows || (a.defer_above > 0 && nvl > a.defer_above));
-        if (defer && lane == 0) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
+        // SCAN: a small window whose polygon has more than CAP (at most mid_cap) vertices goes to the
+        // one-leaf path with larger buffers (k_prepare_big over mid_list); every other polygon
+        // counted by rows is deferred to k_area_bands. Otherwise the large ones to k_prepare_big.
+        const bool small_win = (long long)(x1 - x0) * (y1 - y0) < a.T;
+        const bool mid = SCAN && e == 0 && small_win && nvl > CAP && nvl <= a.mid_cap;
+        const bool by_rows = SCAN && !mid && (!small_win || nvl > CAP);
+        const bool defer = e == 0 && (by_rows || mid || (a.defer_above > 0 && nvl > a.defer_above));
+        if (lane == 0 && defer) {
+            if (mid) a.mid_list[atomicAdd(a.mid_n, 1u)] = (int)i;
+            else a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
+        }
         if (e == 0 && !defer && x1 > x0 && y1 > y0) {
             const int nv = (int)nvl;
             const bool res = nv <= CAP;
@@ -988,7 +998,10 @@ __device__ __forceinline__ long long find_pair(const long long* ioff, long long 
     return lo;
 }
 
-constexpr int kItemChunk = 4;
+#ifndef SCCG_ITEM_CHUNK
+#define SCCG_ITEM_CHUNK 4
+#endif
+constexpr int kItemChunk = SCCG_ITEM_CHUNK;     // items a warp takes from a queue at a time
 
 // One work item: sub-window `sub` of pair i's window, cut into side x side items. With OVF, an item
 // whose window-culled edges do not fit the buffers is appended to the overflow list (for a kernel

@@ -683,7 +683,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
         if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
         if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
-        need += carve_size<int>(s->n + 1);
+        need += carve_size<int>(s->n + 1) * 2;
         max_n = std::max<long long>(max_n, s->n);
     }
     need += band_build_scratch(max_n);     // for the band index of deferred polygons, after the sync
@@ -706,17 +706,26 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
     for (int k = 0; k < n_sets; ++k) {
         const sccg_polyset* s = sets + k;
         int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
+        int* mid_list = cv.take<int>(s->n + 1);
         unsigned* big_n = &stats[k].deferred;
         cudaStream_t sk = (two_streams && (k & 1)) ? ctx->side_stream : st;
         if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
-                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
+                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words,
+                       kCapMid, mid_list, &stats[k].deferred_mid};
             r = launch_prepare<kCapSmall, true>(ctx, a, sk);
+            if (r) return r;
+            // small windows of polygons with 65..kCapMid vertices: one-leaf PixelBox, 128-edge buffers
+            PrepArgs am = a;
+            am.big_list = mid_list;
+            am.big_n = &stats[k].deferred_mid;
+            r = launch_prepare_big<kCapMid>(ctx, am, sk);
             if (r) return r;
         } else if (s->n > 0) {
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
-                       ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words};
+                       ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words,
+                       0, nullptr, nullptr};
             // polygons with more than kCapSmall vertices are listed and done with the larger buffers
             r = launch_prepare<kCapSmall, false>(ctx, a, sk);
             if (r) return r;
