@@ -42,6 +42,7 @@ struct PrepStats {
     unsigned long long band_bytes;    // sum of the band index block sizes
     unsigned deferred;                // polygons listed for a second kernel (area not yet written)
     unsigned deferred_mid;            // ... for the one-leaf pass with mid-size buffers
+    unsigned deferred_mid2;           // ... for the one-leaf pass with the next larger buffers
 };
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
@@ -132,6 +133,9 @@ struct PrepArgs {
     int mid_cap;            // SCAN: small-window polygons with CAP < nv <= mid_cap are listed in mid_list
     int* mid_list;
     unsigned* mid_n;
+    int mid2_cap;           // SCAN: ... with mid_cap < nv <= mid2_cap in mid2_list (0: none)
+    int* mid2_list;
+    unsigned* mid2_n;
 };
 
 // SCAN: a polygon whose window holds fewer than T pixels and whose edges fit the buffer is pixelized
@@ -179,10 +183,12 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
         // counted by rows is deferred to k_area_bands. Otherwise the large ones to k_prepare_big.
         const bool small_win = (long long)(x1 - x0) * (y1 - y0) < a.T;
         const bool mid = SCAN && e == 0 && small_win && nvl > CAP && nvl <= a.mid_cap;
-        const bool by_rows = SCAN && !mid && (!small_win || nvl > CAP);
-        const bool defer = e == 0 && (by_rows || mid || (a.defer_above > 0 && nvl > a.defer_above));
+        const bool mid2 = SCAN && e == 0 && small_win && nvl > a.mid_cap && nvl <= a.mid2_cap;
+        const bool by_rows = SCAN && !mid && !mid2 && (!small_win || nvl > CAP);
+        const bool defer = e == 0 && (by_rows || mid || mid2 || (a.defer_above > 0 && nvl > a.defer_above));
         if (lane == 0 && defer) {
             if (mid) a.mid_list[atomicAdd(a.mid_n, 1u)] = (int)i;
+            else if (mid2) a.mid2_list[atomicAdd(a.mid2_n, 1u)] = (int)i;
             else a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
         }
         if (e == 0 && !defer && x1 > x0 && y1 > y0) {
@@ -1001,15 +1007,28 @@ __device__ __forceinline__ long long find_pair(const long long* ioff, long long 
 #ifndef SCCG_ITEM_CHUNK
 #define SCCG_ITEM_CHUNK 4
 #endif
-constexpr int kItemChunk = SCCG_ITEM_CHUNK;     // items a warp takes from a queue at a time
+#ifndef SCCG_ITEM_CHUNK_MAX
+#define SCCG_ITEM_CHUNK_MAX 64
+#endif
+// Items a warp takes from a queue at a time: guided self-scheduling, a quarter of the remaining
+// items' share per warp, between these bounds (large takes early spread the pair search over many
+// items, small ones at the end keep the tail short).
+constexpr int kItemChunk = SCCG_ITEM_CHUNK;
+constexpr int kItemChunkMax = SCCG_ITEM_CHUNK_MAX;
+
+// Overflow list entries: pair index and sub-window, packed (no search needed to find the pair).
+__device__ __forceinline__ unsigned long long ovf_pack(long long i, long long sub)
+{
+    return ((unsigned long long)i << 32) | (unsigned long long)(uint32_t)sub;
+}
 
 // One work item: sub-window `sub` of pair i's window, cut into side x side items. With OVF, an item
 // whose window-culled edges do not fit the buffers is appended to the overflow list (for a kernel
 // with larger buffers) instead of being read chunk by chunk from the whole rings; when the list is
 // full the item is done here anyway. Whole warp, converged.
 template <int CAP, int STK, bool COUNT, bool OVF>
-__device__ __forceinline__ void do_item(const AreasArgs a, int side, const long long* nitems, long long i, long long it,
-                                        long long sub, long long* ovf_list, unsigned long long* ovf_n,
+__device__ __forceinline__ void do_item(const AreasArgs a, int side, const long long* nitems, long long i,
+                                        long long sub, unsigned long long* ovf_list, unsigned long long* ovf_n,
                                         long long ovf_cap, WarpSmem<CAP, STK>& S, int lane, WorkCounters& wc)
 {
     const int ia = a.pa[i], ib = a.pb[i];
@@ -1033,7 +1052,7 @@ __device__ __forceinline__ void do_item(const AreasArgs a, int side, const long 
         if (lane == 0) slot = atomicAdd(ovf_n, 1ull);
         slot = __shfl_sync(kFull, slot, 0);
         if ((long long)slot < ovf_cap) {
-            if (lane == 0) ovf_list[slot] = it;
+            if (lane == 0) ovf_list[slot] = ovf_pack(i, sub);
             return;
         }
     }
@@ -1053,7 +1072,7 @@ __device__ __forceinline__ void do_item(const AreasArgs a, int side, const long 
 template <int CAP, int STK, bool COUNT, bool OVF>
 __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int side, const long long* nitems,
                                                                const long long* ioff, unsigned long long* head,
-                                                               long long* ovf_list, unsigned long long* ovf_n,
+                                                               unsigned long long* ovf_list, unsigned long long* ovf_n,
                                                                long long ovf_cap)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
@@ -1061,32 +1080,37 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_persistent(const AreasArgs a, int 
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
     WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const long long total = ioff[a.n];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    long long seen = 0;                        // queue head at this warp's last take (<= the current one)
     for (;;) {
+        const long long take = min((long long)kItemChunkMax, max((long long)kItemChunk, (total - seen) / (4 * nwarps)));
         unsigned long long first = 0;
-        if (lane == 0) first = atomicAdd(head, (unsigned long long)kItemChunk);
+        if (lane == 0) first = atomicAdd(head, (unsigned long long)take);
         first = __shfl_sync(kFull, first, 0);
         if ((long long)first >= total) break;
-        const long long last = min((long long)first + kItemChunk, total);
+        seen = (long long)first;
+        const long long last = min((long long)first + take, total);
         long long i = find_pair(ioff, a.n, (long long)first, lane);
         for (long long it = (long long)first; it < last; ++it) {
             if (ioff[i + 1] <= it) {                  // warp-uniform: next pair, else search again
                 ++i;
                 if (ioff[i + 1] <= it) i = find_pair(ioff, a.n, it, lane);
             }
-            do_item<CAP, STK, COUNT, OVF>(a, side, nitems, i, it, it - ioff[i], ovf_list, ovf_n, ovf_cap, S, lane,
-                                          wc);
+            do_item<CAP, STK, COUNT, OVF>(a, side, nitems, i, it - ioff[i], ovf_list, ovf_n, ovf_cap, S, lane, wc);
         }
     }
     if (COUNT) flush_counters(a.counters, wc);
 }
 
-// The items another persistent launch appended to its overflow list (its queue's ioff), one at a
-// time from a second queue head.
-template <int CAP, int STK, bool COUNT>
+// The items another launch appended to its overflow list, one at a time from a second queue head.
+// With OVF, items that do not fit these buffers either are appended in turn to list 2 (for a launch
+// with larger buffers).
+template <int CAP, int STK, bool COUNT, bool OVF>
 __global__ void SCCG_ITEM_BOUNDS k_pair_areas_overflow(const AreasArgs a, int side, const long long* nitems,
-                                                             const long long* ioff, const long long* ovf_list,
+                                                             const unsigned long long* ovf_list,
                                                              const unsigned long long* ovf_n, long long ovf_cap,
-                                                             unsigned long long* head)
+                                                             unsigned long long* head, unsigned long long* ovf2_list,
+                                                             unsigned long long* ovf2_n, long long ovf2_cap)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1098,9 +1122,9 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_overflow(const AreasArgs a, int si
         if (lane == 0) j = atomicAdd(head, 1ull);
         j = __shfl_sync(kFull, j, 0);
         if ((long long)j >= n) break;
-        const long long it = ovf_list[j];
-        const long long i = find_pair(ioff, a.n, it, lane);
-        do_item<CAP, STK, COUNT, false>(a, side, nitems, i, it, it - ioff[i], nullptr, nullptr, 0, S, lane, wc);
+        const unsigned long long e = ovf_list[j];
+        do_item<CAP, STK, COUNT, OVF>(a, side, nitems, (long long)(e >> 32), (long long)(uint32_t)e, ovf2_list, ovf2_n,
+                                      ovf2_cap, S, lane, wc);
     }
     if (COUNT) flush_counters(a.counters, wc);
 }

@@ -163,12 +163,27 @@ static_assert(kMaxPrepSets * sizeof(PrepStats) <= 4096, "prepare stats must fit 
 constexpr int kCapSmall = 64;     // edge buffer of the one-warp-per-item kernels (4 warps per CTA)
 constexpr int kCapMid = SCCG_CAP_MID;   // persistent form, pairs with a polygon over kCapSmall vertices
 constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices (2 warps per CTA)
+#ifndef SCCG_CAP_OVF
+#define SCCG_CAP_OVF 256
+#endif
+#ifndef SCCG_PREP_MID2
+#define SCCG_PREP_MID2 256
+#endif
+#ifndef SCCG_WARPS_256
+#define SCCG_WARPS_256 2
+#endif
+// persistent form: first overflow level (0: items over kCapMid go straight to kCapBig)
+constexpr int kCapOvf = SCCG_CAP_OVF;
+// prepare by rows: small windows of polygons with kCapMid < nv <= kCapMid2 take the one-leaf path
+constexpr int kCapMid2 = SCCG_PREP_MID2;
+static_assert(kCapOvf == 0 || (kCapOvf > kCapMid && kCapOvf < kCapBig), "overflow levels must grow");
+static_assert(kCapMid2 == 0 || kCapMid2 > kCapMid, "prepare buffer classes must grow");
 
 int edge_cap_for(int max_nv) { return max_nv <= kCapSmall ? kCapSmall : kCapBig; }
 int warps_for(const sccg_ctx* ctx, int cap)
 {
     const int w = std::max(1, std::min(8, ctx->params.warps_per_cta));
-    return cap > kCapMid ? std::min(w, 2) : w;
+    return cap >= kCapBig ? std::min(w, 2) : cap > kCapMid ? std::min(w, SCCG_WARPS_256) : w;
 }
 
 template <int CAP>
@@ -189,6 +204,18 @@ long long grid_for(const sccg_ctx* ctx, long long items, int per_block, int max_
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return g;
+}
+
+template <class K>
+int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
+{
+    int per_sm = ctx->params.ctas_per_sm;
+    if (per_sm <= 0) {
+        SCCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpc, smem));
+        per_sm = std::max(per_sm, 1);
+    }
+    *grid = (unsigned)(ctx->sm_count * per_sm);
+    return SCCG_OK;
 }
 
 template <int CAP, bool SCAN>
@@ -213,8 +240,10 @@ int launch_prepare_big(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
     const size_t smem = warp_smem<CAP>() * wpc;
     auto kfn = ctx->count_work ? k_prepare_big<CAP, kStack, true> : k_prepare_big<CAP, kStack, false>;
     int r = set_smem(ctx, kfn, smem);
+    unsigned grid = 0;
+    if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &grid);     // every warp slot of the device
     if (r) return r;
-    kfn<<<(unsigned)(2 * ctx->sm_count), 32 * wpc, smem, st>>>(a);
+    kfn<<<grid, 32 * wpc, smem, st>>>(a);
     SCCG_LAUNCHED(ctx, "k_prepare_big");
     ctx->launches += 1;
     return SCCG_OK;
@@ -236,22 +265,10 @@ int launch_plain(sccg_ctx* ctx, const AreasArgs& a, cudaStream_t st)
     return SCCG_OK;
 }
 
-template <class K>
-int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
-{
-    int per_sm = ctx->params.ctas_per_sm;
-    if (per_sm <= 0) {
-        SCCG_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 32 * wpc, smem));
-        per_sm = std::max(per_sm, 1);
-    }
-    *grid = (unsigned)(ctx->sm_count * per_sm);
-    return SCCG_OK;
-}
-
 template <int CAP, bool OVF>
 int launch_persistent(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
-                      unsigned long long* head, long long* ovf_list, unsigned long long* ovf_n, long long ovf_cap,
-                      cudaStream_t st)
+                      unsigned long long* head, unsigned long long* ovf_list, unsigned long long* ovf_n,
+                      long long ovf_cap, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
     const size_t smem = warp_smem<CAP>() * wpc;
@@ -267,19 +284,21 @@ int launch_persistent(sccg_ctx* ctx, const AreasArgs& a, int side, const long lo
     return SCCG_OK;
 }
 
-template <int CAP>
-int launch_overflow(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
-                    const long long* ovf_list, const unsigned long long* ovf_n, long long ovf_cap,
-                    unsigned long long* head, cudaStream_t st)
+template <int CAP, bool OVF>
+int launch_overflow(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems,
+                    const unsigned long long* ovf_list, const unsigned long long* ovf_n, long long ovf_cap,
+                    unsigned long long* head, unsigned long long* ovf2_list, unsigned long long* ovf2_n,
+                    long long ovf2_cap, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
     const size_t smem = warp_smem<CAP>() * wpc;
-    auto kfn = ctx->count_work ? k_pair_areas_overflow<CAP, kStack, true> : k_pair_areas_overflow<CAP, kStack, false>;
+    auto kfn = ctx->count_work ? k_pair_areas_overflow<CAP, kStack, true, OVF>
+                               : k_pair_areas_overflow<CAP, kStack, false, OVF>;
     int r = set_smem(ctx, kfn, smem);
     unsigned grid = 0;
     if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &grid);
     if (r) return r;
-    kfn<<<grid, 32 * wpc, smem, st>>>(a, side, nitems, ioff, ovf_list, ovf_n, ovf_cap, head);
+    kfn<<<grid, 32 * wpc, smem, st>>>(a, side, nitems, ovf_list, ovf_n, ovf_cap, head, ovf2_list, ovf2_n, ovf2_cap);
     SCCG_LAUNCHED(ctx, "k_pair_areas_overflow");
     ctx->launches += 1;
     return SCCG_OK;
@@ -312,12 +331,14 @@ int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* 
 
 // overflow list capacity of the persistent form (items beyond it are done in place, chunked)
 long long overflow_cap(long long n_pairs) { return n_pairs + 65536; }
+// ... of the second level (items that do not fit the first overflow level's buffers either)
+long long overflow2_cap(long long n_pairs) { return kCapOvf ? n_pairs / 4 + 65536 : 0; }
 
 size_t persistent_scratch(long long n_pairs)
 {
     const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
     return carve_size<long long>(n_pairs + 1) * 4 + carve_size<long long>(nb) + carve_size<unsigned long long>(4) +
-           carve_size<long long>(overflow_cap(n_pairs));
+           carve_size<long long>(overflow_cap(n_pairs)) + carve_size<long long>(overflow2_cap(n_pairs));
 }
 
 int split_side(const sccg_ctx* ctx)
@@ -339,9 +360,12 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     long long* ioff_s = cv.take<long long>(n_pairs + 1);
     long long* ioff_b = cv.take<long long>(n_pairs + 1);
     long long* bsum = cv.take<long long>(nb);
-    unsigned long long* head = cv.take<unsigned long long>(4);   // 3 queue heads + overflow count
+    // queue heads: small, big, overflow 1, overflow 2; counts: overflow 1, overflow 2
+    unsigned long long* head = cv.take<unsigned long long>(6);
     const long long ovf_cap = overflow_cap(n_pairs);
-    long long* ovf_list = cv.take<long long>(ovf_cap);
+    unsigned long long* ovf_list = cv.take<unsigned long long>(ovf_cap);
+    const long long ovf2_cap = overflow2_cap(n_pairs);
+    unsigned long long* ovf2_list = cv.take<unsigned long long>(ovf2_cap);
     const unsigned g = (unsigned)((n_pairs + 255) / 256);
     // pairs whose polygons all fit the small edge buffers go to one queue, the rest to another
     k_plan<<<g, 256, 0, st>>>(a, side, kCapSmall, nitems_s, nitems_b);
@@ -350,16 +374,25 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
     if (!r && cap > kCapSmall) r = device_scan(ctx, nitems_b, n_pairs, ioff_b, bsum, st);
     if (r) return r;
-    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, 4 * sizeof(unsigned long long), st));
+    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, 6 * sizeof(unsigned long long), st));
     if (cap > kCapSmall) {
         // the big-polygon queue on the side stream, beside the small one: mid-size buffers, and the
         // items whose culled edges still do not fit go to the largest buffers afterwards
         SCCG_CUDA(ctx, cudaEventRecord(ctx->fork_event, st));
         SCCG_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->fork_event, 0));
-        r = launch_persistent<kCapMid, true>(ctx, a, side, nitems_b, ioff_b, head + 1, ovf_list, head + 3, ovf_cap,
+        r = launch_persistent<kCapMid, true>(ctx, a, side, nitems_b, ioff_b, head + 1, ovf_list, head + 4, ovf_cap,
                                              ctx->side_stream);
-        if (!r) r = launch_overflow<kCapBig>(ctx, a, side, nitems_b, ioff_b, ovf_list, head + 3, ovf_cap, head + 2,
-                                             ctx->side_stream);
+        if (kCapOvf) {
+            // two overflow levels: kCapOvf-edge buffers, then the largest for what still does not fit
+            if (!r) r = launch_overflow<kCapOvf ? kCapOvf : kCapBig, true>(ctx, a, side, nitems_b, ovf_list, head + 4,
+                                                                           ovf_cap, head + 2, ovf2_list, head + 5,
+                                                                           ovf2_cap, ctx->side_stream);
+            if (!r) r = launch_overflow<kCapBig, false>(ctx, a, side, nitems_b, ovf2_list, head + 5, ovf2_cap, head + 3,
+                                                        nullptr, nullptr, 0, ctx->side_stream);
+        } else if (!r) {
+            r = launch_overflow<kCapBig, false>(ctx, a, side, nitems_b, ovf_list, head + 4, ovf_cap, head + 2, nullptr,
+                                                nullptr, 0, ctx->side_stream);
+        }
         if (r) return r;
         SCCG_CUDA(ctx, cudaEventRecord(ctx->join_event, ctx->side_stream));
     }
@@ -683,7 +716,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
         if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
         if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
-        need += carve_size<int>(s->n + 1) * 2;
+        need += carve_size<int>(s->n + 1) * 3;
         max_n = std::max<long long>(max_n, s->n);
     }
     need += band_build_scratch(max_n);     // for the band index of deferred polygons, after the sync
@@ -692,7 +725,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
     Carve cv(ctx->ws);
     PrepStats* stats = cv.take<PrepStats>(n_sets);
     int* big_lists[kMaxPrepSets];
-    const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0, 0};
+    const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0, 0, 0};
     // the initial stats are written by a copy from pinned memory, kept ordered on the stream
     PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
     for (int k = 0; k < n_sets; ++k) hstats[k] = init;
@@ -707,13 +740,14 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         const sccg_polyset* s = sets + k;
         int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
         int* mid_list = cv.take<int>(s->n + 1);
+        int* mid2_list = cv.take<int>(s->n + 1);
         unsigned* big_n = &stats[k].deferred;
         cudaStream_t sk = (two_streams && (k & 1)) ? ctx->side_stream : st;
         if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words,
-                       kCapMid, mid_list, &stats[k].deferred_mid};
+                       kCapMid, mid_list, &stats[k].deferred_mid, kCapMid2, mid2_list, &stats[k].deferred_mid2};
             r = launch_prepare<kCapSmall, true>(ctx, a, sk);
             if (r) return r;
             // small windows of polygons with 65..kCapMid vertices: one-leaf PixelBox, 128-edge buffers
@@ -722,10 +756,17 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
             am.big_n = &stats[k].deferred_mid;
             r = launch_prepare_big<kCapMid>(ctx, am, sk);
             if (r) return r;
+            if (kCapMid2) {
+                // ... and with kCapMid+1..kCapMid2 vertices, with the larger buffers
+                am.big_list = mid2_list;
+                am.big_n = &stats[k].deferred_mid2;
+                r = launch_prepare_big<kCapMid2 ? kCapMid2 : kCapBig>(ctx, am, sk);
+                if (r) return r;
+            }
         } else if (s->n > 0) {
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words,
-                       0, nullptr, nullptr};
+                       0, nullptr, nullptr, 0, nullptr, nullptr};
             // polygons with more than kCapSmall vertices are listed and done with the larger buffers
             r = launch_prepare<kCapSmall, false>(ctx, a, sk);
             if (r) return r;
