@@ -65,6 +65,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-chunks", type=int, default=4, help="tile chunks of the end-to-end pipeline")
+    p.add_argument("--e2e-growth", type=float, default=1.75, help="size ratio of consecutive pipeline chunks")
     p.add_argument("--params", type=str, default="", help="JSON tunables for the context")
     p.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
                    help="time T / split_pixels / warps_per_cta on the workload before the run (untimed); "
@@ -602,7 +603,7 @@ def main():
         from paper_1208_0277_gb300.pipeline import HostSet, Pipeline
         pipe = Pipeline(ctx, HostSet(host["Aoff"], host["Axy"], host["Atile"]),
                         HostSet(host["Boff"], host["Bxy"], host["Btile"]), w.n_tiles, chunks=args.e2e_chunks,
-                        initial_pairs=n_pairs + 1024)
+                        initial_pairs=n_pairs + 1024, growth=args.e2e_growth)
         e_pa, _, e_inter, _, e_J = pipe.run()               # warm-up, and the same results as the device run
         e2e_same = bool(len(e_pa) == n_pairs and e_J["J"] == main_r["J"]["J"] and
                         e_J["Jprime"] == main_r["J"]["Jprime"])
@@ -618,7 +619,7 @@ def main():
         e_ms, _ = whole_job(1e3 * (time.perf_counter() - t0), n_pairs, dist, dev)
         e2e = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pipe.h2d_bytes,
                "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
-               "chunks": len(pipe.chunks), "same_results_as_device_run": e2e_same,
+               "chunks": len(pipe.chunks), "chunk_growth": args.e2e_growth, "same_results_as_device_run": e2e_same,
                "how": "paper_1208_0277_gb300.pipeline: tiles in chunks, H2D of chunk k+1 overlapped with chunk k "
                       "(prepare, candidate pairs, persistent pair areas), results D2H as they finish, one Jaccard; "
                       "host wall clock"}

@@ -1129,6 +1129,19 @@ __global__ void SCCG_ITEM_BOUNDS k_pair_areas_overflow(const AreasArgs a, int si
     if (COUNT) flush_counters(a.counters, wc);
 }
 
+// Small transfers done by kernels instead of the copy engines, so that they are never queued behind
+// a bulk host-to-device copy of the next batch (pinned host memory is addressed directly).
+__global__ void k_copy64(const unsigned long long* src, unsigned long long* dst, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+__global__ void k_zero32(uint32_t* p, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
 // Chunk-local candidate pairs to indices into the whole sets (pipelined front end).
 __global__ void k_rebase_pairs(int32_t* pa, int32_t* pb, long long n, int base_a, int base_b)
 {

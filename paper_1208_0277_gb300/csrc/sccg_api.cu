@@ -31,6 +31,7 @@ struct sccg_ctx {
                                                  // entries; prepare's temporary band index)
     size_t aux_size[3] = {0, 0, 0};
     void* pinned = nullptr;         // small host-pinned staging area
+    void* pinned_dev = nullptr;     // ... as addressed by kernels
     WorkCounters* counters = nullptr;   // device work counters (counting mode)
     int count_work = 0;
     unsigned long long launches = 0;    // kernels launched by this context (all calls)
@@ -206,6 +207,29 @@ long long grid_for(const sccg_ctx* ctx, long long items, int per_block, int max_
     return g;
 }
 
+// Zero `bytes` (a multiple of 4) of device memory, and copy `bytes` (a multiple of 8, 8-byte
+// aligned, at most a few KB) between device memory and the pinned staging area, by kernels: the
+// copy engines may be busy with a caller's bulk copies of the next batch.
+int zero_async(sccg_ctx* ctx, void* p, size_t bytes, cudaStream_t st)
+{
+    const long long n = (long long)(bytes / 4);
+    if (n <= 0) return SCCG_OK;
+    const long long g = std::min<long long>((n + 255) / 256, 4LL * ctx->sm_count);
+    k_zero32<<<(unsigned)g, 256, 0, st>>>(static_cast<uint32_t*>(p), n);
+    SCCG_LAUNCHED(ctx, "k_zero32");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+int small_copy(sccg_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st)
+{
+    k_copy64<<<1, 128, 0, st>>>(static_cast<const unsigned long long*>(src), static_cast<unsigned long long*>(dst),
+                                (int)(bytes / 8));
+    SCCG_LAUNCHED(ctx, "k_copy64");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
 template <class K>
 int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
 {
@@ -317,8 +341,7 @@ int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* 
                 cudaStream_t st)
 {
     if (n == 0) {
-        SCCG_CUDA(ctx, cudaMemsetAsync(offs, 0, sizeof(long long), st));
-        return SCCG_OK;
+        return zero_async(ctx, offs, sizeof(long long), st);
     }
     const long long nb = (n + kScanBlock - 1) / kScanBlock;
     k_scan_reduce<<<(unsigned)nb, kScanBlock, 0, st>>>(counts, n, bsum);
@@ -374,7 +397,8 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
     if (!r && cap > kCapSmall) r = device_scan(ctx, nitems_b, n_pairs, ioff_b, bsum, st);
     if (r) return r;
-    SCCG_CUDA(ctx, cudaMemsetAsync(head, 0, 6 * sizeof(unsigned long long), st));
+    r = zero_async(ctx, head, 6 * sizeof(unsigned long long), st);
+    if (r) return r;
     if (cap > kCapSmall) {
         // the big-polygon queue on the side stream, beside the small one: mid-size buffers, and the
         // items whose culled edges still do not fit go to the largest buffers afterwards
@@ -618,6 +642,12 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete ctx; return SCCG_ECUDA; }
     ctx->sm_count = prop.multiProcessorCount;
     if (cudaMallocHost(&ctx->pinned, 4096) != cudaSuccess) { cudaGetLastError(); delete ctx; return SCCG_ENOMEM; }
+    if (cudaHostGetDevicePointer(&ctx->pinned_dev, ctx->pinned, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(ctx->pinned);
+        delete ctx;
+        return SCCG_ECUDA;
+    }
     if (cudaMalloc(&ctx->counters, sizeof(WorkCounters)) != cudaSuccess ||
         cudaMemset(ctx->counters, 0, sizeof(WorkCounters)) != cudaSuccess) {
         cudaGetLastError();
@@ -726,10 +756,12 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
     PrepStats* stats = cv.take<PrepStats>(n_sets);
     int* big_lists[kMaxPrepSets];
     const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0, 0, 0};
-    // the initial stats are written by a copy from pinned memory, kept ordered on the stream
+    // the initial stats are copied from pinned memory by a kernel, kept ordered on the stream
+    static_assert(sizeof(PrepStats) % 8 == 0, "prepare stats are copied in 8-byte words");
     PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
     for (int k = 0; k < n_sets; ++k) hstats[k] = init;
-    SCCG_CUDA(ctx, cudaMemcpyAsync(stats, hstats, n_sets * sizeof init, cudaMemcpyHostToDevice, st));
+    r = small_copy(ctx, stats, ctx->pinned_dev, n_sets * sizeof init, st);
+    if (r) return r;
     // odd-numbered sets run on the side stream, beside the even ones (one fork, one join)
     const bool two_streams = n_sets > 1;
     if (two_streams) {
@@ -779,7 +811,8 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         SCCG_CUDA(ctx, cudaStreamWaitEvent(st, ctx->join_event, 0));
     }
     const Carve after_lists = cv;        // scratch of the band builds below starts here
-    SCCG_CUDA(ctx, cudaMemcpyAsync(hstats, stats, n_sets * sizeof init, cudaMemcpyDeviceToHost, st));
+    r = small_copy(ctx, ctx->pinned_dev, stats, n_sets * sizeof init, st);
+    if (r) return r;
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
     int status = SCCG_OK;
     for (int k = 0; k < n_sets; ++k) {
@@ -897,7 +930,8 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     r = device_scan(ctx, ncells, n_tiles, cellbase, bsum, st);
     if (r) return r;
     // 1st sync: number of grid cells
-    SCCG_CUDA(ctx, cudaMemcpyAsync(h, cellbase + n_tiles, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    r = small_copy(ctx, ctx->pinned_dev, cellbase + n_tiles, sizeof(long long), st);
+    if (r) return r;
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
     const long long ncell = *h;
     const long long nbc = (std::max(ncell, 1LL) + kScanBlock - 1) / kScanBlock + 1;
@@ -909,8 +943,9 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     long long* cell_off = ca.take<long long>(ncell + 1);
     int* cursor = ca.take<int>(ncell + 1);
     long long* bsum2 = ca.take<long long>(nbc);
-    SCCG_CUDA(ctx, cudaMemsetAsync(ccount, 0, sizeof(unsigned long long) * (ncell + 1), st));
-    SCCG_CUDA(ctx, cudaMemsetAsync(cursor, 0, sizeof(int) * (ncell + 1), st));
+    r = zero_async(ctx, ccount, sizeof(unsigned long long) * (ncell + 1), st);
+    if (!r) r = zero_async(ctx, cursor, sizeof(int) * (ncell + 1), st);
+    if (r) return r;
     const unsigned gb = (unsigned)((std::max(nB, 1LL) + 255) / 256);
     if (nB > 0) {
         k_bin_count<<<gb, 256, 0, st>>>(mB, B->tile, nB, grid, cellbase, ccount);
@@ -920,7 +955,8 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     r = device_scan(ctx, reinterpret_cast<const long long*>(ccount), ncell, cell_off, bsum2, st);
     if (r) return r;
     // 2nd sync: number of cell registrations
-    SCCG_CUDA(ctx, cudaMemcpyAsync(h, cell_off + ncell, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    r = small_copy(ctx, ctx->pinned_dev, cell_off + ncell, sizeof(long long), st);
+    if (r) return r;
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
     const long long nent = *h;
     r = aux_reserve(ctx, 1, carve_size<int>(nent + 1));
@@ -932,7 +968,8 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
         ctx->launches += 1;
     }
     ProbeArgs pr{mA, A->tile, nA, mB, grid, cellbase, cell_off, entries, n_tiles};
-    SCCG_CUDA(ctx, cudaMemsetAsync(small, 0, sizeof(unsigned long long) * 4, st));
+    r = zero_async(ctx, small, sizeof(unsigned long long) * 4, st);
+    if (r) return r;
     unsigned* big_n = reinterpret_cast<unsigned*>(small);
     const unsigned ga = (unsigned)((std::max(nA, 1LL) + 255) / 256);
     if (nA > 0) {
@@ -956,7 +993,8 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
         SCCG_LAUNCHED(ctx, "k_gather_tile_offsets");
         ctx->launches += 1;
     }
-    SCCG_CUDA(ctx, cudaMemcpyAsync(h, offs + nA, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    r = small_copy(ctx, ctx->pinned_dev, offs + nA, sizeof(long long), st);
+    if (r) return r;
     if (tpo_host)
         SCCG_CUDA(ctx, cudaMemcpyAsync(tile_pair_off, tpo_dev, sizeof(long long) * (n_tiles + 1),
                                        cudaMemcpyDeviceToHost, st));
@@ -1211,7 +1249,8 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
     r = jaccard_launch(ctx, inter, uni, n_pairs, res, st);
     if (r) return r;
     if (!dev_out) {
-        SCCG_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, res, sizeof(JaccardOut), cudaMemcpyDeviceToHost, st));
+        r = small_copy(ctx, ctx->pinned_dev, res, sizeof(JaccardOut), st);
+        if (r) return r;
         SCCG_CUDA(ctx, cudaStreamSynchronize(st));
         memcpy(out, ctx->pinned, sizeof(JaccardOut));
     }

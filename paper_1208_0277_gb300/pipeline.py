@@ -3,12 +3,17 @@ Fig. 6: while the GPU works on one batch of tiles, the next batch is being moved
 
 The two polygon sets live in pinned host memory, grouped by tile. They are cut into chunks of
 consecutive tiles; chunk k+1 is copied host -> device on a copy stream while chunk k is prepared,
-filtered and compared on the compute stream, into two alternating device buffers. Each chunk's
+filtered and compared on the compute stream, into two alternating device buffers. Chunk sizes (in
+vertices, at tile boundaries) grow by a constant factor, so that the first copy, which nothing
+overlaps, is short while each later copy still ends before the work on the chunk before it (the
+copy moves a vertex faster than the kernels consume one). Results go back to pinned host memory on
+a third stream as each chunk finishes. Each chunk's
 candidate pairs and areas land in one device result array (and are copied back to pinned host memory
 as they finish); the Jaccard reduction runs once over all pairs at the end, so J and J' are the same
 bits as for one call over the whole sets. Every step runs in the library's kernels (chunk-local pair
-indices are rebased on the device by sccg_rebase_pairs); the host only rebases the chunks' vertex
-offset arrays before copying them.
+indices are rebased on the device by sccg_rebase_pairs); the chunks' vertex offset and tile arrays
+are rebased once, when the pipeline is built, into pinned buffers of their own, so that a run only
+issues copies and launches.
 """
 from __future__ import annotations
 
@@ -47,7 +52,7 @@ class HostSet:
 
 
 class _Side:
-    """Device and staging buffers of one set for one of the two alternating chunk slots."""
+    """Device buffers of one set for one of the two alternating chunk slots."""
 
     def __init__(self, dev, max_n: int, max_v: int):
         import torch
@@ -56,23 +61,20 @@ class _Side:
         self.tile = torch.empty(max(max_n, 1), dtype=torch.int32, device=dev)
         self.mbr = torch.empty((max(max_n, 1), 4), dtype=torch.int32, device=dev)
         self.area = torch.empty(max(max_n, 1), dtype=torch.int64, device=dev)
-        self.h_off = torch.empty(max_n + 1, dtype=torch.int64).pin_memory()
-        self.h_tile = torch.empty(max(max_n, 1), dtype=torch.int32).pin_memory()
 
 
 class Pipeline:
     """Chunked, copy-overlapped cross comparison of two HostSets on one device.
 
-    chunks: number of tile chunks (the copy of chunk k+1 overlaps the work on chunk k)."""
+    chunks: number of tile chunks (the copy of chunk k+1 overlaps the work on chunk k).
+    growth: size ratio of consecutive chunks (1: equal chunks)."""
 
     def __init__(self, ctx, A: HostSet, B: HostSet, n_tiles: int, chunks: int = 4, mode: int = MODE_PERSISTENT,
-                 initial_pairs: int | None = None):
+                 initial_pairs: int | None = None, growth: float = 1.75):
         import torch
         self.ctx, self.A, self.B, self.mode = ctx, A, B, mode
         self.dev = torch.device("cuda", ctx.device)
-        k = max(1, min(chunks, n_tiles))
-        edges = np.linspace(0, n_tiles, k + 1).round().astype(np.int64)
-        self.chunks = [(int(edges[i]), int(edges[i + 1])) for i in range(k) if edges[i + 1] > edges[i]]
+        self.chunks = self._cut(A, B, n_tiles, max(1, min(chunks, n_tiles)), growth)
         self.ranges = [(A.range_of_tiles(t0, t1), B.range_of_tiles(t0, t1)) for t0, t1 in self.chunks]
         max_na = max(a1 - a0 for (a0, a1), _ in self.ranges)
         max_nb = max(b1 - b0 for _, (b0, b1) in self.ranges)
@@ -81,14 +83,46 @@ class Pipeline:
         self.slots = [(_Side(self.dev, max_na, max_va), _Side(self.dev, max_nb, max_vb)) for _ in range(2)]
         self.copy_stream = torch.cuda.Stream(device=self.dev)
         self.compute_stream = torch.cuda.Stream(device=self.dev)
+        self.d2h_stream = torch.cuda.Stream(device=self.dev)
+        self.done = torch.cuda.Event()
         self.copied = [torch.cuda.Event() for _ in range(2)]
         self.freed = [torch.cuda.Event() for _ in range(2)]
         self._alloc_results(initial_pairs if initial_pairs else max(A.n + B.n, 1 << 16))
-        self.h2d_bytes = A.bytes() + B.bytes()
+        # chunk-local offsets (from 0) and tiles (from the chunk's first tile), pinned, per chunk
+        self.staged = []
+        for k, ((a0, a1), (b0, b1)) in enumerate(self.ranges):
+            t0 = self.chunks[k][0]
+            per = []
+            for S, i0, i1 in ((A, a0, a1), (B, b0, b1)):
+                off = _pin(S.off_np[i0:i1 + 1] - S.off_np[i0], np.int64)
+                tile = _pin(S.tile_np[i0:i1] - t0, np.int32)
+                per.append((off, tile, int(S.off_np[i0]), int(S.off_np[i1])))
+            self.staged.append(per)
+        self.h2d_bytes = sum(off.numel() * 8 + tile.numel() * 4 + (v1 - v0) * 8
+                             for per in self.staged for off, tile, v0, v1 in per)
+
+    @staticmethod
+    def _cut(A: HostSet, B: HostSet, n_tiles: int, k: int, growth: float):
+        """Tile ranges of k chunks whose vertex counts grow by `growth` (cut at tile boundaries)."""
+        verts = np.zeros(n_tiles, dtype=np.float64)
+        for S in (A, B):
+            if S.n:
+                np.add.at(verts, S.tile_np, np.diff(S.off_np).astype(np.float64))
+        cum = np.concatenate([[0.0], np.cumsum(verts)])
+        w = np.power(float(growth), np.arange(k))
+        targets = np.cumsum(w) / w.sum() * cum[-1]
+        edges = [0]
+        for t in targets[:-1]:
+            e = int(np.searchsorted(cum, t, "left"))
+            edges.append(min(max(e, edges[-1] + 1), n_tiles))
+        edges.append(n_tiles)
+        return [(edges[i], edges[i + 1]) for i in range(k) if edges[i + 1] > edges[i]]
 
     def _alloc_results(self, cap: int, keep: int = 0):
         import torch
         old = getattr(self, "res", None)
+        if old is not None:
+            self.d2h_stream.synchronize()    # the old pinned buffers are complete before they are copied
         res = {"pa": torch.empty(cap, dtype=torch.int32, device=self.dev),
                "pb": torch.empty(cap, dtype=torch.int32, device=self.dev),
                "inter": torch.empty(cap, dtype=torch.int64, device=self.dev),
@@ -101,20 +135,15 @@ class Pipeline:
         self.res, self.host, self.cap = res, host, cap
 
     def _copy_in(self, slot: int, k: int):
-        """Host -> device copies of chunk k into `slot` on the copy stream."""
+        """Host -> device copies of chunk k into `slot` on the copy stream (after the work that last
+        used the slot's device buffers)."""
         import torch
-        (a0, a1), (b0, b1) = self.ranges[k]
-        t0 = self.chunks[k][0]
-        self.copied[slot].synchronize()     # the slot's pinned staging buffers are free again
         with torch.cuda.stream(self.copy_stream):
             self.copy_stream.wait_event(self.freed[slot])
-            for side, S, i0, i1 in ((self.slots[slot][0], self.A, a0, a1), (self.slots[slot][1], self.B, b0, b1)):
-                n = i1 - i0
-                v0, v1 = int(S.off_np[i0]), int(S.off_np[i1])
-                np.subtract(S.off_np[i0:i1 + 1], v0, out=side.h_off.numpy()[:n + 1])
-                np.subtract(S.tile_np[i0:i1], t0, out=side.h_tile.numpy()[:n])
-                side.off[:n + 1].copy_(side.h_off[:n + 1], non_blocking=True)
-                side.tile[:n].copy_(side.h_tile[:n], non_blocking=True)
+            for side, S, (off, tile, v0, v1) in zip(self.slots[slot], (self.A, self.B), self.staged[k]):
+                n = tile.numel()
+                side.off[:n + 1].copy_(off, non_blocking=True)
+                side.tile[:n].copy_(tile, non_blocking=True)
                 side.xy[:2 * (v1 - v0)].copy_(S.xy[2 * v0:2 * v1], non_blocking=True)
             self.copied[slot].record(self.copy_stream)
 
@@ -154,12 +183,17 @@ class Pipeline:
                                    out=(self.res["inter"][P:P + n], self.res["uni"][P:P + n]))
                     ctx.rebase_pairs(pa, pb, a0, b0, stream=cs)
                 self.freed[slot].record(cs)
-                for key in ("pa", "pb", "inter", "uni"):
-                    self.host[key][P:P + n].copy_(self.res[key][P:P + n], non_blocking=True)
+            if n:
+                self.done.record(cs)
+                self.d2h_stream.wait_event(self.done)
+                with torch.cuda.stream(self.d2h_stream):
+                    for key in ("pa", "pb", "inter", "uni"):
+                        self.host[key][P:P + n].copy_(self.res[key][P:P + n], non_blocking=True)
             P += n
         with torch.cuda.stream(cs):
             J = ctx.jaccard(self.res["inter"][:P], self.res["uni"][:P], stream=cs)
         cs.synchronize()
+        self.d2h_stream.synchronize()
         self.d2h_bytes = P * (4 + 4 + 8 + 8) + 48
         return (self.host["pa"][:P].numpy(), self.host["pb"][:P].numpy(), self.host["inter"][:P].numpy(),
                 self.host["uni"][:P].numpy(), J)

@@ -10,15 +10,15 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("chunks,initial", [(1, None), (3, None), (7, 1000)])
-def test_pipeline_equals_resident_path_and_oracle(chunks, initial):
+@pytest.mark.parametrize("chunks,initial,growth", [(1, None, 1.75), (3, None, 1.75), (3, None, 1.0), (7, 1000, 1.75)])
+def test_pipeline_equals_resident_path_and_oracle(chunks, initial, growth):
     import paper_1208_0277_gb300 as P
     from paper_1208_0277_gb300.pipeline import HostSet, Pipeline
     P.build()
     w = W.batched_uneven(seed=6, n_tiles=12, count_lo=50, count_hi=1500)
     ctx = P.Context(0)
     pipe = Pipeline(ctx, HostSet.from_polyset(w.A), HostSet.from_polyset(w.B), w.n_tiles, chunks=chunks,
-                    initial_pairs=initial)
+                    initial_pairs=initial, growth=growth)
     pa, pb, inter, uni, J = pipe.run()
     pa, pb, inter, uni = (np.array(x, dtype=np.int64) for x in (pa, pb, inter, uni))   # views of reused buffers
     A, B = ctx.upload(w.A), ctx.upload(w.B)
