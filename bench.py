@@ -5,8 +5,10 @@ intersection/union pixel areas.
 One step = the whole path over one synthetic workload resident in HBM:
   a1+a2  prepare both result sets (MBRs, validation, ||p|| per polygon)
   a3     candidate pairs (same tile, overlapping MBRs)
-  a4+a5  pair areas ||p n q|| and ||p u q|| (one kernel launch per tile, as in the per-tile form of
-         Sec. 4.1), or the persistent single-launch form (--form persistent)
+  a4+a5  pair areas ||p n q|| and ||p u q||: by default the persistent form (device work queue of
+         64 x 64 sub-window items) replayed with the Jaccard as one CUDA graph (--form graph); also
+         one kernel launch per tile as in the per-tile form of Sec. 4.1 (--form tiles), or the
+         persistent form launched directly (--form persistent)
   a6     Jaccard J and J' (Sec. 2.1)
 
 Default workload: a 100,000 x 100,000 px slide cut into 4096^2 tiles, ~1M nucleus polygons per set
@@ -53,7 +55,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--form", choices=["tiles", "persistent", "graph"], default=None,
-                   help="a4 form timed as the headline (default: tiles for configs 1-2, graph for 3-5)")
+                   help="a4 form timed as the headline (default: tiles for config 1, graph for 2-5)")
     p.add_argument("--config", type=int, default=2,
                    help="1 single tile, 2 whole slide (default), 3 batched uneven tiles, 4 heavy tail, "
                    "5 serving over 3")
@@ -64,8 +66,8 @@ def parse_args():
     p.add_argument("--tiles", type=int, default=0, help="restrict to the first N tiles (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--e2e-chunks", type=int, default=4, help="tile chunks of the end-to-end pipeline")
-    p.add_argument("--e2e-growth", type=float, default=1.75, help="size ratio of consecutive pipeline chunks")
+    p.add_argument("--e2e-chunks", type=int, default=3, help="tile chunks of the end-to-end pipeline")
+    p.add_argument("--e2e-growth", type=float, default=2.0, help="size ratio of consecutive pipeline chunks")
     p.add_argument("--params", type=str, default="", help="JSON tunables for the context")
     p.add_argument("--autotune", choices=["auto", "on", "off"], default="auto",
                    help="time T / split_pixels / warps_per_cta on the workload before the run (untimed); "
@@ -413,7 +415,7 @@ def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
 def main():
     args = parse_args()
     if args.form is None:
-        args.form = "graph" if args.config in (3, 4, 5) else "tiles"
+        args.form = "graph" if args.config in (2, 3, 4, 5) else "tiles"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -69,8 +69,8 @@ class Pipeline:
     chunks: number of tile chunks (the copy of chunk k+1 overlaps the work on chunk k).
     growth: size ratio of consecutive chunks (1: equal chunks)."""
 
-    def __init__(self, ctx, A: HostSet, B: HostSet, n_tiles: int, chunks: int = 4, mode: int = MODE_PERSISTENT,
-                 initial_pairs: int | None = None, growth: float = 1.75):
+    def __init__(self, ctx, A: HostSet, B: HostSet, n_tiles: int, chunks: int = 3, mode: int = MODE_PERSISTENT,
+                 initial_pairs: int | None = None, growth: float = 2.0):
         import torch
         self.ctx, self.A, self.B, self.mode = ctx, A, B, mode
         self.dev = torch.device("cuda", ctx.device)
