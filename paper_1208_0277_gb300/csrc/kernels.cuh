@@ -1142,6 +1142,161 @@ __global__ void k_zero32(uint32_t* p, long long n)
         p[i] = 0u;
 }
 
+// ----------------------------------------------------------------------------------------------
+// Streaming form of the persistent pair areas, for items that are one leaf each (side^2 < T, parity
+// words): the leaf's parity words are XORed straight from the polygons' rings (or their band
+// blocks), 32 edges at a time held in registers, so no edge buffer bounds a polygon's size, the
+// shared memory per warp is the two polygons' parity words only, and every item goes to one queue.
+// ----------------------------------------------------------------------------------------------
+struct StreamSmem {
+    XorRows xp;
+    XorRows xq;
+};
+
+// XOR the crossings of ring v[0..nv) with rows y0 .. y0 + nr - 1 (columns x0 .. x0 + W - 1) into X.
+__device__ __forceinline__ void xor_stream_ring(const int2* v, int nv, int x0, int y0, int nr, int W, int nw,
+                                                XorRows& X, int lane, unsigned long long& entries)
+{
+    for (int base = 0; base < nv; base += 32) {
+        const int e = base + lane;
+        int ylo = 0, dy = 0, dx = 0, xl = 0;
+        if (e < nv) {
+            const int f = (e + 1 == nv) ? 0 : e + 1;
+            int2 p = v[e];
+            int2 q = v[f];
+            if (q.y < p.y) { const int2 t = p; p = q; q = t; }
+            ylo = p.y; dy = q.y - p.y; dx = q.x - p.x; xl = p.x;
+        }
+        xor_group(e < nv, ylo, dy, dx, xl, x0, y0, nr, W, nw, X, lane, entries);
+    }
+}
+
+// ... of the edge records listed in the band block `blk` (polygon minimum y `miny`) for the bands
+// of those rows; a record listed in several of them is taken from the first (as stage_banded).
+__device__ __forceinline__ void xor_stream_bands(const char* blk, int miny, int x0, int y0, int nr, int W, int nw,
+                                                 XorRows& X, int lane, unsigned long long& entries)
+{
+    const int* head = reinterpret_cast<const int*>(blk);
+    const int nb = head[0];
+    const int* boff = head + 4;
+    const int4* ent = reinterpret_cast<const int4*>(blk + 16 + ((4LL * (2 * nb + 1) + 15) & ~15LL));
+    const int b0 = min(max((y0 - miny) >> kBandShift, 0), nb - 1);
+    const int b1 = min(max((y0 + nr - 1 - miny) >> kBandShift, 0), nb - 1);
+    for (int b = b0; b <= b1; ++b) {
+        const int e0 = boff[b], e1 = boff[b + 1];
+        for (int base = e0; base < e1; base += 32) {
+            const int k = base + lane;
+            bool has = false;
+            int4 rec = make_int4(0, 0, 0, 0);
+            if (k < e1) {
+                rec = ent[k];
+                has = max(b0, (rec.x - miny) >> kBandShift) == b;
+            }
+            xor_group(has, rec.x, rec.y, rec.z, rec.w, x0, y0, nr, W, nw, X, lane, entries);
+        }
+    }
+}
+
+// Work item `sub` of pair i (as do_item), one leaf, streamed. Whole warp, converged.
+template <bool COUNT>
+__device__ __forceinline__ void do_item_stream(const AreasArgs a, int side, const long long* nitems, long long i,
+                                               long long sub, StreamSmem& S, int lane, WorkCounters& wc)
+{
+    const int ia = a.pa[i], ib = a.pb[i];
+    const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
+    const int wx0 = max(ma.x, mb.x), wy0 = max(ma.y, mb.y);
+    const int wx1 = min(ma.z, mb.z), wy1 = min(ma.w, mb.w);
+    const int gx = (wx1 - wx0 + side - 1) / side;
+    const int sx = (int)(sub % gx), sy = (int)(sub / gx);
+    const int x0 = wx0 + sx * side, y0 = wy0 + sy * side;
+    const int x1 = min(x0 + side, wx1), y1 = min(y0 + side, wy1);
+    const int W = x1 - x0, H = y1 - y0;
+    const int2* vp = reinterpret_cast<const int2*>(a.xyA) + a.offA[ia];
+    const int np = (int)(a.offA[ia + 1] - a.offA[ia]);
+    const int2* vq = reinterpret_cast<const int2*>(a.xyB) + a.offB[ib];
+    const int nq = (int)(a.offB[ib + 1] - a.offB[ib]);
+    const char* bp = band_block(a.bandsA, ia);
+    const char* bq = band_block(a.bandsB, ib);
+    if (COUNT && lane == 0) wc.window_pixels += (unsigned long long)W * H;
+    uint32_t acc = 0;
+    for (int cx = 0; cx < W; cx += 32 * kXorMaxWords) {
+        const int Wp = min(32 * kXorMaxWords, W - cx), nw = (Wp + 31) >> 5;
+        const int nr = min(64, kXorWords / nw);
+        for (int r0 = 0; r0 < H; r0 += nr) {
+            const int nrr = min(nr, H - r0);
+            __syncwarp();
+            for (int k = lane; k < nrr; k += 32) {
+                S.xp.F[k] = 0;
+                S.xq.F[k] = 0;
+            }
+            for (int k = lane; k < nrr * nw; k += 32) {
+                S.xp.P[k] = 0;
+                S.xq.P[k] = 0;
+            }
+            __syncwarp();
+            unsigned long long ce = 0;
+            if (bp) xor_stream_bands(bp, ma.y, x0 + cx, y0 + r0, nrr, Wp, nw, S.xp, lane, ce);
+            else xor_stream_ring(vp, np, x0 + cx, y0 + r0, nrr, Wp, nw, S.xp, lane, ce);
+            if (bq) xor_stream_bands(bq, mb.y, x0 + cx, y0 + r0, nrr, Wp, nw, S.xq, lane, ce);
+            else xor_stream_ring(vq, nq, x0 + cx, y0 + r0, nrr, Wp, nw, S.xq, lane, ce);
+            __syncwarp();
+            for (int k = lane; k < nrr; k += 32) {
+                for (int j = 0; j < nw; ++j) {
+                    const uint32_t in = __funnelshift_lc(0xffffffffu, 0u, (unsigned)min(32, Wp - 32 * j));
+                    acc += __popc(in & xor_word(S.xp, k, nw, j) & xor_word(S.xq, k, nw, j));
+                }
+                if (COUNT) {
+                    wc.row_edges += (unsigned long long)nw;
+                    wc.leaf_pixels += (unsigned long long)Wp * 2;
+                }
+            }
+            if (COUNT) wc.row_entries += ce;
+        }
+    }
+    const uint32_t cnt = warp_sum(acc);
+    if (lane == 0) {
+        if (nitems[i] == 1) {
+            a.inter[i] = (int64_t)cnt;
+            a.uni[i] = a.areaA[ia] + a.areaB[ib] - (int64_t)cnt;
+        } else {
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.inter + i), (unsigned long long)cnt);
+        }
+    }
+}
+
+// Persistent streaming pair areas over one item queue (guided self-scheduling, as
+// k_pair_areas_persistent).
+template <bool COUNT>
+__global__ void SCCG_ITEM_BOUNDS k_pair_areas_stream(const AreasArgs a, int side, const long long* nitems,
+                                                     const long long* ioff, unsigned long long* head)
+{
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StreamSmem& S = reinterpret_cast<StreamSmem*>(smem4)[warp];
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const long long total = ioff[a.n];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    long long seen = 0;
+    for (;;) {
+        const long long take = min((long long)kItemChunkMax, max((long long)kItemChunk, (total - seen) / (4 * nwarps)));
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(head, (unsigned long long)take);
+        first = __shfl_sync(kFull, first, 0);
+        if ((long long)first >= total) break;
+        seen = (long long)first;
+        const long long last = min((long long)first + take, total);
+        long long i = find_pair(ioff, a.n, (long long)first, lane);
+        for (long long it = (long long)first; it < last; ++it) {
+            if (ioff[i + 1] <= it) {
+                ++i;
+                if (ioff[i + 1] <= it) i = find_pair(ioff, a.n, it, lane);
+            }
+            do_item_stream<COUNT>(a, side, nitems, i, it - ioff[i], S, lane, wc);
+        }
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
 // Chunk-local candidate pairs to indices into the whole sets (pipelined front end).
 __global__ void k_rebase_pairs(int32_t* pa, int32_t* pb, long long n, int base_a, int base_b)
 {

@@ -380,6 +380,39 @@ __device__ __forceinline__ void xor_rows(const int4* E, const float* R, int ne, 
     }
 }
 
+// The same XOR for edges held in registers instead of a staged buffer: each lane holds at most one
+// edge {ylo, dy, dx, xl} (`has`), and an (edge, row) crossing's edge is fetched from its lane by
+// shuffles. Edges with no pixel centre of the rows right of them (max x <= x0) are skipped, as the
+// staging skips them. No buffer bounds the number of edges. Whole warp, converged; the trip count
+// is warp-uniform.
+__device__ __forceinline__ void xor_group(bool has, int ylo, int dy, int dx, int xl, int x0, int y0, int nr, int W,
+                                          int nw, XorRows& X, int lane, unsigned long long& entries)
+{
+    int cnt = 0;
+    if (has && max(xl, xl + dx) > x0) cnt = max(0, min(ylo + dy, y0 + nr) - max(ylo, y0));
+    int total;
+    const int excl = warp_excl(cnt, lane, total);
+    if (total == 0) return;
+    const float r2 = cnt > 0 ? __frcp_rn((float)(2 * dy)) : 0.0f;     // dy > 0 whenever cnt > 0
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        const int own = flat_owner(excl, t);
+        const int eo = __shfl_sync(kFull, excl, own);
+        const int oy = __shfl_sync(kFull, ylo, own), ody = __shfl_sync(kFull, dy, own);
+        const int odx = __shfl_sync(kFull, dx, own), oxl = __shfl_sync(kFull, xl, own);
+        const float orr = __shfl_sync(kFull, r2, own);
+        if (t < total) {
+            const int y = max(oy, y0) + (t - eo);
+            const int c = min(crossing_count_r(oy, ody, odx, oxl, y, x0, orr), W);
+            const int q = c >> 5, rem = c & 31;
+            const int r = y - y0;
+            if (q) atomicXor(&X.F[r], 1u << q);
+            if (rem) atomicXor(&X.P[r * nw + q], (1u << rem) - 1u);
+        }
+    }
+    entries += (unsigned long long)cnt;
+}
+
 // Parity word j of row r (see XorRows).
 __device__ __forceinline__ uint32_t xor_word(const XorRows& X, int r, int nw, int j)
 {

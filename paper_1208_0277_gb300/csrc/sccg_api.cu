@@ -173,6 +173,9 @@ constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices
 #ifndef SCCG_WARPS_256
 #define SCCG_WARPS_256 2
 #endif
+#ifndef SCCG_STREAM
+#define SCCG_STREAM 1     // persistent form: stream the edges when every item is one leaf
+#endif
 // persistent form: first overflow level (0: items over kCapMid go straight to kCapBig)
 constexpr int kCapOvf = SCCG_CAP_OVF;
 // prepare by rows: small windows of polygons with kCapMid < nv <= kCapMid2 take the one-leaf path
@@ -308,6 +311,22 @@ int launch_persistent(sccg_ctx* ctx, const AreasArgs& a, int side, const long lo
     return SCCG_OK;
 }
 
+int launch_stream(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems, const long long* ioff,
+                  unsigned long long* head, cudaStream_t st)
+{
+    const int wpc = warps_for(ctx, kCapSmall);
+    const size_t smem = sizeof(StreamSmem) * wpc;
+    auto kfn = ctx->count_work ? k_pair_areas_stream<true> : k_pair_areas_stream<false>;
+    int r = set_smem(ctx, kfn, smem);
+    unsigned grid = 0;
+    if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &grid);
+    if (r) return r;
+    kfn<<<grid, 32 * wpc, smem, st>>>(a, side, nitems, ioff, head);
+    SCCG_LAUNCHED(ctx, "k_pair_areas_stream");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
 template <int CAP, bool OVF>
 int launch_overflow(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems,
                     const unsigned long long* ovf_list, const unsigned long long* ovf_n, long long ovf_cap,
@@ -390,6 +409,20 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     const long long ovf2_cap = overflow2_cap(n_pairs);
     unsigned long long* ovf2_list = cv.take<unsigned long long>(ovf2_cap);
     const unsigned g = (unsigned)((n_pairs + 255) / 256);
+    if (SCCG_STREAM && ctx->params.leaf_words && (long long)side * side < ctx->params.T) {
+        // every item is one leaf: one queue, edges streamed from the rings (no edge buffers)
+        k_plan<<<g, 256, 0, st>>>(a, side, 0x7fffffff, nitems_s, nitems_b);
+        SCCG_LAUNCHED(ctx, "k_plan");
+        ctx->launches += 1;
+        int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
+        if (!r) r = zero_async(ctx, head, sizeof(unsigned long long), st);
+        if (!r) r = launch_stream(ctx, a, side, nitems_s, ioff_s, head, st);
+        if (r) return r;
+        k_union<<<g, 256, 0, st>>>(a, nitems_s, nitems_b);
+        SCCG_LAUNCHED(ctx, "k_union");
+        ctx->launches += 1;
+        return SCCG_OK;
+    }
     // pairs whose polygons all fit the small edge buffers go to one queue, the rest to another
     k_plan<<<g, 256, 0, st>>>(a, side, kCapSmall, nitems_s, nitems_b);
     SCCG_LAUNCHED(ctx, "k_plan");
