@@ -41,8 +41,6 @@ struct PrepStats {
     long long first_bad;
     unsigned long long band_bytes;    // sum of the band index block sizes
     unsigned deferred;                // polygons listed for a second kernel (area not yet written)
-    unsigned deferred_mid;            // ... for the one-leaf pass with mid-size buffers
-    unsigned deferred_mid2;           // ... for the one-leaf pass with the next larger buffers
 };
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
@@ -130,24 +128,20 @@ struct PrepArgs {
     int* big_list;
     unsigned* big_n;
     int words;              // as AreasArgs::words
-    int mid_cap;            // SCAN: small-window polygons with CAP < nv <= mid_cap are listed in mid_list
-    int* mid_list;
-    unsigned* mid_n;
-    int mid2_cap;           // SCAN: ... with mid_cap < nv <= mid2_cap in mid2_list (0: none)
-    int* mid2_list;
-    unsigned* mid2_n;
 };
 
-// SCAN: a polygon whose window holds fewer than T pixels and whose edges fit the buffer is pixelized
-// here (PixelBox's one-leaf case, cheapest for small windows); every other one is listed for
-// k_area_bands (by rows). Otherwise by PixelBox on the polygon alone, deferring polygons with more
-// than defer_above vertices to k_prepare_big.
+// SCAN: a polygon whose window holds fewer than T pixels is pixelized here as one leaf, its edges
+// streamed from the ring (PixelBox's one-leaf case, cheapest for small windows; shared memory per
+// warp: one XorRows); every other one is listed for k_area_bands (by rows). Otherwise by PixelBox on
+// the polygon alone (per-warp WarpSmem), deferring polygons with more than defer_above vertices to
+// k_prepare_big.
 template <int CAP, int STK, bool COUNT, bool SCAN>
 __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[warp];
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[SCAN ? 0 : warp];
+    XorRows& X = reinterpret_cast<XorRows*>(smem4)[SCAN ? warp : 0];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
@@ -178,20 +172,15 @@ __global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
                 e = kErrRange;
         }
         uint32_t area = 0;
-        // SCAN: a small window whose polygon has more than CAP (at most mid_cap) vertices goes to the
-        // one-leaf path with larger buffers (k_prepare_big over mid_list); every other polygon
-        // counted by rows is deferred to k_area_bands. Otherwise the large ones to k_prepare_big.
+        // SCAN: a polygon whose window is not small is deferred to k_area_bands (by rows).
+        // Otherwise the large ones to k_prepare_big.
         const bool small_win = (long long)(x1 - x0) * (y1 - y0) < a.T;
-        const bool mid = SCAN && e == 0 && small_win && nvl > CAP && nvl <= a.mid_cap;
-        const bool mid2 = SCAN && e == 0 && small_win && nvl > a.mid_cap && nvl <= a.mid2_cap;
-        const bool by_rows = SCAN && !mid && !mid2 && (!small_win || nvl > CAP);
-        const bool defer = e == 0 && (by_rows || mid || mid2 || (a.defer_above > 0 && nvl > a.defer_above));
-        if (lane == 0 && defer) {
-            if (mid) a.mid_list[atomicAdd(a.mid_n, 1u)] = (int)i;
-            else if (mid2) a.mid2_list[atomicAdd(a.mid2_n, 1u)] = (int)i;
-            else a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
-        }
-        if (e == 0 && !defer && x1 > x0 && y1 > y0) {
+        const bool by_rows = SCAN && !small_win;
+        const bool defer = e == 0 && (by_rows || (!SCAN && a.defer_above > 0 && nvl > a.defer_above));
+        if (lane == 0 && defer) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
+        if (SCAN && e == 0 && !defer && x1 > x0 && y1 > y0) {
+            area = area_stream<COUNT>(v, (int)nvl, x0, y0, x1, y1, X, lane, wc);
+        } else if (!SCAN && e == 0 && !defer && x1 > x0 && y1 > y0) {
             const int nv = (int)nvl;
             const bool res = nv <= CAP;
             __syncwarp();
@@ -1152,24 +1141,6 @@ struct StreamSmem {
     XorRows xp;
     XorRows xq;
 };
-
-// XOR the crossings of ring v[0..nv) with rows y0 .. y0 + nr - 1 (columns x0 .. x0 + W - 1) into X.
-__device__ __forceinline__ void xor_stream_ring(const int2* v, int nv, int x0, int y0, int nr, int W, int nw,
-                                                XorRows& X, int lane, unsigned long long& entries)
-{
-    for (int base = 0; base < nv; base += 32) {
-        const int e = base + lane;
-        int ylo = 0, dy = 0, dx = 0, xl = 0;
-        if (e < nv) {
-            const int f = (e + 1 == nv) ? 0 : e + 1;
-            int2 p = v[e];
-            int2 q = v[f];
-            if (q.y < p.y) { const int2 t = p; p = q; q = t; }
-            ylo = p.y; dy = q.y - p.y; dx = q.x - p.x; xl = p.x;
-        }
-        xor_group(e < nv, ylo, dy, dx, xl, x0, y0, nr, W, nw, X, lane, entries);
-    }
-}
 
 // ... of the edge records listed in the band block `blk` (polygon minimum y `miny`) for the bands
 // of those rows; a record listed in several of them is taken from the first (as stage_banded).

@@ -419,6 +419,62 @@ __device__ __forceinline__ uint32_t xor_word(const XorRows& X, int r, int nw, in
     return X.P[r * nw + j] ^ ((__popc(X.F[r] >> (j + 1)) & 1) ? 0xffffffffu : 0u);
 }
 
+// XOR the crossings of ring v[0..nv) with rows y0 .. y0 + nr - 1 (columns x0 .. x0 + W - 1) into X.
+__device__ __forceinline__ void xor_stream_ring(const int2* v, int nv, int x0, int y0, int nr, int W, int nw,
+                                                XorRows& X, int lane, unsigned long long& entries)
+{
+    for (int base = 0; base < nv; base += 32) {
+        const int e = base + lane;
+        int ylo = 0, dy = 0, dx = 0, xl = 0;
+        if (e < nv) {
+            const int f = (e + 1 == nv) ? 0 : e + 1;
+            int2 p = v[e];
+            int2 q = v[f];
+            if (q.y < p.y) { const int2 t = p; p = q; q = t; }
+            ylo = p.y; dy = q.y - p.y; dx = q.x - p.x; xl = p.x;
+        }
+        xor_group(e < nv, ylo, dy, dx, xl, x0, y0, nr, W, nw, X, lane, entries);
+    }
+}
+
+// ||p|| over its window [x0, x1) x [y0, y1) (the polygon's MBR) as one leaf, edges streamed from the
+// ring: pieces of up to 992 columns, passes of up to 64 rows, one lane per row in the reduction.
+// Returns the warp-wide count. Whole warp, converged.
+template <bool COUNT>
+__device__ __forceinline__ uint32_t area_stream(const int2* v, int nv, int x0, int y0, int x1, int y1, XorRows& X,
+                                                int lane, WorkCounters& wc)
+{
+    const int W = x1 - x0, H = y1 - y0;
+    uint32_t acc = 0;
+    if (COUNT && lane == 0) wc.window_pixels += (unsigned long long)W * H;
+    for (int cx = 0; cx < W; cx += 32 * kXorMaxWords) {
+        const int Wp = min(32 * kXorMaxWords, W - cx), nw = (Wp + 31) >> 5;
+        const int nr = min(64, kXorWords / nw);
+        for (int r0 = 0; r0 < H; r0 += nr) {
+            const int nrr = min(nr, H - r0);
+            __syncwarp();
+            for (int k = lane; k < nrr; k += 32) X.F[k] = 0;
+            for (int k = lane; k < nrr * nw; k += 32) X.P[k] = 0;
+            __syncwarp();
+            unsigned long long ce = 0;
+            xor_stream_ring(v, nv, x0 + cx, y0 + r0, nrr, Wp, nw, X, lane, ce);
+            __syncwarp();
+            for (int k = lane; k < nrr; k += 32) {
+                for (int j = 0; j < nw; ++j) {
+                    const uint32_t in = __funnelshift_lc(0xffffffffu, 0u, (unsigned)min(32, Wp - 32 * j));
+                    acc += __popc(in & xor_word(X, k, nw, j));
+                }
+                if (COUNT) {
+                    wc.row_edges += (unsigned long long)nw;
+                    wc.leaf_pixels += (unsigned long long)Wp;
+                }
+            }
+            if (COUNT) wc.row_entries += ce;
+        }
+    }
+    return warp_sum(acc);
+}
+
 // Box packing: window-relative coordinates (< 2^15) in 15 bits each; bit 15 of the low halves
 // carries the "still needs testing against P / Q" flags.
 __device__ __forceinline__ uint2 pack_box(int x0, int y0, int x1, int y1, int fl)

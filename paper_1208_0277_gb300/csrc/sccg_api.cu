@@ -167,9 +167,6 @@ constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices
 #ifndef SCCG_CAP_OVF
 #define SCCG_CAP_OVF 256
 #endif
-#ifndef SCCG_PREP_MID2
-#define SCCG_PREP_MID2 256
-#endif
 #ifndef SCCG_WARPS_256
 #define SCCG_WARPS_256 2
 #endif
@@ -178,10 +175,7 @@ constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices
 #endif
 // persistent form: first overflow level (0: items over kCapMid go straight to kCapBig)
 constexpr int kCapOvf = SCCG_CAP_OVF;
-// prepare by rows: small windows of polygons with kCapMid < nv <= kCapMid2 take the one-leaf path
-constexpr int kCapMid2 = SCCG_PREP_MID2;
 static_assert(kCapOvf == 0 || (kCapOvf > kCapMid && kCapOvf < kCapBig), "overflow levels must grow");
-static_assert(kCapMid2 == 0 || kCapMid2 > kCapMid, "prepare buffer classes must grow");
 
 int edge_cap_for(int max_nv) { return max_nv <= kCapSmall ? kCapSmall : kCapBig; }
 int warps_for(const sccg_ctx* ctx, int cap)
@@ -249,7 +243,7 @@ template <int CAP, bool SCAN>
 int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
-    const size_t smem = warp_smem<CAP>() * wpc;
+    const size_t smem = (SCAN ? sizeof(XorRows) : warp_smem<CAP>()) * wpc;    // SCAN: streamed leaves only
     const long long grid = grid_for(ctx, a.n, wpc, 64);
     auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN> : k_prepare<CAP, kStack, false, SCAN>;
     int r = set_smem(ctx, kfn, smem);
@@ -779,7 +773,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
         if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
         if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
-        need += carve_size<int>(s->n + 1) * 3;
+        need += carve_size<int>(s->n + 1);
         max_n = std::max<long long>(max_n, s->n);
     }
     need += band_build_scratch(max_n);     // for the band index of deferred polygons, after the sync
@@ -788,7 +782,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
     Carve cv(ctx->ws);
     PrepStats* stats = cv.take<PrepStats>(n_sets);
     int* big_lists[kMaxPrepSets];
-    const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0, 0, 0};
+    const PrepStats init{0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0};
     // the initial stats are copied from pinned memory by a kernel, kept ordered on the stream
     static_assert(sizeof(PrepStats) % 8 == 0, "prepare stats are copied in 8-byte words");
     PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
@@ -804,34 +798,17 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
     for (int k = 0; k < n_sets; ++k) {
         const sccg_polyset* s = sets + k;
         int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
-        int* mid_list = cv.take<int>(s->n + 1);
-        int* mid2_list = cv.take<int>(s->n + 1);
         unsigned* big_n = &stats[k].deferred;
         cudaStream_t sk = (two_streams && (k & 1)) ? ctx->side_stream : st;
         if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
-                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words,
-                       kCapMid, mid_list, &stats[k].deferred_mid, kCapMid2, mid2_list, &stats[k].deferred_mid2};
+                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
             r = launch_prepare<kCapSmall, true>(ctx, a, sk);
             if (r) return r;
-            // small windows of polygons with 65..kCapMid vertices: one-leaf PixelBox, 128-edge buffers
-            PrepArgs am = a;
-            am.big_list = mid_list;
-            am.big_n = &stats[k].deferred_mid;
-            r = launch_prepare_big<kCapMid>(ctx, am, sk);
-            if (r) return r;
-            if (kCapMid2) {
-                // ... and with kCapMid+1..kCapMid2 vertices, with the larger buffers
-                am.big_list = mid2_list;
-                am.big_n = &stats[k].deferred_mid2;
-                r = launch_prepare_big<kCapMid2 ? kCapMid2 : kCapBig>(ctx, am, sk);
-                if (r) return r;
-            }
         } else if (s->n > 0) {
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
-                       ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words,
-                       0, nullptr, nullptr, 0, nullptr, nullptr};
+                       ctx->params.T, ctx->counters, kCapSmall, big_list, big_n, ctx->params.leaf_words};
             // polygons with more than kCapSmall vertices are listed and done with the larger buffers
             r = launch_prepare<kCapSmall, false>(ctx, a, sk);
             if (r) return r;
