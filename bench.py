@@ -20,6 +20,7 @@ slide (seed 1 + rank), no collective on the data path (weak scaling).
 from __future__ import annotations
 
 import argparse
+import math
 import hashlib
 import json
 import os
@@ -575,8 +576,12 @@ def main():
     peak_tops = sms * 4 * 32 * 2070e6 / 1e12
     ph = main_r["phases_ms"]
     if ph["pair_areas"] >= ph["prepare"]:
+        prm = ctx.params()
+        side = math.isqrt(max(prm["split_pixels"], 1))
+        streamed = prm["leaf_words"] and side * side < prm["T"]      # every item one leaf: streamed kernel
         dom, dom_ms, dom_ops, dom_launches = ("k_pair_areas_plain" if args.form == "tiles" else
-                                              "k_pair_areas_persistent"), ph["pair_areas"], ops(work_areas), None
+                                              "k_pair_areas_stream" if streamed else "k_pair_areas_persistent"
+                                              ), ph["pair_areas"], ops(work_areas), None
     else:
         dom, dom_ms, dom_ops, dom_launches = "k_prepare", ph["prepare"], ops(work_prep), 2
     achieved = dom_ops / (dom_ms / 1e3) / 1e12
