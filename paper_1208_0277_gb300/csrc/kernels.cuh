@@ -21,6 +21,15 @@
 #else
 #define SCCG_ITEM_BOUNDS __launch_bounds__(256)
 #endif
+// The kernels whose leaves stream their edges need little shared memory, so registers set their
+// occupancy: at least 5 resident CTAs of 256 threads for k_prepare and 6 for k_pair_areas_stream,
+// measured best on the whole slide and the uneven tiles.
+#ifndef SCCG_PREP_MIN_BLOCKS
+#define SCCG_PREP_MIN_BLOCKS 5
+#endif
+#ifndef SCCG_STREAM_MIN_BLOCKS
+#define SCCG_STREAM_MIN_BLOCKS 6
+#endif
 
 namespace sccg {
 
@@ -136,7 +145,7 @@ struct PrepArgs {
 // the polygon alone (per-warp WarpSmem), deferring polygons with more than defer_above vertices to
 // k_prepare_big.
 template <int CAP, int STK, bool COUNT, bool SCAN>
-__global__ void SCCG_ITEM_BOUNDS k_prepare(const PrepArgs a)
+__global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const PrepArgs a)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1238,7 +1247,7 @@ __device__ __forceinline__ void do_item_stream(const AreasArgs a, int side, cons
 // Persistent streaming pair areas over one item queue (guided self-scheduling, as
 // k_pair_areas_persistent).
 template <bool COUNT>
-__global__ void SCCG_ITEM_BOUNDS k_pair_areas_stream(const AreasArgs a, int side, const long long* nitems,
+__global__ void __launch_bounds__(256, SCCG_STREAM_MIN_BLOCKS) k_pair_areas_stream(const AreasArgs a, int side, const long long* nitems,
                                                      const long long* ioff, unsigned long long* head)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
