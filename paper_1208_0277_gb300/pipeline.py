@@ -70,7 +70,7 @@ class Pipeline:
     growth: size ratio of consecutive chunks (1: equal chunks)."""
 
     def __init__(self, ctx, A: HostSet, B: HostSet, n_tiles: int, chunks: int = 3, mode: int = MODE_PERSISTENT,
-                 initial_pairs: int | None = None, growth: float = 2.0):
+                 initial_pairs: int | None = None, growth: float = 1.5):
         import torch
         self.ctx, self.A, self.B, self.mode = ctx, A, B, mode
         self.dev = torch.device("cuda", ctx.device)
