@@ -559,6 +559,9 @@ def main():
         if sampler:
             sampler.mark("t_end")
         clocks = sampler.stop() if sampler else None
+        if sampler:
+            # nvidia-smi's exit (NVML teardown) can hold up the next form's driver calls: let it settle
+            time.sleep(1.0)
         launches = ctx.launch_count() - launches0
         ms, _ = whole_job(start.elapsed_time(end), n_pairs, dist, dev)
         ph = np.array([[p[k].elapsed_time(p[k + 1]) for k in range(4)] for p in phases])
