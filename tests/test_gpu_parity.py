@@ -141,11 +141,13 @@ def test_tile_pair_offsets_and_one_launch_per_tile(ctx):
     np.testing.assert_array_equal(uni.cpu().numpy(), ref_u)
 
 
-@pytest.mark.parametrize("split", [32, 100, 4096])
-def test_persistent_queue_matches_oracle(sccg, split):
+@pytest.mark.parametrize("split,T", [(32, 256), (100, 256), (4096, 256), (4096, 8192), (900, 1 << 22)])
+def test_persistent_queue_matches_oracle(sccg, split, T):
     """Persistent form: one launch, device work queue, windows cut into items of about `split`
-    pixels (many items per pair for small `split`); results identical to the oracle."""
-    c = sccg.Context(0, {"split_pixels": split, "T": 256})
+    pixels (many items per pair for small `split`); results identical to the oracle. Items of
+    fewer than T pixels are single leaves and stream their edges (k_pair_areas_stream); larger
+    ones are staged and subdivided (k_pair_areas_persistent and its overflow levels)."""
+    c = sccg.Context(0, {"split_pixels": split, "T": T})
     w = W.single_tile(seed=5, n=500)
     assert_same(gpu_run(c, w, mode=1), O.cross_compare(w.A, w.B))
     A = medium_polygons(12)
@@ -171,8 +173,8 @@ def test_heavy_tail_tissue_and_nuclei(sccg, mode):
     np.testing.assert_array_equal(g["uni"][idx], bu)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_band_index_gives_the_same_results(sccg, mode):
+@pytest.mark.parametrize("mode,T", [(0, 64), (1, 64), (1, 8192)])
+def test_band_index_gives_the_same_results(sccg, mode, T):
     """Polygons with >= 1024 vertices get a band index; items then stage only their bands' edges.
     Concave tissue rings and rectilinear staircases (horizontal edges on band boundaries) against
     nuclei, with small work items in the persistent form so item windows start at many offsets
@@ -184,7 +186,7 @@ def test_band_index_gives_the_same_results(sccg, mode):
     small, _ = W.staircase_rings(rng, 300, max_cols=12, max_h=15, origin_span=600)
     ws = rings_workload([np.asarray(r) for r in stairs] + [np.asarray(r) for r in small],
                         [np.asarray(r) for r in small] + [np.asarray(r) for r in stairs])
-    c = sccg.Context(0, {"split_pixels": 400, "T": 64})
+    c = sccg.Context(0, {"split_pixels": 400, "T": T})     # T = 8192: items stream their bands' records
     for wk in (w, ws):
         with_bands = gpu_run(c, wk, mode=mode)
         A, B = c.upload(wk.A, bands=False), c.upload(wk.B, bands=False)
