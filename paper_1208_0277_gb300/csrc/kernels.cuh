@@ -495,14 +495,26 @@ __global__ void k_tile_grid(const int4* __restrict__ mbrB, const long long* __re
     ncells[warp] = (long long)g.gx * g.gy;
 }
 
+// Sizes of the grid's buffers fixed before the counts are known: ok (when not null) is cleared as
+// soon as a count exceeds its buffer, and every kernel after it then does nothing (the caller reads
+// ok with the pair count and redoes the call with exact sizes). One thread.
+__global__ void k_cap_check(const long long* total, long long cap, unsigned long long* ok, int first)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool fit = *total <= cap;
+        *ok = (first ? fit : (*ok != 0ull && fit)) ? 1ull : 0ull;
+    }
+}
+
 // One thread per B polygon: count its registrations per cell.
 __global__ void __launch_bounds__(256) k_bin_count(const int4* __restrict__ mbrB, const int32_t* __restrict__ tileB,
                                                    long long nB, const TileGrid* __restrict__ grid,
                                                    const long long* __restrict__ cellbase,
-                                                   unsigned long long* __restrict__ count)
+                                                   unsigned long long* __restrict__ count,
+                                                   const unsigned long long* __restrict__ ok)
 {
     const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nB) return;
+    if (b >= nB || (ok && !*ok)) return;
     const int t = tileB ? tileB[b] : 0;
     const TileGrid g = grid[t];
     const int4 m = mbrB[b];
@@ -517,10 +529,11 @@ __global__ void __launch_bounds__(256) k_bin_count(const int4* __restrict__ mbrB
 __global__ void __launch_bounds__(256) k_bin_fill(const int4* __restrict__ mbrB, const int32_t* __restrict__ tileB,
                                                   long long nB, const TileGrid* __restrict__ grid,
                                                   const long long* __restrict__ cellbase, int* __restrict__ cursor,
-                                                  const long long* __restrict__ cell_off, int* __restrict__ entries)
+                                                  const long long* __restrict__ cell_off, int* __restrict__ entries,
+                                                  const unsigned long long* __restrict__ ok)
 {
     const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nB) return;
+    if (b >= nB || (ok && !*ok)) return;
     const int t = tileB ? tileB[b] : 0;
     const TileGrid g = grid[t];
     const int4 m = mbrB[b];
@@ -539,12 +552,14 @@ struct ProbeArgs {
     const int4* mbrB;
     const TileGrid* grid; const long long* cellbase; const long long* cell_off; const int* entries;
     int n_tiles;
+    const unsigned long long* ok;     // not null: probe nothing unless *ok (see k_cap_check)
 };
 
 // The cells an A polygon probes (clamped to its tile's grid); false when there are none.
 __device__ __forceinline__ bool probe_range(const ProbeArgs& p, long long a, int4& A, TileGrid& g, long long& base,
                                             int& cx0, int& cx1, int& cy0, int& cy1)
 {
+    if (p.ok && !*p.ok) return false;
     const int t = p.tileA ? p.tileA[a] : 0;
     if (t >= p.n_tiles) return false;
     g = p.grid[t];

@@ -34,6 +34,11 @@ struct sccg_ctx {
     void* pinned_dev = nullptr;     // ... as addressed by kernels
     WorkCounters* counters = nullptr;   // device work counters (counting mode)
     int count_work = 0;
+    // candidate pairs: grid buffers sized before the counts are known (1), only from the counts
+    // (0, two more synchronisations), or too small on purpose (2, to test the redo); per B polygon
+    int cand_speculative = 1;
+    double cand_cells_per_b = 2.0;
+    double cand_entries_per_b = 4.0;
     unsigned long long launches = 0;    // kernels launched by this context (all calls)
     static constexpr int kTileStreams = 8;
     cudaStream_t tstream[kTileStreams] = {};
@@ -729,6 +734,11 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     else if (!strcmp(name, "area_method")) p.area_method = (int32_t)value;
     else if (!strcmp(name, "leaf_words")) p.leaf_words = (int32_t)value;
     else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
+    else if (!strcmp(name, "candidate_speculative")) {
+        if (value < 0 || value > 2) return SCCG_EINVAL;
+        ctx->cand_speculative = (int)value;
+        return SCCG_OK;
+    }
     else return SCCG_EINVAL;
     const int r = validate_params(p);
     if (r) return r;
@@ -897,23 +907,22 @@ int sccg_build_bands(sccg_ctx* ctx, sccg_polyset* s, void* buf, int64_t bytes, v
     return SCCG_OK;
 }
 
-int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, int32_t* pa,
-                         int32_t* pb, int64_t capacity, int64_t* n_pairs, int64_t* tile_pair_off,
-                         void* stream)
+// Candidate pairs (validated arguments). spec: size the grid buffers from cells_per_b and
+// entries_per_b instead of synchronising on their counts; *fits = false then means they were too
+// small and nothing was written. *ncell_out / *nent_out: the sizes used (the exact counts when !spec).
+int candidate_pairs_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, int32_t* pa, int32_t* pb,
+                        int64_t capacity, int64_t* n_pairs, int64_t* tile_pair_off, bool tpo_host, cudaStream_t st,
+                        bool spec, double cells_per_b, double entries_per_b, bool* fits, long long* ncell_out,
+                        long long* nent_out)
 {
-    if (!ctx || !n_pairs || capacity < 0) return SCCG_EINVAL;
-    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
-    if (capacity > 0 && (!is_device_ptr(pa) || !is_device_ptr(pb))) return SCCG_EINVAL;
-    const bool tpo_host = tile_pair_off && !is_device_ptr(tile_pair_off);
-    DeviceGuard g(ctx->device);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int n_tiles = std::max(std::max(A->n_tiles, B->n_tiles), 1);
     const long long nA = A->n, nB = B->n;
     const long long nscan = std::max<long long>(std::max(nA, (long long)n_tiles), 1);
     const long long nb = (nscan + kScanBlock - 1) / kScanBlock + 1;
     const size_t need = carve_size<long long>(n_tiles + 1) * 5 + carve_size<TileGrid>(n_tiles) +
                         carve_size<long long>(nA + 1) * 2 + carve_size<long long>(nb) +
-                        carve_size<int>(nA + 1) + carve_size<unsigned long long>(4);
+                        carve_size<int>(nA + 1) + carve_size<unsigned long long>(4) +
+                        carve_size<unsigned long long>(1);
     int r = ws_reserve(ctx, need);
     if (r) return r;
     Carve cv(ctx->ws);
@@ -928,6 +937,7 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     long long* bsum = cv.take<long long>(nb);
     int* big_list = cv.take<int>(nA + 1);
     unsigned long long* small = cv.take<unsigned long long>(4);   // [0] big count (as unsigned)
+    unsigned long long* ok = spec ? cv.take<unsigned long long>(1) : nullptr;
     long long* h = static_cast<long long*>(ctx->pinned);
     const int4* mA = reinterpret_cast<const int4*>(A->mbr);
     const int4* mB = reinterpret_cast<const int4*>(B->mbr);
@@ -939,11 +949,19 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     ctx->launches += 3;
     r = device_scan(ctx, ncells, n_tiles, cellbase, bsum, st);
     if (r) return r;
-    // 1st sync: number of grid cells
-    r = small_copy(ctx, ctx->pinned_dev, cellbase + n_tiles, sizeof(long long), st);
-    if (r) return r;
-    SCCG_CUDA(ctx, cudaStreamSynchronize(st));
-    const long long ncell = *h;
+    long long ncell = 0;
+    if (spec) {
+        ncell = cells_per_b < 0 ? 1 : (long long)(cells_per_b * (double)nB) + 64LL * n_tiles + 1024;
+        k_cap_check<<<1, 32, 0, st>>>(cellbase + n_tiles, ncell, ok, 1);
+        SCCG_LAUNCHED(ctx, "k_cap_check");
+        ctx->launches += 1;
+    } else {
+        // 1st sync: number of grid cells
+        r = small_copy(ctx, ctx->pinned_dev, cellbase + n_tiles, sizeof(long long), st);
+        if (r) return r;
+        SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+        ncell = *h;
+    }
     const long long nbc = (std::max(ncell, 1LL) + kScanBlock - 1) / kScanBlock + 1;
     r = aux_reserve(ctx, 0, carve_size<unsigned long long>(ncell + 1) + carve_size<long long>(ncell + 1) +
                                 carve_size<int>(ncell + 1) + carve_size<long long>(nbc));
@@ -958,26 +976,36 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
     if (r) return r;
     const unsigned gb = (unsigned)((std::max(nB, 1LL) + 255) / 256);
     if (nB > 0) {
-        k_bin_count<<<gb, 256, 0, st>>>(mB, B->tile, nB, grid, cellbase, ccount);
+        k_bin_count<<<gb, 256, 0, st>>>(mB, B->tile, nB, grid, cellbase, ccount, ok);
         SCCG_LAUNCHED(ctx, "k_bin_count");
         ctx->launches += 1;
     }
     r = device_scan(ctx, reinterpret_cast<const long long*>(ccount), ncell, cell_off, bsum2, st);
     if (r) return r;
-    // 2nd sync: number of cell registrations
-    r = small_copy(ctx, ctx->pinned_dev, cell_off + ncell, sizeof(long long), st);
-    if (r) return r;
-    SCCG_CUDA(ctx, cudaStreamSynchronize(st));
-    const long long nent = *h;
+    long long nent = 0;
+    if (spec) {
+        nent = entries_per_b < 0 ? 1 : (long long)(entries_per_b * (double)nB) + 1024;
+        k_cap_check<<<1, 32, 0, st>>>(cell_off + ncell, nent, ok, 0);
+        SCCG_LAUNCHED(ctx, "k_cap_check");
+        ctx->launches += 1;
+    } else {
+        // 2nd sync: number of cell registrations
+        r = small_copy(ctx, ctx->pinned_dev, cell_off + ncell, sizeof(long long), st);
+        if (r) return r;
+        SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+        nent = *h;
+    }
+    *ncell_out = ncell;
+    *nent_out = nent;
     r = aux_reserve(ctx, 1, carve_size<int>(nent + 1));
     if (r) return r;
     int* entries = static_cast<int*>(ctx->aux[1]);
     if (nB > 0) {
-        k_bin_fill<<<gb, 256, 0, st>>>(mB, B->tile, nB, grid, cellbase, cursor, cell_off, entries);
+        k_bin_fill<<<gb, 256, 0, st>>>(mB, B->tile, nB, grid, cellbase, cursor, cell_off, entries, ok);
         SCCG_LAUNCHED(ctx, "k_bin_fill");
         ctx->launches += 1;
     }
-    ProbeArgs pr{mA, A->tile, nA, mB, grid, cellbase, cell_off, entries, n_tiles};
+    ProbeArgs pr{mA, A->tile, nA, mB, grid, cellbase, cell_off, entries, n_tiles, ok};
     r = zero_async(ctx, small, sizeof(unsigned long long) * 4, st);
     if (r) return r;
     unsigned* big_n = reinterpret_cast<unsigned*>(small);
@@ -1004,14 +1032,47 @@ int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyse
         ctx->launches += 1;
     }
     r = small_copy(ctx, ctx->pinned_dev, offs + nA, sizeof(long long), st);
+    if (!r && spec) r = small_copy(ctx, static_cast<char*>(ctx->pinned_dev) + 8, ok, sizeof(unsigned long long), st);
     if (r) return r;
     if (tpo_host)
         SCCG_CUDA(ctx, cudaMemcpyAsync(tile_pair_off, tpo_dev, sizeof(long long) * (n_tiles + 1),
                                        cudaMemcpyDeviceToHost, st));
-    // 3rd sync: number of pairs
+    // last (with spec, only) sync: number of pairs
     SCCG_CUDA(ctx, cudaStreamSynchronize(st));
-    *n_pairs = *h;
-    return *h > capacity ? SCCG_ECAPACITY : SCCG_OK;
+    *n_pairs = h[0];
+    *fits = !spec || h[1] != 0;
+    if (!*fits) return SCCG_OK;
+    return h[0] > capacity ? SCCG_ECAPACITY : SCCG_OK;
+}
+
+int sccg_candidate_pairs(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, int32_t* pa,
+                         int32_t* pb, int64_t capacity, int64_t* n_pairs, int64_t* tile_pair_off,
+                         void* stream)
+{
+    if (!ctx || !n_pairs || capacity < 0) return SCCG_EINVAL;
+    if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
+    if (capacity > 0 && (!is_device_ptr(pa) || !is_device_ptr(pb))) return SCCG_EINVAL;
+    const bool tpo_host = tile_pair_off && !is_device_ptr(tile_pair_off);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int mode = ctx->cand_speculative;
+    bool fits = true;
+    long long ncell = 0, nent = 0;
+    if (mode) {
+        const double cpb = mode == 2 ? -1.0 : ctx->cand_cells_per_b;
+        const double epb = mode == 2 ? -1.0 : ctx->cand_entries_per_b;
+        const int r = candidate_pairs_run(ctx, A, B, pa, pb, capacity, n_pairs, tile_pair_off, tpo_host, st, true, cpb,
+                                          epb, &fits, &ncell, &nent);
+        if (r || fits) return r;
+    }
+    // the buffers were too small (or sizing by counts was asked for): exact sizes, then remember them
+    const int r = candidate_pairs_run(ctx, A, B, pa, pb, capacity, n_pairs, tile_pair_off, tpo_host, st, false, 0.0,
+                                      0.0, &fits, &ncell, &nent);
+    if ((r == SCCG_OK || r == SCCG_ECAPACITY) && mode == 1 && B->n > 0) {
+        ctx->cand_cells_per_b = std::max(ctx->cand_cells_per_b, 1.25 * (double)ncell / (double)B->n);
+        ctx->cand_entries_per_b = std::max(ctx->cand_entries_per_b, 1.25 * (double)nent / (double)B->n);
+    }
+    return r;
 }
 
 int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, const int32_t* pa,

@@ -452,3 +452,30 @@ def test_invalid_inputs_rejected_on_the_host(ctx, sccg):
     st = ctx.lib.sccg_pair_areas(ctx.h, ctypes.byref(A.c), ctypes.byref(A.c), host.ctypes.data,
                                  host.ctypes.data, 1, host.ctypes.data, host.ctypes.data, 0, None)
     assert st == 1
+
+
+@pytest.mark.parametrize("kind", ["single", "heavy"])
+def test_candidate_pairs_speculative_sizes(sccg, kind):
+    """The candidate-pair grid's buffers sized before their counts are known (default), from the
+    counts (two more synchronisations), or too small on purpose (the call notices and redoes itself
+    with exact sizes): the same pairs, in the same order, with the same tile offsets, as the oracle."""
+    if kind == "single":
+        w = W.single_tile(seed=8, n=700)
+    else:
+        w = W.heavy_tail(seed=4, n_tiles=2, nuclei_per_tile=1200, tissue_lo=3, tissue_hi=4, tissue_nv_lo=300,
+                         tissue_nv_hi=900, tissue_s_lo=300.0, tissue_s_hi=900.0)
+    mbr_a = O.polygon_areas(w.A.off, w.A.xy, method="rle")[1]
+    mbr_b = O.polygon_areas(w.B.off, w.B.xy, method="rle")[1]
+    ref_pa, ref_pb = O.candidate_pairs(mbr_a, w.A.tile, mbr_b, w.B.tile)
+    got = []
+    for mode in (1, 0, 2, 1):
+        c = sccg.Context(0)
+        c.set_param("candidate_speculative", mode)
+        A, B = c.upload(w.A), c.upload(w.B)
+        pa, pb, tpo = c.candidate_pairs(A, B, with_tile_offsets=True)
+        got.append((pa.cpu().numpy(), pb.cpu().numpy(), np.asarray(tpo)))
+        c.close()
+    for pa, pb, tpo in got:
+        np.testing.assert_array_equal(pa, ref_pa)
+        np.testing.assert_array_equal(pb, ref_pb)
+        np.testing.assert_array_equal(tpo, got[0][2])
