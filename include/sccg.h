@@ -254,9 +254,10 @@ int sccg_rebase_pairs(sccg_ctx* ctx, int32_t* pa, int32_t* pb, int64_t n_pairs, 
  * service). Same results as sccg_jaccard, but it needs no context and allocates nothing: its scratch
  * (4096 partial-sum slots, 160 KB) is a fixed array in device memory that every GPU loading this
  * library keeps until the process exits. It is meant for callers that must not allocate device
- * memory: code running while a CUDA graph is being captured (allocation calls are not allowed
- * there), plugins inside a host application that owns all device memory through its own pool, and
- * latency-critical loops where cudaMalloc/cudaFree would synchronise the device.
+ * memory: plugins inside a host application that owns all device memory through its own pool or
+ * budget (a cudaMalloc of theirs would go around it, or fail because the pool holds the device),
+ * deployments that forbid allocation after start-up, and latency-critical loops where
+ * cudaMalloc/cudaFree would synchronise the device.
  *   inter, uni  device, [n_pairs] (as written by sccg_pair_areas)
  *   out         DEVICE pointer to one sccg_jaccard_result, written asynchronously on `stream`
  *   n_pairs     at most 268,435,456 (4096 slots x 65,536 pairs); larger counts return SCCG_ERANGE

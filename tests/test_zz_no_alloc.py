@@ -1,8 +1,8 @@
 """The allocation-free Jaccard entry point, sccg_jaccard_static, against sccg_jaccard.
 
-Some callers of this library may not allocate device memory: code that runs while a CUDA graph is
-being captured (allocation calls are not allowed during capture), plugins inside a host
-application that owns all device memory through its own pool, and latency-critical loops in which
+Some callers of this library may not allocate device memory: plugins inside a host application
+that owns all device memory through its own pool (their own cudaMalloc would bypass it or fail),
+deployments that forbid allocation after start-up, and latency-critical loops in which
 cudaMalloc/cudaFree would synchronise the device. They use sccg_jaccard_static, whose scratch is a
 fixed array compiled into the library rather than context memory. This file checks it through the
 C ABI, on two calls in a row, against the context-based sccg_jaccard (exact equality: the results
