@@ -202,7 +202,9 @@ int sccg_launch_count(const sccg_ctx* ctx, uint64_t* out /* host */);
  *   J' = (1/n_nonzero) sum inter_k / union_k   (Eq. 1)
  * Each ratio is the IEEE double quotient; the ratios are summed exactly in 128-bit fixed point and
  * rounded once to the nearest double, then divided by n_nonzero, so J' does not depend on the
- * summation order. Both are 0 when no pair intersects.
+ * summation order. Both are 0 when no pair intersects. The fixed-point sum is exact for fewer than
+ * 2^43 pairs: larger n_pairs return SCCG_ERANGE (here and in sccg_batch_run; a segment of
+ * sccg_jaccard_segments cannot hold that many pairs in device memory).
  * `out` may be a host pointer (the call then SYNCHRONISES the stream) or a device pointer (the
  * call stays asynchronous and writes the struct on the stream). */
 typedef struct sccg_jaccard_result {
@@ -227,7 +229,7 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                    int64_t* inter, int64_t* uni, sccg_jaccard_result* out, void* stream);
 
 
-/* Other spatial operators through the same machinery (Sec. 5, "Implications of PixelBox to other
+/* Other spatial operators through the same machinery (Sec. 3.4, "Implications of PixelBox to other
  * spatial operators"; device arrays, asynchronous, both sets prepared):
  * sccg_contains: ST_Contains from the pixel areas, as the paper states it: out[k] bit 0 is set when
  *   the A polygon contains the B polygon (inter[k] = ||q|| > 0), bit 1 when the B polygon contains
@@ -261,11 +263,14 @@ int sccg_rebase_pairs(sccg_ctx* ctx, int32_t* pa, int32_t* pb, int64_t n_pairs, 
  *   inter, uni  device, [n_pairs] (as written by sccg_pair_areas)
  *   out         DEVICE pointer to one sccg_jaccard_result, written asynchronously on `stream`
  *   n_pairs     at most 268,435,456 (4096 slots x 65,536 pairs); larger counts return SCCG_ERANGE
- * The first call on a device (the current device) looks up the array's device address; make that
- * first call before any stream capture. All calls share the one array and leave their partial sums
- * in it; each call writes every slot it reads before reading it, so nothing needs clearing, but two
- * calls whose work overlaps on the GPU (different streams, or different host threads) race on the
- * array and must be serialised by the caller. Returns SCCG_EINVAL for host pointers or n_pairs < 0. */
+ * Every call looks up the array's device address in the current context (a context the caller
+ * created with the driver API has its own copy of the array); the first call in a context also loads
+ * the library's kernels there, so make that first call before any stream capture. inter, uni, out
+ * and `stream` must belong to the current device. All calls share the one array and leave their
+ * partial sums in it; each call writes every slot it reads before reading it, so nothing needs
+ * clearing, but two calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race on the array and must be serialised by the caller. Returns SCCG_EINVAL for host
+ * pointers, pointers on another device or n_pairs < 0. */
 int sccg_jaccard_static(const int64_t* inter, const int64_t* uni, int64_t n_pairs,
                         sccg_jaccard_result* out, void* stream);
 
@@ -283,6 +288,18 @@ int sccg_gather_pairs(sccg_ctx* ctx, const int32_t* src_pa, const int32_t* src_p
 int sccg_jaccard_segments(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni,
                           const int64_t* seg_off, int32_t n_segments,
                           sccg_jaccard_result* out, void* stream);
+
+/* ------------------------------------------------------------------------------------------- */
+/* measurement                                                                                  */
+/* ------------------------------------------------------------------------------------------- */
+/* Integer ALU issue rate of CUDA device `device`, the denominator against which the pair-area and
+ * prepare kernels' integer work is reported (the paper has no counterpart; Sec. 3.3 and Sec. 5.3
+ * argue the method is bound by the per-pixel and per-box position tests). Runs one kernel of 8 CTAs of
+ * 256 threads per SM, each thread `iters` iterations of 24 independent-chain int32 operations
+ * (multiply-add, three-input XOR, three-input add: one integer-unit instruction each), after a short
+ * warm-up, on a private stream timed by CUDA events. ms (host): the kernel's time; lane_ops (host):
+ * the int32 operations it executed (lane_ops / ms is the rate). Synchronous; allocates a few bytes. */
+int sccg_alu_probe(int device, int32_t iters, double* ms, double* lane_ops);
 
 /* ------------------------------------------------------------------------------------------- */
 /* work accounting                                                                              */

@@ -212,7 +212,7 @@ def cross_compare(A, B, method: str = "brute", nthreads: int | None = None):
 # ---------------------------------------------------------------------------- other operators
 
 def touches(ring_p, ring_q) -> bool:
-    """ST_Touches by the rule given with the other operators of Sec. 5: no edge crossing, no vertex
+    """ST_Touches by the rule given with the other operators of Sec. 3.4: no edge crossing, no vertex
     of one strictly within the other, some vertex of one on an edge of the other."""
     a, b = _ring(ring_p), _ring(ring_q)
     return bool(_load().oracle_touches(_ptr(a), a.size // 2, _ptr(b), b.size // 2))
@@ -229,7 +229,7 @@ def touches_pairs(A, B, pa, pb):
 
 
 def contains_flags(area_a, area_b, pa, pb, inter):
-    """ST_Contains as Sec. 5 states it, on pixel areas: bit 0 = the A polygon contains the B polygon
+    """ST_Contains as Sec. 3.4 states it, on pixel areas: bit 0 = the A polygon contains the B polygon
     (||p n q|| = ||q|| > 0), bit 1 = the B polygon contains the A polygon (||p n q|| = ||p|| > 0)."""
     pa, pb, inter = (np.asarray(x, dtype=np.int64) for x in (pa, pb, inter))
     aa, ab = np.asarray(area_a)[pa], np.asarray(area_b)[pb]

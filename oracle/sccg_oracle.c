@@ -296,7 +296,7 @@ i64 oracle_candidate_pairs(const int32_t* mbr_a, const int32_t* tile_a, i64 na,
 }
 
 /* ------------------------------------------------------------------------------------------- */
-/* ST_Touches by the rule stated with the other operators of Sec. 5 ("Implications of PixelBox    */
+/* ST_Touches by the rule stated with the other operators of Sec. 3.4 ("Implications of PixelBox  */
 /* to other spatial operators"): two polygons touch when no edge of one crosses an edge of the    */
 /* other, no vertex of one lies within the other, and at least one vertex of one lies on an edge  */
 /* of the other. Read exactly, with integer orientation tests (|coordinates| <= 2^28, products    */

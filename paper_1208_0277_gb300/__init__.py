@@ -324,6 +324,16 @@ class Context:
                     row_edges=a[5], scan_entries=a[6], scan_pairs=a[7], leaf_pixels=a[8], window_pixels=a[9])
 
 
+def alu_probe(device: int = 0, iters: int = 4096) -> tuple[float, float]:
+    """(ms, int32 lane operations) of one run of the library's integer ALU issue-rate kernel."""
+    lib = _native.load()
+    ms, ops = ctypes.c_double(), ctypes.c_double()
+    st = lib.sccg_alu_probe(int(device), int(iters), ctypes.byref(ms), ctypes.byref(ops))
+    if st != SCCG_OK:
+        raise SccgError(st, "sccg_alu_probe")
+    return ms.value, ops.value
+
+
 def cross_compare(ctx: Context, A: DevicePolySet, B: DevicePolySet, mode: int = MODE_PLAIN, stream=None):
     """The whole path on prepared sets: candidate pairs, pair areas, Jaccard."""
     pa, pb = ctx.candidate_pairs(A, B, stream=stream)

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(_ROOT, "include")
 BUILD_DIR = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsccg.so")
 SOURCES = ["sccg_api.cu"]
-HEADERS = ["pixelbox.cuh", "scanline.cuh", "kernels.cuh"]
+HEADERS = ["leaf64.cuh", "pixelbox.cuh", "scanline.cuh", "kernels.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 # Every symbol include/sccg.h declares (checked by the CPU test suite).
@@ -27,6 +27,7 @@ EXPORTS = [
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
     "sccg_jaccard_static", "sccg_work_counters", "sccg_build_bands", "sccg_gather_pairs",
     "sccg_jaccard_segments", "sccg_rebase_pairs", "sccg_prepare_sets", "sccg_contains", "sccg_touches",
+    "sccg_alu_probe",
 ]
 
 _lock = threading.Lock()
@@ -126,6 +127,8 @@ def load(path: str | None = None):
             "sccg_contains": ([V, PS, PS, V, V, V, I64, V, V], I),
             "sccg_touches": ([V, PS, PS, V, V, I64, V, V], I),
             "sccg_work_counters": ([V, ctypes.POINTER(ctypes.c_uint64), I], I),
+            "sccg_alu_probe": ([I, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                               I),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)

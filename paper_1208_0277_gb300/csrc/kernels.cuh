@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 
+#include "leaf64.cuh"
 #include "pixelbox.cuh"
 #include "scanline.cuh"
 
@@ -29,6 +30,9 @@
 #endif
 #ifndef SCCG_STREAM_MIN_BLOCKS
 #define SCCG_STREAM_MIN_BLOCKS 6
+#endif
+#ifndef SCCG_LEAF_MIN_BLOCKS
+#define SCCG_LEAF_MIN_BLOCKS 4
 #endif
 
 namespace sccg {
@@ -123,6 +127,9 @@ __device__ __forceinline__ long long band_block_size(const int2* v, int nv, int 
 // ----------------------------------------------------------------------------------------------
 // a1 + a2: per-polygon MBR, validation and pixel area ||p||. One warp per polygon.
 // ----------------------------------------------------------------------------------------------
+static_assert(sizeof(Leaf64) <= sizeof(XorRows), "k_prepare's leaf rows share the XorRows bytes");
+
+
 struct PrepArgs {
     long long n;
     const int64_t* off;
@@ -151,6 +158,7 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[SCAN ? 0 : warp];
     XorRows& X = reinterpret_cast<XorRows*>(smem4)[SCAN ? warp : 0];
+    Leaf64& L = *reinterpret_cast<Leaf64*>(&X);        // small windows use the same per-warp bytes
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
@@ -188,7 +196,10 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
         const bool defer = e == 0 && (by_rows || (!SCAN && a.defer_above > 0 && nvl > a.defer_above));
         if (lane == 0 && defer) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
         if (SCAN && e == 0 && !defer && x1 > x0 && y1 > y0) {
-            area = area_stream<COUNT>(v, (int)nvl, x0, y0, x1, y1, X, lane, wc);
+            if (x1 - x0 <= kLeafSide && y1 - y0 <= kLeafSide)
+                area = leaf_area<COUNT>(v, (int)nvl, x0, y0, x1, y1, L, lane, wc);
+            else
+                area = area_stream<COUNT>(v, (int)nvl, x0, y0, x1, y1, X, lane, wc);
         } else if (!SCAN && e == 0 && !defer && x1 > x0 && y1 > y0) {
             const int nv = (int)nvl;
             const bool res = nv <= CAP;
@@ -1292,6 +1303,221 @@ __global__ void __launch_bounds__(256, SCCG_STREAM_MIN_BLOCKS) k_pair_areas_stre
     if (COUNT) flush_counters(a.counters, wc);
 }
 
+// ----------------------------------------------------------------------------------------------
+// Leaf form of the persistent pair areas, for items of at most 64 x 64 pixels that are one leaf each
+// (side <= 64, side^2 < T): both polygons' parity rows are XORed from their rings (or band blocks)
+// streamed as one edge sequence (leaf64.cuh). Each warp reads the data of 32 consecutive pairs at
+// once into a shared table (one lane per pair: item range, MBRs, ring pointers and sizes, band blocks,
+// ||p|| + ||q||), so the dependent index -> MBR -> offset loads are paid once per 32 pairs instead of
+// at the start of every item.
+// ----------------------------------------------------------------------------------------------
+struct LeafPair {
+    long long i0, i1;           // the pair's items: i0 .. i1 - 1
+    int4 ma, mb;                // MBRs of p and q
+    const int2* vp;
+    const int2* vq;
+    const char* bp;             // band blocks (nullptr: none)
+    const char* bq;
+    long long sum_area;         // ||p|| + ||q||
+    int np, nq;
+};
+
+struct LeafSmem {
+    Leaf64 L;
+    LeafPair tab[32];
+    int2 vbuf[2][kLeafVerts];   // staged vertices of the current and the next work item
+};
+static_assert(sizeof(Leaf64) % 16 == 0 && sizeof(LeafPair) % 16 == 0, "LeafSmem keeps its int4 fields aligned");
+
+// ... of the edge records listed in band block `blk` (polygon minimum y `miny`) for the bands of rows
+// y0 .. y0 + H - 1, into the rows at word `base`; a record listed in several of those bands is taken
+// from the first (as xor_stream_bands). Whole warp, converged.
+template <bool COUNT>
+__device__ __forceinline__ void leaf_bands(const char* blk, int miny, int base, int x0, int y0, int W, int H,
+                                           Leaf64& L, int lane, unsigned long long& entries)
+{
+    const int* head = reinterpret_cast<const int*>(blk);
+    const int nb = head[0];
+    const int* boff = head + 4;
+    const int4* ent = reinterpret_cast<const int4*>(blk + 16 + ((4LL * (2 * nb + 1) + 15) & ~15LL));
+    const int b0 = min(max((y0 - miny) >> kBandShift, 0), nb - 1);
+    const int b1 = min(max((y0 + H - 1 - miny) >> kBandShift, 0), nb - 1);
+    for (int b = b0; b <= b1; ++b) {
+        const int e0 = boff[b], e1 = boff[b + 1];
+        for (int k0 = e0; k0 < e1; k0 += 32) {
+            const int k = k0 + lane;
+            bool has = false;
+            int4 rec = make_int4(0, 0, 0, 0);
+            if (k < e1) {
+                rec = ent[k];
+                has = max(b0, (rec.x - miny) >> kBandShift) == b;
+            }
+            // record {ylo, dy, dx, xl}: lower endpoint (xl, ylo), upper (xl + dx, ylo + dy)
+            const LeafEdge e = leaf_edge(has, make_int2(rec.w, rec.x), make_int2(rec.w + rec.z, rec.x + rec.y), x0, y0,
+                                         H, base);
+            leaf_batch<COUNT>(e, W, L, lane, entries);
+        }
+    }
+}
+
+// Lane j: the table entry of pair i + j. Whole warp.
+__device__ __forceinline__ void leaf_fill(const AreasArgs& a, const long long* ioff, long long i, LeafPair* tab,
+                                          int lane)
+{
+    const long long p = i + lane;
+    LeafPair e;
+    e.i0 = e.i1 = 0x7fffffffffffffffLL;
+    e.ma = e.mb = make_int4(0, 0, 0, 0);
+    e.vp = e.vq = nullptr;
+    e.bp = e.bq = nullptr;
+    e.sum_area = 0;
+    e.np = e.nq = 0;
+    if (p < a.n) {
+        e.i0 = ioff[p];
+        e.i1 = ioff[p + 1];
+        if (e.i1 > e.i0) {               // a pair with items has valid indices (k_plan)
+            const int ia = a.pa[p], ib = a.pb[p];
+            e.ma = a.mbrA[ia];
+            e.mb = a.mbrB[ib];
+            const long long oa = a.offA[ia], ob = a.offB[ib];
+            e.np = (int)(a.offA[ia + 1] - oa);
+            e.nq = (int)(a.offB[ib + 1] - ob);
+            e.vp = reinterpret_cast<const int2*>(a.xyA) + oa;
+            e.vq = reinterpret_cast<const int2*>(a.xyB) + ob;
+            e.bp = band_block(a.bandsA, ia);
+            e.bq = band_block(a.bandsB, ib);
+            e.sum_area = a.areaA[ia] + a.areaB[ib];
+        }
+    }
+    tab[lane] = e;
+}
+
+// Start copying the vertices of a work item's two rings into buf (P's then Q's) when both fit and
+// neither polygon reads a band block; commits one cp.async group either way (possibly empty) and
+// returns whether the item is staged. Whole warp.
+__device__ __forceinline__ bool leaf_stage(const LeafPair& te, int2* buf, int lane)
+{
+    const int np = te.np, nq = te.nq;
+    const bool ok = !te.bp && !te.bq && np + nq <= kLeafVerts;
+    if (ok) {
+        const int2* vp = te.vp;
+        const int2* vq = te.vq;
+        for (int k = lane; k < np + nq; k += 32) cp_async8(buf + k, k < np ? vp + k : vq + (k - np));
+    }
+    cp_async_commit();
+    return ok;
+}
+
+// Item `sub` of pair pi (table entry e), one leaf of at most 64 x 64 pixels; buf: its staged
+// vertices (leaf_stage), or nullptr to read the rings (or band blocks) from global memory.
+// Whole warp, converged.
+template <bool COUNT>
+__device__ __forceinline__ void leaf_item(const AreasArgs& a, int side, const LeafPair& te, long long pi,
+                                          long long sub, const int2* buf, Leaf64& L, int lane, WorkCounters& wc)
+{
+    const int4 ma = te.ma, mb = te.mb;
+    const int wx0 = max(ma.x, mb.x), wy0 = max(ma.y, mb.y);
+    const int wx1 = min(ma.z, mb.z), wy1 = min(ma.w, mb.w);
+    const int gx = (wx1 - wx0 + side - 1) / side;
+    const int sx = (int)(sub % gx), sy = (int)(sub / gx);
+    const int x0 = wx0 + sx * side, y0 = wy0 + sy * side;
+    const int W = min(x0 + side, wx1) - x0, H = min(y0 + side, wy1) - y0;
+    if (W <= 0 || H <= 0 || W > kLeafSide || H > kLeafSide) return;     // not an item of this kernel
+    const int2* vp = te.vp;
+    const int2* vq = te.vq;
+    const char* bp = te.bp;
+    const char* bq = te.bq;
+    const int np = te.np, nq = te.nq;
+    const bool single = te.i1 - te.i0 == 1;
+    const long long sum_area = te.sum_area;
+    if (COUNT && lane == 0) wc.window_pixels += (unsigned long long)W * H;
+    __syncwarp();
+    leaf_clear(L, W, H, true, lane);
+    __syncwarp();
+    unsigned long long ce = 0;
+    if (buf) {
+        leaf_rings_staged<COUNT>(buf, np, nq, x0, y0, W, H, L, lane, ce);
+    } else if (!bp && !bq) {
+        leaf_rings<COUNT>(vp, np, 0, vq, nq, kLeafQ, x0, y0, W, H, L, lane, ce);
+    } else {
+        if (bp) leaf_bands<COUNT>(bp, ma.y, 0, x0, y0, W, H, L, lane, ce);
+        else leaf_rings<COUNT>(vp, np, 0, vp, 0, 0, x0, y0, W, H, L, lane, ce);
+        if (bq) leaf_bands<COUNT>(bq, mb.y, kLeafQ, x0, y0, W, H, L, lane, ce);
+        else leaf_rings<COUNT>(vq, nq, kLeafQ, vq, 0, kLeafQ, x0, y0, W, H, L, lane, ce);
+    }
+    __syncwarp();
+    const uint32_t cnt = leaf_pixels<COUNT>(L, W, H, true, lane, wc);
+    if (COUNT) wc.row_entries += ce;
+    if (lane == 0) {
+        if (single) {
+            a.inter[pi] = (int64_t)cnt;
+            a.uni[pi] = sum_area - (int64_t)cnt;
+        } else {
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.inter + pi), (unsigned long long)cnt);
+        }
+    }
+}
+
+// Persistent leaf pair areas over one item queue (guided self-scheduling, as k_pair_areas_stream).
+template <bool COUNT>
+__global__ void __launch_bounds__(256, SCCG_LEAF_MIN_BLOCKS) k_pair_areas_leaf(const AreasArgs a, int side,
+                                                                               const long long* ioff,
+                                                                               unsigned long long* head)
+{
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    LeafSmem& S = reinterpret_cast<LeafSmem*>(smem4)[warp];
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const long long total = ioff[a.n];
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    long long seen = 0;
+    for (;;) {
+        const long long take = min((long long)kItemChunkMax, max((long long)kItemChunk, (total - seen) / (4 * nwarps)));
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(head, (unsigned long long)take);
+        first = __shfl_sync(kFull, first, 0);
+        if ((long long)first >= total) break;
+        seen = (long long)first;
+        const long long last = min((long long)first + take, total);
+        long long i = find_pair(ioff, a.n, (long long)first, lane);
+        long long it = (long long)first;
+        while (it < last) {
+            __syncwarp();
+            leaf_fill(a, ioff, i, S.tab, lane);
+            __syncwarp();
+            int j = 0;
+            while (j < 32 && S.tab[j].i1 <= it) ++j;          // warp-uniform (shared table)
+            if (j < 32) {
+                // two-stage pipeline: the next item's vertices are copied while this one is computed
+                int cur = 0;
+                bool staged = leaf_stage(S.tab[j], S.vbuf[cur], lane);
+                for (;;) {
+                    const long long nit = it + 1;
+                    int j2 = j;
+                    while (j2 < 32 && S.tab[j2].i1 <= nit) ++j2;
+                    const bool more = nit < last && j2 < 32;
+                    __syncwarp();                              // every lane is done with vbuf[cur ^ 1]
+                    bool nstaged = false;
+                    if (more) nstaged = leaf_stage(S.tab[j2], S.vbuf[cur ^ 1], lane);
+                    else cp_async_commit();
+                    cp_async_wait<1>();                        // this item's copies have landed
+                    __syncwarp();
+                    leaf_item<COUNT>(a, side, S.tab[j], i + j, it - S.tab[j].i0, staged ? S.vbuf[cur] : nullptr,
+                                     S.L, lane, wc);
+                    it = nit;
+                    if (!more) break;
+                    j = j2;
+                    staged = nstaged;
+                    cur ^= 1;
+                }
+                cp_async_wait<0>();
+            }
+            if (it < last) i += 32;       // the next item's pair lies beyond this table
+        }
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
 // Chunk-local candidate pairs to indices into the whole sets (pipelined front end).
 __global__ void k_rebase_pairs(int32_t* pa, int32_t* pb, long long n, int base_a, int base_b)
 {
@@ -1302,7 +1528,7 @@ __global__ void k_rebase_pairs(int32_t* pa, int32_t* pb, long long n, int base_a
 }
 
 // ----------------------------------------------------------------------------------------------
-// Other operators through the same results (Sec. 5, implications of PixelBox for other spatial
+// Other operators through the same results (Sec. 3.4, implications of PixelBox for other spatial
 // operators): ST_Contains from the areas, ST_Touches from edge and vertex tests.
 // ----------------------------------------------------------------------------------------------
 // bit 0: the A polygon contains the B polygon (||p n q|| = ||q|| > 0); bit 1: the B polygon contains
@@ -1390,21 +1616,59 @@ __global__ void __launch_bounds__(256) k_touches(const int32_t* pa, const int32_
 }
 
 // ----------------------------------------------------------------------------------------------
-// a6: Jaccard reductions (exact integer sums; ratios summed in 128-bit fixed point, scale 2^100)
+// Integer ALU issue rate (the denominator of the pair-area kernels' roofline): every thread runs
+// kAluChains independent chains of int32 multiply-add, three-input XOR and three-input add, each
+// statement one instruction of the integer units (IMAD, LOP3, IADD3 classes); kAluPerIter of them per
+// iteration. The operands depend on the thread and on `seed`, and the result is stored only when it
+// equals `seed`, so nothing can be folded away or skipped.
+// ----------------------------------------------------------------------------------------------
+constexpr int kAluChains = 12;
+constexpr int kAluPerIter = 24;     // statements per loop iteration (two rounds over the chains)
+
+__global__ void __launch_bounds__(256) k_alu_probe(int iters, uint32_t seed, uint32_t* sink)
+{
+    uint32_t r[kAluChains];
+#pragma unroll
+    for (int k = 0; k < kAluChains; ++k) r[k] = (threadIdx.x + 977u * blockIdx.x) * (2u * k + 1u) ^ (seed + k);
+    const uint32_t m = seed | 1u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int round = 0; round < 2; ++round) {
+#pragma unroll
+            for (int k = 0; k < kAluChains; k += 3) {
+                r[k] = r[k] * m + r[k + 1];                     // multiply-add
+                r[k + 1] = r[k + 1] ^ r[k + 2] ^ r[k];          // three-input XOR
+                r[k + 2] = r[k + 2] + r[k] + r[k + 1];          // three-input add
+            }
+        }
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int k = 0; k < kAluChains; ++k) x ^= r[k];
+    if (x == seed) sink[0] = x;
+}
+
+// ----------------------------------------------------------------------------------------------
+// a6: Jaccard reductions (exact integer sums; ratios summed in 128-bit fixed point, scale 2^84)
 // ----------------------------------------------------------------------------------------------
 struct JPart {
     unsigned long long si, su, nz, fx_lo, fx_hi;
 };
 
-// r = inter/union as an IEEE double, returned as r * 2^100 (exact: r >= 2^-30, so its last
-// significand bit has weight >= 2^-82).
+// Fixed-point scale of the J' sum. A ratio r = inter/union with 0 < inter <= union < 2^31 lies in
+// [2^-31, 1], so its last significand bit weighs at least 2^-83 and r * 2^84 is an integer below
+// 2^85: the sum of fewer than 2^43 ratios is exact in 128 bits (kJaccardMaxPairs).
+constexpr int kJScale = 84;
+constexpr long long kJaccardMaxPairs = 1LL << 43;
+
+// r = inter/union as an IEEE double, returned as r * 2^kJScale (exact, see above).
 __device__ __forceinline__ unsigned __int128 ratio_fixed(long long inter, long long uni)
 {
     const double r = __ddiv_rn((double)inter, (double)uni);
     const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
     const int ex = (int)((bits >> 52) & 0x7ff);
     const unsigned long long man = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = min(max(ex - 1075 + 100, 0), 74);   // in range whenever 0 < inter <= union < 2^31
+    const int sh = min(max(ex - 1075 + kJScale, 0), 74);   // 1 .. 32 whenever 0 < inter <= union < 2^31
     return (unsigned __int128)man << sh;
 }
 
@@ -1531,7 +1795,7 @@ __global__ void __launch_bounds__(256) k_jaccard_final(const JPart* parts, int n
     } else {
         r.J = __ddiv_rn(__ll2double_rn((long long)t.si), __ll2double_rn((long long)t.su));
         const unsigned __int128 s = ((unsigned __int128)t.fx_hi << 64) | t.fx_lo;
-        const double sum = u128_to_double_scaled(s, -100);
+        const double sum = u128_to_double_scaled(s, -kJScale);
         r.Jprime = __ddiv_rn(sum, __ll2double_rn((long long)t.nz));
     }
     *out = r;
@@ -1611,7 +1875,7 @@ __global__ void __launch_bounds__(256) k_jaccard_segments(const int64_t* __restr
             } else {
                 r.J = __ddiv_rn(__ll2double_rn((long long)t.si), __ll2double_rn((long long)t.su));
                 const unsigned __int128 s = ((unsigned __int128)t.fx_hi << 64) | t.fx_lo;
-                r.Jprime = __ddiv_rn(u128_to_double_scaled(s, -100), __ll2double_rn((long long)t.nz));
+                r.Jprime = __ddiv_rn(u128_to_double_scaled(s, -kJScale), __ll2double_rn((long long)t.nz));
             }
             out[sgm] = r;
         }

@@ -6,7 +6,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <mutex>
 #include <new>
 
 #include "kernels.cuh"
@@ -178,6 +177,9 @@ constexpr int kCapBig = 512;      // edge buffer for polygons with more vertices
 #ifndef SCCG_STREAM
 #define SCCG_STREAM 1     // persistent form: stream the edges when every item is one leaf
 #endif
+#ifndef SCCG_LEAF
+#define SCCG_LEAF 1       // ... through k_pair_areas_leaf when items are at most 64 x 64 pixels
+#endif
 // persistent form: first overflow level (0: items over kCapMid go straight to kCapBig)
 constexpr int kCapOvf = SCCG_CAP_OVF;
 static_assert(kCapOvf == 0 || (kCapOvf > kCapMid && kCapOvf < kCapBig), "overflow levels must grow");
@@ -326,6 +328,22 @@ int launch_stream(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* 
     return SCCG_OK;
 }
 
+int launch_leaf(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* ioff, unsigned long long* head,
+                cudaStream_t st)
+{
+    const int wpc = warps_for(ctx, kCapSmall);
+    const size_t smem = sizeof(LeafSmem) * wpc;
+    auto kfn = ctx->count_work ? k_pair_areas_leaf<true> : k_pair_areas_leaf<false>;
+    int r = set_smem(ctx, kfn, smem);
+    unsigned grid = 0;
+    if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &grid);
+    if (r) return r;
+    kfn<<<grid, 32 * wpc, smem, st>>>(a, side, ioff, head);
+    SCCG_LAUNCHED(ctx, "k_pair_areas_leaf");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
 template <int CAP, bool OVF>
 int launch_overflow(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* nitems,
                     const unsigned long long* ovf_list, const unsigned long long* ovf_n, long long ovf_cap,
@@ -415,7 +433,8 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
         ctx->launches += 1;
         int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
         if (!r) r = zero_async(ctx, head, sizeof(unsigned long long), st);
-        if (!r) r = launch_stream(ctx, a, side, nitems_s, ioff_s, head, st);
+        if (!r) r = (SCCG_LEAF && side <= kLeafSide) ? launch_leaf(ctx, a, side, ioff_s, head, st)
+                                                     : launch_stream(ctx, a, side, nitems_s, ioff_s, head, st);
         if (r) return r;
         k_union<<<g, 256, 0, st>>>(a, nitems_s, nitems_b);
         SCCG_LAUNCHED(ctx, "k_union");
@@ -551,7 +570,6 @@ int validate_params(const sccg_params& p)
 constexpr int kStaticParts = 4096;            // partial-sum slots in the fixed array
 constexpr long long kStaticChunk = 65536;     // pairs reduced into one slot
 constexpr long long kStaticMaxPairs = kStaticParts * kStaticChunk;   // 268,435,456 pairs
-constexpr int kStaticMaxDevices = 64;
 
 // One CTA reduces pairs [blockIdx.x * chunk, min(n, (blockIdx.x + 1) * chunk)) into parts[blockIdx.x],
 // exactly as k_jaccard_partial does for its grid-stride share.
@@ -603,30 +621,33 @@ __global__ void __launch_bounds__(256) k_jaccard_partial_chunked(const int64_t* 
 // The fixed scratch array. Every GPU that loads this library holds it until the process exits.
 static __device__ __align__(256) JPart g_jaccard_static_parts[kStaticParts];
 
-std::mutex g_static_mu;
-void* g_static_addr[kStaticMaxDevices] = {};
-
-// Device address of the fixed array on the current device, looked up once per device (the host-side
-// name of a __device__ variable is not a device address and must never be passed to a kernel).
+// Device address of the fixed array in the current context. It is looked up on every call rather
+// than cached: a context created by the caller (cuCtxCreate) holds its own copy of the array, and a
+// device reset can load the library's module at another address, so a cached address could belong
+// to another context. (The host-side name of a __device__ variable is not a device address and is
+// never passed to a kernel.)
 int static_parts_address(JPart** out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_jaccard_static_parts);
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
         return SCCG_ECUDA;
     }
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_jaccard_static_parts);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return SCCG_ECUDA;
-        }
-        g_static_addr[dev] = p;
-    }
-    *out = static_cast<JPart*>(g_static_addr[dev]);
+    *out = static_cast<JPart*>(p);
     return SCCG_OK;
+}
+
+// p is device (or managed) memory of device `dev`.
+bool is_device_ptr_on(const void* p, int dev)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -1160,6 +1181,7 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
                    void* stream)
 {
     if (!ctx || !out || n_pairs < 0) return SCCG_EINVAL;
+    if (n_pairs >= kJaccardMaxPairs) return SCCG_ERANGE;
     if (check_prepared(A) || check_prepared(B)) return SCCG_EINVAL;
     if (!is_device_ptr(out)) return SCCG_EINVAL;
     if (n_pairs > 0 && (!is_device_ptr(pa) || !is_device_ptr(pb) || !is_device_ptr(inter) || !is_device_ptr(uni)))
@@ -1308,6 +1330,7 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
 {
     static_assert(sizeof(JaccardOut) == sizeof(sccg_jaccard_result), "layout");
     if (!ctx || !out || n_pairs < 0) return SCCG_EINVAL;
+    if (n_pairs >= kJaccardMaxPairs) return SCCG_ERANGE;
     if (n_pairs > 0 && (!is_device_ptr(inter) || !is_device_ptr(uni))) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1328,14 +1351,61 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
     return SCCG_OK;
 }
 
+int sccg_alu_probe(int device, int32_t iters, double* ms, double* lane_ops)
+{
+    if (iters <= 0 || !ms || !lane_ops) return SCCG_EINVAL;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+        cudaGetLastError();
+        return SCCG_EINVAL;
+    }
+    DeviceGuard g(device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return SCCG_ECUDA;
+    const unsigned grid = (unsigned)sms * 8u;         // 8 CTAs of 256 threads: 64 warps per SM
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    uint32_t* sink = nullptr;
+    int r = SCCG_OK;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || cudaMalloc(&sink, sizeof(uint32_t)) != cudaSuccess) {
+        r = SCCG_ECUDA;
+    }
+    if (!r) {
+        k_alu_probe<<<grid, 256, 0, st>>>(std::max(1, iters / 16), 0x9E3779B9u, sink);   // warm-up
+        cudaEventRecord(e0, st);
+        k_alu_probe<<<grid, 256, 0, st>>>(iters, 0x9E3779B9u, sink);
+        cudaEventRecord(e1, st);
+        float t = 0.0f;
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            r = SCCG_ECUDA;
+        } else {
+            *ms = (double)t;
+            *lane_ops = (double)grid * 256.0 * (double)iters * (double)kAluPerIter;
+        }
+    }
+    cudaGetLastError();
+    if (sink) cudaFree(sink);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return r;
+}
+
 int sccg_jaccard_static(const int64_t* inter, const int64_t* uni, int64_t n_pairs, sccg_jaccard_result* out,
                         void* stream)
 {
     static_assert(sizeof(JaccardOut) == sizeof(sccg_jaccard_result), "layout");
     if (n_pairs < 0 || !out) return SCCG_EINVAL;
     if (n_pairs > kStaticMaxPairs) return SCCG_ERANGE;
-    if (!is_device_ptr(out)) return SCCG_EINVAL;
-    if (n_pairs > 0 && (!is_device_ptr(inter) || !is_device_ptr(uni))) return SCCG_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SCCG_ECUDA;
+    }
+    if (!is_device_ptr_on(out, dev)) return SCCG_EINVAL;
+    if (n_pairs > 0 && (!is_device_ptr_on(inter, dev) || !is_device_ptr_on(uni, dev))) return SCCG_EINVAL;
     JPart* parts = nullptr;
     int r = static_parts_address(&parts);
     if (r) return r;

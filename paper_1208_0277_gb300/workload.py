@@ -110,41 +110,48 @@ def _pack(x, y, counts, tiles) -> PolySet:
     return PolySet(off=off, xy=xy, tile=np.asarray(tiles, dtype=np.int32))
 
 
-def _fallback_square(x, y, counts, cx, cy, s):
-    """Replace rings left with fewer than 3 vertices by a small axis-aligned square."""
-    bad = np.nonzero(counts < 3)[0]
-    if bad.size == 0:
-        return x, y, counts
-    owner, _ = _segment_ids(counts)
-    keep = ~np.isin(owner, bad)
-    xs, ys = [], []
-    new_counts = counts.copy()
-    # rebuild by concatenation in polygon order
-    parts_x, parts_y = [], []
-    starts = np.cumsum(counts) - counts
-    for i in range(counts.shape[0]):
-        if counts[i] >= 3:
-            parts_x.append(x[starts[i]:starts[i] + counts[i]])
-            parts_y.append(y[starts[i]:starts[i] + counts[i]])
-        else:
-            h = max(1, int(round(s[i] / 4)))
-            x0, y0 = int(round(cx[i])), int(round(cy[i]))
-            parts_x.append(np.array([x0 - h, x0 + h, x0 + h, x0 - h], dtype=x.dtype))
-            parts_y.append(np.array([y0 - h, y0 - h, y0 + h, y0 + h], dtype=y.dtype))
-            new_counts[i] = 4
-    del keep, xs, ys
-    return np.concatenate(parts_x), np.concatenate(parts_y), new_counts
-
-
 def star_rings(rng, cx, cy, s, nv, kind="nucleus"):
     """Star-shaped integer rings around centres (cx, cy) with MBR target s and nv vertices.
 
     Angles theta_k = 2*pi*(k + u_k)/nv with u_k ~ U[0, 1) are strictly increasing, so the real ring is
     star-shaped. Radii: 'nucleus' r_k = (s/2)*U(0.75, 1); 'tissue' r_k = (s/2)*(0.55 + 0.45*h(theta_k))
     with h a sum of 3..6 random low-frequency harmonics normalised to [0, 1] (strongly concave).
-    Vertices are rounded to integers and cyclic duplicates dropped.
+    Vertices are rounded to integers and cyclic duplicates dropped; a ring left with fewer than 3
+    vertices is rejected and drawn again (new angles and radii, same centre, size and vertex count).
     Returns (x int64, y int64, counts int64).
     """
+    x, y, counts = _star_draw(rng, cx, cy, s, nv, kind)
+    for _ in range(100):
+        bad = np.nonzero(counts < 3)[0]
+        if bad.size == 0:
+            return x, y, counts
+        bx, by, bc = _star_draw(rng, np.asarray(cx, dtype=np.float64)[bad], np.asarray(cy, dtype=np.float64)[bad],
+                                np.asarray(s, dtype=np.float64)[bad], np.asarray(nv, dtype=np.int64)[bad], kind)
+        x, y, counts = _replace_rings(x, y, counts, bad, bx, by, bc)
+    raise ValueError("star polygons keep collapsing below 3 vertices (sizes too small for integer rounding)")
+
+
+def _replace_rings(x, y, counts, idx, nx, ny, ncounts):
+    """Rings idx[k] of (x, y, counts) replaced by the k-th ring of (nx, ny, ncounts)."""
+    starts = np.concatenate([[0], np.cumsum(counts)])
+    nstarts = np.concatenate([[0], np.cumsum(ncounts)])
+    new_counts = counts.copy()
+    new_counts[idx] = ncounts
+    src = {int(i): k for k, i in enumerate(idx)}
+    parts_x, parts_y = [], []
+    for i in range(counts.shape[0]):
+        k = src.get(i)
+        if k is None:
+            parts_x.append(x[starts[i]:starts[i + 1]])
+            parts_y.append(y[starts[i]:starts[i + 1]])
+        else:
+            parts_x.append(nx[nstarts[k]:nstarts[k + 1]])
+            parts_y.append(ny[nstarts[k]:nstarts[k + 1]])
+    return np.concatenate(parts_x), np.concatenate(parts_y), new_counts
+
+
+def _star_draw(rng, cx, cy, s, nv, kind):
+    """One draw of star_rings' rings (before rejection of collapsed rings)."""
     cx = np.asarray(cx, dtype=np.float64)
     cy = np.asarray(cy, dtype=np.float64)
     s = np.asarray(s, dtype=np.float64)
@@ -175,9 +182,7 @@ def star_rings(rng, cx, cy, s, nv, kind="nucleus"):
         raise ValueError(kind)
     x = np.rint(cx[owner] + r * np.cos(theta)).astype(np.int64)
     y = np.rint(cy[owner] + r * np.sin(theta)).astype(np.int64)
-    x, y, counts = _dedup_rings(x, y, nv)
-    x, y, counts = _fallback_square(x, y, counts, cx, cy, s)
-    return x, y, counts
+    return _dedup_rings(x, y, nv)
 
 
 def staircase_rings(rng, n, max_cols=12, max_h=15, origin_span=200):
@@ -259,7 +264,6 @@ def _derive_b(rng, A: PolySet, kinds: np.ndarray, shift_nuc: int, shift_tissue: 
     bad = counts < 3
     if bad.any():
         # jitter collapsed a ring: fall back to the shifted copy without jitter
-        bidx = np.nonzero(bad)[0]
         parts_x, parts_y = [], []
         starts = np.cumsum(counts) - counts
         for i in range(counts.shape[0]):
@@ -272,7 +276,6 @@ def _derive_b(rng, A: PolySet, kinds: np.ndarray, shift_nuc: int, shift_tissue: 
                 parts_y.append(p[:, 1] + sy[i])
                 counts[i] = p.shape[0]
         x, y = np.concatenate(parts_x), np.concatenate(parts_y)
-        del bidx
     nx, ny, ncounts, ntiles = new_fn(rng, n_drop)
     x = np.concatenate([x, nx])
     y = np.concatenate([y, ny])

@@ -1,4 +1,4 @@
-"""Other spatial operators (Sec. 5): ST_Contains from the pixel areas and ST_Touches by the stated
+"""Other spatial operators (Sec. 3.4): ST_Contains from the pixel areas and ST_Touches by the stated
 edge/vertex rule, through the C ABI, against the oracle (exact)."""
 import numpy as np
 import pytest

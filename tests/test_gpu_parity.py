@@ -156,6 +156,52 @@ def test_persistent_queue_matches_oracle(sccg, split, T):
     assert_same(gpu_run(c, wm, mode=1), O.cross_compare(A, B, method="rle"))
 
 
+def leaf_case_rings(seed):
+    """Pairs whose windows are exactly 1, 2, 31, 32, 33, 63 and 64 pixels wide and high (rectangles,
+    and triangles and diamonds with steep edges and centres on diagonals inside such windows), pairs
+    with touching MBRs (empty windows, no work items) between them, and random stars."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ra, rb = [], []
+    x = 0
+    for s in (1, 2, 31, 32, 33, 63, 64, 64, 33, 32):
+        for _ in range(3):
+            dx, dy = int(rng.integers(1, 9)), int(rng.integers(1, 9))
+            ra.append([[x, 0], [x + s + dx, 0], [x + s + dx, s + dy], [x, s + dy]])
+            rb.append([[x + dx, dy], [x + dx + s, dy], [x + dx + s, dy + s], [x + dx, dy + s]])
+            # touching MBRs: the window is one column wide and empty of pixels
+            ra.append([[x, 200], [x + 10, 200], [x + 10, 210], [x, 210]])
+            rb.append([[x + 10, 200], [x + 20, 205], [x + 10, 210]])
+            # a steep triangle (edges spanning up to s rows) against a diamond, both in one window
+            ra.append([[x, 300], [x + s // 2 + 1, 300 + s], [x + s + 1, 300]])
+            h = s // 2 + 1
+            rb.append([[x + h, 300], [x + s + 1, 300 + h], [x + h, 300 + s + 1], [x, 300 + h]])
+            x += s + 20
+    cx = rng.uniform(0, x, 200)
+    cy = rng.uniform(400, 600, 200)
+    sz = rng.uniform(10.0, 70.0, 200)
+    nv = rng.integers(3, 80, 200)
+    xs, ys, c = W.star_rings(rng, cx, cy, sz, nv)
+    st = np.concatenate([[0], np.cumsum(c)])
+    stars = [np.stack([xs[st[i]:st[i + 1]], ys[st[i]:st[i + 1]]], 1) for i in range(200)]
+    ra += [r for r in stars[:100]]
+    rb += [r + rng.integers(-4, 5, 2) for r in stars[:100]]
+    rb += [r for r in stars[100:]]
+    return [np.asarray(r) for r in ra], [np.asarray(r) for r in rb]
+
+
+@pytest.mark.parametrize("split", [4096, 1024, 300])
+def test_leaf_items_window_sizes_steep_edges_and_empty_pairs(sccg, split):
+    """The leaf form of the persistent queue (items of at most 64 x 64 pixels, one leaf each, both
+    rings streamed as one edge sequence): windows of 1 to 64 pixels a side (one or two 32-pixel halves
+    per row), edges spanning many rows (their crossings spread over the lanes), pairs without items
+    between pairs with items, and over 32 pairs per queue take (the per-warp pair table is refilled);
+    side 64 and smaller sides that cut windows into several items. Against the oracle."""
+    c = sccg.Context(0, {"split_pixels": split, "T": 8192})
+    ra, rb = leaf_case_rings(31)
+    w = rings_workload(ra, rb)
+    assert_same(gpu_run(c, w, mode=1), O.cross_compare(w.A, w.B))
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_heavy_tail_tissue_and_nuclei(sccg, mode):
     """Tissue polygons (500-2000 vertices, 400-1200 px) among nuclei: large A polygons take the

@@ -257,7 +257,7 @@ def test_jaccard_pairs_with_zero_intersection_are_excluded():
     assert O.jaccard(np.zeros(3, np.int64), np.ones(3, np.int64))["J"] == 0.0
 
 
-# ------------------------------------------------------------------ other operators (Sec. 5)
+# ------------------------------------------------------------------ other operators (Sec. 3.4)
 
 SQ = [[0, 0], [4, 0], [4, 4], [0, 4]]
 
