@@ -57,9 +57,12 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--form", choices=["tiles", "persistent", "graph"], default=None,
                    help="a4 form timed as the headline (default: tiles for config 1, graph for 2-5)")
-    p.add_argument("--config", type=int, default=2,
-                   help="1 single tile, 2 whole slide (default), 3 batched uneven tiles, 4 heavy tail, "
-                   "5 serving over 3")
+    p.add_argument("--config", type=int, default=3,
+                   help="1 single tile, 2 whole slide, 3 batched uneven tiles (default: the largest single-GPU "
+                   "workload), 4 heavy tail, 5 serving over 3")
+    p.add_argument("--other-configs", type=str, default="auto",
+                   help="comma-separated configs measured after the headline one in the same run and reported under "
+                   "other_configs ('auto': 2,4 after config 3 or 5; 'none')")
     p.add_argument("--serve-jobs", type=int, default=0, help="jobs per offered load (default 3000 for config 5, "
                    "1000 otherwise)")
     p.add_argument("--serve-loads", type=str, default="", help="comma-separated offered loads (fractions of the "
@@ -119,7 +122,7 @@ def make_workload(config: int, seed: int, tiles: int):
 def kernel_source_hash() -> str:
     """Hash of the device code (the kernels whose DRAM traffic profiles/traffic.json records)."""
     h = hashlib.sha256()
-    for f in ("pixelbox.cuh", "scanline.cuh", "kernels.cuh"):
+    for f in ("leaf64.cuh", "pixelbox.cuh", "scanline.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_1208_0277_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -385,25 +388,31 @@ def reference_arm(args):
 # ------------------------------------------------------------------------------------------------
 
 def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
+    """Peak (every job submitted at once) and Poisson loads at fractions of it, each replayed from an
+    arrival trace; latency from each job's scheduled arrival to its result in host memory."""
     import numpy as np
     from paper_1208_0277_gb300 import serve
     rng = np.random.default_rng(seed)
     srv = serve.Server(A, B, pa, pb, device=device, slots=3, max_batch_pairs=1 << 20, max_batch_jobs=1024)
     try:
         warm = serve.draw_jobs(rng, tpo, 64)
-        [f.result() for f in [srv.submit(j) for j in warm]]
+        [f.result() for f in srv.submit_many(warm)]
         burst = serve.draw_jobs(rng, tpo, n_jobs)
         t0 = time.perf_counter()
-        res = [f.result() for f in [srv.submit(j) for j in burst]]
+        res = [f.result() for f in srv.submit_many(burst)]
         peak = serve.latency_summary(res, time.perf_counter() - t0)
         mean_pairs = peak["pairs"] / peak["jobs"]
-        out = {"peak": dict(peak, note="all jobs submitted at once"), "loads": []}
+        out = {"peak": dict(peak, note="all jobs submitted at once"), "loads": [],
+               "server": {"slots": len(srv.slots), "max_batch_pairs": srv.cap_pairs, "arena_pairs": srv.arena_pairs,
+                          "device_bytes": srv.device_bytes(), "mem_budget_bytes": srv.mem_budget_bytes},
+               "latency": "scheduled arrival (Poisson trace) -> areas and Jaccard of the job in host memory"}
         for load in loads:
             jobs = serve.draw_jobs(rng, tpo, n_jobs)
             rate = load * peak["pairs_per_s"] / mean_pairs
             res, wall = serve.run_load(srv, jobs, rate, rng)
-            out["loads"].append(dict(serve.latency_summary(res, wall), offered_load=load,
+            out["loads"].append(dict(serve.latency_summary(res, wall, rate), offered_load=load,
                                      offered_jobs_per_s=rate))
+        out["waited_for_memory"] = srv.waited_for_memory
         return out
     finally:
         srv.close()
@@ -413,49 +422,110 @@ def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
 # our arm
 # ------------------------------------------------------------------------------------------------
 
-def main():
-    args = parse_args()
-    if args.form is None:
-        args.form = "graph" if args.config in (2, 3, 4, 5) else "tiles"
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.ablation:
-        ablation(args)
-        return
-    if args.impl == "reference":
-        if rank == 0:
-            reference_arm(args)
-        return
+FORM_NAMES = {"tiles": "one kernel launch per tile",
+              "persistent": "persistent single launch, device work queue",
+              "graph": "persistent launch + Jaccard replayed as one CUDA graph"}
 
+
+_ALU = {}
+
+
+def alu_peak(device: int) -> dict:
+    """The integer ALU issue rate measured on this GPU (sccg_alu_probe: independent int32 multiply-add,
+    three-input XOR and three-input add chains, 64 warps per SM), best of three runs of about 100 ms,
+    with the SM clock sampled while they run. Measured once per process."""
+    if device in _ALU:
+        return _ALU[device]
+    import torch
+    import paper_1208_0277_gb300 as P
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    ms, _ = P.alu_probe(device, 2048)
+    iters = max(64, int(2048 * 100.0 / max(ms, 1e-3)))
+    sampler = ClockSampler(device)
+    sampler.start()
+    sampler.wait_ready()
+    sampler.mark("t_start")
+    best = 0.0
+    for _ in range(3):
+        ms, ops = P.alu_probe(device, iters)
+        best = max(best, ops / (ms / 1e3))
+    sampler.mark("t_end")
+    clocks = sampler.stop()
+    time.sleep(1.0)
+    mhz = clocks["sm_mhz"] if clocks else None
+    per_clk = best / (sms * mhz * 1e6) if mhz else None
+    _ALU[device] = {"lane_ops_per_s": best, "sm_mhz": mhz, "lane_ops_per_sm_clock": per_clk,
+                    "note": (f"measured: sccg_alu_probe (int32 multiply-add / three-input XOR / three-input add "
+                             f"chains, {sms} SMs x 64 warps), best of 3 runs of about 100 ms"
+                             + (f"; {per_clk:.1f} lane-ops per SM per clock at the sampled {mhz:.0f} MHz"
+                                if per_clk else ""))}
+    return _ALU[device]
+
+
+def oracle_dense_tiles(w, pa, pb, tpo, inter, uni, A, B, n_extra: int = 3, seed: int = 7):
+    """Parity at full density: the tile with the most polygons and n_extra seeded other tiles, each
+    compared element by element with the oracle (its O(n m) candidate pairs and its exact
+    row-interval areas of every polygon and every pair of the tile). Returns (summary, seconds)."""
+    import numpy as np
+    import oracle as O
+    from paper_1208_0277_gb300 import workload as W
+    O.build()
+    counts = np.bincount(w.A.tile, minlength=w.n_tiles)
+    dense = int(np.argmax(counts))
+    rng = np.random.default_rng(seed)
+    rest = np.delete(np.arange(w.n_tiles), dense)
+    tiles = sorted([dense] + [int(t) for t in rng.choice(rest, min(n_extra, len(rest)), replace=False)])
+    a_start = np.searchsorted(w.A.tile, np.arange(w.n_tiles + 1))
+    b_start = np.searchsorted(w.B.tile, np.arange(w.n_tiles + 1))
+    ok, pairs, polys = True, 0, 0
+    t0 = time.perf_counter()
+    for t in tiles:
+        sub = W.subset_tiles(w, [t])
+        ref = O.cross_compare(sub.A, sub.B, method="rle")
+        k0, k1 = int(tpo[t]), int(tpo[t + 1])
+        a0, a1, b0, b1 = int(a_start[t]), int(a_start[t + 1]), int(b_start[t]), int(b_start[t + 1])
+        g = dict(pa=pa[k0:k1].cpu().numpy().astype(np.int64) - a0, pb=pb[k0:k1].cpu().numpy().astype(np.int64) - b0,
+                 inter=inter[k0:k1].cpu().numpy(), uni=uni[k0:k1].cpu().numpy(),
+                 area_a=A.area[a0:a1].cpu().numpy(), area_b=B.area[b0:b1].cpu().numpy(),
+                 mbr_a=A.mbr[a0:a1].cpu().numpy(), mbr_b=B.mbr[b0:b1].cpu().numpy())
+        ok = ok and all(np.array_equal(g[k], ref[k]) for k in g)
+        pairs += k1 - k0
+        polys += (a1 - a0) + (b1 - b0)
+    el = time.perf_counter() - t0
+    return {"tiles": tiles, "densest_tile": dense, "densest_tile_polygons": int(counts[dense]),
+            "pairs": pairs, "polygons": polys, "bit_exact": bool(ok),
+            "how": "oracle O(n m) candidate pairs and exact row-interval areas of every polygon and every pair of "
+                   "the densest tile and of seeded other tiles, compared element by element (MBRs, ||p||, pairs, "
+                   "inter, union)"}, el
+
+
+def measure(args, config: int, rank: int, world: int, local_rank: int, dist, full: bool) -> dict:
+    """Time one workload: W warm-up and K timed steps of each form (the headline form first, with the
+    clock sampled), one counting step for the roofline, and the oracle parity sample. full: also the
+    end-to-end pipeline from host memory, the CPU baseline and the serving loads."""
     import numpy as np
     import torch
 
     import paper_1208_0277_gb300 as P
 
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-
-    P.build()
+    form_main = args.form or ("graph" if config in (2, 3, 4, 5) else "tiles")
     params = json.loads(args.params) if args.params else None
     ctx = P.Context(local_rank, params)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
-    w, desc = make_workload(args.config, 1 + rank, args.tiles)
+    w, desc = make_workload(config, 1 + rank, args.tiles)
     gen_s = time.perf_counter() - t0
 
     # inputs resident in HBM (also kept in pinned host memory for the end-to-end measurement)
-    host = {}
-    devb = {}
+    host, devb = {}, {}
     for name, ps in (("A", w.A), ("B", w.B)):
         for f in ("off", "xy", "tile"):
-            a = torch.from_numpy(getattr(ps, f)).pin_memory()
-            host[name + f] = a
+            a = torch.from_numpy(getattr(ps, f))
+            if full:
+                a = a.pin_memory()
+                host[name + f] = a
             devb[name + f] = a.to(dev)
     nA, nB = w.A.n, w.B.n
     outs = {
@@ -467,10 +537,11 @@ def main():
     pa0, pb0, tpo0 = ctx.candidate_pairs(A, B, with_tile_offsets=True)
     n_pairs = int(pa0.numel())
     tuned = None
-    if args.autotune == "on" or (args.autotune == "auto" and args.config in (3, 4, 5)):
+    if args.autotune == "on" or (args.autotune == "auto" and config in (3, 4, 5)):
         from paper_1208_0277_gb300 import tune
-        tuned = tune.tune(ctx, A, B, pa0, pb0, mode=P.MODE_PLAIN if args.form == "tiles" else P.MODE_PERSISTENT)
-        print(f"autotune: {tuned['params']} ({len(tuned['table'])} trials, {tuned['ms']} ms)", file=sys.stderr)
+        tuned = tune.tune(ctx, A, B, pa0, pb0, mode=P.MODE_PLAIN if form_main == "tiles" else P.MODE_PERSISTENT)
+        print(f"config {config} autotune: {tuned['params']} ({len(tuned['table'])} trials, {tuned['ms']} ms)",
+              file=sys.stderr)
     cap = n_pairs
     pa = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     pb = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
@@ -480,6 +551,7 @@ def main():
     jres = torch.zeros(48, dtype=torch.uint8, device=dev)    # device Jaccard result of the graph form
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    tpo_box = [tpo0]
 
     def step(form: str, phases=None):
         e = [ev() for _ in range(5)] if phases is not None else None
@@ -488,6 +560,7 @@ def main():
                                  (devb["Boff"], devb["Bxy"], devb["Btile"], (outs["Bmbr"], outs["Barea"]))])
         if e: e[1].record(stream)
         p_a, p_b, tpo = ctx.candidate_pairs(a, b, capacity=cap, with_tile_offsets=True, out=(pa, pb))
+        tpo_box[0] = tpo
         if e: e[2].record(stream)
         if form == "tiles":
             i, u = ctx.pair_areas_tiles(a, b, p_a, p_b, tpo, out=(inter, uni))
@@ -503,10 +576,11 @@ def main():
         return J
 
     if args.profile_once:
-        J = step(args.form)
+        J = step(form_main)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_once": args.form, "pairs": n_pairs, "J": J["J"]}), flush=True)
-        return
+        print(json.dumps({"profile_once": form_main, "config": config, "pairs": n_pairs, "J": J["J"]}), flush=True)
+        ctx.close()
+        return {}
 
     # one counting step (untimed): algorithmic work per phase for the roofline
     ctx.set_param("count_work", 1)
@@ -515,7 +589,7 @@ def main():
     b_ = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
     work_prep = ctx.work_counters(reset=True)
     p_a, p_b, tpo = ctx.candidate_pairs(a_, b_, capacity=cap, with_tile_offsets=True, out=(pa, pb))
-    if args.form == "tiles":
+    if form_main == "tiles":
         ctx.pair_areas_tiles(a_, b_, p_a, p_b, tpo, out=(inter, uni))
     else:
         ctx.pair_areas(a_, b_, p_a, p_b, mode=P.MODE_PERSISTENT, out=(inter, uni))
@@ -533,9 +607,9 @@ def main():
     # (up to 4000^2 px against thousands of edges) are what the persistent forms' items are for
     skipped = {"tiles": "not timed on the heavy tail: one warp per whole tissue window (about 12 s per "
                         "step); the persistent forms cut those windows into 64 x 64 items"} \
-        if args.config == 4 and args.form != "tiles" else {}
-    for form in [args.form] + [f for f in ("tiles", "persistent", "graph") if f != args.form and f not in skipped]:
-        sampler = ClockSampler(local_rank) if form == args.form else None
+        if config == 4 and form_main != "tiles" else {}
+    for form in [form_main] + [f for f in ("tiles", "persistent", "graph") if f != form_main and f not in skipped]:
+        sampler = ClockSampler(local_rank) if form == form_main else None
         if sampler:
             sampler.start()
             sampler.wait_ready()
@@ -569,47 +643,75 @@ def main():
                              phases_ms=dict(zip(["prepare", "candidate_pairs", "pair_areas", "jaccard"],
                                                 ph.mean(axis=0).round(4).tolist())))
 
-    main_r = results[args.form]
-    ms_per_step = main_r["ms"] / args.steps
+    main_r = results[form_main]
     _, total_pairs = whole_job(0.0, n_pairs, dist, dev)       # every rank compares its own slide
     value = total_pairs * args.steps / (main_r["ms"] / 1e3)
 
-    # roofline of the dominant kernel (average over the timed steps, CUDA events on its stream)
+    # roofline of both hot kernels (average over the timed steps, CUDA events on their stream)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tops = sms * 4 * 32 * 2070e6 / 1e12
+    alu = alu_peak(local_rank)
+    peak_tops = alu["lane_ops_per_s"] / 1e12
     ph = main_r["phases_ms"]
-    if ph["pair_areas"] >= ph["prepare"]:
-        prm = ctx.params()
-        side = math.isqrt(max(prm["split_pixels"], 1))
-        streamed = prm["leaf_words"] and side * side < prm["T"]      # every item one leaf: streamed kernel
-        dom, dom_ms, dom_ops, dom_launches = ("k_pair_areas_plain" if args.form == "tiles" else
-                                              "k_pair_areas_stream" if streamed else "k_pair_areas_persistent"
-                                              ), ph["pair_areas"], ops(work_areas), None
-    else:
-        dom, dom_ms, dom_ops, dom_launches = "k_prepare", ph["prepare"], ops(work_prep), 2
-    achieved = dom_ops / (dom_ms / 1e3) / 1e12
-    traffic = None
+    prm = ctx.params()
+    side = math.isqrt(max(prm["split_pixels"], 1))
+    streamed = prm["leaf_words"] and side * side < prm["T"]      # every item one leaf: streamed kernel
+    k_areas = ("k_pair_areas_plain" if form_main == "tiles" else
+               ("k_pair_areas_leaf" if side <= 64 else "k_pair_areas_stream") if streamed else
+               "k_pair_areas_persistent")
+    traffic_tab = {}
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         try:
-            tj = json.load(open(prof))
-            ent = tj.get(dom, {})
-            if ent.get("source_hash") == kernel_source_hash() and ent.get("workload") == desc["workload"]:
-                traffic = ent.get("bytes_per_step")
+            traffic_tab = json.load(open(prof))
         except (ValueError, OSError):
-            traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32/fp32 ALU lane-ops)",
-                "frac": achieved / peak_tops, "traffic": traffic, "kernel": dom,
-                "peak_note": f"derived: {sms} SMs x 4 SMSPs x 32 lanes x 2070 MHz (max SM clock of measured peaks)",
+            traffic_tab = {}
+
+    def roof(kernel, phase_ms, wc):
+        achieved = ops(wc) / (phase_ms / 1e3) / 1e12
+        ent = traffic_tab.get(kernel, {})
+        traffic = (ent.get("bytes_per_step") if ent.get("source_hash") == kernel_source_hash() and
+                   ent.get("workload") == desc["workload"] else None)
+        return {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32/fp32 ALU lane-ops)",
+                "frac": achieved / peak_tops, "traffic": traffic, "kernel": kernel, "phase_ms": phase_ms,
+                "peak_note": alu["note"],
                 "achieved_note": "algorithmic ops (strip-edge x 17 + box-edge x 33 + leaf (edge, row) crossing x "
                                  "16 + leaf (row, word) x 10 + area crossing value x 14 + area comparison x 4, "
                                  "counted on device) per step / phase time (CUDA events)",
-                "work": work_areas if dom != "k_prepare" else work_prep}
+                "work": wc}
+
+    r_areas = roof(k_areas, ph["pair_areas"], work_areas)
+    r_prep = roof("k_prepare", ph["prepare"], work_prep)
+    roofline, roofline_other = (r_areas, r_prep) if ph["pair_areas"] >= ph["prepare"] else (r_prep, r_areas)
+
+    out = {
+        "config_id": config, "value": value, "ms_per_step": main_r["ms"] / args.steps,
+        "form": FORM_NAMES[form_main], "desc": desc, "pairs_per_step": n_pairs, "polygons": [nA, nB],
+        "tiles": w.n_tiles, "input_bytes": sum(devb[k].numel() * devb[k].element_size() for k in devb),
+        "generation_s": round(gen_s, 1), "params": prm,
+        "autotune": ({"params": tuned["params"], "trials": len(tuned["table"]), "mode": tuned["mode"],
+                      "best_ms": tuned["ms"]} if tuned else None),
+        "roofline": roofline, "roofline_other": roofline_other,
+        # the pair path alone (a3-a6: sets prepared once and resident)
+        "a3_a6": {"value": total_pairs * args.steps / ((main_r["ms"] - args.steps * ph["prepare"]) / 1e3),
+                  "ms_per_step": main_r["ms"] / args.steps - ph["prepare"],
+                  "note": "whole step minus the prepare phase (CUDA events): candidate pairs, pair areas and "
+                          "unions, Jaccard on resident prepared sets"},
+        "rates": {"pixel_tests_per_s": work_areas["leaf_pixels"] / (ph["pair_areas"] / 1e3),
+                  "window_pixels_per_s": work_areas["window_pixels"] / (ph["pair_areas"] / 1e3),
+                  "note": "pixel tests = (pixel, polygon) memberships decided one pixel at a time in leaves; "
+                          "window pixels = pixels of the pair windows (or work items) resolved"},
+        "clocks": main_r["clocks"], "gpu_launches": main_r["launches"], "phases_ms": ph,
+        "jaccard": {"J": main_r["J"]["J"], "Jprime": main_r["J"]["Jprime"], "n_nonzero": main_r["J"]["n_nonzero"]},
+        "other_forms": {f: {"form": FORM_NAMES[f], "value": total_pairs * args.steps / (o["ms"] / 1e3),
+                            "ms_per_step": o["ms"] / args.steps, "phases_ms": o["phases_ms"],
+                            "gpu_launches": o["launches"]}
+                        for f, o in results.items() if f != form_main} |
+                       {f: {"form": FORM_NAMES[f], "skipped": why} for f, why in skipped.items()},
+    }
 
     # end-to-end through the public API with host buffers: the copy-overlapped pipeline over pinned
     # host sets (H2D of every input byte and D2H of every pair's indices and areas plus J each step)
-    e2e = None
-    if not args.no_e2e:
+    if full and not args.no_e2e:
         from paper_1208_0277_gb300.pipeline import HostSet, Pipeline
         pipe = Pipeline(ctx, HostSet(host["Aoff"], host["Axy"], host["Atile"]),
                         HostSet(host["Boff"], host["Bxy"], host["Btile"]), w.n_tiles, chunks=args.e2e_chunks,
@@ -627,94 +729,174 @@ def main():
             pipe.run()
         torch.cuda.synchronize()
         e_ms, _ = whole_job(1e3 * (time.perf_counter() - t0), n_pairs, dist, dev)
-        e2e = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pipe.h2d_bytes,
-               "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
-               "chunks": len(pipe.chunks), "chunk_growth": args.e2e_growth, "same_results_as_device_run": e2e_same,
-               "how": "paper_1208_0277_gb300.pipeline: tiles in chunks, H2D of chunk k+1 overlapped with chunk k "
-                      "(prepare, candidate pairs, persistent pair areas), results D2H as they finish, one Jaccard; "
-                      "host wall clock"}
+        out["e2e"] = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pipe.h2d_bytes,
+                      "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
+                      "chunks": len(pipe.chunks), "chunk_growth": args.e2e_growth,
+                      "same_results_as_device_run": e2e_same,
+                      "how": "paper_1208_0277_gb300.pipeline: tiles in chunks, H2D of chunk k+1 overlapped with chunk "
+                             "k (prepare, candidate pairs, persistent pair areas), results D2H as they finish, one "
+                             "Jaccard; host wall clock"}
+        del pipe
 
-    # CPU baseline (rank 0, N=1): the oracle on the host cores, with a parity check on the sample
-    cpu = None
-    parity = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == 4:
+    # oracle parity on the device results of the last timed step (rank 0, N = 1), and the CPU baseline
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
         O.build()
-        (o_pa, o_pb), idx, (o_i, o_u), el = oracle_sample_pairs(w, target_s=15.0)
-        k0 = len(o_pa)
-        cpu = {"value": len(idx) / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"uniform sample of {len(idx)} of the {k0} candidate pairs of tile 0 ({el:.1f} s): the "
-                         "oracle's exact row-interval pair areas (its brute force would take hours on the "
-                         "4000^2-px tissue windows); extrapolated per pair"}
-        parity = {"sample_pairs": int(len(idx)), "tile0_pairs": k0,
-                  "bit_exact": bool(np.array_equal(pa[:k0].cpu().numpy(), o_pa) and
-                                    np.array_equal(pb[:k0].cpu().numpy(), o_pb) and
-                                    np.array_equal(inter[:k0].cpu().numpy()[idx], o_i) and
-                                    np.array_equal(uni[:k0].cpu().numpy()[idx], o_u))}
-    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle as O
-        O.build()
-        res, tiles, el = oracle_sample(w, target_s=15.0)
-        k = len(res["pa"])
-        cpu = {"value": k / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"first {tiles} of {w.n_tiles} tiles ({k} candidate pairs, {el:.1f} s): brute-force "
-                         "pixel areas of both sets, candidate pairs, pair areas, Jaccard"}
-        g_pa = pa[:k].cpu().numpy()
-        g_pb = pb[:k].cpu().numpy()
-        g_i = inter[:k].cpu().numpy()
-        g_u = uni[:k].cpu().numpy()
-        parity = {"sample_pairs": k,
-                  "bit_exact": bool(np.array_equal(g_pa, res["pa"]) and np.array_equal(g_pb, res["pb"]) and
-                                    np.array_equal(g_i, res["inter"]) and np.array_equal(g_u, res["uni"]))}
+        torch.cuda.synchronize()
+        if config == 4:
+            (o_pa, o_pb), idx, (o_i, o_u), el = oracle_sample_pairs(w, target_s=15.0)
+            k0 = len(o_pa)
+            cpu = {"value": len(idx) / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"uniform sample of {len(idx)} of the {k0} candidate pairs of tile 0 ({el:.1f} s): the "
+                             "oracle's exact row-interval pair areas (its brute force would take hours on the "
+                             "4000^2-px tissue windows); extrapolated per pair"}
+            parity = {"sample_pairs": int(len(idx)), "tile0_pairs": k0,
+                      "bit_exact": bool(np.array_equal(pa[:k0].cpu().numpy(), o_pa) and
+                                        np.array_equal(pb[:k0].cpu().numpy(), o_pb) and
+                                        np.array_equal(inter[:k0].cpu().numpy()[idx], o_i) and
+                                        np.array_equal(uni[:k0].cpu().numpy()[idx], o_u))}
+        else:
+            res, tiles, el = oracle_sample(w, target_s=15.0)
+            k = len(res["pa"])
+            cpu = {"value": k / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"first {tiles} of {w.n_tiles} tiles ({k} candidate pairs, {el:.1f} s): brute-force "
+                             "pixel areas of both sets, candidate pairs, pair areas, Jaccard"}
+            parity = {"sample_pairs": k, "sample_tiles": tiles,
+                      "bit_exact": bool(np.array_equal(pa[:k].cpu().numpy(), res["pa"]) and
+                                        np.array_equal(pb[:k].cpu().numpy(), res["pb"]) and
+                                        np.array_equal(inter[:k].cpu().numpy(), res["inter"]) and
+                                        np.array_equal(uni[:k].cpu().numpy(), res["uni"]))}
+            if config in (3, 5):
+                dense, dense_s = oracle_dense_tiles(w, pa, pb, tpo_box[0], inter, uni, A, B)
+                parity["dense_tiles"] = dict(dense, seconds=round(dense_s, 1))
+                parity["bit_exact"] = parity["bit_exact"] and dense["bit_exact"]
+        out["parity_vs_oracle"] = parity
+        if full:
+            out["cpu_baseline"] = cpu
+        else:
+            out["oracle_pairs_per_s"] = cpu["value"]
 
-    serving = None
-    loads_arg = args.serve_loads or ("0.5,0.8,0.95" if args.config == 5 else "0.8")
-    if loads_arg != "none":
-        loads = [float(x) for x in loads_arg.split(",") if x]
-        n_jobs = args.serve_jobs or (3000 if args.config == 5 else 1000)
-        serving = serving_results(A, B, pa[:n_pairs], pb[:n_pairs], tpo0, loads, n_jobs, local_rank)
-        serving["jobs_per_load"] = n_jobs
-        serving["job_pairs"] = "log-uniform 100-50,000, clipped to the tile's candidate pairs"
+    # stream admission of tile tasks (Sec. 4.2's buffer triggers, GPU streams only): static round robin
+    # against admission by buffer state with the smallest tasks moved to idle streams
+    if full and config in (3, 5) and rank == 0:
+        from paper_1208_0277_gb300 import schedule
+        tasks = schedule.tile_tasks(tpo_box[0])
+        sched = {"tasks": len(tasks), "streams": 4, "depth": 4, "window": 2,
+                 "task": "one tile's pair areas, one kernel launch (one warp per pair)",
+                 "how": "host wall clock from the first admission to the last completion, median of 3 after 1 "
+                        "warm-up; results checked against the resident run"}
+        for policy in ("static", "dynamic"):
+            ts, mig, waits, same = [], 0, 0, True
+            for rep in range(4):
+                i2 = torch.full_like(inter, -7)
+                u2 = torch.full_like(uni, -7)
+                ex = schedule.GpuExecutor(ctx, A, B, pa[:n_pairs], pb[:n_pairs], i2, u2, n_streams=4,
+                                          device=local_rank)
+                sch = schedule.Scheduler(ex, n_streams=4, depth=4, window=2, policy=policy)
+                torch.cuda.synchronize()
+                el, _ = sch.run(tasks)
+                torch.cuda.synchronize()
+                if rep:
+                    ts.append(el)
+                    mig, waits = sch.migrations, sch.producer_waits
+                same = same and bool(torch.equal(i2[:n_pairs], inter[:n_pairs]) and
+                                     torch.equal(u2[:n_pairs], uni[:n_pairs]))
+            el = statistics.median(ts)
+            sched[policy] = {"ms": 1e3 * el, "pairs_per_s": n_pairs / el, "migrations": mig,
+                             "producer_waits": waits, "same_results": same}
+        out["stream_admission"] = sched
 
+    if full:
+        loads_arg = args.serve_loads or ("0.5,0.8,0.95" if config in (3, 5) else "0.8")
+        if loads_arg != "none":
+            loads = [float(x) for x in loads_arg.split(",") if x]
+            n_jobs = args.serve_jobs or (3000 if config in (3, 5) else 1000)
+            serving = serving_results(A, B, pa[:n_pairs], pb[:n_pairs], tpo0, loads, n_jobs, local_rank)
+            serving["jobs_per_load"] = n_jobs
+            serving["job_pairs"] = "log-uniform 100-50,000, clipped to the tile's candidate pairs"
+            if config in (3, 5):
+                serving["workload"] = ("serving (the config-5 workload): jobs of one tile each over the resident sets "
+                                       "above, Poisson arrivals at fractions of the measured peak")
+            out["serving"] = serving
+    ctx.close()
+    del A, B, devb, host, outs, pa, pb, inter, uni
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def other_configs_of(args) -> list:
+    if args.other_configs == "auto":
+        return [2, 4] if args.config in (3, 5) and not args.tiles else []
+    if args.other_configs in ("", "none"):
+        return []
+    return [int(x) for x in args.other_configs.split(",") if x]
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.ablation:
+        ablation(args)
+        return
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return
+
+    import torch
+
+    import paper_1208_0277_gb300 as P
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    P.build()
+
+    head = measure(args, args.config, rank, world, local_rank, dist, full=True)
+    if args.profile_once:
+        return
+    others = {}
+    for c in other_configs_of(args):
+        sub = measure(args, c, rank, world, local_rank, dist, full=False)
+        others[str(c)] = {k: sub[k] for k in ("desc", "value", "ms_per_step", "form", "pairs_per_step", "polygons",
+                                              "tiles", "phases_ms", "other_forms", "roofline", "roofline_other",
+                                              "a3_a6", "autotune", "params", "clocks", "generation_s",
+                                              "parity_vs_oracle", "oracle_pairs_per_s", "gpu_launches")
+                          if k in sub}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    Jd = main_r["J"]
-    form_names = {"tiles": "one kernel launch per tile",
-                  "persistent": "persistent single launch, device work queue",
-                  "graph": "persistent launch + Jaccard replayed as one CUDA graph"}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": dict(desc, form=form_names[args.form],
-                       pairs_per_step=n_pairs, polygons=[nA, nB], tiles=w.n_tiles,
-                       l2="inputs larger than L2 (no flush needed)",
-                       input_bytes=sum(devb[k].numel() * devb[k].element_size() for k in devb),
-                       generation_s=round(gen_s, 1), seed=1 + rank, params=ctx.params(),
-                       autotune=({"params": tuned["params"], "trials": len(tuned["table"]), "mode": tuned["mode"],
-                                  "best_ms": tuned["ms"]} if tuned else None)),
-        "roofline": roofline,
-        # secondary rates of the pair-area phase (counts from the counting step, time from the timed steps)
-        "rates": {"pixel_tests_per_s": work_areas["leaf_pixels"] / (ph["pair_areas"] / 1e3),
-                  "window_pixels_per_s": work_areas["window_pixels"] / (ph["pair_areas"] / 1e3),
-                  "note": "pixel tests = (pixel, polygon) memberships decided one pixel at a time in leaves; "
-                          "window pixels = pixels of the pair windows (or work items) resolved"},
-        "cpu_baseline": cpu,
-        "e2e": e2e,
-        "clocks": main_r["clocks"],
-        "gpu_launches": main_r["launches"],
-        "phases_ms": main_r["phases_ms"],
-        "jaccard": {"J": Jd["J"], "Jprime": Jd["Jprime"], "n_nonzero": Jd["n_nonzero"]},
-        "parity_vs_oracle": parity,
-        "serving": serving,
-        "p99_job_ms": (serving["loads"][-1]["p99_ms"] if serving and serving["loads"] else None),
-        "other_forms": {f: {"form": form_names[f], "value": total_pairs * args.steps / (o["ms"] / 1e3),
-                            "ms_per_step": o["ms"] / args.steps, "phases_ms": o["phases_ms"],
-                            "gpu_launches": o["launches"]}
-                        for f, o in results.items() if f != args.form} |
-                       {f: {"form": form_names[f], "skipped": why} for f, why in skipped.items()},
+        "config": head["desc"],
+        "run": {k: head[k] for k in ("form", "pairs_per_step", "polygons", "tiles", "input_bytes", "generation_s",
+                                     "params", "autotune")} |
+               {"config_id": args.config, "seed": 1 + rank, "l2": "inputs larger than L2 (no flush needed)"},
+        "roofline": head["roofline"],
+        "roofline_other": head["roofline_other"],
+        "a3_a6": head["a3_a6"],
+        "rates": head["rates"],
+        "cpu_baseline": head.get("cpu_baseline"),
+        "e2e": head.get("e2e"),
+        "clocks": head["clocks"],
+        "gpu_launches": head["gpu_launches"],
+        "phases_ms": head["phases_ms"],
+        "jaccard": head["jaccard"],
+        "parity_vs_oracle": head.get("parity_vs_oracle"),
+        "serving": head.get("serving"),
+        "p99_job_ms": (head["serving"]["loads"][-1]["p99_ms"] if head.get("serving") and head["serving"]["loads"]
+                       else None),
+        "other_forms": head["other_forms"],
+        "stream_admission": head.get("stream_admission"),
+        "other_configs": others,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -85,6 +85,10 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out);
 int sccg_ctx_destroy(sccg_ctx* ctx);
 int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value);
 int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out /* host */);
+/* Grow the context's scratch now so that sccg_pair_areas (PERSISTENT), sccg_batch_run and
+ * sccg_jaccard on up to max_pairs pairs allocate nothing later (growing synchronises the device; a
+ * serving loop does it once at start-up). SCCG_ERANGE for max_pairs >= 2^43. */
+int sccg_ctx_reserve(sccg_ctx* ctx, int64_t max_pairs);
 /* Text of the last CUDA error seen by this context ("" if none). */
 const char* sccg_last_error(const sccg_ctx* ctx);
 

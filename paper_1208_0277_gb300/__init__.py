@@ -97,6 +97,11 @@ class Context:
     def set_param(self, name: str, value: int):
         self._check(self.lib.sccg_ctx_set_param(self.h, name.encode(), int(value)), "sccg_ctx_set_param")
 
+    def reserve(self, max_pairs: int):
+        """Size the context's scratch for up to max_pairs pairs now (no allocation, and no device
+        synchronisation, in later pair-area and Jaccard calls up to that size)."""
+        self._check(self.lib.sccg_ctx_reserve(self.h, int(max_pairs)), "sccg_ctx_reserve")
+
     def params(self) -> dict:
         p = _native.ParamsC()
         self._check(self.lib.sccg_ctx_get_params(self.h, ctypes.byref(p)), "sccg_ctx_get_params")
@@ -265,9 +270,10 @@ class Context:
     def decode_jaccard_array(raw) -> list:
         """Decode a host bytes/uint8 array of 48-byte Jaccard structs."""
         import numpy as np
-        buf = np.asarray(raw, dtype=np.uint8).tobytes()
-        return [{k: getattr(r, k) for k, _ in r._fields_}
-                for r in (_native.JaccardC.from_buffer_copy(buf, 48 * i) for i in range(len(buf) // 48))]
+        names = [k for k, _ in _native.JaccardC._fields_]
+        dt = np.dtype([(k, "<i8") for k in names[:4]] + [(k, "<f8") for k in names[4:]])
+        buf = np.ascontiguousarray(np.asarray(raw, dtype=np.uint8))
+        return [dict(zip(names, r)) for r in np.frombuffer(buf.tobytes(), dtype=dt).tolist()]
 
     def launch_count(self) -> int:
         c = ctypes.c_uint64(0)

@@ -27,7 +27,7 @@ EXPORTS = [
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
     "sccg_jaccard_static", "sccg_work_counters", "sccg_build_bands", "sccg_gather_pairs",
     "sccg_jaccard_segments", "sccg_rebase_pairs", "sccg_prepare_sets", "sccg_contains", "sccg_touches",
-    "sccg_alu_probe",
+    "sccg_alu_probe", "sccg_ctx_reserve",
 ]
 
 _lock = threading.Lock()
@@ -110,6 +110,7 @@ def load(path: str | None = None):
             "sccg_ctx_destroy": ([V], I),
             "sccg_ctx_set_param": ([V, ctypes.c_char_p, I64], I),
             "sccg_ctx_get_params": ([V, ctypes.POINTER(ParamsC)], I),
+            "sccg_ctx_reserve": ([V, I64], I),
             "sccg_last_error": ([V], ctypes.c_char_p),
             "sccg_prepare": ([V, PS, V], I),
             "sccg_prepare_sets": ([V, PS, I, V], I),

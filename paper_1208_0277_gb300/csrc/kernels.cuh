@@ -1353,9 +1353,8 @@ __device__ __forceinline__ void leaf_bands(const char* blk, int miny, int base, 
                 has = max(b0, (rec.x - miny) >> kBandShift) == b;
             }
             // record {ylo, dy, dx, xl}: lower endpoint (xl, ylo), upper (xl + dx, ylo + dy)
-            const LeafEdge e = leaf_edge(has, make_int2(rec.w, rec.x), make_int2(rec.w + rec.z, rec.x + rec.y), x0, y0,
-                                         H, base);
-            leaf_batch<COUNT>(e, W, L, lane, entries);
+            leaf_batch<COUNT>(has, make_int2(rec.w, rec.x), make_int2(rec.w + rec.z, rec.x + rec.y), x0, y0, W, H,
+                              base, L, lane, entries);
         }
     }
 }
@@ -1418,9 +1417,14 @@ __device__ __forceinline__ void leaf_item(const AreasArgs& a, int side, const Le
     const int4 ma = te.ma, mb = te.mb;
     const int wx0 = max(ma.x, mb.x), wy0 = max(ma.y, mb.y);
     const int wx1 = min(ma.z, mb.z), wy1 = min(ma.w, mb.w);
-    const int gx = (wx1 - wx0 + side - 1) / side;
-    const int sx = (int)(sub % gx), sy = (int)(sub / gx);
-    const int x0 = wx0 + sx * side, y0 = wy0 + sy * side;
+    const bool single = te.i1 - te.i0 == 1;
+    int x0 = wx0, y0 = wy0;
+    if (!single) {        // sub-window sub of gx per row (fewer than 2^31 items per pair)
+        const int gx = (wx1 - wx0 + side - 1) / side;
+        const int sy = (int)sub / gx;
+        x0 += ((int)sub - sy * gx) * side;
+        y0 += sy * side;
+    }
     const int W = min(x0 + side, wx1) - x0, H = min(y0 + side, wy1) - y0;
     if (W <= 0 || H <= 0 || W > kLeafSide || H > kLeafSide) return;     // not an item of this kernel
     const int2* vp = te.vp;
@@ -1428,7 +1432,6 @@ __device__ __forceinline__ void leaf_item(const AreasArgs& a, int side, const Le
     const char* bp = te.bp;
     const char* bq = te.bq;
     const int np = te.np, nq = te.nq;
-    const bool single = te.i1 - te.i0 == 1;
     const long long sum_area = te.sum_area;
     if (COUNT && lane == 0) wc.window_pixels += (unsigned long long)W * H;
     __syncwarp();

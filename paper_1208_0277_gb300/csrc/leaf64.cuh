@@ -74,30 +74,6 @@ struct LeafEdge {
     float rc;
 };
 
-// Edge a -> b (either order) of the polygon whose rows start at word `base`. An edge with no point
-// right of x0 crosses no pixel centre of the window (every centre lies right of x = x0), and a
-// horizontal one straddles no row: both get span 0. Every product is below 2^30 under the library's
-// coordinate and extent limits (|N| <= (2 dy) |dx| + (2 |x0 - xl| + 1) dy with dy, |dx|, |x0 - xl|
-// at most 2^14 + 64).
-__device__ __forceinline__ LeafEdge leaf_edge(bool has, int2 a, int2 b, int x0, int y0, int H, int base)
-{
-    const bool up = a.y <= b.y;
-    const int ylo = up ? a.y : b.y, yhi = up ? b.y : a.y;
-    const int xl = up ? a.x : b.x, xh = up ? b.x : a.x;
-    LeafEdge e;
-    const int dy = yhi - ylo, dx = xh - xl;
-    const int rlo = max(ylo, y0);
-    const int d2 = dy + dy;
-    e.dx2 = dx + dx;
-    e.N0 = (2 * (rlo - ylo) + 1) * dx - (2 * (x0 - xl) + 1) * dy;
-    e.cap = d2 << 6;
-    e.rc = rcp_approx(small_int_to_float(max(d2, 1)));
-    e.w = base + rlo - y0;
-    const int rhi = min(yhi, y0 + H);
-    e.span = (has && max(xl, xh) > x0) ? max(rhi - rlo, 0) : 0;
-    return e;
-}
-
 // The crossing of an edge with a straddled row (N, words w and w + 64): XOR the prefix mask of its
 // c = ceil(clamp(N, 0, cap) / d2) crossed pixels into the row's halves (pixels beyond the window's
 // width are masked off when the rows are counted). WIDE: the window is over 32 pixels wide.
@@ -113,12 +89,12 @@ __device__ __forceinline__ void leaf_cross(int N, int cap, float rc, int w, Leaf
     }
 }
 
-// All crossings of the batch's edges (one per lane) with the window's rows. Whole warp, converged.
+// All crossings of the batch's edges (one per lane, set up in e; maxs = the warp's longest span)
+// with the window's rows. Whole warp, converged.
 template <bool COUNT, bool WIDE>
-__device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, Leaf64& L, int lane, unsigned long long& entries)
+__device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, int maxs, Leaf64& L, int lane,
+                                             unsigned long long& entries)
 {
-    const int maxs = __reduce_max_sync(kFull, e.span);
-    if (maxs == 0) return;
     if (COUNT) entries += (unsigned long long)e.span;
     if (maxs <= kLeafLoopSpan) {
         for (int s = 0; s < maxs; ++s)
@@ -140,11 +116,34 @@ __device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, Leaf64& L, int l
     }
 }
 
+// One batch of edges, lane k holding edge a -> b (either order; `has` false past the ring's end) of
+// the polygon whose rows start at word `base`, against the window [x0, x0 + W) x [y0, y0 + H).
+// The rows an edge straddles are found first, and a batch with none stops there. An edge with no
+// point right of x0 crosses no pixel centre of the window (every centre lies right of x = x0), and a
+// horizontal one straddles no row: both get span 0. Every product is below 2^30 under the library's
+// coordinate and extent limits (|N| <= (2 dy) |dx| + (2 |x0 - xl| + 1) dy with dy, |dx|, |x0 - xl|
+// at most 2^14 + 64). Whole warp, converged.
 template <bool COUNT>
-__device__ __forceinline__ void leaf_batch(const LeafEdge& e, int W, Leaf64& L, int lane, unsigned long long& entries)
+__device__ __forceinline__ void leaf_batch(bool has, int2 a, int2 b, int x0, int y0, int W, int H, int base,
+                                           Leaf64& L, int lane, unsigned long long& entries)
 {
-    if (W > 32) leaf_batch_w<COUNT, true>(e, L, lane, entries);
-    else leaf_batch_w<COUNT, false>(e, L, lane, entries);
+    const bool up = a.y <= b.y;
+    const int ylo = up ? a.y : b.y, yhi = up ? b.y : a.y;
+    const int rlo = max(ylo, y0);
+    LeafEdge e;
+    e.span = (has && max(a.x, b.x) > x0) ? max(min(yhi, y0 + H) - rlo, 0) : 0;
+    const int maxs = __reduce_max_sync(kFull, e.span);
+    if (maxs == 0) return;
+    const int xl = up ? a.x : b.x;
+    const int dy = yhi - ylo, dx = (up ? b.x : a.x) - xl;
+    const int d2 = dy + dy;
+    e.dx2 = dx + dx;
+    e.N0 = (2 * (rlo - ylo) + 1) * dx - (2 * (x0 - xl) + 1) * dy;
+    e.cap = d2 << 6;
+    e.rc = rcp_approx(small_int_to_float(max(d2, 1)));
+    e.w = base + rlo - y0;
+    if (W > 32) leaf_batch_w<COUNT, true>(e, maxs, L, lane, entries);
+    else leaf_batch_w<COUNT, false>(e, maxs, L, lane, entries);
 }
 
 // The edges of ring vp[0 .. np) (rows at word basep) followed by those of ring vq[0 .. nq) (rows at
@@ -167,8 +166,7 @@ __device__ __forceinline__ void leaf_rings(const int2* vp, int np, int basep, co
             a = v[kk];
             b = v[kk + 1 == n ? 0 : kk + 1];
         }
-        const LeafEdge e = leaf_edge(has, a, b, x0, y0, H, isq ? baseq : basep);
-        leaf_batch<COUNT>(e, W, L, lane, entries);
+        leaf_batch<COUNT>(has, a, b, x0, y0, W, H, isq ? baseq : basep, L, lane, entries);
     }
 }
 
@@ -208,8 +206,7 @@ __device__ __forceinline__ void leaf_rings_staged(const int2* buf, int np, int n
             a = buf[k];
             b = buf[isq ? (k + 1 == E ? np : k + 1) : (k + 1 == np ? 0 : k + 1)];
         }
-        const LeafEdge e = leaf_edge(has, a, b, x0, y0, H, isq ? kLeafQ : 0);
-        leaf_batch<COUNT>(e, W, L, lane, entries);
+        leaf_batch<COUNT>(has, a, b, x0, y0, W, H, isq ? kLeafQ : 0, L, lane, entries);
     }
 }
 

@@ -767,6 +767,15 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     return SCCG_OK;
 }
 
+int sccg_ctx_reserve(sccg_ctx* ctx, int64_t max_pairs)
+{
+    if (!ctx || max_pairs < 0) return SCCG_EINVAL;
+    if (max_pairs >= kJaccardMaxPairs) return SCCG_ERANGE;
+    DeviceGuard g(ctx->device);
+    return ws_reserve(ctx, std::max(persistent_scratch(std::max<long long>(max_pairs, 1)),
+                                    jaccard_scratch(ctx, max_pairs)));
+}
+
 int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out)
 {
     if (!ctx || !out) return SCCG_EINVAL;

@@ -5,22 +5,31 @@ one tile, plus the Jaccard similarities over that slice (Sec. 4.1: the work unit
 the aggregator groups tasks into GPU batches). The two polygon sets and their candidate pairs stay
 resident in device memory; jobs only name pair ranges.
 
-Execution: ``slots`` batch slots, each with its own library context (scratch), CUDA stream and
-preallocated device and pinned-host buffers sized by ``max_batch_pairs`` / ``max_batch_jobs``. A
-batcher thread forms a batch whenever a slot is free: it admits pending jobs in arrival order while
-they fit the slot, so jobs that arrive while other batches run on the GPU join the next batch, and
-batches on different slots overlap on the device. Per batch, on the slot's stream:
+Device memory and admission. The server is given a device-memory budget. Its fixed part is paid at
+construction: per batch slot a library context whose scratch is reserved for the largest batch
+(``Context.reserve``: no allocation, hence no device synchronisation, while serving), a CUDA stream
+and per-job arrays. The rest of the budget is a pair arena: every batch in flight holds one
+contiguous range of it for its pairs' indices and areas (24 bytes per pair). A job is admitted
+(in arrival order) only when a slot is free and the arena has room for its pairs next to the other
+jobs of the forming batch; otherwise it waits until a batch completes and frees its range. A job
+that could never fit (more pairs than a slot or the arena holds) is refused at submit time.
+
+Execution. A batcher thread forms a batch whenever a slot is free and jobs are pending, so jobs that
+arrive while other batches run on the GPU join the next batch, and batches on different slots
+overlap on the device. Per batch, on the slot's stream:
   1. copy the jobs' (source offset, destination offset) pairs host -> device,
-  2. gather the jobs' pair slices into the slot's pair buffer (``sccg_gather_pairs``),
+  2. gather the jobs' pair slices into the batch's arena range (``sccg_gather_pairs``),
   3. exact pair areas, persistent form (``sccg_pair_areas``),
   4. per-job Jaccard (``sccg_jaccard_segments``),
   5. copy areas and Jaccard structs device -> pinned host, record an event.
-A completer thread waits for each batch's event in order and resolves the jobs' futures.
+Each slot has its own completer thread that waits for its batch's event, so batches are resolved in
+the order they finish, not the order they were formed.
 
-Admission: memory is bounded by construction (``slots`` x the slot buffers, checked against
-``mem_budget_bytes`` when the server is built); a job larger than a slot is refused with
-``ValueError`` at submit time; otherwise jobs wait in the queue until a slot frees up. A job whose
-future the client cancels before it is admitted to a batch is dropped.
+Latency. A job carries its scheduled arrival time (``t_arrival``, set by the client that replays an
+arrival trace; the submit time otherwise); a result's latency runs from that arrival to the moment
+its areas and Jaccard are in host memory, so a client or batcher that falls behind shows up in the
+latency rather than hiding it. A job whose future the client cancels before it is admitted to a
+batch is dropped.
 """
 from __future__ import annotations
 
@@ -34,13 +43,16 @@ import numpy as np
 
 from . import Context, MODE_PERSISTENT
 
+ARENA_BYTES_PER_PAIR = 4 + 4 + 8 + 8     # pair indices and the two areas of one pair in a batch
+SCRATCH_BYTES_PER_PAIR = 48              # the persistent form's per-pair queue scratch (context)
+
 
 @dataclasses.dataclass
 class Job:
     p0: int                 # first candidate-pair index (into the resident pair list)
     p1: int                 # one past the last
     tile: int = -1
-    t_submit: float = 0.0
+    t_arrival: float = 0.0  # scheduled arrival (perf_counter clock); 0: the submit time
 
 
 @dataclasses.dataclass
@@ -48,25 +60,54 @@ class JobResult:
     inter: np.ndarray       # int64 [p1 - p0]
     uni: np.ndarray         # int64 [p1 - p0]
     jaccard: dict
-    t_submit: float
+    t_arrival: float
     t_done: float
     batch_jobs: int
 
     @property
     def latency_ms(self) -> float:
-        return 1e3 * (self.t_done - self.t_submit)
+        return 1e3 * (self.t_done - self.t_arrival)
+
+
+class Arena:
+    """First-fit allocator of contiguous pair ranges [0, capacity) (host bookkeeping only)."""
+
+    def __init__(self, capacity: int):
+        self.capacity = int(capacity)
+        self.free = [(0, self.capacity)]          # sorted, disjoint (start, length)
+
+    def largest(self) -> int:
+        return max((n for _, n in self.free), default=0)
+
+    def take(self, n: int) -> int:
+        for k, (s, m) in enumerate(self.free):
+            if m >= n:
+                if m == n:
+                    del self.free[k]
+                else:
+                    self.free[k] = (s + n, m - n)
+                return s
+        raise MemoryError(n)
+
+    def give(self, s: int, n: int):
+        self.free.append((s, n))
+        self.free.sort()
+        merged = []
+        for a, m in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == a:
+                merged[-1] = (merged[-1][0], merged[-1][1] + m)
+            else:
+                merged.append((a, m))
+        self.free = merged
 
 
 class _Slot:
     def __init__(self, device, params, cap_pairs, cap_jobs):
         import torch
         self.ctx = Context(device, params)
+        self.ctx.reserve(cap_pairs)
         dev = torch.device("cuda", device)
         self.stream = torch.cuda.Stream(device=dev)
-        self.pa = torch.empty(cap_pairs, dtype=torch.int32, device=dev)
-        self.pb = torch.empty(cap_pairs, dtype=torch.int32, device=dev)
-        self.inter = torch.empty(cap_pairs, dtype=torch.int64, device=dev)
-        self.uni = torch.empty(cap_pairs, dtype=torch.int64, device=dev)
         self.seg_src = torch.empty(cap_jobs, dtype=torch.int64, device=dev)
         self.seg_dst = torch.empty(cap_jobs + 1, dtype=torch.int64, device=dev)
         self.jres = torch.empty(48 * cap_jobs, dtype=torch.uint8, device=dev)
@@ -76,81 +117,132 @@ class _Slot:
         self.h_uni = torch.empty(cap_pairs, dtype=torch.int64).pin_memory()
         self.h_jres = torch.empty(48 * cap_jobs, dtype=torch.uint8).pin_memory()
         self.event = torch.cuda.Event()
+        self.batch = None           # (jobs, dst offsets, arena start, pairs) of the batch in flight
+        self.cv = threading.Condition()
 
-    def device_bytes(self) -> int:
-        return sum(t.numel() * t.element_size() for t in (self.pa, self.pb, self.inter, self.uni, self.seg_src,
-                                                          self.seg_dst, self.jres))
+    @staticmethod
+    def fixed_bytes(cap_pairs, cap_jobs) -> int:
+        return cap_jobs * 8 + (cap_jobs + 1) * 8 + 48 * cap_jobs + SCRATCH_BYTES_PER_PAIR * cap_pairs
 
 
 class Server:
     def __init__(self, A, B, pa, pb, device: int = 0, slots: int = 3, max_batch_pairs: int = 1 << 19,
-                 max_batch_jobs: int = 1024, mem_budget_bytes: int = 8 << 30, params: dict | None = None):
-        """A, B: prepared DevicePolySets; pa, pb: resident candidate pairs (int32 device tensors)."""
+                 max_batch_jobs: int = 1024, mem_budget_bytes: int = 8 << 30, arena_pairs: int | None = None,
+                 params: dict | None = None):
+        """A, B: prepared DevicePolySets; pa, pb: resident candidate pairs (int32 device tensors).
+        mem_budget_bytes bounds the slots' fixed memory plus the pair arena; arena_pairs (default:
+        the rest of the budget, at most slots x max_batch_pairs) sets the arena explicitly."""
+        import torch
         self.A, self.B, self.pa, self.pb = A, B, pa, pb
         self.cap_pairs, self.cap_jobs = int(max_batch_pairs), int(max_batch_jobs)
+        fixed = slots * _Slot.fixed_bytes(self.cap_pairs, self.cap_jobs)
+        room = (mem_budget_bytes - fixed) // ARENA_BYTES_PER_PAIR
+        if arena_pairs is None:
+            arena_pairs = min(room, slots * self.cap_pairs)
+        if fixed > mem_budget_bytes or arena_pairs > room or arena_pairs < 1:
+            raise ValueError(f"{slots} slots of {max_batch_pairs} pairs and an arena of {arena_pairs} pairs do not "
+                             f"fit a budget of {mem_budget_bytes} bytes")
+        self.mem_budget_bytes = int(mem_budget_bytes)
+        dev = torch.device("cuda", device)
+        self.arena = Arena(arena_pairs)
+        self.a_pa = torch.empty(arena_pairs, dtype=torch.int32, device=dev)
+        self.a_pb = torch.empty(arena_pairs, dtype=torch.int32, device=dev)
+        self.a_inter = torch.empty(arena_pairs, dtype=torch.int64, device=dev)
+        self.a_uni = torch.empty(arena_pairs, dtype=torch.int64, device=dev)
         self.slots = [_Slot(device, params, self.cap_pairs, self.cap_jobs) for _ in range(slots)]
-        # per-slot context scratch of the persistent form (two item queues, overflow list) is ~48 bytes
-        # per pair
-        need = sum(s.device_bytes() + 48 * self.cap_pairs for s in self.slots)
-        if need > mem_budget_bytes:
-            raise ValueError(f"{slots} slots of {max_batch_pairs} pairs need {need} bytes > budget {mem_budget_bytes}")
         self.free = collections.deque(range(slots))
         self.pending = collections.deque()
-        self.inflight = collections.deque()
         self.cv = threading.Condition()
-        self.done_cv = threading.Condition()
         self.stop = False
         self.batches = 0
         self.batched_jobs = 0
+        self.waited_for_memory = 0       # batch formations cut short because the arena was full
         self.batcher = threading.Thread(target=self._batch_loop, daemon=True)
-        self.completer = threading.Thread(target=self._complete_loop, daemon=True)
+        self.completers = [threading.Thread(target=self._complete_loop, args=(k,), daemon=True)
+                           for k in range(slots)]
         self.batcher.start()
-        self.completer.start()
+        for t in self.completers:
+            t.start()
+
+    @property
+    def arena_pairs(self) -> int:
+        return self.arena.capacity
+
+    def device_bytes(self) -> int:
+        return (len(self.slots) * _Slot.fixed_bytes(self.cap_pairs, self.cap_jobs) +
+                self.arena.capacity * ARENA_BYTES_PER_PAIR)
 
     # ------------------------------------------------------------------ client side
-    def submit(self, job: Job) -> cf.Future:
+    def _check(self, job: Job):
         n = job.p1 - job.p0
-        if n <= 0 or n > self.cap_pairs or job.p0 < 0 or job.p1 > self.pa.numel():
-            raise ValueError(f"job of {n} pairs at [{job.p0}, {job.p1}) does not fit a batch slot")
-        fut = cf.Future()
-        job.t_submit = time.perf_counter()
+        if n <= 0 or n > self.cap_pairs or n > self.arena.capacity or job.p0 < 0 or job.p1 > self.pa.numel():
+            raise ValueError(f"job of {n} pairs at [{job.p0}, {job.p1}) does not fit a batch slot or the pair arena")
+
+    def submit(self, job: Job) -> cf.Future:
+        return self.submit_many([job])[0]
+
+    def submit_many(self, jobs) -> list:
+        """Queue jobs in the given order (one lock acquisition); jobs without a scheduled arrival
+        time get the submit time."""
+        for j in jobs:
+            self._check(j)
+        now = time.perf_counter()
+        futs = []
         with self.cv:
-            self.pending.append((job, fut))
+            for j in jobs:
+                if not j.t_arrival:
+                    j.t_arrival = now
+                f = cf.Future()
+                self.pending.append((j, f))
+                futs.append(f)
             self.cv.notify()
-        return fut
+        return futs
 
     def close(self):
         with self.cv:
             self.stop = True
             self.cv.notify_all()
-        with self.done_cv:
-            self.done_cv.notify_all()
+        for s in self.slots:
+            with s.cv:
+                s.cv.notify_all()
         self.batcher.join(timeout=10)
-        self.completer.join(timeout=10)
+        for t in self.completers:
+            t.join(timeout=10)
 
     # ------------------------------------------------------------------ server side
+    def _form(self):
+        """Pending jobs in arrival order that fit one batch and the arena's largest free range
+        (called with self.cv held). Cancelled jobs are dropped."""
+        jobs, npairs = [], 0
+        room = min(self.cap_pairs, self.arena.largest())
+        while self.pending and len(jobs) < self.cap_jobs:
+            job, fut = self.pending[0]
+            n = job.p1 - job.p0
+            if npairs + n > room:
+                if npairs + n <= self.cap_pairs:
+                    self.waited_for_memory += 1
+                break
+            self.pending.popleft()
+            if not fut.set_running_or_notify_cancel():
+                continue                     # cancelled by the client before admission
+            jobs.append((job, fut))
+            npairs += n
+        return jobs, npairs
+
     def _batch_loop(self):
         import torch
         while True:
             with self.cv:
-                while not self.stop and (not self.pending or not self.free):
+                while True:
+                    if self.stop:
+                        return
+                    if self.pending and self.free:
+                        jobs, npairs = self._form()
+                        if jobs:
+                            break
                     self.cv.wait(timeout=0.01)
-                if self.stop:
-                    return
-                jobs, npairs = [], 0
-                while self.pending and len(jobs) < self.cap_jobs:
-                    job, fut = self.pending[0]
-                    n = job.p1 - job.p0
-                    if npairs + n > self.cap_pairs:
-                        break
-                    self.pending.popleft()
-                    if not fut.set_running_or_notify_cancel():
-                        continue                     # cancelled by the client before admission
-                    jobs.append((job, fut))
-                    npairs += n
-                if not jobs:
-                    continue
                 slot_id = self.free.popleft()
+                start = self.arena.take(npairs)
             slot = self.slots[slot_id]
             k = len(jobs)
             src = np.array([j.p0 for j, _ in jobs], dtype=np.int64)
@@ -158,45 +250,51 @@ class Server:
             np.cumsum([j.p1 - j.p0 for j, _ in jobs], out=dst[1:])
             slot.h_src[:k].copy_(torch.from_numpy(src))
             slot.h_dst[:k + 1].copy_(torch.from_numpy(dst))
+            rng = slice(start, start + npairs)
             with torch.cuda.stream(slot.stream):
                 slot.seg_src[:k].copy_(slot.h_src[:k], non_blocking=True)
                 slot.seg_dst[:k + 1].copy_(slot.h_dst[:k + 1], non_blocking=True)
                 c = slot.ctx
-                c.gather_pairs(self.pa, self.pb, slot.seg_src[:k], slot.seg_dst[:k + 1], slot.pa, slot.pb,
-                               stream=slot.stream)
-                c.pair_areas(self.A, self.B, slot.pa[:npairs], slot.pb[:npairs], mode=MODE_PERSISTENT,
-                             out=(slot.inter, slot.uni), stream=slot.stream)
-                c.jaccard_segments(slot.inter, slot.uni, slot.seg_dst[:k + 1], slot.jres, stream=slot.stream)
-                slot.h_inter[:npairs].copy_(slot.inter[:npairs], non_blocking=True)
-                slot.h_uni[:npairs].copy_(slot.uni[:npairs], non_blocking=True)
+                c.gather_pairs(self.pa, self.pb, slot.seg_src[:k], slot.seg_dst[:k + 1], self.a_pa[rng],
+                               self.a_pb[rng], stream=slot.stream)
+                c.pair_areas(self.A, self.B, self.a_pa[rng], self.a_pb[rng], mode=MODE_PERSISTENT,
+                             out=(self.a_inter[rng], self.a_uni[rng]), stream=slot.stream)
+                c.jaccard_segments(self.a_inter[rng], self.a_uni[rng], slot.seg_dst[:k + 1], slot.jres,
+                                   stream=slot.stream)
+                slot.h_inter[:npairs].copy_(self.a_inter[rng], non_blocking=True)
+                slot.h_uni[:npairs].copy_(self.a_uni[rng], non_blocking=True)
                 slot.h_jres[:48 * k].copy_(slot.jres[:48 * k], non_blocking=True)
                 slot.event.record(slot.stream)
-            with self.done_cv:
-                self.inflight.append((slot_id, jobs, dst))
+            with slot.cv:
+                slot.batch = (jobs, dst, start, npairs)
+                slot.cv.notify()
+            with self.cv:
                 self.batches += 1
                 self.batched_jobs += k
-                self.done_cv.notify()
 
-    def _complete_loop(self):
+    def _complete_loop(self, slot_id: int):
+        slot = self.slots[slot_id]
         while True:
-            with self.done_cv:
-                while not self.inflight and not self.stop:
-                    self.done_cv.wait(timeout=0.01)
-                if not self.inflight and self.stop:
+            with slot.cv:
+                while slot.batch is None and not self.stop:
+                    slot.cv.wait(timeout=0.01)
+                if slot.batch is None:
                     return
-                slot_id, jobs, dst = self.inflight.popleft()
-            slot = self.slots[slot_id]
+                jobs, dst, start, npairs = slot.batch
             slot.event.synchronize()
+            now = time.perf_counter()
             k = len(jobs)
-            inter = slot.h_inter[:dst[-1]].numpy().copy()
-            uni = slot.h_uni[:dst[-1]].numpy().copy()
+            inter = slot.h_inter[:npairs].numpy().copy()
+            uni = slot.h_uni[:npairs].numpy().copy()
             jac = Context.decode_jaccard_array(slot.h_jres[:48 * k].numpy())
+            with slot.cv:
+                slot.batch = None
             with self.cv:
+                self.arena.give(start, npairs)
                 self.free.append(slot_id)
                 self.cv.notify()
-            now = time.perf_counter()
             for j, (job, fut) in enumerate(jobs):
-                fut.set_result(JobResult(inter[dst[j]:dst[j + 1]], uni[dst[j]:dst[j + 1]], jac[j], job.t_submit,
+                fut.set_result(JobResult(inter[dst[j]:dst[j + 1]], uni[dst[j]:dst[j + 1]], jac[j], job.t_arrival,
                                          now, k))
 
 
@@ -214,24 +312,37 @@ def draw_jobs(rng, tile_pair_off, n_jobs: int, lo: int = 100, hi: int = 50_000):
 
 
 def run_load(server: Server, jobs, rate_jobs_s: float, rng):
-    """Submit `jobs` with Poisson arrivals at rate_jobs_s; return (results, wall seconds)."""
-    gaps = rng.exponential(1.0 / rate_jobs_s, len(jobs))
-    t0 = time.perf_counter()
+    """Replay a Poisson arrival trace at rate_jobs_s: every job is stamped with its scheduled arrival
+    time and submitted as soon as that time has passed (all jobs that are due go in one call, so a
+    slow client delays submission, which then counts in the latency, instead of thinning the load).
+    Returns (results, wall seconds from the first scheduled arrival to the last result)."""
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_jobs_s, len(jobs)))
     futs = []
-    t_next = t0
-    for job, g in zip(jobs, gaps):
-        t_next += g
-        d = t_next - time.perf_counter()
-        if d > 0:
-            time.sleep(d)
-        futs.append(server.submit(job))
+    k = 0
+    t0 = time.perf_counter() + 0.002
+    while k < len(jobs):
+        now = time.perf_counter() - t0
+        j = int(np.searchsorted(arrivals, now, side="right"))
+        if j > k:
+            for i in range(k, j):
+                jobs[i].t_arrival = t0 + float(arrivals[i])
+            futs += server.submit_many(jobs[k:j])
+            k = j
+        else:
+            wait = float(arrivals[k]) - now
+            if wait > 0.0004:
+                time.sleep(wait - 0.0002)
     res = [f.result() for f in futs]
-    return res, time.perf_counter() - t0
+    return res, max(r.t_done for r in res) - (t0 + float(arrivals[0]))
 
 
-def latency_summary(results, wall_s: float) -> dict:
+def latency_summary(results, wall_s: float, offered_jobs_per_s: float | None = None) -> dict:
     lat = np.array([r.latency_ms for r in results])
     pairs = sum(len(r.inter) for r in results)
-    return {"jobs": len(results), "pairs": int(pairs), "pairs_per_s": pairs / wall_s,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_batch_jobs": float(np.mean([r.batch_jobs for r in results]))}
+    out = {"jobs": len(results), "pairs": int(pairs), "pairs_per_s": pairs / wall_s,
+           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_batch_jobs": float(np.mean([r.batch_jobs for r in results]))}
+    if offered_jobs_per_s:
+        out["offered_pairs_per_s"] = offered_jobs_per_s * pairs / len(results)
+        out["achieved_over_offered"] = out["pairs_per_s"] / out["offered_pairs_per_s"]
+    return out
