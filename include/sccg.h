@@ -71,6 +71,10 @@ typedef struct sccg_params {
                                 per-row parity words, each edge flipping the pixels left of its
                                 crossing; 0: as 32-pixel row strips tested against every edge (the
                                 per-pixel test of Sec. 3.1). Same results. */
+    int32_t pair_lanes;      /* threads per pair in the persistent form's leaf path (items of at most
+                                64 x 64 pixels): 32 (default) one warp per item; 1: pairs whose window
+                                is at most 32 x 32 pixels with at most 96 edges in both rings are done
+                                one lane per pair (beside the warp path for the others). Same results. */
 } sccg_params;
 
 /* sccg_prepare's method for ||p||. ROWS: per pixel row, the crossing positions of the edges that

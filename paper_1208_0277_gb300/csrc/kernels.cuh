@@ -34,6 +34,9 @@
 #ifndef SCCG_LEAF_MIN_BLOCKS
 #define SCCG_LEAF_MIN_BLOCKS 4
 #endif
+#ifndef SCCG_LANE_MIN_BLOCKS
+#define SCCG_LANE_MIN_BLOCKS 6
+#endif
 
 namespace sccg {
 
@@ -127,7 +130,10 @@ __device__ __forceinline__ long long band_block_size(const int2* v, int nv, int 
 // ----------------------------------------------------------------------------------------------
 // a1 + a2: per-polygon MBR, validation and pixel area ||p||. One warp per polygon.
 // ----------------------------------------------------------------------------------------------
-static_assert(sizeof(Leaf64) <= sizeof(XorRows), "k_prepare's leaf rows share the XorRows bytes");
+// Per-warp shared memory of k_prepare's streamed areas: the XorRows of area_stream or the Leaf64 of
+// leaf_area (the same bytes).
+constexpr size_t kPrepWarpBytes = ((sizeof(XorRows) > sizeof(Leaf64) ? sizeof(XorRows) : sizeof(Leaf64)) + 15) &
+                                  ~size_t(15);
 
 
 struct PrepArgs {
@@ -157,8 +163,9 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[SCAN ? 0 : warp];
-    XorRows& X = reinterpret_cast<XorRows*>(smem4)[SCAN ? warp : 0];
-    Leaf64& L = *reinterpret_cast<Leaf64*>(&X);        // small windows use the same per-warp bytes
+    char* wbytes = reinterpret_cast<char*>(smem4) + (SCAN ? warp * kPrepWarpBytes : 0);
+    XorRows& X = *reinterpret_cast<XorRows*>(wbytes);
+    Leaf64& L = *reinterpret_cast<Leaf64*>(wbytes);      // small windows use the same per-warp bytes
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
@@ -1325,7 +1332,6 @@ struct LeafPair {
 struct LeafSmem {
     Leaf64 L;
     LeafPair tab[32];
-    int2 vbuf[2][kLeafVerts];   // staged vertices of the current and the next work item
 };
 static_assert(sizeof(Leaf64) % 16 == 0 && sizeof(LeafPair) % 16 == 0, "LeafSmem keeps its int4 fields aligned");
 
@@ -1391,28 +1397,11 @@ __device__ __forceinline__ void leaf_fill(const AreasArgs& a, const long long* i
     tab[lane] = e;
 }
 
-// Start copying the vertices of a work item's two rings into buf (P's then Q's) when both fit and
-// neither polygon reads a band block; commits one cp.async group either way (possibly empty) and
-// returns whether the item is staged. Whole warp.
-__device__ __forceinline__ bool leaf_stage(const LeafPair& te, int2* buf, int lane)
-{
-    const int np = te.np, nq = te.nq;
-    const bool ok = !te.bp && !te.bq && np + nq <= kLeafVerts;
-    if (ok) {
-        const int2* vp = te.vp;
-        const int2* vq = te.vq;
-        for (int k = lane; k < np + nq; k += 32) cp_async8(buf + k, k < np ? vp + k : vq + (k - np));
-    }
-    cp_async_commit();
-    return ok;
-}
-
-// Item `sub` of pair pi (table entry e), one leaf of at most 64 x 64 pixels; buf: its staged
-// vertices (leaf_stage), or nullptr to read the rings (or band blocks) from global memory.
-// Whole warp, converged.
+// Item `sub` of pair pi (table entry te), one leaf of at most 64 x 64 pixels, its rings (or band
+// blocks) streamed from global memory. Whole warp, converged.
 template <bool COUNT>
 __device__ __forceinline__ void leaf_item(const AreasArgs& a, int side, const LeafPair& te, long long pi,
-                                          long long sub, const int2* buf, Leaf64& L, int lane, WorkCounters& wc)
+                                          long long sub, Leaf64& L, int lane, WorkCounters& wc)
 {
     const int4 ma = te.ma, mb = te.mb;
     const int wx0 = max(ma.x, mb.x), wy0 = max(ma.y, mb.y);
@@ -1438,9 +1427,7 @@ __device__ __forceinline__ void leaf_item(const AreasArgs& a, int side, const Le
     leaf_clear(L, W, H, true, lane);
     __syncwarp();
     unsigned long long ce = 0;
-    if (buf) {
-        leaf_rings_staged<COUNT>(buf, np, nq, x0, y0, W, H, L, lane, ce);
-    } else if (!bp && !bq) {
+    if (!bp && !bq) {
         leaf_rings<COUNT>(vp, np, 0, vq, nq, kLeafQ, x0, y0, W, H, L, lane, ce);
     } else {
         if (bp) leaf_bands<COUNT>(bp, ma.y, 0, x0, y0, W, H, L, lane, ce);
@@ -1489,34 +1476,167 @@ __global__ void __launch_bounds__(256, SCCG_LEAF_MIN_BLOCKS) k_pair_areas_leaf(c
             leaf_fill(a, ioff, i, S.tab, lane);
             __syncwarp();
             int j = 0;
-            while (j < 32 && S.tab[j].i1 <= it) ++j;          // warp-uniform (shared table)
-            if (j < 32) {
-                // two-stage pipeline: the next item's vertices are copied while this one is computed
-                int cur = 0;
-                bool staged = leaf_stage(S.tab[j], S.vbuf[cur], lane);
-                for (;;) {
-                    const long long nit = it + 1;
-                    int j2 = j;
-                    while (j2 < 32 && S.tab[j2].i1 <= nit) ++j2;
-                    const bool more = nit < last && j2 < 32;
-                    __syncwarp();                              // every lane is done with vbuf[cur ^ 1]
-                    bool nstaged = false;
-                    if (more) nstaged = leaf_stage(S.tab[j2], S.vbuf[cur ^ 1], lane);
-                    else cp_async_commit();
-                    cp_async_wait<1>();                        // this item's copies have landed
-                    __syncwarp();
-                    leaf_item<COUNT>(a, side, S.tab[j], i + j, it - S.tab[j].i0, staged ? S.vbuf[cur] : nullptr,
-                                     S.L, lane, wc);
-                    it = nit;
-                    if (!more) break;
-                    j = j2;
-                    staged = nstaged;
-                    cur ^= 1;
-                }
-                cp_async_wait<0>();
+            while (it < last) {
+                while (j < 32 && S.tab[j].i1 <= it) ++j;      // warp-uniform (shared table)
+                if (j == 32) break;
+                leaf_item<COUNT>(a, side, S.tab[j], i + j, it - S.tab[j].i0, S.L, lane, wc);
+                ++it;
             }
-            if (it < last) i += 32;       // the next item's pair lies beyond this table
+            i += 32;
         }
+    }
+    if (COUNT) flush_counters(a.counters, wc);
+}
+
+// ----------------------------------------------------------------------------------------------
+// One lane per pair (threads per pair = 1) for pairs whose window is at most 32 x 32 pixels and
+// whose rings are short: the lane streams both rings itself and keeps the two polygons' parity rows
+// in its own column of the warp's shared memory (word (row << 5) | lane: every lane in its own bank,
+// no atomics), so the warp-wide steps of the leaf kernel (batch setup, span maxima, prefix sums,
+// owner searches, reductions) disappear and 32 pairs progress at once.
+// ----------------------------------------------------------------------------------------------
+constexpr int kLaneSide = 32;            // largest window side of a lane pair
+#ifndef SCCG_LANE_MAX_EDGES
+#define SCCG_LANE_MAX_EDGES 96
+#endif
+constexpr int kLaneMaxEdges = SCCG_LANE_MAX_EDGES;   // edges of both rings of a lane pair, at most
+
+struct LaneSmem {
+    uint32_t r[2 * kLaneSide][32];       // [row][lane]: rows 0..31 of P, then of Q
+};
+
+// k_plan for the leaf kernel. With `lanes`, pairs with a window of at most kLaneSide x kLaneSide
+// pixels and at most kLaneMaxEdges edges in both rings get lane[i] = 1 and no items (the lane kernel
+// does them whole); the others get their items as in k_plan (lane[i] = 0).
+__global__ void k_plan_leaf(const AreasArgs a, int side, int lanes, long long* nitems, long long* lane)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int ia, ib, wx0, wy0, wx1, wy1;
+    long long k = 0;
+    bool by_lane = false;
+    if (!pair_window(a, i, ia, ib, wx0, wy0, wx1, wy1)) {
+        a.inter[i] = -1;
+        a.uni[i] = -1;
+    } else if (wx1 <= wx0 || wy1 <= wy0) {
+        a.inter[i] = 0;
+        a.uni[i] = a.areaA[ia] + a.areaB[ib];
+    } else {
+        const long long e = (a.offA[ia + 1] - a.offA[ia]) + (a.offB[ib + 1] - a.offB[ib]);
+        by_lane = lanes && wx1 - wx0 <= kLaneSide && wy1 - wy0 <= kLaneSide && e <= kLaneMaxEdges;
+        if (!by_lane) {
+            k = (long long)((wx1 - wx0 + side - 1) / side) * ((wy1 - wy0 + side - 1) / side);
+            if (k > 1) a.inter[i] = 0;     // accumulated by atomics
+        }
+    }
+    nitems[i] = k;
+    lane[i] = by_lane ? 1 : 0;
+}
+
+// The parity rows of ring vp[0 .. np) (rows 0 .. H-1 of the lane's column) and, when nq > 0, of ring
+// vq[0 .. nq) (rows kLaneSide ..) over the window [x0, x0 + W) x [y0, y0 + H), W, H <= kLaneSide.
+// The rings are walked as one edge sequence; each step either takes the next edge (its rows
+// straddled inside the window, set up as leaf_batch does) or XORs the crossing of the current edge
+// with its next row into the row's word (leaf_cross's rule: the first c = ceil(N / 2dy) pixels right
+// of x0 flip), so the lane's trip count is its edges plus its crossings. R: the lane's column,
+// R[row << 5]. Returns the number of (edge, row) crossings.
+__device__ __forceinline__ unsigned lane_walk(const int2* vp, int np, const int2* vq, int nq, int x0, int y0, int H,
+                                              uint32_t* R)
+{
+    for (int r = 0; r < H; ++r) {
+        R[r << 5] = 0u;
+        if (nq) R[(kLaneSide + r) << 5] = 0u;
+    }
+    const int2* v = vp;
+    int n = np, j = 1, rowbase = 0;
+    int2 prev = vp[np - 1];
+    int2 nxt = vp[0];
+    int s = 0, span = 0, N = 0, dx2 = 0, cap = 0, w = 0;
+    float rc = 1.0f;
+    unsigned crossings = 0;
+    for (;;) {
+        if (s >= span) {
+            if (j > n) {                        // this ring is done
+                if (rowbase || nq == 0) break;
+                v = vq;
+                n = nq;
+                j = 1;
+                rowbase = kLaneSide;
+                prev = vq[nq - 1];
+                nxt = vq[0];
+            }
+            const int2 cur = nxt;
+            if (j < n) nxt = v[j];              // the next edge's vertex, loaded ahead
+            ++j;
+            const bool up = prev.y <= cur.y;
+            const int ylo = up ? prev.y : cur.y, yhi = up ? cur.y : prev.y;
+            const int xl = up ? prev.x : cur.x, xh = up ? cur.x : prev.x;
+            const int rlo = max(ylo, y0);
+            span = max(prev.x, cur.x) > x0 ? max(min(yhi, y0 + H) - rlo, 0) : 0;
+            s = 0;
+            if (span > 0) {
+                const int dy = yhi - ylo, dx = xh - xl;
+                dx2 = dx + dx;
+                N = (2 * (rlo - ylo) + 1) * dx - (2 * (x0 - xl) + 1) * dy;
+                cap = (dy + dy) << 5;
+                rc = rcp_approx(small_int_to_float(dy + dy));
+                w = rowbase + rlo - y0;
+                crossings += (unsigned)span;
+            }
+            prev = cur;
+        }
+        if (s < span) {
+            const int c = leaf_ceil_div(min(max(N, 0), cap), rc);
+            R[(w + s) << 5] ^= low_mask(c);
+            N += dx2;
+            ++s;
+        }
+    }
+    return crossings;
+}
+
+// ||p n q|| of a lane pair (lane_walk over both rings, then the rows inside both, W columns).
+template <bool COUNT>
+__device__ __forceinline__ uint32_t lane_pair_inter(const int2* vp, int np, const int2* vq, int nq, int x0, int y0,
+                                                    int W, int H, uint32_t* R, WorkCounters& wc)
+{
+    const unsigned crossings = lane_walk(vp, np, vq, nq, x0, y0, H, R);
+    const uint32_t vm = low_mask(W);
+    uint32_t acc = 0;
+    for (int r = 0; r < H; ++r) acc += __popc(R[r << 5] & R[(kLaneSide + r) << 5] & vm);
+    if (COUNT) {
+        wc.row_entries += crossings;
+        wc.row_edges += (unsigned long long)H;
+        wc.leaf_pixels += 2ull * W * H;
+        wc.window_pixels += (unsigned long long)W * H;
+    }
+    return acc;
+}
+
+// Every pair k_plan_leaf marked (lane[i] = 1), one per lane, grid-stride over the pairs.
+template <bool COUNT>
+__global__ void __launch_bounds__(128, SCCG_LANE_MIN_BLOCKS) k_pair_areas_lanes(const AreasArgs a,
+                                                                                const long long* lane)
+{
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    uint32_t* R = &reinterpret_cast<LaneSmem*>(smem4)[warp].r[0][ln];
+    WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) {
+        if (lane[p] != 1) continue;
+        const int ia = a.pa[p], ib = a.pb[p];
+        const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
+        const int x0 = max(ma.x, mb.x), y0 = max(ma.y, mb.y);
+        const int W = min(ma.z, mb.z) - x0, H = min(ma.w, mb.w) - y0;
+        if (W <= 0 || H <= 0 || W > kLaneSide || H > kLaneSide) continue;     // not a lane pair
+        const long long oa = a.offA[ia], ob = a.offB[ib];
+        const uint32_t cnt = lane_pair_inter<COUNT>(reinterpret_cast<const int2*>(a.xyA) + oa,
+                                                    (int)(a.offA[ia + 1] - oa),
+                                                    reinterpret_cast<const int2*>(a.xyB) + ob,
+                                                    (int)(a.offB[ib + 1] - ob), x0, y0, W, H, R, wc);
+        a.inter[p] = (int64_t)cnt;
+        a.uni[p] = a.areaA[ia] + a.areaB[ib] - (int64_t)cnt;
     }
     if (COUNT) flush_counters(a.counters, wc);
 }

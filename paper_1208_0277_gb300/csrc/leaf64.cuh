@@ -90,7 +90,10 @@ __device__ __forceinline__ void leaf_cross(int N, int cap, float rc, int w, Leaf
 }
 
 // All crossings of the batch's edges (one per lane, set up in e; maxs = the warp's longest span)
-// with the window's rows. Whole warp, converged.
+// with the window's rows. Spans of at most kLeafLoopSpan rows: each lane walks its own edge's rows.
+// Longer ones: the batch's (edge, row) crossings are spread evenly over the lanes (warp prefix sum of
+// the spans; each lane finds its crossing's edge by a binary search over the lanes' offsets and
+// fetches it by shuffles). Whole warp, converged.
 template <bool COUNT, bool WIDE>
 __device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, int maxs, Leaf64& L, int lane,
                                              unsigned long long& entries)
@@ -167,46 +170,6 @@ __device__ __forceinline__ void leaf_rings(const int2* vp, int np, int basep, co
             b = v[kk + 1 == n ? 0 : kk + 1];
         }
         leaf_batch<COUNT>(has, a, b, x0, y0, W, H, isq ? baseq : basep, L, lane, entries);
-    }
-}
-
-// Asynchronous 8-byte global -> shared copies (cp.async, grouped per thread): a warp stages the next
-// work item's vertices while it computes the current one.
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit()
-{
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-// Wait until at most N of this thread's most recent groups are still in flight.
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-constexpr int kLeafVerts = 128;           // vertices of both rings staged per work item
-
-// As leaf_rings, with both rings' vertices staged in shared memory: P's at buf[0 .. np), Q's at
-// buf[np .. np + nq).
-template <bool COUNT>
-__device__ __forceinline__ void leaf_rings_staged(const int2* buf, int np, int nq, int x0, int y0, int W, int H,
-                                                  Leaf64& L, int lane, unsigned long long& entries)
-{
-    const int E = np + nq;
-    for (int b0 = 0; b0 < E; b0 += 32) {
-        const int k = b0 + lane;
-        const bool has = k < E;
-        const bool isq = k >= np;
-        int2 a = make_int2(0, 0), b = make_int2(0, 0);
-        if (has) {
-            a = buf[k];
-            b = buf[isq ? (k + 1 == E ? np : k + 1) : (k + 1 == np ? 0 : k + 1)];
-        }
-        leaf_batch<COUNT>(has, a, b, x0, y0, W, H, isq ? kLeafQ : 0, L, lane, entries);
     }
 }
 

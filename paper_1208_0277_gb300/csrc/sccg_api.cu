@@ -53,6 +53,7 @@ struct sccg_ctx {
     long long batch_n = -1;
     sccg_params batch_params{};
     int batch_count_work = 0;
+    unsigned long long batch_launches = 0;   // kernels launched by one replay of the graph
     char last_err[256] = {0};
 };
 
@@ -250,7 +251,7 @@ template <int CAP, bool SCAN>
 int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
-    const size_t smem = (SCAN ? sizeof(XorRows) : warp_smem<CAP>()) * wpc;    // SCAN: streamed leaves only
+    const size_t smem = (SCAN ? kPrepWarpBytes : warp_smem<CAP>()) * wpc;    // SCAN: streamed leaves only
     const long long grid = grid_for(ctx, a.n, wpc, 64);
     auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN> : k_prepare<CAP, kStack, false, SCAN>;
     int r = set_smem(ctx, kfn, smem);
@@ -324,6 +325,21 @@ int launch_stream(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* 
     if (r) return r;
     kfn<<<grid, 32 * wpc, smem, st>>>(a, side, nitems, ioff, head);
     SCCG_LAUNCHED(ctx, "k_pair_areas_stream");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+int launch_lanes(sccg_ctx* ctx, const AreasArgs& a, const long long* lane, cudaStream_t st)
+{
+    constexpr int wpc = 4;                               // k_pair_areas_lanes: CTAs of 128 threads
+    const size_t smem = sizeof(LaneSmem) * wpc;
+    auto kfn = ctx->count_work ? k_pair_areas_lanes<true> : k_pair_areas_lanes<false>;
+    int r = set_smem(ctx, kfn, smem);
+    unsigned grid = 0;
+    if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &grid);
+    if (r) return r;
+    kfn<<<grid, 32 * wpc, smem, st>>>(a, lane);
+    SCCG_LAUNCHED(ctx, "k_pair_areas_lanes");
     ctx->launches += 1;
     return SCCG_OK;
 }
@@ -426,6 +442,31 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
     const long long ovf2_cap = overflow2_cap(n_pairs);
     unsigned long long* ovf2_list = cv.take<unsigned long long>(ovf2_cap);
     const unsigned g = (unsigned)((n_pairs + 255) / 256);
+    if (SCCG_LEAF && ctx->params.leaf_words && side <= kLeafSide && (long long)side * side < ctx->params.T) {
+        // every item is one leaf of at most 64 x 64 pixels: the items through the leaf kernel's queue;
+        // with pair_lanes = 1 small pairs one lane each, on the side stream beside it
+        const bool lanes = ctx->params.pair_lanes == 1;
+        k_plan_leaf<<<g, 256, 0, st>>>(a, side, lanes ? 1 : 0, nitems_s, nitems_b);
+        SCCG_LAUNCHED(ctx, "k_plan_leaf");
+        ctx->launches += 1;
+        int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
+        if (!r) r = zero_async(ctx, head, sizeof(unsigned long long), st);
+        if (r) return r;
+        if (lanes) {
+            SCCG_CUDA(ctx, cudaEventRecord(ctx->fork_event, st));
+            SCCG_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->fork_event, 0));
+            r = launch_lanes(ctx, a, nitems_b, ctx->side_stream);
+            if (r) return r;
+            SCCG_CUDA(ctx, cudaEventRecord(ctx->join_event, ctx->side_stream));
+        }
+        r = launch_leaf(ctx, a, side, ioff_s, head, st);
+        if (r) return r;
+        if (lanes) SCCG_CUDA(ctx, cudaStreamWaitEvent(st, ctx->join_event, 0));
+        k_union<<<g, 256, 0, st>>>(a, nitems_s, nitems_b);
+        SCCG_LAUNCHED(ctx, "k_union");
+        ctx->launches += 1;
+        return SCCG_OK;
+    }
     if (SCCG_STREAM && ctx->params.leaf_words && (long long)side * side < ctx->params.T) {
         // every item is one leaf: one queue, edges streamed from the rings (no edge buffers)
         k_plan<<<g, 256, 0, st>>>(a, side, 0x7fffffff, nitems_s, nitems_b);
@@ -433,8 +474,7 @@ int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t s
         ctx->launches += 1;
         int r = device_scan(ctx, nitems_s, n_pairs, ioff_s, bsum, st);
         if (!r) r = zero_async(ctx, head, sizeof(unsigned long long), st);
-        if (!r) r = (SCCG_LEAF && side <= kLeafSide) ? launch_leaf(ctx, a, side, ioff_s, head, st)
-                                                     : launch_stream(ctx, a, side, nitems_s, ioff_s, head, st);
+        if (!r) r = launch_stream(ctx, a, side, nitems_s, ioff_s, head, st);
         if (r) return r;
         k_union<<<g, 256, 0, st>>>(a, nitems_s, nitems_b);
         SCCG_LAUNCHED(ctx, "k_union");
@@ -534,10 +574,11 @@ size_t band_build_scratch(long long n)
 int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
-    static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method", "leaf_words"};
+    static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method", "leaf_words",
+                                  "pair_lanes"};
     int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm, &p->area_method,
-                         &p->leaf_words};
-    for (int k = 0; k < 6; ++k) {
+                         &p->leaf_words, &p->pair_lanes};
+    for (int k = 0; k < 7; ++k) {
         char key[64];
         snprintf(key, sizeof key, "\"%s\"", names[k]);
         const char* at = strstr(js, key);
@@ -560,6 +601,7 @@ int validate_params(const sccg_params& p)
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return SCCG_EINVAL;
     if (p.area_method != SCCG_AREA_ROWS && p.area_method != SCCG_AREA_PIXELBOX) return SCCG_EINVAL;
     if (p.leaf_words != 0 && p.leaf_words != 1) return SCCG_EINVAL;
+    if (p.pair_lanes != 1 && p.pair_lanes != 32) return SCCG_EINVAL;
     return SCCG_OK;
 }
 
@@ -687,6 +729,7 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     ctx->params.ctas_per_sm = 0;
     ctx->params.area_method = SCCG_AREA_ROWS;
     ctx->params.leaf_words = 1;
+    ctx->params.pair_lanes = 32;
     int r = parse_params(params_json, &ctx->params);
     if (!r) r = validate_params(ctx->params);
     if (r) { delete ctx; return r; }
@@ -754,6 +797,7 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     else if (!strcmp(name, "ctas_per_sm")) p.ctas_per_sm = (int32_t)value;
     else if (!strcmp(name, "area_method")) p.area_method = (int32_t)value;
     else if (!strcmp(name, "leaf_words")) p.leaf_words = (int32_t)value;
+    else if (!strcmp(name, "pair_lanes")) p.pair_lanes = (int32_t)value;
     else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
     else if (!strcmp(name, "candidate_speculative")) {
         if (value < 0 || value > 2) return SCCG_EINVAL;
@@ -1222,6 +1266,7 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
         if (!r) r = jaccard_launch(ctx, inter, uni, n_pairs, reinterpret_cast<JaccardOut*>(out), ctx->cap_stream);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        ctx->batch_launches = ctx->launches - launches0;     // kernels in the graph
         ctx->launches = launches0;
         if (r) {
             if (graph) cudaGraphDestroy(graph);
@@ -1240,8 +1285,7 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
         ctx->batch_count_work = ctx->count_work;
     }
     SCCG_CUDA(ctx, cudaGraphLaunch(ctx->batch_exec, st));
-    // plan, 3 scan passes and one persistent launch per queue, union, 2 Jaccard
-    ctx->launches += n_pairs > 0 ? (edge_cap_for(std::max(A->max_nv, B->max_nv)) > kCapSmall ? 13 : 8) : 2;
+    ctx->launches += ctx->batch_launches;
     return SCCG_OK;
 }
 

@@ -5,9 +5,11 @@ Picks, by timing on the resident sets and candidate pairs it is given, the sampl
 form (split_pixels: how many warps a large pair is spread over) and the warps per CTA (how many
 pairs or items share an SM slot). Every candidate runs the real kernels through the library (CUDA
 events on the launching stream, median of a few launches after warm-up); results are identical for
-every setting, so the tuner only compares times. The search is a small coordinate descent: T first
-over a log grid, then split_pixels, then warps per CTA, each with the others fixed at their best so
-far, which covers the parameters that interact (T and the item size) without timing the full grid.
+every setting, so the tuner only compares times. The search first tries a short list of (item size,
+T) pairs, the two parameters that together decide which kernel runs (one-leaf items stream their
+edges; larger ones are subdivided), then a coordinate descent: T over a log grid, split_pixels,
+warps per CTA and, where the items are leaves of at most 64 x 64 pixels, the threads per pair
+(one warp per item, or one lane per small pair), each with the others fixed at their best so far.
 
 `tune(ctx, A, B, pa, pb)` returns the best parameters and the timing table; `load`/`save` keep
 results in a JSON file keyed by a workload signature, so that a serving process or a benchmark can
@@ -16,6 +18,7 @@ reuse them.
 from __future__ import annotations
 
 import json
+import math
 import os
 import statistics
 
@@ -24,6 +27,13 @@ from . import MODE_PERSISTENT, MODE_PLAIN
 T_GRID = (2048, 4096, 8192, 16384, 65536)
 SPLIT_GRID = (1024, 2048, 4096, 16384)
 WPC_GRID = (2, 4, 8)
+LANES_GRID = (32, 1)       # threads per pair in the leaf path: one warp per item, or one lane per small pair
+# Work-item forms of the persistent queue, (split_pixels, T): items of split_pixels pixels are one
+# leaf each when split_pixels < T (streamed: windows up to 64 x 64 through the leaf kernel, larger
+# ones through the streamed kernel), otherwise they are subdivided into sampling boxes (staged
+# kernels). The item size and T decide together which kernel runs, so they are searched as pairs.
+FORM_GRID = ((1024, 8192), (2048, 8192), (4096, 8192), (4096, 16384), (16384, 65536), (65536, 262144),
+             (4096, 2048), (16384, 8192))
 
 
 def _time(ctx, fn, reps: int, warm: int) -> float:
@@ -42,9 +52,11 @@ def _time(ctx, fn, reps: int, warm: int) -> float:
 
 
 def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: int = 1,
-         t_grid=T_GRID, split_grid=SPLIT_GRID, wpc_grid=WPC_GRID) -> dict:
-    """Coordinate descent over T, split_pixels (persistent form only) and warps_per_cta for the
-    pair areas of (pa, pb). Leaves ctx set to the best parameters. Returns
+         t_grid=T_GRID, split_grid=SPLIT_GRID, wpc_grid=WPC_GRID, form_grid=FORM_GRID,
+         lanes_grid=LANES_GRID) -> dict:
+    """For the persistent form, the best (split_pixels, T) pair of form_grid first; then coordinate
+    descent over T, split_pixels (persistent form only) and warps_per_cta for the pair areas of
+    (pa, pb). Leaves ctx set to the best parameters. Returns
     {"params": {...}, "ms": best, "table": [(params, ms), ...]}."""
     import torch
     n = pa.numel()
@@ -60,23 +72,35 @@ def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: in
         table.append((dict(params), round(ms, 4)))
         return ms
 
-    best_ms = run({k: best[k] for k in ("T", "split_pixels", "warps_per_cta")})
+    keys = ("T", "split_pixels", "warps_per_cta", "pair_lanes")
+    best_ms = run({k: best[k] for k in keys})
+    if mode == MODE_PERSISTENT:
+        for split, T in form_grid:
+            if (split, T) == (best["split_pixels"], best["T"]):
+                continue
+            trial = {k: best[k] for k in keys} | {"T": T, "split_pixels": split}
+            ms = run(trial)
+            if ms < best_ms:
+                best_ms, best = ms, dict(best, **trial)
     axes = [("T", t_grid)]
     if mode == MODE_PERSISTENT:
         axes.append(("split_pixels", split_grid))
     axes.append(("warps_per_cta", wpc_grid))
+    side = math.isqrt(max(best["split_pixels"], 1))
+    if mode == MODE_PERSISTENT and side <= 64 and side * side < best["T"]:
+        axes.append(("pair_lanes", lanes_grid))        # only the leaf path has the choice
     for name, grid in axes:
         for v in grid:
             if v == best[name]:
                 continue
-            trial = {k: best[k] for k in ("T", "split_pixels", "warps_per_cta")}
+            trial = {k: best[k] for k in keys}
             trial[name] = v
             ms = run(trial)
             if ms < best_ms:
                 best_ms, best = ms, dict(best, **trial)
-    for k in ("T", "split_pixels", "warps_per_cta"):
+    for k in keys:
         ctx.set_param(k, best[k])
-    return {"params": {k: best[k] for k in ("T", "split_pixels", "warps_per_cta")}, "ms": round(best_ms, 4),
+    return {"params": {k: best[k] for k in keys}, "ms": round(best_ms, 4),
             "mode": "persistent" if mode == MODE_PERSISTENT else ("plain" if mode == MODE_PLAIN else str(mode)),
             "table": table}
 

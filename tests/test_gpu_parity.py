@@ -189,14 +189,16 @@ def leaf_case_rings(seed):
     return [np.asarray(r) for r in ra], [np.asarray(r) for r in rb]
 
 
+@pytest.mark.parametrize("lanes", [32, 1])
 @pytest.mark.parametrize("split", [4096, 1024, 300])
-def test_leaf_items_window_sizes_steep_edges_and_empty_pairs(sccg, split):
+def test_leaf_items_window_sizes_steep_edges_and_empty_pairs(sccg, split, lanes):
     """The leaf form of the persistent queue (items of at most 64 x 64 pixels, one leaf each, both
     rings streamed as one edge sequence): windows of 1 to 64 pixels a side (one or two 32-pixel halves
     per row), edges spanning many rows (their crossings spread over the lanes), pairs without items
     between pairs with items, and over 32 pairs per queue take (the per-warp pair table is refilled);
-    side 64 and smaller sides that cut windows into several items. Against the oracle."""
-    c = sccg.Context(0, {"split_pixels": split, "T": 8192})
+    side 64 and smaller sides that cut windows into several items; with one warp per item, and with
+    small pairs (windows up to 32 x 32, up to 96 edges) one lane each. Against the oracle."""
+    c = sccg.Context(0, {"split_pixels": split, "T": 8192, "pair_lanes": lanes})
     ra, rb = leaf_case_rings(31)
     w = rings_workload(ra, rb)
     assert_same(gpu_run(c, w, mode=1), O.cross_compare(w.A, w.B))
@@ -525,3 +527,42 @@ def test_candidate_pairs_speculative_sizes(sccg, kind):
         np.testing.assert_array_equal(pa, ref_pa)
         np.testing.assert_array_equal(pb, ref_pb)
         np.testing.assert_array_equal(tpo, got[0][2])
+
+
+@pytest.mark.parametrize("T", [8192, 600])
+def test_prepare_lane_and_warp_boundaries(sccg, T):
+    """Polygon areas around the limits between one lane per polygon (bounding box at most 32 x 32 px,
+    at most 128 vertices, fewer than T pixels) and one warp per polygon: boxes 31 to 33 px a side,
+    127 to 129 vertices, rings with collinear runs and a box that reaches T; also a set where every
+    polygon is a lane polygon and one where none is."""
+    rng = np.random.Generator(np.random.PCG64(17))
+    rings = []
+    for side in (31, 32, 33):
+        for nv in (4, 127, 128, 129):
+            t = np.sort(rng.uniform(0, 2 * np.pi, nv))
+            x = np.rint(100 * len(rings) + side / 2 + (side / 2) * np.cos(t))
+            y = np.rint(side / 2 + (side / 2) * np.sin(t))
+            rings.append(np.stack([x, y], 1).astype(np.int64))
+        # a rectangle whose edges run along its box, with extra collinear vertices
+        x0 = 100 * len(rings)
+        rings.append(np.array([[x0, 0], [x0 + side // 2, 0], [x0 + side, 0], [x0 + side, side], [x0, side]]))
+    import paper_1208_0277_gb300 as P
+    c = P.Context(0, {"T": T})
+    for sel in (rings, [r for r in rings if len(r) <= 128], [r for r in rings if len(r) > 128]):
+        ps = W.from_rings([np.asarray(r) for r in sel])
+        d = c.upload(ps)
+        torch.cuda.synchronize()
+        ref_area, ref_mbr = O.polygon_areas(ps.off, ps.xy)
+        np.testing.assert_array_equal(d.area.cpu().numpy()[: ps.n], ref_area)
+        np.testing.assert_array_equal(d.mbr.cpu().numpy()[: ps.n], ref_mbr)
+
+
+def test_full_density_uneven_tile(sccg):
+    """One tile of the 2,000-uneven-tiles workload at its densest (20,000 polygons per set, MBR
+    lognormal 8-400 px, 4-512 vertices), through the persistent form with the default parameters:
+    every MBR, polygon area, candidate pair and pair area against the oracle (its O(n m) pairs and
+    exact row-interval areas), element by element."""
+    w = W.batched_uneven(seed=11, n_tiles=1, count_lo=20_000, count_hi=20_000)
+    assert w.A.n == 20_000
+    c = sccg.Context(0)
+    assert_same(gpu_run(c, w, mode=1), O.cross_compare(w.A, w.B, method="rle"))

@@ -31,7 +31,7 @@ def test_tuner_picks_from_its_grid_and_keeps_results_exact(mode):
     pa, pb = ctx.candidate_pairs(A, B)
     res = tune.tune(ctx, A, B, pa, pb, mode=mode, reps=2, warm=1)
     p = ctx.params()
-    assert res["params"]["T"] in tune.T_GRID + (8192,)
+    assert res["params"]["T"] in tune.T_GRID + tuple(T for _, T in tune.FORM_GRID) + (8192,)
     assert res["params"]["warps_per_cta"] in tune.WPC_GRID + (4,)
     for k, v in res["params"].items():
         assert p[k] == v
