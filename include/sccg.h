@@ -65,8 +65,9 @@ typedef struct sccg_params {
     int32_t split_pixels;    /* persistent form: a pair's window is cut into work items of at
                                 most about this many pixels (heavy pairs spread across warps) */
     int32_t ctas_per_sm;     /* persistent form: resident CTAs per SM (0 = occupancy maximum) */
-    int32_t area_method;     /* how sccg_prepare counts ||p||: SCCG_AREA_ROWS (default) or
-                                SCCG_AREA_PIXELBOX; both give the same exact pixel count */
+    int32_t area_method;     /* how sccg_prepare counts ||p||: SCCG_AREA_ROWS (default),
+                                SCCG_AREA_PIXELBOX (same exact pixel count) or SCCG_AREA_SHOELACE
+                                (rectilinear simple sets: the closed form) */
     int32_t leaf_words;      /* 1 (default): a leaf window (fewer than T pixels) is pixelized from
                                 per-row parity words, each edge flipping the pixels left of its
                                 crossing; 0: as 32-pixel row strips tested against every edge (the
@@ -80,8 +81,12 @@ typedef struct sccg_params {
 /* sccg_prepare's method for ||p||. ROWS: per pixel row, the crossing positions of the edges that
  * straddle it (sorted) delimit the inside pixels, so cost follows the edges per row (the exact
  * pixel-count counterpart of the shoelace area the paper uses, Sec. 3.2). PIXELBOX: Algorithm 1
- * applied to the polygon alone. */
-enum { SCCG_AREA_ROWS = 0, SCCG_AREA_PIXELBOX = 1 };
+ * applied to the polygon alone. SHOELACE: for sets the caller flags as rectilinear and simple (the
+ * paper's raster-boundary polygons, Sec. 3.1, Fig. 3): a polygon whose edges are all axis-parallel
+ * (checked on the device) gets |shoelace area| (Sec. 3.2, POLYAREA), which equals its pixel count
+ * when the ring is simple (not checked: the caller's flag vouches for it); any other polygon is
+ * counted as with ROWS. */
+enum { SCCG_AREA_ROWS = 0, SCCG_AREA_PIXELBOX = 1, SCCG_AREA_SHOELACE = 2 };
 
 /* Create a context on CUDA device `device`. params_json may be NULL or a flat JSON object with any
  * of the sccg_params field names, e.g. {"T": 1024, "warps_per_cta": 8}. */

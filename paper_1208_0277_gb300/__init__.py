@@ -25,6 +25,7 @@ MODE_PERSISTENT = 1
 MODE_NOSEP = 2         # PixelBox-NoSep (Sec. 5.2): union counted directly, for comparison
 AREA_ROWS = 0          # sccg_prepare counts ||p|| row by row (default)
 AREA_PIXELBOX = 1      # ... or by PixelBox on the polygon alone
+AREA_SHOELACE = 2      # ... or, for sets flagged rectilinear and simple, by the shoelace formula
 
 
 class SccgError(RuntimeError):

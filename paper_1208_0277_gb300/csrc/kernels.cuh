@@ -23,13 +23,14 @@
 #define SCCG_ITEM_BOUNDS __launch_bounds__(256)
 #endif
 // The kernels whose leaves stream their edges need little shared memory, so registers set their
-// occupancy: at least 5 resident CTAs of 256 threads for k_prepare and 6 for k_pair_areas_stream,
-// measured best on the whole slide and the uneven tiles.
+// occupancy: at least 5 resident CTAs of 256 threads for k_prepare (measured best on the whole slide
+// and the uneven tiles) and 4 for k_pair_areas_stream (the heavy tail's large items; 6.6 against
+// 7.4 ms with 6).
 #ifndef SCCG_PREP_MIN_BLOCKS
 #define SCCG_PREP_MIN_BLOCKS 5
 #endif
 #ifndef SCCG_STREAM_MIN_BLOCKS
-#define SCCG_STREAM_MIN_BLOCKS 6
+#define SCCG_STREAM_MIN_BLOCKS 4
 #endif
 #ifndef SCCG_LEAF_MIN_BLOCKS
 #define SCCG_LEAF_MIN_BLOCKS 4
@@ -150,6 +151,7 @@ struct PrepArgs {
     int* big_list;
     unsigned* big_n;
     int words;              // as AreasArgs::words
+    int shoelace;           // 1: ||p|| of a polygon whose edges are all axis-parallel from its shoelace sum
 };
 
 // SCAN: a polygon whose window holds fewer than T pixels is pixelized here as one leaf, its edges
@@ -196,13 +198,39 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
                 e = kErrRange;
         }
         uint32_t area = 0;
+        // Rectilinear sets (Sec. 3.2's POLYAREA): when every edge of the ring is axis-parallel, ||p|| is
+        // |twice the shoelace sum| / 2 (coordinates taken relative to the box corner, so every product
+        // stays below 2^28 and the sum below 2^52); the caller's flag vouches that the ring is simple,
+        // where this equals the pixel count. A ring with any other edge is counted by pixels below.
+        bool closed_form = false;
+        if (SCAN && a.shoelace && e == 0) {
+            const int nv = (int)nvl;
+            long long twice = 0;
+            bool axis = true;
+            for (int base = 0; base < nv; base += 32) {
+                const int k = base + lane;
+                if (k < nv) {
+                    const int2 p = v[k];
+                    const int2 q = v[k + 1 == nv ? 0 : k + 1];
+                    axis &= (p.x == q.x) | (p.y == q.y);
+                    twice += (long long)(p.x - x0) * (q.y - y0) - (long long)(q.x - x0) * (p.y - y0);
+                }
+            }
+            axis = __all_sync(kFull, axis);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) twice += __shfl_xor_sync(kFull, twice, o);
+            if (axis) {
+                closed_form = true;
+                area = (uint32_t)((twice < 0 ? -twice : twice) >> 1);
+            }
+        }
         // SCAN: a polygon whose window is not small is deferred to k_area_bands (by rows).
         // Otherwise the large ones to k_prepare_big.
         const bool small_win = (long long)(x1 - x0) * (y1 - y0) < a.T;
         const bool by_rows = SCAN && !small_win;
-        const bool defer = e == 0 && (by_rows || (!SCAN && a.defer_above > 0 && nvl > a.defer_above));
+        const bool defer = e == 0 && !closed_form && (by_rows || (!SCAN && a.defer_above > 0 && nvl > a.defer_above));
         if (lane == 0 && defer) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
-        if (SCAN && e == 0 && !defer && x1 > x0 && y1 > y0) {
+        if (SCAN && e == 0 && !defer && !closed_form && x1 > x0 && y1 > y0) {
             if (x1 - x0 <= kLeafSide && y1 - y0 <= kLeafSide)
                 area = leaf_area<COUNT>(v, (int)nvl, x0, y0, x1, y1, L, lane, wc);
             else
@@ -1184,6 +1212,7 @@ struct StreamSmem {
     XorRows xq;
 };
 
+
 // ... of the edge records listed in the band block `blk` (polygon minimum y `miny`) for the bands
 // of those rows; a record listed in several of them is taken from the first (as stage_banded).
 __device__ __forceinline__ void xor_stream_bands(const char* blk, int miny, int x0, int y0, int nr, int W, int nw,
@@ -1209,6 +1238,7 @@ __device__ __forceinline__ void xor_stream_bands(const char* blk, int miny, int 
         }
     }
 }
+
 
 // Work item `sub` of pair i (as do_item), one leaf, streamed. Whole warp, converged.
 template <bool COUNT>

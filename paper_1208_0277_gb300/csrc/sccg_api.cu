@@ -599,7 +599,8 @@ int validate_params(const sccg_params& p)
     if (p.warps_per_cta < 1 || p.warps_per_cta > 8) return SCCG_EINVAL;
     if (p.split_pixels < 32) return SCCG_EINVAL;
     if (p.ctas_per_sm < 0 || p.ctas_per_sm > 64) return SCCG_EINVAL;
-    if (p.area_method != SCCG_AREA_ROWS && p.area_method != SCCG_AREA_PIXELBOX) return SCCG_EINVAL;
+    if (p.area_method != SCCG_AREA_ROWS && p.area_method != SCCG_AREA_PIXELBOX && p.area_method != SCCG_AREA_SHOELACE)
+        return SCCG_EINVAL;
     if (p.leaf_words != 0 && p.leaf_words != 1) return SCCG_EINVAL;
     if (p.pair_lanes != 1 && p.pair_lanes != 32) return SCCG_EINVAL;
     return SCCG_OK;
@@ -884,10 +885,11 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
         unsigned* big_n = &stats[k].deferred;
         cudaStream_t sk = (two_streams && (k & 1)) ? ctx->side_stream : st;
-        if (s->n > 0 && ctx->params.area_method == SCCG_AREA_ROWS) {
+        if (s->n > 0 && ctx->params.area_method != SCCG_AREA_PIXELBOX) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
-                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words};
+                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words,
+                       ctx->params.area_method == SCCG_AREA_SHOELACE ? 1 : 0};
             r = launch_prepare<kCapSmall, true>(ctx, a, sk);
             if (r) return r;
         } else if (s->n > 0) {
@@ -917,7 +919,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         s->n_tiles = std::max(res.n_tiles, s->n > 0 ? 1 : 0);
         s->band_bytes = res.band_bytes ? band_head_bytes(s->n) + (long long)res.band_bytes : 0;
         s->bands = nullptr;
-        if (!res.err && res.deferred && ctx->params.area_method == SCCG_AREA_ROWS) {
+        if (!res.err && res.deferred && ctx->params.area_method != SCCG_AREA_PIXELBOX) {
             // areas of the deferred polygons by rows; those with 1024 or more vertices from a
             // temporary band index
             int rr = SCCG_OK;

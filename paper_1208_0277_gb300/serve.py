@@ -284,8 +284,10 @@ class Server:
             slot.event.synchronize()
             now = time.perf_counter()
             k = len(jobs)
-            inter = slot.h_inter[:npairs].numpy().copy()
-            uni = slot.h_uni[:npairs].numpy().copy()
+            # out of the slot's pinned staging before the slot is reused (torch's copy runs on several
+            # cores and without the interpreter lock)
+            inter = slot.h_inter[:npairs].clone().numpy()
+            uni = slot.h_uni[:npairs].clone().numpy()
             jac = Context.decode_jaccard_array(slot.h_jres[:48 * k].numpy())
             with slot.cv:
                 slot.batch = None

@@ -436,6 +436,21 @@ def test_rectilinear_staircases_match_shoelace(ctx):
     assert_same(g, O.cross_compare(w.A, w.B))
 
 
+def test_shoelace_areas_of_rectilinear_sets(sccg):
+    """area_method SHOELACE (Sec. 3.2's closed form for sets flagged rectilinear and simple): the
+    staircases' areas come from their shoelace sums and equal the oracle's pixel counts (and the
+    column sums); star polygons mixed into the set have diagonal edges and are counted by pixels;
+    the pair areas and unions that use these areas match the oracle."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    rings, heights = W.staircase_rings(rng, 300, max_cols=60, max_h=40)
+    stars = [np.asarray(r) for r in leaf_case_rings(5)[0][-40:]]
+    w = rings_workload(rings + stars, stars + rings)
+    c = sccg.Context(0, {"area_method": sccg.AREA_SHOELACE})
+    g = gpu_run(c, w, mode=1)
+    np.testing.assert_array_equal(g["area_a"][: len(rings)], [int(h.sum()) for h in heights])
+    assert_same(g, O.cross_compare(w.A, w.B))
+
+
 def test_coordinate_and_extent_limits(ctx):
     L = 1 << 28
     big = [[L - 16384, L - 5], [L, L - 5], [L, L], [L - 16384, L]]            # extent exactly 16384
