@@ -415,6 +415,8 @@ def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
     from paper_1208_0277_gb300 import serve
     rng = np.random.default_rng(seed)
     srv = serve.Server(A, B, pa, pb, device=device, slots=3, max_batch_pairs=1 << 20, max_batch_jobs=1024)
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(0.0005)        # the client, batcher and completer threads share the interpreter
     try:
         warm = serve.draw_jobs(rng, tpo, 64)
         [f.result() for f in srv.submit_many(warm)]
@@ -436,6 +438,7 @@ def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
         out["waited_for_memory"] = srv.waited_for_memory
         return out
     finally:
+        sys.setswitchinterval(switch)
         srv.close()
 
 
@@ -561,8 +564,12 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
     if args.autotune == "on" or (args.autotune == "auto" and config in (3, 4, 5)):
         from paper_1208_0277_gb300 import tune
         tuned = tune.tune(ctx, A, B, pa0, pb0, mode=P.MODE_PLAIN if form_main == "tiles" else P.MODE_PERSISTENT)
-        print(f"config {config} autotune: {tuned['params']} ({len(tuned['table'])} trials, {tuned['ms']} ms)",
-              file=sys.stderr)
+        tuned_prep = tune.tune_prepare(ctx, [(devb["Aoff"], devb["Axy"], devb["Atile"], (outs["Ambr"], outs["Aarea"])),
+                                             (devb["Boff"], devb["Bxy"], devb["Btile"], (outs["Bmbr"], outs["Barea"]))])
+        tuned["params"]["area_T"] = tuned_prep["area_T"]
+        tuned["prepare"] = tuned_prep
+        print(f"config {config} autotune: {tuned['params']} ({len(tuned['table'])} trials, {tuned['ms']} ms; "
+              f"prepare {tuned_prep['table']})", file=sys.stderr)
     cap = n_pairs
     pa = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
     pb = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
@@ -710,7 +717,7 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         "tiles": w.n_tiles, "input_bytes": sum(devb[k].numel() * devb[k].element_size() for k in devb),
         "generation_s": round(gen_s, 1), "params": prm,
         "autotune": ({"params": tuned["params"], "trials": len(tuned["table"]), "mode": tuned["mode"],
-                      "best_ms": tuned["ms"]} if tuned else None),
+                      "best_ms": tuned["ms"], "prepare_ms_by_area_T": tuned["prepare"]["table"]} if tuned else None),
         "roofline": roofline, "roofline_other": roofline_other,
         # the pair path alone (a3-a6: sets prepared once and resident)
         "a3_a6": {"value": total_pairs * args.steps / ((main_r["ms"] - args.steps * ph["prepare"]) / 1e3),

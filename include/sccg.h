@@ -76,6 +76,9 @@ typedef struct sccg_params {
                                 64 x 64 pixels): 32 (default) one warp per item; 1: pairs whose window
                                 is at most 32 x 32 pixels with at most 96 edges in both rings are done
                                 one lane per pair (beside the warp path for the others). Same results. */
+    int32_t area_T;          /* sccg_prepare (ROWS and SHOELACE methods): a polygon whose bounding box
+                                holds fewer than area_T pixels is counted as one leaf of streamed
+                                parity words, a larger one by rows (default 65536). Same results. */
 } sccg_params;
 
 /* sccg_prepare's method for ||p||. ROWS: per pixel row, the crossing positions of the edges that

@@ -575,10 +575,10 @@ int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
     static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method", "leaf_words",
-                                  "pair_lanes"};
+                                  "pair_lanes", "area_T"};
     int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm, &p->area_method,
-                         &p->leaf_words, &p->pair_lanes};
-    for (int k = 0; k < 7; ++k) {
+                         &p->leaf_words, &p->pair_lanes, &p->area_T};
+    for (int k = 0; k < 8; ++k) {
         char key[64];
         snprintf(key, sizeof key, "\"%s\"", names[k]);
         const char* at = strstr(js, key);
@@ -603,6 +603,7 @@ int validate_params(const sccg_params& p)
         return SCCG_EINVAL;
     if (p.leaf_words != 0 && p.leaf_words != 1) return SCCG_EINVAL;
     if (p.pair_lanes != 1 && p.pair_lanes != 32) return SCCG_EINVAL;
+    if (p.area_T < 2 || p.area_T > (1 << 28)) return SCCG_EINVAL;
     return SCCG_OK;
 }
 
@@ -731,6 +732,7 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     ctx->params.area_method = SCCG_AREA_ROWS;
     ctx->params.leaf_words = 1;
     ctx->params.pair_lanes = 32;
+    ctx->params.area_T = 65536;
     int r = parse_params(params_json, &ctx->params);
     if (!r) r = validate_params(ctx->params);
     if (r) { delete ctx; return r; }
@@ -799,6 +801,7 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     else if (!strcmp(name, "area_method")) p.area_method = (int32_t)value;
     else if (!strcmp(name, "leaf_words")) p.leaf_words = (int32_t)value;
     else if (!strcmp(name, "pair_lanes")) p.pair_lanes = (int32_t)value;
+    else if (!strcmp(name, "area_T")) p.area_T = (int32_t)value;
     else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
     else if (!strcmp(name, "candidate_speculative")) {
         if (value < 0 || value > 2) return SCCG_EINVAL;
@@ -888,7 +891,7 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         if (s->n > 0 && ctx->params.area_method != SCCG_AREA_PIXELBOX) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
-                       ctx->params.T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words,
+                       ctx->params.area_T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words,
                        ctx->params.area_method == SCCG_AREA_SHOELACE ? 1 : 0};
             r = launch_prepare<kCapSmall, true>(ctx, a, sk);
             if (r) return r;

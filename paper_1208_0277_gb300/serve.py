@@ -29,7 +29,9 @@ Latency. A job carries its scheduled arrival time (``t_arrival``, set by the cli
 arrival trace; the submit time otherwise); a result's latency runs from that arrival to the moment
 its areas and Jaccard are in host memory, so a client or batcher that falls behind shows up in the
 latency rather than hiding it. A job whose future the client cancels before it is admitted to a
-batch is dropped.
+batch is dropped. Each job's handle is a Ticket (result with an optional timeout, cancel): one
+condition per server is notified per completed batch, which keeps the host cost per job small at
+tens of thousands of jobs per second.
 """
 from __future__ import annotations
 
@@ -67,6 +69,38 @@ class JobResult:
     @property
     def latency_ms(self) -> float:
         return 1e3 * (self.t_done - self.t_arrival)
+
+
+class Ticket:
+    """The handle of a submitted job (a light future: one shared condition per server rather than a
+    lock per job). result(timeout) blocks until the job's batch has completed; cancel() withdraws a
+    job that has not been admitted to a batch yet."""
+    __slots__ = ("job", "_srv", "_res", "_state")     # state: 0 queued, 1 admitted, 2 done, 3 cancelled
+
+    def __init__(self, job, srv):
+        self.job, self._srv, self._res, self._state = job, srv, None, 0
+
+    def cancel(self) -> bool:
+        with self._srv.cv:
+            if self._state == 0:
+                self._state = 3
+            return self._state == 3
+
+    def cancelled(self) -> bool:
+        return self._state == 3
+
+    def done(self) -> bool:
+        return self._state >= 2
+
+    def result(self, timeout: float | None = None):
+        if self._state != 2:
+            with self._srv.done_cv:
+                ok = self._srv.done_cv.wait_for(lambda: self._state >= 2, timeout)
+            if self._state == 3:
+                raise cf.CancelledError()
+            if not ok:
+                raise TimeoutError("job not completed in time")
+        return self._res
 
 
 class Arena:
@@ -153,6 +187,7 @@ class Server:
         self.free = collections.deque(range(slots))
         self.pending = collections.deque()
         self.cv = threading.Condition()
+        self.done_cv = threading.Condition()     # notified whenever a batch's tickets complete
         self.stop = False
         self.batches = 0
         self.batched_jobs = 0
@@ -178,30 +213,30 @@ class Server:
         if n <= 0 or n > self.cap_pairs or n > self.arena.capacity or job.p0 < 0 or job.p1 > self.pa.numel():
             raise ValueError(f"job of {n} pairs at [{job.p0}, {job.p1}) does not fit a batch slot or the pair arena")
 
-    def submit(self, job: Job) -> cf.Future:
+    def submit(self, job: Job) -> Ticket:
         return self.submit_many([job])[0]
 
     def submit_many(self, jobs) -> list:
         """Queue jobs in the given order (one lock acquisition); jobs without a scheduled arrival
-        time get the submit time."""
+        time get the submit time. Returns one Ticket per job."""
         for j in jobs:
             self._check(j)
         now = time.perf_counter()
-        futs = []
+        tickets = [Ticket(j, self) for j in jobs]
         with self.cv:
             for j in jobs:
                 if not j.t_arrival:
                     j.t_arrival = now
-                f = cf.Future()
-                self.pending.append((j, f))
-                futs.append(f)
+            self.pending.extend(tickets)
             self.cv.notify()
-        return futs
+        return tickets
 
     def close(self):
         with self.cv:
             self.stop = True
             self.cv.notify_all()
+        with self.done_cv:
+            self.done_cv.notify_all()
         for s in self.slots:
             with s.cv:
                 s.cv.notify_all()
@@ -216,16 +251,18 @@ class Server:
         jobs, npairs = [], 0
         room = min(self.cap_pairs, self.arena.largest())
         while self.pending and len(jobs) < self.cap_jobs:
-            job, fut = self.pending[0]
-            n = job.p1 - job.p0
+            t = self.pending[0]
+            if t._state == 3:                    # cancelled by the client before admission
+                self.pending.popleft()
+                continue
+            n = t.job.p1 - t.job.p0
             if npairs + n > room:
                 if npairs + n <= self.cap_pairs:
                     self.waited_for_memory += 1
                 break
             self.pending.popleft()
-            if not fut.set_running_or_notify_cancel():
-                continue                     # cancelled by the client before admission
-            jobs.append((job, fut))
+            t._state = 1
+            jobs.append(t)
             npairs += n
         return jobs, npairs
 
@@ -245,9 +282,9 @@ class Server:
                 start = self.arena.take(npairs)
             slot = self.slots[slot_id]
             k = len(jobs)
-            src = np.array([j.p0 for j, _ in jobs], dtype=np.int64)
+            src = np.array([t.job.p0 for t in jobs], dtype=np.int64)
             dst = np.zeros(k + 1, dtype=np.int64)
-            np.cumsum([j.p1 - j.p0 for j, _ in jobs], out=dst[1:])
+            np.cumsum([t.job.p1 - t.job.p0 for t in jobs], out=dst[1:])
             slot.h_src[:k].copy_(torch.from_numpy(src))
             slot.h_dst[:k + 1].copy_(torch.from_numpy(dst))
             rng = slice(start, start + npairs)
@@ -295,9 +332,11 @@ class Server:
                 self.arena.give(start, npairs)
                 self.free.append(slot_id)
                 self.cv.notify()
-            for j, (job, fut) in enumerate(jobs):
-                fut.set_result(JobResult(inter[dst[j]:dst[j + 1]], uni[dst[j]:dst[j + 1]], jac[j], job.t_arrival,
-                                         now, k))
+            for j, t in enumerate(jobs):
+                t._res = JobResult(inter[dst[j]:dst[j + 1]], uni[dst[j]:dst[j + 1]], jac[j], t.job.t_arrival, now, k)
+                t._state = 2
+            with self.done_cv:
+                self.done_cv.notify_all()
 
 
 def draw_jobs(rng, tile_pair_off, n_jobs: int, lo: int = 100, hi: int = 50_000):

@@ -105,6 +105,22 @@ def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: in
             "table": table}
 
 
+AREA_T_GRID = (8192, 65536, 262144)
+
+
+def tune_prepare(ctx, specs, reps: int = 3, warm: int = 1, grid=AREA_T_GRID) -> dict:
+    """area_T for sccg_prepare on the sets in specs ([(off, xy, tile, (mbr, area)), ...]): the box
+    size under which a polygon is one streamed leaf rather than counted by rows. Leaves ctx at the
+    best; returns {"area_T": best, "ms": best_ms, "table": [(area_T, ms), ...]}."""
+    table = []
+    for v in grid:
+        ctx.set_param("area_T", v)
+        table.append((v, round(_time(ctx, lambda: ctx.prepare_sets(specs), reps, warm), 4)))
+    best = min(table, key=lambda t: t[1])
+    ctx.set_param("area_T", best[0])
+    return {"area_T": best[0], "ms": best[1], "table": table}
+
+
 def signature(A, B, n_pairs: int) -> str:
     """A workload key: set sizes, vertex counts, largest polygon and extent, pair count."""
     return (f"nA={A.c.n},nB={B.c.n},vA={A.xy.numel() // 2},vB={B.xy.numel() // 2},"

@@ -64,7 +64,7 @@ def test_threshold_does_not_change_results(sccg, T, words):
     """T only decides where subdivision stops (Sec. 3.4) and leaf_words how a leaf is pixelized;
     results must be identical for every setting."""
     w = W.single_tile(seed=3, n=400)
-    c = sccg.Context(0, {"T": T, "leaf_words": words})
+    c = sccg.Context(0, {"T": T, "area_T": T, "leaf_words": words})
     assert_same(gpu_run(c, w), O.cross_compare(w.A, w.B))
 
 
@@ -97,7 +97,7 @@ def test_medium_and_large_polygons_subdivision_and_chunked_edges(sccg, T):
     B = medium_polygons(11, kind="tissue")
     w = W.Workload("medium", A, B, 1, 2048, 0)
     for words in (1, 0):
-        c = sccg.Context(0, {"T": T, "leaf_words": words})
+        c = sccg.Context(0, {"T": T, "area_T": T, "leaf_words": words})
         g = gpu_run(c, w)
         ref = O.cross_compare(A, B, method="rle")
         assert_same(g, ref)
@@ -408,8 +408,9 @@ def comb_ring(teeth, h=40):
     return pts
 
 
+@pytest.mark.parametrize("area_T", [65536, 64])
 @pytest.mark.parametrize("method", [0, 1])
-def test_polygon_area_methods_match_oracle(sccg, method):
+def test_polygon_area_methods_match_oracle(sccg, method, area_T):
     """||p|| by rows (default) and by PixelBox on the polygon alone, on shapes that stress each:
     rows crossed by more edges than one pass holds (combs of 520 and 700 teeth), self-intersecting
     random rings, concave tissue polygons, staircases and ties."""
@@ -419,7 +420,7 @@ def test_polygon_area_methods_match_oracle(sccg, method):
     ties = [[[0, 0], [4, 2], [0, 4]], [[0, 0], [2, 2], [4, 0]], [[0, 0], [4, 4], [0, 8], [-4, 4]]]
     rings = [comb_ring(700), comb_ring(520, 9), comb_ring(30)] + selfx + ties + [np.asarray(r).tolist() for r in stairs]
     sets = [W.from_rings(rings), medium_polygons(12, n=40, kind="tissue"), W.single_tile(seed=5, n=400).A]
-    ctx = sccg.Context(0, {"area_method": method})
+    ctx = sccg.Context(0, {"area_method": method, "area_T": area_T})
     for P in sets:
         d = ctx.upload(P)
         torch.cuda.synchronize()
@@ -544,12 +545,12 @@ def test_candidate_pairs_speculative_sizes(sccg, kind):
         np.testing.assert_array_equal(tpo, got[0][2])
 
 
-@pytest.mark.parametrize("T", [8192, 600])
-def test_prepare_lane_and_warp_boundaries(sccg, T):
-    """Polygon areas around the limits between one lane per polygon (bounding box at most 32 x 32 px,
-    at most 128 vertices, fewer than T pixels) and one warp per polygon: boxes 31 to 33 px a side,
-    127 to 129 vertices, rings with collinear runs and a box that reaches T; also a set where every
-    polygon is a lane polygon and one where none is."""
+@pytest.mark.parametrize("area_T", [8192, 600])
+def test_prepare_leaf_and_rows_boundaries(sccg, area_T):
+    """Polygon areas around the limits of k_prepare's paths (one leaf of parity rows for boxes up to
+    64 x 64 px under area_T pixels, streamed parity words above 64 px, rows from area_T on): boxes 31 to
+    33 px a side, 4 to 129 vertices, rings with collinear runs, boxes on both sides of area_T; also the
+    polygons of at most 128 vertices alone and the others alone."""
     rng = np.random.Generator(np.random.PCG64(17))
     rings = []
     for side in (31, 32, 33):
@@ -562,7 +563,7 @@ def test_prepare_lane_and_warp_boundaries(sccg, T):
         x0 = 100 * len(rings)
         rings.append(np.array([[x0, 0], [x0 + side // 2, 0], [x0 + side, 0], [x0 + side, side], [x0, side]]))
     import paper_1208_0277_gb300 as P
-    c = P.Context(0, {"T": T})
+    c = P.Context(0, {"area_T": area_T})
     for sel in (rings, [r for r in rings if len(r) <= 128], [r for r in rings if len(r) > 128]):
         ps = W.from_rings([np.asarray(r) for r in sel])
         d = c.upload(ps)

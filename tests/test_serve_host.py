@@ -36,3 +36,35 @@ def test_arena_random_sequence_never_overlaps():
     for s, n in held:
         a.give(s, n)
     assert a.free == [(0, 1000)]
+
+
+def test_ticket_states():
+    """A queued ticket can be cancelled (its result then raises); an admitted one cannot; a
+    completed one returns its result at once; waiting on an unfinished one times out."""
+    import concurrent.futures as cf
+    import threading
+
+    from paper_1208_0277_gb300.serve import Job, Ticket
+
+    class Srv:
+        cv = threading.Condition()
+        done_cv = threading.Condition()
+
+    srv = Srv()
+    t = Ticket(Job(0, 5), srv)
+    assert t.cancel() and t.cancelled() and t.done()
+    with pytest.raises(cf.CancelledError):
+        t.result(timeout=0.01)
+    u = Ticket(Job(0, 5), srv)
+    u._state = 1                                     # admitted to a batch
+    assert not u.cancel()
+    with pytest.raises(TimeoutError):
+        u.result(timeout=0.01)
+
+    def finish():
+        u._res = "areas"
+        u._state = 2
+        with srv.done_cv:
+            srv.done_cv.notify_all()
+    threading.Timer(0.02, finish).start()
+    assert u.result(timeout=5) == "areas" and u.done()
