@@ -74,7 +74,7 @@ typedef struct sccg_params {
                                 per-pixel test of Sec. 3.1). Same results. */
     int32_t pair_lanes;      /* threads per pair in the persistent form's leaf path (items of at most
                                 64 x 64 pixels): 32 (default) one warp per item; 1: pairs whose window
-                                is at most 32 x 32 pixels with at most 96 edges in both rings are done
+                                is at most 32 x 32 pixels with at most 64 edges in both rings are done
                                 one lane per pair (beside the warp path for the others). Same results. */
     int32_t area_T;          /* sccg_prepare (ROWS and SHOELACE methods): a polygon whose bounding box
                                 holds fewer than area_T pixels is counted as one leaf of streamed

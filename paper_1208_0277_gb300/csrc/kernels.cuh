@@ -36,7 +36,7 @@
 #define SCCG_LEAF_MIN_BLOCKS 4
 #endif
 #ifndef SCCG_LANE_MIN_BLOCKS
-#define SCCG_LANE_MIN_BLOCKS 6
+#define SCCG_LANE_MIN_BLOCKS 4
 #endif
 
 namespace sccg {
@@ -1527,13 +1527,25 @@ __global__ void __launch_bounds__(256, SCCG_LEAF_MIN_BLOCKS) k_pair_areas_leaf(c
 // ----------------------------------------------------------------------------------------------
 constexpr int kLaneSide = 32;            // largest window side of a lane pair
 #ifndef SCCG_LANE_MAX_EDGES
-#define SCCG_LANE_MAX_EDGES 96
+#define SCCG_LANE_MAX_EDGES 64
 #endif
 constexpr int kLaneMaxEdges = SCCG_LANE_MAX_EDGES;   // edges of both rings of a lane pair, at most
 
 struct LaneSmem {
     uint32_t r[2 * kLaneSide][32];       // [row][lane]: rows 0..31 of P, then of Q
+    int2 v[kLaneMaxEdges][32];           // [vertex][lane]: the lane's P ring, then its Q ring
 };
+
+// Asynchronous 8-byte global -> shared copy (cp.async), and waiting for all of this thread's.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 // k_plan for the leaf kernel. With `lanes`, pairs with a window of at most kLaneSide x kLaneSide
 // pixels and at most kLaneMaxEdges edges in both rings get lane[i] = 1 and no items (the lane kernel
@@ -1570,6 +1582,7 @@ __global__ void k_plan_leaf(const AreasArgs a, int side, int lanes, long long* n
 // with its next row into the row's word (leaf_cross's rule: the first c = ceil(N / 2dy) pixels right
 // of x0 flip), so the lane's trip count is its edges plus its crossings. R: the lane's column,
 // R[row << 5]. Returns the number of (edge, row) crossings.
+template <int STRIDE>
 __device__ __forceinline__ unsigned lane_walk(const int2* vp, int np, const int2* vq, int nq, int x0, int y0, int H,
                                               uint32_t* R)
 {
@@ -1579,7 +1592,7 @@ __device__ __forceinline__ unsigned lane_walk(const int2* vp, int np, const int2
     }
     const int2* v = vp;
     int n = np, j = 1, rowbase = 0;
-    int2 prev = vp[np - 1];
+    int2 prev = vp[(np - 1) * STRIDE];
     int2 nxt = vp[0];
     int s = 0, span = 0, N = 0, dx2 = 0, cap = 0, w = 0;
     float rc = 1.0f;
@@ -1592,11 +1605,11 @@ __device__ __forceinline__ unsigned lane_walk(const int2* vp, int np, const int2
                 n = nq;
                 j = 1;
                 rowbase = kLaneSide;
-                prev = vq[nq - 1];
+                prev = vq[(nq - 1) * STRIDE];
                 nxt = vq[0];
             }
             const int2 cur = nxt;
-            if (j < n) nxt = v[j];              // the next edge's vertex, loaded ahead
+            if (j < n) nxt = v[j * STRIDE];     // the next edge's vertex, loaded ahead
             ++j;
             const bool up = prev.y <= cur.y;
             const int ylo = up ? prev.y : cur.y, yhi = up ? cur.y : prev.y;
@@ -1625,12 +1638,14 @@ __device__ __forceinline__ unsigned lane_walk(const int2* vp, int np, const int2
     return crossings;
 }
 
-// ||p n q|| of a lane pair (lane_walk over both rings, then the rows inside both, W columns).
+// ||p n q|| of a lane pair (lane_walk over both rings staged in the lane's column, then the rows
+// inside both, W columns).
+constexpr int kLaneStride = 32;          // int2 steps between a lane's consecutive staged vertices
 template <bool COUNT>
 __device__ __forceinline__ uint32_t lane_pair_inter(const int2* vp, int np, const int2* vq, int nq, int x0, int y0,
                                                     int W, int H, uint32_t* R, WorkCounters& wc)
 {
-    const unsigned crossings = lane_walk(vp, np, vq, nq, x0, y0, H, R);
+    const unsigned crossings = lane_walk<kLaneStride>(vp, np, vq, nq, x0, y0, H, R);
     const uint32_t vm = low_mask(W);
     uint32_t acc = 0;
     for (int r = 0; r < H; ++r) acc += __popc(R[r << 5] & R[(kLaneSide + r) << 5] & vm);
@@ -1643,30 +1658,52 @@ __device__ __forceinline__ uint32_t lane_pair_inter(const int2* vp, int np, cons
     return acc;
 }
 
-// Every pair k_plan_leaf marked (lane[i] = 1), one per lane, grid-stride over the pairs.
+// Every pair k_plan_leaf marked (lane[i] = 1), one per lane: each warp takes 32 consecutive pairs,
+// every lane copies its pair's two rings into its column of shared memory with asynchronous copies
+// (all in flight at once; vertex k of the lane at v[k][lane], so the lanes' later reads of their own
+// k-th vertices fall in different banks), then walks them. Grid-stride over groups of 32 pairs.
 template <bool COUNT>
-__global__ void __launch_bounds__(128, SCCG_LANE_MIN_BLOCKS) k_pair_areas_lanes(const AreasArgs a,
-                                                                                const long long* lane)
+__global__ void __launch_bounds__(64, SCCG_LANE_MIN_BLOCKS) k_pair_areas_lanes(const AreasArgs a,
+                                                                               const long long* lane)
 {
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    uint32_t* R = &reinterpret_cast<LaneSmem*>(smem4)[warp].r[0][ln];
+    LaneSmem& S = reinterpret_cast<LaneSmem*>(smem4)[warp];
+    uint32_t* R = &S.r[0][ln];
     WorkCounters wc = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) {
-        if (lane[p] != 1) continue;
-        const int ia = a.pa[p], ib = a.pb[p];
-        const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
-        const int x0 = max(ma.x, mb.x), y0 = max(ma.y, mb.y);
-        const int W = min(ma.z, mb.z) - x0, H = min(ma.w, mb.w) - y0;
-        if (W <= 0 || H <= 0 || W > kLaneSide || H > kLaneSide) continue;     // not a lane pair
-        const long long oa = a.offA[ia], ob = a.offB[ib];
-        const uint32_t cnt = lane_pair_inter<COUNT>(reinterpret_cast<const int2*>(a.xyA) + oa,
-                                                    (int)(a.offA[ia + 1] - oa),
-                                                    reinterpret_cast<const int2*>(a.xyB) + ob,
-                                                    (int)(a.offB[ib + 1] - ob), x0, y0, W, H, R, wc);
-        a.inter[p] = (int64_t)cnt;
-        a.uni[p] = a.areaA[ia] + a.areaB[ib] - (int64_t)cnt;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.n; base += stride) {
+        const long long p = base + ln;
+        bool mine = p < a.n && lane[p] == 1;
+        int ia = 0, ib = 0, x0 = 0, y0 = 0, W = 0, H = 0, np = 0, nq = 0;
+        const int2* vp = nullptr;
+        const int2* vq = nullptr;
+        if (mine) {
+            ia = a.pa[p];
+            ib = a.pb[p];
+            const int4 ma = a.mbrA[ia], mb = a.mbrB[ib];
+            x0 = max(ma.x, mb.x);
+            y0 = max(ma.y, mb.y);
+            W = min(ma.z, mb.z) - x0;
+            H = min(ma.w, mb.w) - y0;
+            const long long oa = a.offA[ia], ob = a.offB[ib];
+            np = (int)(a.offA[ia + 1] - oa);
+            nq = (int)(a.offB[ib + 1] - ob);
+            vp = reinterpret_cast<const int2*>(a.xyA) + oa;
+            vq = reinterpret_cast<const int2*>(a.xyB) + ob;
+            mine = W > 0 && H > 0 && W <= kLaneSide && H <= kLaneSide && np + nq <= kLaneMaxEdges;
+        }
+        __syncwarp();                                  // the lanes are done with the previous columns
+        if (mine) {
+            for (int k = 0; k < np; ++k) cp_async8(&S.v[k][ln], vp + k);
+            for (int k = 0; k < nq; ++k) cp_async8(&S.v[np + k][ln], vq + k);
+        }
+        cp_async_wait_all();
+        if (mine) {
+            const uint32_t cnt = lane_pair_inter<COUNT>(&S.v[0][ln], np, &S.v[np][ln], nq, x0, y0, W, H, R, wc);
+            a.inter[p] = (int64_t)cnt;
+            a.uni[p] = a.areaA[ia] + a.areaB[ib] - (int64_t)cnt;
+        }
     }
     if (COUNT) flush_counters(a.counters, wc);
 }

@@ -331,7 +331,7 @@ int launch_stream(sccg_ctx* ctx, const AreasArgs& a, int side, const long long* 
 
 int launch_lanes(sccg_ctx* ctx, const AreasArgs& a, const long long* lane, cudaStream_t st)
 {
-    constexpr int wpc = 4;                               // k_pair_areas_lanes: CTAs of 128 threads
+    constexpr int wpc = 2;                               // k_pair_areas_lanes: CTAs of 64 threads
     const size_t smem = sizeof(LaneSmem) * wpc;
     auto kfn = ctx->count_work ? k_pair_areas_lanes<true> : k_pair_areas_lanes<false>;
     int r = set_smem(ctx, kfn, smem);

@@ -197,7 +197,7 @@ def test_leaf_items_window_sizes_steep_edges_and_empty_pairs(sccg, split, lanes)
     per row), edges spanning many rows (their crossings spread over the lanes), pairs without items
     between pairs with items, and over 32 pairs per queue take (the per-warp pair table is refilled);
     side 64 and smaller sides that cut windows into several items; with one warp per item, and with
-    small pairs (windows up to 32 x 32, up to 96 edges) one lane each. Against the oracle."""
+    small pairs (windows up to 32 x 32, up to 64 edges) one lane each. Against the oracle."""
     c = sccg.Context(0, {"split_pixels": split, "T": 8192, "pair_lanes": lanes})
     ra, rb = leaf_case_rings(31)
     w = rings_workload(ra, rb)
