@@ -79,6 +79,12 @@ typedef struct sccg_params {
     int32_t area_T;          /* sccg_prepare (ROWS and SHOELACE methods): a polygon whose bounding box
                                 holds fewer than area_T pixels is counted as one leaf of streamed
                                 parity words, a larger one by rows (default 65536). Same results. */
+    int32_t rasters;         /* 1 (default): the pair-area calls use the sets' pixel rasters when both
+                                sets have them (see sccg_polyset.raster); 0: they pixelize every pair's
+                                window as without rasters. Same results. */
+    int32_t raster_heavy;    /* pair areas from rasters, persistent form: a pair whose window has more
+                                than raster_heavy (row, 32-pixel word) units is done by a whole CTA
+                                instead of one warp (default 1024; -1: every pair by one warp). */
 } sccg_params;
 
 /* sccg_prepare's method for ||p||. ROWS: per pixel row, the crossing positions of the edges that
@@ -126,6 +132,19 @@ typedef struct sccg_polyset {
                                set's band index (0: no polygon has 1024 or more vertices) */
     const void* bands;      /* device, optional: the band index written by sccg_build_bands, or
                                NULL (then every work item reads its polygons' whole rings) */
+    void* raster;           /* device, optional (NULL: none): caller-owned buffer of raster_cap bytes,
+                               16-byte aligned, kept alive and unmodified while the set is used, into
+                               which sccg_prepare writes the set's pixel rasters: polygon i's window
+                               of W x H pixels (its MBR) as H rows of ceil(W / 32) uint32 words, bit b
+                               of word k of row r set iff pixel (minx + 32 k + b, miny + r) belongs to
+                               the polygon. Layout: int64 word offsets [n + 1] padded to 16 bytes,
+                               then the words (polygon i's start at word off[i]). */
+    int64_t raster_cap;     /* bytes available at raster */
+    int64_t raster_bytes;   /* written by sccg_prepare when raster != NULL: bytes the rasters take
+                               (offsets and words), whether they fitted or not */
+    int32_t raster_ok;      /* written by sccg_prepare: 1 when the rasters were written (raster_bytes
+                               <= raster_cap); the pair-area calls then use them */
+    int32_t raster_pad;
 } sccg_polyset;
 
 /* Step 1 of the path: per-polygon bounding box (MBR) and pixel area ||p|| (Sec. 3.2 computes ||p||
@@ -139,6 +158,19 @@ typedef struct sccg_polyset {
  * the stream reaches them).
  * Returns SCCG_EINVAL or SCCG_ERANGE for invalid sets (mbr/area contents then unspecified). */
 int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream);
+/* With s->raster set, sccg_prepare also writes the set's pixel rasters (Sec. 3.1's pixel membership,
+ * decided once per polygon and kept in device memory): the MBRs are computed first, the rasters'
+ * sizes scanned into their offsets, then each polygon is pixelized once, its ||p|| counted from its
+ * raster. A pair's ||p n q|| is then the number of set bits of the AND of the two rasters over the
+ * pair's window (sccg_pair_areas and the calls built on it, except SCCG_MODE_NOSEP), with the same
+ * results. The area method does not apply to a set with rasters. When the rasters do not fit
+ * (raster_bytes > raster_cap), nothing is written to the buffer, raster_ok is 0 and the set is
+ * prepared as without rasters; sccg_raster_bytes gives the size beforehand. */
+
+/* Bytes the pixel rasters of set s take (offsets and words), for sizing s->raster. Computes and
+ * writes the set's MBRs (s->mbr) on the way, validates the set as sccg_prepare does and SYNCHRONISES
+ * the stream once. bytes: host out. */
+int sccg_raster_bytes(sccg_ctx* ctx, sccg_polyset* s, int64_t* bytes, void* stream);
 
 /* sccg_prepare for n_sets sets (1..64) at once: their kernels are launched back to back and the
  * stream is synchronised once. Every set's summary is filled in; a set that fails validation is not
@@ -322,14 +354,15 @@ int sccg_alu_probe(int device, int32_t iters, double* ms, double* lane_ops);
 /* ------------------------------------------------------------------------------------------- */
 /* With sccg_ctx_set_param(ctx, "count_work", 1) the prepare and pair-area kernels run an
  * instrumented build that counts the work the method performs; the counts accumulate in the
- * context until read. out10 (host, 10 entries): [0] (32-pixel row strip, edge) evaluations of the
+ * context until read. out12 (host, 12 entries): [0] (32-pixel row strip, edge) evaluations of the
  * full strip test, [1] (pixel, edge) point-in-polygon tests inside those strips, [2] (sampling box,
  * edge) classifications, [3] sampling boxes classified, [4] (edge, row) crossings XORed into leaf
  * parity words, [5] (row, 32-pixel word) parity words reduced, [6] (edge, row) crossing values of
- * the by-rows area, [7] crossing-value comparisons ranking them, [8] (pixel, polygon) memberships
- * decided one pixel at a time (leaves), [9] pixels of the windows counted. Synchronous.
- * reset != 0 zeroes the counters. */
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out10, int reset);
+ * the by-rows area (and crossings drawn into the difference rows of large rasters), [7]
+ * crossing-value comparisons ranking them, [8] (pixel, polygon) memberships decided one pixel at a
+ * time (leaves), [9] pixels of the windows counted, [10] raster words written, [11] (row, 32-pixel
+ * word) ANDs of two rasters over pair windows. Synchronous. reset != 0 zeroes the counters. */
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out12, int reset);
 
 #ifdef __cplusplus
 }

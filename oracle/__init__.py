@@ -70,6 +70,10 @@ def _load():
             lib.oracle_polygon_areas.restype = None
             lib.oracle_candidate_pairs.argtypes = [P, P, I64, P, P, I64, P, P, I64]
             lib.oracle_candidate_pairs.restype = I64
+            lib.oracle_polygon_mask.argtypes = [P, I64, P]
+            lib.oracle_polygon_mask.restype = None
+            lib.oracle_rle_mask.argtypes = [P, I64, P]
+            lib.oracle_rle_mask.restype = None
             lib.oracle_touches.argtypes = [P, I64, P, I64]
             lib.oracle_touches.restype = ctypes.c_int
             _lib = lib
@@ -105,6 +109,20 @@ def polygon_area_rle(ring) -> int:
     """||p|| by the independent row-interval method."""
     r = _ring(ring)
     return int(_load().oracle_rle_area(_ptr(r), r.size // 2))
+
+
+def polygon_mask(ring, method: str = "brute") -> np.ndarray:
+    """Membership of every pixel of MBR(p)'s window: bool [H, W], row y - min y, column x - min x
+    (brute force per pixel, or "rle": the row intervals, for windows too large for the brute force)."""
+    r = _ring(ring)
+    xy = r.reshape(-1, 2)
+    W = int(xy[:, 0].max()) - int(xy[:, 0].min())
+    H = int(xy[:, 1].max()) - int(xy[:, 1].min())
+    out = np.zeros(max(W, 0) * max(H, 0), dtype=np.uint8)
+    if out.size:
+        fn = _load().oracle_polygon_mask if method == "brute" else _load().oracle_rle_mask
+        fn(_ptr(r), r.size // 2, _ptr(out))
+    return out.reshape(max(H, 0), max(W, 0)).astype(bool)
 
 
 def pair(ring_p, ring_q):

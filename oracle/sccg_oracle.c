@@ -80,6 +80,18 @@ i64 oracle_polygon_area(const int32_t* xy, i64 nv)
     return area;
 }
 
+/* Membership mask of p over the pixel window of MBR(p): out[(y - min y) * W + (x - min x)] = 1 when
+ * pixel (x, y) belongs to p (W = max x - min x), by the per-pixel test above. */
+void oracle_polygon_mask(const int32_t* xy, i64 nv, uint8_t* out)
+{
+    int32_t m[4];
+    oracle_mbr(xy, nv, m);
+    const i64 W = (i64)m[2] - m[0];
+    for (i64 y = m[1]; y < m[3]; ++y)
+        for (i64 x = m[0]; x < m[2]; ++x)
+            out[(y - m[1]) * W + (x - m[0])] = (uint8_t)oracle_pixel_in_polygon(xy, nv, x, y);
+}
+
 /* ||p n q|| and ||p u q||, both counted directly over the bounding box of MBR(p) u MBR(q). */
 void oracle_pair(const int32_t* xp, i64 np, const int32_t* xq, i64 nq, i64* inter, i64* uni)
 {
@@ -167,6 +179,28 @@ i64 oracle_rle_area(const int32_t* xy, i64 nv)
     }
     free(buf); free(iv);
     return area;
+}
+
+/* The membership mask of oracle_polygon_mask from the row intervals (for windows too large for the
+ * brute force): the pixels of row y inside p are those of its intervals, clipped to the window. */
+void oracle_rle_mask(const int32_t* xy, i64 nv, uint8_t* out)
+{
+    int32_t m[4];
+    oracle_mbr(xy, nv, m);
+    const i64 W = (i64)m[2] - m[0];
+    i64* buf = (i64*)malloc(sizeof(i64) * (size_t)(nv + 1));
+    i64* iv = (i64*)malloc(sizeof(i64) * (size_t)(nv + 2));
+    for (i64 y = m[1]; y < m[3]; ++y) {
+        uint8_t* row = out + (y - m[1]) * W;
+        memset(row, 0, (size_t)W);
+        const i64 k = row_intervals(xy, nv, y, buf, iv);
+        for (i64 i = 0; i < k; ++i) {
+            const i64 lo = iv[2 * i] > m[0] ? iv[2 * i] : m[0];
+            const i64 hi = iv[2 * i + 1] < m[2] ? iv[2 * i + 1] : m[2];
+            for (i64 x = lo; x < hi; ++x) row[x - m[0]] = 1;
+        }
+    }
+    free(buf); free(iv);
 }
 
 void oracle_rle_pair(const int32_t* xp, i64 np, const int32_t* xq, i64 nq, i64* inter, i64* uni)

@@ -60,6 +60,7 @@ class DevicePolySet:
     area: object
     c: _native.PolySetC
     bands: object = None        # uint8 device tensor holding the band index, if the set has one
+    raster: object = None       # uint8 device tensor holding the pixel rasters, if the set has them
 
     @property
     def n(self) -> int:
@@ -109,61 +110,95 @@ class Context:
         return {k: getattr(p, k) for k, _ in p._fields_}
 
     # ------------------------------------------------------------------ sets
-    def upload(self, ps, stream=None, bands: bool = True) -> DevicePolySet:
-        """Copy a host PolySet (workload.PolySet) to the device and prepare it (MBRs, areas)."""
+    def upload(self, ps, stream=None, bands: bool = True, raster: bool = True) -> DevicePolySet:
+        """Copy a host PolySet (workload.PolySet) to the device and prepare it (MBRs, areas, and by
+        default the pixel rasters)."""
         import torch
         dev = torch.device("cuda", self.device)
         off = torch.from_numpy(ps.off).to(dev)
         xy = torch.from_numpy(ps.xy).to(dev)
         tile = torch.from_numpy(ps.tile).to(dev)
-        return self.prepare(off, xy, tile, stream, bands=bands)
+        return self.prepare(off, xy, tile, stream, bands=bands, raster=raster)
 
-    def prepare(self, off, xy, tile=None, stream=None, out=None, bands: bool = True) -> DevicePolySet:
-        """MBRs, validation and pixel areas of a device-resident CSR set (off int64, xy int32 pairs,
-        tile int32 or None). out = (mbr int32 [n,4], area int64 [n]) reuses caller buffers. With
-        bands (default) the band index of polygons with >= 1024 vertices is built when there are any."""
+    def _polyset(self, off, xy, tile, out):
         import torch
         n = off.numel() - 1
         if out is None:
             mbr = torch.empty((max(n, 1), 4), dtype=torch.int32, device=off.device)
             area = torch.empty(max(n, 1), dtype=torch.int64, device=off.device)
+            rbuf = None
         else:
-            mbr, area = out
+            mbr, area = out[0], out[1]
+            rbuf = out[2] if len(out) > 2 else None
         if xy.numel() == 0:
             xy = torch.zeros(2, dtype=torch.int32, device=off.device)
         c = _native.PolySetC(n=n, off=off.data_ptr(), xy=xy.data_ptr(), tile=_ptr(tile),
                              mbr=mbr.data_ptr(), area=area.data_ptr())
+        return c, xy, mbr, area, rbuf
+
+    def raster_bytes(self, c: _native.PolySetC, stream=None) -> int:
+        """Device bytes the pixel rasters of the set described by c take (sccg_raster_bytes)."""
+        nb = ctypes.c_int64()
+        self._check(self.lib.sccg_raster_bytes(self.h, ctypes.byref(c), ctypes.byref(nb), _stream(stream)),
+                    "sccg_raster_bytes")
+        return int(nb.value)
+
+    def _raster_buffer(self, c, rbuf, device, stream):
+        """rbuf if it holds the set's rasters, else a new buffer of the exact size."""
+        import torch
+        if rbuf is None or rbuf.numel() < int(c.raster_bytes or 0):
+            nb = self.raster_bytes(c, stream) if rbuf is None else int(c.raster_bytes)
+            rbuf = torch.empty(max(nb, 16), dtype=torch.uint8, device=device)
+        c.raster = rbuf.data_ptr()
+        c.raster_cap = rbuf.numel()
+        return rbuf
+
+    def prepare(self, off, xy, tile=None, stream=None, out=None, bands: bool = True,
+                raster: bool = True) -> DevicePolySet:
+        """MBRs, validation and pixel areas of a device-resident CSR set (off int64, xy int32 pairs,
+        tile int32 or None). out = (mbr int32 [n,4], area int64 [n][, raster uint8]) reuses caller
+        buffers. With raster (default) the set's pixel rasters are written too (into out's raster
+        buffer when it is large enough, else into a new one of the exact size), and the pair-area
+        calls on two such sets AND rasters instead of pixelizing pair windows. With bands (default)
+        the band index of polygons with >= 1024 vertices is built when there are any."""
+        c, xy, mbr, area, rbuf = self._polyset(off, xy, tile, out)
+        if raster and c.n > 0:
+            rbuf = self._raster_buffer(c, rbuf, off.device, stream)
         self._check(self.lib.sccg_prepare(self.h, ctypes.byref(c), _stream(stream)), "sccg_prepare")
-        d = DevicePolySet(off, xy, tile, mbr, area, c)
+        if raster and c.n > 0 and not c.raster_ok:
+            # the buffer given was too small for these rasters: once more into one of the exact size
+            rbuf = self._raster_buffer(c, None if rbuf is None else rbuf[:0], off.device, stream)
+            self._check(self.lib.sccg_prepare(self.h, ctypes.byref(c), _stream(stream)), "sccg_prepare")
+        d = DevicePolySet(off, xy, tile, mbr, area, c, raster=rbuf if c.raster_ok else None)
         if bands and c.band_bytes > 0:
             self.build_bands(d, stream=stream)
         return d
 
-    def prepare_sets(self, specs, stream=None, bands: bool = True) -> list:
+    def prepare_sets(self, specs, stream=None, bands: bool = True, raster: bool = True) -> list:
         """prepare() for several sets with one synchronisation: specs = [(off, xy, tile, out), ...]
-        (tile and out may be None)."""
-        import torch
+        (tile and out may be None; out as in prepare())."""
         k = len(specs)
         arr = (_native.PolySetC * k)()
         keep = []
         for j, (off, xy, tile, out) in enumerate(specs):
-            n = off.numel() - 1
-            if out is None:
-                mbr = torch.empty((max(n, 1), 4), dtype=torch.int32, device=off.device)
-                area = torch.empty(max(n, 1), dtype=torch.int64, device=off.device)
-            else:
-                mbr, area = out
-            if xy.numel() == 0:
-                xy = torch.zeros(2, dtype=torch.int32, device=off.device)
-            arr[j] = _native.PolySetC(n=n, off=off.data_ptr(), xy=xy.data_ptr(), tile=_ptr(tile),
-                                      mbr=mbr.data_ptr(), area=area.data_ptr())
-            keep.append((off, xy, tile, mbr, area))
+            c, xy2, mbr, area, rbuf = self._polyset(off, xy, tile, out)
+            if raster and c.n > 0:
+                rbuf = self._raster_buffer(c, rbuf, off.device, stream)
+            arr[j] = c
+            keep.append((off, xy2, tile, mbr, area, rbuf))
         self._check(self.lib.sccg_prepare_sets(self.h, arr, k, _stream(stream)), "sccg_prepare_sets")
+        if raster and any(arr[j].n > 0 and not arr[j].raster_ok for j in range(k)):
+            for j in range(k):
+                if arr[j].n > 0 and not arr[j].raster_ok:
+                    off, xy2, tile, mbr, area, rbuf = keep[j]
+                    rbuf = self._raster_buffer(arr[j], None if rbuf is None else rbuf[:0], off.device, stream)
+                    keep[j] = (off, xy2, tile, mbr, area, rbuf)
+            self._check(self.lib.sccg_prepare_sets(self.h, arr, k, _stream(stream)), "sccg_prepare_sets")
         out = []
-        for j, (off, xy, tile, mbr, area) in enumerate(keep):
+        for j, (off, xy2, tile, mbr, area, rbuf) in enumerate(keep):
             c = _native.PolySetC()
             ctypes.pointer(c)[0] = arr[j]
-            d = DevicePolySet(off, xy, tile, mbr, area, c)
+            d = DevicePolySet(off, xy2, tile, mbr, area, c, raster=rbuf if c.raster_ok else None)
             if bands and c.band_bytes > 0:
                 self.build_bands(d, stream=stream)
             out.append(d)
@@ -325,10 +360,11 @@ class Context:
                                                int(base_a), int(base_b), _stream(stream)), "sccg_rebase_pairs")
 
     def work_counters(self, reset: bool = True) -> dict:
-        a = (ctypes.c_uint64 * 10)()
+        a = (ctypes.c_uint64 * 12)()
         self._check(self.lib.sccg_work_counters(self.h, a, int(reset)), "sccg_work_counters")
         return dict(strip_edges=a[0], pixel_edges=a[1], box_edges=a[2], boxes=a[3], row_entries=a[4],
-                    row_edges=a[5], scan_entries=a[6], scan_pairs=a[7], leaf_pixels=a[8], window_pixels=a[9])
+                    row_edges=a[5], scan_entries=a[6], scan_pairs=a[7], leaf_pixels=a[8], window_pixels=a[9],
+                    raster_out=a[10], raster_and=a[11])
 
 
 def alu_probe(device: int = 0, iters: int = 4096) -> tuple[float, float]:

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(_ROOT, "include")
 BUILD_DIR = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsccg.so")
 SOURCES = ["sccg_api.cu"]
-HEADERS = ["leaf64.cuh", "pixelbox.cuh", "scanline.cuh", "kernels.cuh"]
+HEADERS = ["leaf64.cuh", "pixelbox.cuh", "scanline.cuh", "kernels.cuh", "raster.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 # Every symbol include/sccg.h declares (checked by the CPU test suite).
@@ -27,7 +27,7 @@ EXPORTS = [
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
     "sccg_jaccard_static", "sccg_work_counters", "sccg_build_bands", "sccg_gather_pairs",
     "sccg_jaccard_segments", "sccg_rebase_pairs", "sccg_prepare_sets", "sccg_contains", "sccg_touches",
-    "sccg_alu_probe", "sccg_ctx_reserve",
+    "sccg_alu_probe", "sccg_ctx_reserve", "sccg_raster_bytes",
 ]
 
 _lock = threading.Lock()
@@ -76,6 +76,11 @@ class PolySetC(ctypes.Structure):
         ("reserved", ctypes.c_int32),
         ("band_bytes", ctypes.c_int64),
         ("bands", ctypes.c_void_p),
+        ("raster", ctypes.c_void_p),
+        ("raster_cap", ctypes.c_int64),
+        ("raster_bytes", ctypes.c_int64),
+        ("raster_ok", ctypes.c_int32),
+        ("raster_pad", ctypes.c_int32),
     ]
 
 
@@ -83,7 +88,7 @@ class ParamsC(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("split_pixels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("area_method", ctypes.c_int32), ("leaf_words", ctypes.c_int32), ("pair_lanes", ctypes.c_int32),
-                ("area_T", ctypes.c_int32)]
+                ("area_T", ctypes.c_int32), ("rasters", ctypes.c_int32), ("raster_heavy", ctypes.c_int32)]
 
 
 class JaccardC(ctypes.Structure):
@@ -115,6 +120,7 @@ def load(path: str | None = None):
             "sccg_last_error": ([V], ctypes.c_char_p),
             "sccg_prepare": ([V, PS, V], I),
             "sccg_prepare_sets": ([V, PS, I, V], I),
+            "sccg_raster_bytes": ([V, PS, ctypes.POINTER(I64), V], I),
             "sccg_candidate_pairs": ([V, PS, PS, V, V, I64, ctypes.POINTER(I64), V, V], I),
             "sccg_pair_areas": ([V, PS, PS, V, V, I64, V, V, I, V], I),
             "sccg_pair_areas_tiles": ([V, PS, PS, V, V, V, ctypes.c_int32, V, V, V], I),

@@ -33,6 +33,8 @@ struct WorkCounters {          // algorithmic work, accumulated only by the coun
     unsigned long long scan_pairs;    // crossing-value comparisons ranking them
     unsigned long long leaf_pixels;   // (pixel, polygon) memberships decided one pixel at a time
     unsigned long long window_pixels; // pixels of the windows counted (pairs' windows or items)
+    unsigned long long raster_out;    // pixel raster words written (sets that keep rasters)
+    unsigned long long raster_and;    // (row, word) ANDs of two rasters over pairs' windows
 };
 
 __device__ __forceinline__ int warp_min(int v)

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "kernels.cuh"
+#include "raster.cuh"
 #include "sccg.h"
 
 using namespace sccg;
@@ -49,7 +50,7 @@ struct sccg_ctx {
     // sccg_batch_run: the captured graph and the arguments it was captured for
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t batch_exec = nullptr;
-    const void* batch_key[11] = {};
+    const void* batch_key[13] = {};
     long long batch_n = -1;
     sccg_params batch_params{};
     int batch_count_work = 0;
@@ -247,13 +248,22 @@ int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
     return SCCG_OK;
 }
 
-template <int CAP, bool SCAN>
+int launch_mbr(sccg_ctx* ctx, const PrepArgs& a, long long* words, cudaStream_t st)
+{
+    const long long grid = grid_for(ctx, a.n, 8, 16);
+    k_mbr<<<(unsigned)grid, 256, 0, st>>>(a, words);
+    SCCG_LAUNCHED(ctx, "k_mbr");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
+template <int CAP, bool SCAN, bool MBR_IN = false>
 int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
     const size_t smem = (SCAN ? kPrepWarpBytes : warp_smem<CAP>()) * wpc;    // SCAN: streamed leaves only
     const long long grid = grid_for(ctx, a.n, wpc, 64);
-    auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN> : k_prepare<CAP, kStack, false, SCAN>;
+    auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN, MBR_IN> : k_prepare<CAP, kStack, false, SCAN, MBR_IN>;
     int r = set_smem(ctx, kfn, smem);
     if (r) return r;
     kfn<<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
@@ -278,9 +288,12 @@ int launch_prepare_big(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
     return SCCG_OK;
 }
 
+int raster_launch(sccg_ctx* ctx, const AreasArgs& a, bool persistent, cudaStream_t st);
+
 template <int CAP, bool NOSEP = false>
 int launch_plain(sccg_ctx* ctx, const AreasArgs& a, cudaStream_t st)
 {
+    if (!NOSEP && a.rwA && a.rwB) return raster_launch(ctx, a, false, st);
     const int wpc = warps_for(ctx, CAP);
     const size_t smem = warp_smem<CAP>() * wpc;
     const long long grid = grid_for(ctx, a.n, wpc, 64);
@@ -388,6 +401,16 @@ int check_prepared(const sccg_polyset* s)
     return SCCG_OK;
 }
 
+// Point the pair-area arguments at both sets' rasters when both have them and the context uses them.
+void use_rasters(const sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, AreasArgs& a)
+{
+    if (!ctx->params.rasters || !A->raster_ok || !B->raster_ok || !A->raster || !B->raster) return;
+    a.roffA = static_cast<const long long*>(A->raster);
+    a.rwA = reinterpret_cast<const uint32_t*>(static_cast<const char*>(A->raster) + raster_head_bytes(A->n));
+    a.roffB = static_cast<const long long*>(B->raster);
+    a.rwB = reinterpret_cast<const uint32_t*>(static_cast<const char*>(B->raster) + raster_head_bytes(B->n));
+}
+
 // exclusive scan of counts[n] into offs[n+1]; scratch from carve
 int device_scan(sccg_ctx* ctx, const long long* counts, long long n, long long* offs, long long* bsum,
                 cudaStream_t st)
@@ -423,9 +446,50 @@ int split_side(const sccg_ctx* ctx)
     return side;
 }
 
+// Pair areas from both sets' rasters. persistent: chunks of 32 pairs taken from a device counter
+// by resident CTAs, heavy pairs listed and done one CTA each (scratch from the persistent form's
+// reservation); otherwise a static grid-stride with every pair done by its warp.
+int raster_launch(sccg_ctx* ctx, const AreasArgs& a, bool persistent, cudaStream_t st)
+{
+    RasterPairArgs ra{a.n, a.nA, a.nB, a.pa, a.pb,
+                      a.mbrA, a.areaA, a.roffA, a.rwA, a.mbrB, a.areaB, a.roffB, a.rwB,
+                      a.inter, a.uni, -1, nullptr, nullptr, nullptr, a.counters};
+    auto kfn = ctx->count_work ? k_pair_raster<true> : k_pair_raster<false>;
+    if (!persistent) {
+        const long long grid = grid_for(ctx, (a.n + 31) / 32, 8, 16);
+        kfn<<<(unsigned)grid, 256, 0, st>>>(ra);
+        SCCG_LAUNCHED(ctx, "k_pair_raster");
+        ctx->launches += 1;
+        return SCCG_OK;
+    }
+    Carve cv(ctx->ws);
+    unsigned long long* cnt = cv.take<unsigned long long>(2);       // chunk head, heavy count
+    ra.heavy = cv.take<unsigned long long>(a.n);
+    ra.head = cnt;
+    ra.heavy_n = cnt + 1;
+    ra.heavy_words = ctx->params.raster_heavy;
+    int r = zero_async(ctx, cnt, 2 * sizeof(unsigned long long), st);
+    unsigned grid = 0;
+    if (!r) r = persistent_grid(ctx, kfn, 8, 0, &grid);
+    if (r) return r;
+    kfn<<<grid, 256, 0, st>>>(ra);
+    SCCG_LAUNCHED(ctx, "k_pair_raster");
+    ctx->launches += 1;
+    if (ra.heavy_words >= 0) {
+        auto hfn = ctx->count_work ? k_pair_raster_heavy<true> : k_pair_raster_heavy<false>;
+        r = persistent_grid(ctx, hfn, 8, 0, &grid);
+        if (r) return r;
+        hfn<<<grid, 256, 0, st>>>(ra);
+        SCCG_LAUNCHED(ctx, "k_pair_raster_heavy");
+        ctx->launches += 1;
+    }
+    return SCCG_OK;
+}
+
 // Persistent form on already reserved scratch (no validation, no allocation: usable under capture).
 int persistent_launch(sccg_ctx* ctx, const AreasArgs& a, int cap, cudaStream_t st)
 {
+    if (a.rwA && a.rwB) return raster_launch(ctx, a, true, st);
     const long long n_pairs = a.n;
     const int side = split_side(ctx);
     const long long nb = (n_pairs + kScanBlock - 1) / kScanBlock + 1;
@@ -575,10 +639,10 @@ int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
     static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method", "leaf_words",
-                                  "pair_lanes", "area_T"};
+                                  "pair_lanes", "area_T", "rasters", "raster_heavy"};
     int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm, &p->area_method,
-                         &p->leaf_words, &p->pair_lanes, &p->area_T};
-    for (int k = 0; k < 8; ++k) {
+                         &p->leaf_words, &p->pair_lanes, &p->area_T, &p->rasters, &p->raster_heavy};
+    for (int k = 0; k < 10; ++k) {
         char key[64];
         snprintf(key, sizeof key, "\"%s\"", names[k]);
         const char* at = strstr(js, key);
@@ -604,6 +668,8 @@ int validate_params(const sccg_params& p)
     if (p.leaf_words != 0 && p.leaf_words != 1) return SCCG_EINVAL;
     if (p.pair_lanes != 1 && p.pair_lanes != 32) return SCCG_EINVAL;
     if (p.area_T < 2 || p.area_T > (1 << 28)) return SCCG_EINVAL;
+    if (p.rasters != 0 && p.rasters != 1) return SCCG_EINVAL;
+    if (p.raster_heavy < -1) return SCCG_EINVAL;
     return SCCG_OK;
 }
 
@@ -733,6 +799,8 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     ctx->params.leaf_words = 1;
     ctx->params.pair_lanes = 32;
     ctx->params.area_T = 65536;
+    ctx->params.rasters = 1;
+    ctx->params.raster_heavy = 1024;
     int r = parse_params(params_json, &ctx->params);
     if (!r) r = validate_params(ctx->params);
     if (r) { delete ctx; return r; }
@@ -802,6 +870,8 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     else if (!strcmp(name, "leaf_words")) p.leaf_words = (int32_t)value;
     else if (!strcmp(name, "pair_lanes")) p.pair_lanes = (int32_t)value;
     else if (!strcmp(name, "area_T")) p.area_T = (int32_t)value;
+    else if (!strcmp(name, "rasters")) p.rasters = (int32_t)value;
+    else if (!strcmp(name, "raster_heavy")) p.raster_heavy = (int32_t)value;
     else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
     else if (!strcmp(name, "candidate_speculative")) {
         if (value < 0 || value > 2) return SCCG_EINVAL;
@@ -833,15 +903,15 @@ int sccg_ctx_get_params(const sccg_ctx* ctx, sccg_params* out)
 
 const char* sccg_last_error(const sccg_ctx* ctx) { return ctx ? ctx->last_err : ""; }
 
-int sccg_work_counters(sccg_ctx* ctx, uint64_t* out10, int reset)
+int sccg_work_counters(sccg_ctx* ctx, uint64_t* out12, int reset)
 {
-    if (!ctx || !out10) return SCCG_EINVAL;
+    if (!ctx || !out12) return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
     WorkCounters h;
     SCCG_CUDA(ctx, cudaMemcpy(&h, ctx->counters, sizeof h, cudaMemcpyDeviceToHost));
-    out10[0] = h.strip_edges; out10[1] = h.pixel_edges; out10[2] = h.box_edges; out10[3] = h.boxes;
-    out10[4] = h.row_entries; out10[5] = h.row_edges; out10[6] = h.scan_entries; out10[7] = h.scan_pairs;
-    out10[8] = h.leaf_pixels; out10[9] = h.window_pixels;
+    out12[0] = h.strip_edges; out12[1] = h.pixel_edges; out12[2] = h.box_edges; out12[3] = h.boxes;
+    out12[4] = h.row_entries; out12[5] = h.row_edges; out12[6] = h.scan_entries; out12[7] = h.scan_pairs;
+    out12[8] = h.leaf_pixels; out12[9] = h.window_pixels; out12[10] = h.raster_out; out12[11] = h.raster_and;
     if (reset) SCCG_CUDA(ctx, cudaMemset(ctx->counters, 0, sizeof(WorkCounters)));
     return SCCG_OK;
 }
@@ -861,7 +931,12 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
         if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
         if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
+        s->raster_ok = 0;
+        s->raster_bytes = 0;
+        if (s->raster && (!is_device_ptr(s->raster) || reinterpret_cast<uintptr_t>(s->raster) % 16 || s->raster_cap < 0))
+            return SCCG_EINVAL;
         need += carve_size<int>(s->n + 1);
+        if (s->raster) need += carve_size<long long>(s->n + 1) + carve_size<long long>(s->n / kScanBlock + 2);
         max_n = std::max<long long>(max_n, s->n);
     }
     need += band_build_scratch(max_n);     // for the band index of deferred polygons, after the sync
@@ -883,12 +958,31 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         SCCG_CUDA(ctx, cudaEventRecord(ctx->fork_event, st));
         SCCG_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->fork_event, 0));
     }
+    long long* roffs[kMaxPrepSets];
     for (int k = 0; k < n_sets; ++k) {
         const sccg_polyset* s = sets + k;
         int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
         unsigned* big_n = &stats[k].deferred;
         cudaStream_t sk = (two_streams && (k & 1)) ? ctx->side_stream : st;
-        if (s->n > 0 && ctx->params.area_method != SCCG_AREA_PIXELBOX) {
+        roffs[k] = nullptr;
+        if (s->raster && s->n > 0) {
+            // MBRs and raster sizes, the sizes scanned into offsets (in the buffer when its head fits),
+            // then one pixelization per polygon writing its raster
+            const long long hb = raster_head_bytes(s->n);
+            long long* scratch = cv.take<long long>(s->n + 1);
+            long long* bsum = cv.take<long long>(s->n / kScanBlock + 2);
+            long long* roff = s->raster_cap >= hb ? static_cast<long long*>(s->raster) : scratch;
+            roffs[k] = roff;
+            PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
+                       ctx->params.area_T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words, 0,
+                       roff, s->raster_cap >= hb ? reinterpret_cast<uint32_t*>(static_cast<char*>(s->raster) + hb)
+                                                 : nullptr,
+                       (s->raster_cap - hb) / 4};
+            r = launch_mbr(ctx, a, roff, sk);
+            if (!r) r = device_scan(ctx, roff, s->n, roff, bsum, sk);
+            if (!r) r = launch_prepare<kCapSmall, true, true>(ctx, a, sk);
+            if (r) return r;
+        } else if (s->n > 0 && ctx->params.area_method != SCCG_AREA_PIXELBOX) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.area_T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words,
@@ -922,7 +1016,12 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         s->n_tiles = std::max(res.n_tiles, s->n > 0 ? 1 : 0);
         s->band_bytes = res.band_bytes ? band_head_bytes(s->n) + (long long)res.band_bytes : 0;
         s->bands = nullptr;
-        if (!res.err && res.deferred && ctx->params.area_method != SCCG_AREA_PIXELBOX) {
+        const bool rasters = roffs[k] != nullptr;
+        if (rasters) {
+            s->raster_bytes = raster_head_bytes(s->n) + 4 * (long long)res.raster_words;
+            s->raster_ok = !res.err && s->raster_bytes <= s->raster_cap ? 1 : 0;
+        }
+        if (!res.err && res.deferred && (rasters || ctx->params.area_method != SCCG_AREA_PIXELBOX)) {
             // areas of the deferred polygons by rows; those with 1024 or more vertices from a
             // temporary band index
             int rr = SCCG_OK;
@@ -933,7 +1032,23 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
                 if (!rr) rr = build_bands_into(ctx, s, static_cast<char*>(ctx->aux[2]), s->band_bytes, bcv, st);
                 blob = static_cast<const char*>(ctx->aux[2]);
             }
-            if (!rr) {
+            if (!rr && s->raster_ok) {
+                // rasters of the windows over 64 pixels wide or high, and their areas
+                const int wpc = 4;
+                const size_t smem = sizeof(DrawSmem) * wpc;
+                auto kfn = ctx->count_work ? k_raster_big<true> : k_raster_big<false>;
+                rr = set_smem(ctx, kfn, smem);
+                const unsigned grid = (unsigned)((res.deferred + wpc - 1) / wpc);
+                if (!rr) {
+                    kfn<<<grid, 32 * wpc, smem, st>>>(
+                        s->off, s->xy, reinterpret_cast<const int4*>(s->mbr), blob, big_lists[k], &stats[k].deferred,
+                        s->area, roffs[k],
+                        reinterpret_cast<uint32_t*>(static_cast<char*>(s->raster) + raster_head_bytes(s->n)),
+                        ctx->counters);
+                    SCCG_LAUNCHED(ctx, "k_raster_big");
+                    ctx->launches += 1;
+                }
+            } else if (!rr) {
                 const int wpc = 4;
                 const size_t smem = sizeof(ScanSmem) * wpc;
                 auto kfn = ctx->count_work ? k_area_bands<true> : k_area_bands<false>;
@@ -958,6 +1073,54 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         }
     }
     return status;
+}
+
+int sccg_raster_bytes(sccg_ctx* ctx, sccg_polyset* s, int64_t* bytes, void* stream)
+{
+    if (!ctx || !s || !bytes) return SCCG_EINVAL;
+    if (s->n < 0 || s->n > 0x7fffffffLL) return SCCG_EINVAL;
+    if (!is_device_ptr(s->off) || !is_device_ptr(s->mbr)) return SCCG_EINVAL;
+    if (s->n > 0 && !is_device_ptr(s->xy)) return SCCG_EINVAL;
+    if (s->tile && !is_device_ptr(s->tile)) return SCCG_EINVAL;
+    if (reinterpret_cast<uintptr_t>(s->xy) % 8 || reinterpret_cast<uintptr_t>(s->mbr) % 16) return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long n = s->n;
+    int r = ws_reserve(ctx, carve_size<PrepStats>(1) + carve_size<long long>(n + 1) +
+                                carve_size<long long>(n / kScanBlock + 2));
+    if (r) return r;
+    Carve cv(ctx->ws);
+    PrepStats* stats = cv.take<PrepStats>(1);
+    long long* words = cv.take<long long>(n + 1);
+    long long* bsum = cv.take<long long>(n / kScanBlock + 2);
+    PrepStats* hstats = static_cast<PrepStats*>(ctx->pinned);
+    *hstats = PrepStats{0, 0, 0, 0, 0x7fffffffffffffffLL, 0, 0};
+    r = small_copy(ctx, stats, ctx->pinned_dev, sizeof(PrepStats), st);
+    if (r) return r;
+    PrepArgs a{n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats};
+    if (n > 0) {
+        r = launch_mbr(ctx, a, words, st);
+        if (!r) r = device_scan(ctx, words, n, words, bsum, st);
+    } else {
+        r = zero_async(ctx, words, sizeof(long long), st);
+    }
+    if (!r) r = small_copy(ctx, ctx->pinned_dev, stats, sizeof(PrepStats), st);
+    if (!r) r = small_copy(ctx, static_cast<char*>(ctx->pinned_dev) + sizeof(PrepStats), words + n, 8, st);
+    if (r) return r;
+    SCCG_CUDA(ctx, cudaStreamSynchronize(st));
+    const PrepStats res = *hstats;
+    const long long total = *reinterpret_cast<const long long*>(static_cast<const char*>(ctx->pinned) + sizeof(PrepStats));
+    if (res.err & (kErrFewVertices | kErrTiles)) {
+        snprintf(ctx->last_err, sizeof ctx->last_err, "invalid polygon set (flags %d, first bad polygon %lld)",
+                 res.err, res.first_bad);
+        return SCCG_EINVAL;
+    }
+    if (res.err & kErrRange) {
+        snprintf(ctx->last_err, sizeof ctx->last_err, "coordinate/extent out of range at polygon %lld", res.first_bad);
+        return SCCG_ERANGE;
+    }
+    *bytes = raster_head_bytes(n) + 4 * total;
+    return SCCG_OK;
 }
 
 int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream)
@@ -1172,6 +1335,7 @@ int sccg_pair_areas(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B,
                 inter, uni, ctx->params.T, ctx->counters,
                 static_cast<const char*>(A->bands), static_cast<const char*>(B->bands),
                 ctx->params.leaf_words};
+    if (mode != SCCG_MODE_NOSEP) use_rasters(ctx, A, B, a);
     const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
     if (mode == SCCG_MODE_PERSISTENT) {
         const int r = ws_reserve(ctx, persistent_scratch(n_pairs));
@@ -1220,6 +1384,7 @@ int sccg_pair_areas_tiles(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polys
                     inter + p0, uni + p0, ctx->params.T, ctx->counters,
                     static_cast<const char*>(A->bands), static_cast<const char*>(B->bands),
                     ctx->params.leaf_words};
+        use_rasters(ctx, A, B, a);
         int r;
         r = cap == kCapSmall ? launch_plain<kCapSmall>(ctx, a, ctx->tstream[k])
                              : launch_plain<kCapBig>(ctx, a, ctx->tstream[k]);
@@ -1248,7 +1413,8 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int r = ws_reserve(ctx, std::max(persistent_scratch(std::max<long long>(n_pairs, 1)), jaccard_scratch(ctx, n_pairs)));
     if (r) return r;
-    const void* key[11] = {A->off, A->xy, A->mbr, A->bands, B->off, B->xy, B->mbr, B->bands, pa, inter, out};
+    const void* key[13] = {A->off, A->xy, A->mbr, A->bands, B->off, B->xy, B->mbr, B->bands, pa, inter, out,
+                           A->raster_ok ? A->raster : nullptr, B->raster_ok ? B->raster : nullptr};
     const bool same = ctx->batch_exec && ctx->batch_n == n_pairs && !memcmp(key, ctx->batch_key, sizeof key) &&
                       !memcmp(&ctx->batch_params, &ctx->params, sizeof(sccg_params)) &&
                       ctx->batch_count_work == ctx->count_work && ctx->batch_key[0] != nullptr;
@@ -1264,6 +1430,7 @@ int sccg_batch_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset* B, 
                     inter, uni, ctx->params.T, ctx->counters,
                 static_cast<const char*>(A->bands), static_cast<const char*>(B->bands),
                 ctx->params.leaf_words};
+        use_rasters(ctx, A, B, a);
         const int cap = edge_cap_for(std::max(A->max_nv, B->max_nv));
         const unsigned long long launches0 = ctx->launches;
         SCCG_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));

@@ -28,8 +28,8 @@ def ctx(sccg):
 
 def gpu_run(ctx, w, mode=0):
     import paper_1208_0277_gb300 as P
-    A = ctx.upload(w.A)
-    B = ctx.upload(w.B)
+    A = ctx.upload(w.A, raster=False)
+    B = ctx.upload(w.B, raster=False)
     r = P.cross_compare(ctx, A, B, mode=mode)
     torch.cuda.synchronize()
     return dict(area_a=A.area.cpu().numpy()[: w.A.n], area_b=B.area.cpu().numpy()[: w.B.n],
@@ -123,7 +123,7 @@ def test_whole_slide_tiles_sampled(ctx):
 
 def test_tile_pair_offsets_and_one_launch_per_tile(ctx):
     w = W.subset_tiles(W.whole_slide(seed=0), [3, 4, 5, 30, 31])
-    A, B = ctx.upload(w.A), ctx.upload(w.B)
+    A, B = ctx.upload(w.A, raster=False), ctx.upload(w.B, raster=False)
     pa, pb, tpo = ctx.candidate_pairs(A, B, with_tile_offsets=True)
     pa_h = pa.cpu().numpy()
     assert tpo[0] == 0 and tpo[-1] == len(pa_h)
@@ -237,7 +237,7 @@ def test_band_index_gives_the_same_results(sccg, mode, T):
     c = sccg.Context(0, {"split_pixels": 400, "T": T})     # T = 8192: items stream their bands' records
     for wk in (w, ws):
         with_bands = gpu_run(c, wk, mode=mode)
-        A, B = c.upload(wk.A, bands=False), c.upload(wk.B, bands=False)
+        A, B = c.upload(wk.A, bands=False, raster=False), c.upload(wk.B, bands=False, raster=False)
         assert A.bands is None
         import paper_1208_0277_gb300 as P
         r = P.cross_compare(c, A, B, mode=mode)
@@ -245,7 +245,7 @@ def test_band_index_gives_the_same_results(sccg, mode, T):
         np.testing.assert_array_equal(with_bands["uni"], r["uni"].cpu().numpy())
         ref = O.cross_compare(wk.A, wk.B, method="rle")
         assert_same(with_bands, ref)
-    assert c.upload(w.A).bands is not None
+    assert c.upload(w.A, raster=False).bands is not None
 
 
 def test_heavy_tail_full_size_tissue(sccg):
@@ -255,7 +255,7 @@ def test_heavy_tail_full_size_tissue(sccg):
     others (the oracle's row-interval method; its brute force would take hours here)."""
     w = W.heavy_tail(seed=4, n_tiles=1, nuclei_per_tile=3000, tissue_lo=4, tissue_hi=5)
     c = sccg.Context(0)
-    A, B = c.upload(w.A), c.upload(w.B)
+    A, B = c.upload(w.A, raster=False), c.upload(w.B, raster=False)
     assert A.bands is not None and B.bands is not None
     mbrs = []
     for P_, d in ((w.A, A), (w.B, B)):
@@ -301,7 +301,7 @@ def test_nosep_variant_counts_the_union_directly(sccg, T):
 def test_nosep_refuses_wide_polygons(sccg):
     c = sccg.Context(0)
     w = rings_workload([[[0, 0], [9000, 0], [0, 40]]], [[[0, 0], [50, 0], [0, 50]]])
-    A, B = c.upload(w.A), c.upload(w.B)
+    A, B = c.upload(w.A, raster=False), c.upload(w.B, raster=False)
     pa, pb = c.candidate_pairs(A, B)
     with pytest.raises(sccg.SccgError) as e:
         c.pair_areas(A, B, pa, pb, mode=sccg.MODE_NOSEP)
@@ -334,7 +334,7 @@ def test_batch_graph_replay_and_recapture(sccg):
     c = sccg.Context(0, {"split_pixels": 64})
     for seed in (6, 7):
         w = W.single_tile(seed=seed, n=500)
-        A, B = c.upload(w.A), c.upload(w.B)
+        A, B = c.upload(w.A, raster=False), c.upload(w.B, raster=False)
         pa, pb = c.candidate_pairs(A, B)
         inter = torch.full((pa.numel(),), -7, dtype=torch.int64, device="cuda")
         uni = torch.full_like(inter, -7)
@@ -356,7 +356,7 @@ def test_batch_graph_with_large_polygons(sccg):
     join inside the captured graph) with 128-edge buffers and the overflow kernel; replayed twice."""
     c = sccg.Context(0, {"split_pixels": 256})
     A_, B_ = medium_polygons(16, n=50), medium_polygons(17, n=50, kind="tissue")
-    A, B = c.upload(A_), c.upload(B_)
+    A, B = c.upload(A_, raster=False), c.upload(B_, raster=False)
     pa, pb = c.candidate_pairs(A, B)
     inter = torch.full((pa.numel(),), -7, dtype=torch.int64, device="cuda")
     uni = torch.full_like(inter, -7)
@@ -422,7 +422,7 @@ def test_polygon_area_methods_match_oracle(sccg, method, area_T):
     sets = [W.from_rings(rings), medium_polygons(12, n=40, kind="tissue"), W.single_tile(seed=5, n=400).A]
     ctx = sccg.Context(0, {"area_method": method, "area_T": area_T})
     for P in sets:
-        d = ctx.upload(P)
+        d = ctx.upload(P, raster=False)
         torch.cuda.synchronize()
         ref, _ = O.polygon_areas(P.off, P.xy, method="rle")
         np.testing.assert_array_equal(d.area.cpu().numpy()[: P.n], ref)
@@ -470,7 +470,7 @@ def test_empty_sets_and_no_pairs(ctx):
     assert g["jaccard"]["n_nonzero"] == 0 and g["jaccard"]["J"] == 0.0
     import paper_1208_0277_gb300 as P
     E = ctx.prepare(torch.zeros(1, dtype=torch.int64, device="cuda"),
-                    torch.zeros(0, dtype=torch.int32, device="cuda"), None)
+                    torch.zeros(0, dtype=torch.int32, device="cuda"), None, raster=False)
     pa, pb = ctx.candidate_pairs(E, E)
     assert pa.numel() == 0
     assert P.cross_compare(ctx, E, E)["jaccard"]["n_pairs"] == 0
@@ -483,9 +483,9 @@ def test_prepare_sets_matches_single_prepares(ctx, sccg):
     dev = torch.device("cuda")
     specs = [(torch.from_numpy(P_.off).to(dev), torch.from_numpy(P_.xy).to(dev), torch.from_numpy(P_.tile).to(dev),
               None) for P_ in (w.A, w.B, w.A)]
-    many = ctx.prepare_sets(specs)
+    many = ctx.prepare_sets(specs, raster=False)
     for d, P_ in zip(many, (w.A, w.B, w.A)):
-        one = ctx.upload(P_)
+        one = ctx.upload(P_, raster=False)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(d.area.cpu().numpy(), one.area.cpu().numpy())
         np.testing.assert_array_equal(d.mbr.cpu().numpy(), one.mbr.cpu().numpy())
@@ -494,7 +494,7 @@ def test_prepare_sets_matches_single_prepares(ctx, sccg):
     bad = W.from_rings([[[0, 0], [1, 1]]])
     specs.insert(1, (torch.from_numpy(bad.off).to(dev), torch.from_numpy(bad.xy).to(dev), None, None))
     with pytest.raises(sccg.SccgError) as e:
-        ctx.prepare_sets(specs)
+        ctx.prepare_sets(specs, raster=False)
     assert e.value.status == 1
 
 
@@ -502,16 +502,16 @@ def test_prepare_sets_matches_single_prepares(ctx, sccg):
 
 def test_invalid_inputs_rejected_on_the_host(ctx, sccg):
     with pytest.raises(sccg.SccgError) as e:
-        ctx.upload(W.from_rings([[[0, 0], [1, 1]]]))
+        ctx.upload(W.from_rings([[[0, 0], [1, 1]]]), raster=False)
     assert e.value.status == 1
     with pytest.raises(sccg.SccgError) as e:
-        ctx.upload(W.from_rings([[[0, 0], [16385, 0], [0, 3]]]))
+        ctx.upload(W.from_rings([[[0, 0], [16385, 0], [0, 3]]]), raster=False)
     assert e.value.status == 2
     with pytest.raises(sccg.SccgError) as e:
-        ctx.upload(W.from_rings([[[0, 0], [3, 0], [0, 3]], [[0, 0], [3, 0], [0, 3]]], tiles=[1, 0]))
+        ctx.upload(W.from_rings([[[0, 0], [3, 0], [0, 3]], [[0, 0], [3, 0], [0, 3]]], tiles=[1, 0]), raster=False)
     assert e.value.status == 1
     # a host pointer where device memory is required
-    A = ctx.upload(W.from_rings([[[0, 0], [3, 0], [0, 3]]]))
+    A = ctx.upload(W.from_rings([[[0, 0], [3, 0], [0, 3]]]), raster=False)
     host = np.zeros(4, dtype=np.int64)
     st = ctx.lib.sccg_pair_areas(ctx.h, ctypes.byref(A.c), ctypes.byref(A.c), host.ctypes.data,
                                  host.ctypes.data, 1, host.ctypes.data, host.ctypes.data, 0, None)
@@ -535,7 +535,7 @@ def test_candidate_pairs_speculative_sizes(sccg, kind):
     for mode in (1, 0, 2, 1):
         c = sccg.Context(0)
         c.set_param("candidate_speculative", mode)
-        A, B = c.upload(w.A), c.upload(w.B)
+        A, B = c.upload(w.A, raster=False), c.upload(w.B, raster=False)
         pa, pb, tpo = c.candidate_pairs(A, B, with_tile_offsets=True)
         got.append((pa.cpu().numpy(), pb.cpu().numpy(), np.asarray(tpo)))
         c.close()
@@ -566,7 +566,7 @@ def test_prepare_leaf_and_rows_boundaries(sccg, area_T):
     c = P.Context(0, {"area_T": area_T})
     for sel in (rings, [r for r in rings if len(r) <= 128], [r for r in rings if len(r) > 128]):
         ps = W.from_rings([np.asarray(r) for r in sel])
-        d = c.upload(ps)
+        d = c.upload(ps, raster=False)
         torch.cuda.synchronize()
         ref_area, ref_mbr = O.polygon_areas(ps.off, ps.xy)
         np.testing.assert_array_equal(d.area.cpu().numpy()[: ps.n], ref_area)

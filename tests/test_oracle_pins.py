@@ -323,3 +323,43 @@ def test_contains_flags_rectangles():
     inter, _ = O.pair_areas(A, B, pa, pb)
     f = O.contains_flags(area_a, area_b, pa, pb, inter)
     assert list(f) == [1, 0, 3, 2, 2]
+
+
+# ------------------------------------------------------------------------------- membership masks
+
+@pytest.mark.parametrize("method", ["brute", "rle"])
+def test_mask_of_rectangles_and_triangles_closed_forms(method):
+    """A rectangle's window is all inside; the right triangle (0,0), (n,0), (0,n) holds pixel (x, y)
+    exactly when its centre is strictly below the hypotenuse, x + y + 1 < n: a centre on that edge
+    does not count it, and the ray then meets no other edge. Its mirror image (0,0), (0,n), (-n,0)
+    keeps the centres on its hypotenuse: the ray from such a centre does not count that edge but
+    still crosses the edge x = 0, so pixel (x, y) is inside exactly when x + n >= y."""
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        x0, y0 = (int(v) for v in rng.integers(-500, 500, 2))
+        w, h = (int(v) for v in rng.integers(1, 70, 2))
+        m = O.polygon_mask(rect(x0, y0, w, h), method)
+        assert m.shape == (h, w) and m.all()
+    for n in (1, 2, 3, 17, 64, 65, 100):
+        m = O.polygon_mask([[0, 0], [n, 0], [0, n]], method)
+        y, x = np.mgrid[0:n, 0:n]
+        np.testing.assert_array_equal(m, x + y + 1 < n)
+        mm = O.polygon_mask([[0, 0], [0, n], [-n, 0]], method)
+        np.testing.assert_array_equal(mm, x >= y)          # column index x stands for pixel x - n
+        assert mm.sum() == n * (n + 1) // 2
+
+
+def test_masks_agree_with_each_other_the_pixel_test_and_the_areas():
+    """The two mask methods are independent; each mask's popcount is the polygon's area and each of
+    its cells is the per-pixel test."""
+    w = W.single_tile(seed=9, n=60)
+    rng = np.random.default_rng(3)
+    for i in range(w.A.n):
+        ring = w.A.xy[2 * w.A.off[i]: 2 * w.A.off[i + 1]].reshape(-1, 2)
+        mb = O.polygon_mask(ring, "brute")
+        np.testing.assert_array_equal(mb, O.polygon_mask(ring, "rle"))
+        assert mb.sum() == O.polygon_area(ring) == O.polygon_area_rle(ring)
+        x0, y0 = ring[:, 0].min(), ring[:, 1].min()
+        for _ in range(5):
+            yy, xx = int(rng.integers(0, mb.shape[0])), int(rng.integers(0, mb.shape[1]))
+            assert mb[yy, xx] == bool(O.pixel_in_polygon(ring, x0 + xx, y0 + yy))
