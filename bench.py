@@ -79,6 +79,8 @@ def parse_args():
     p.add_argument("--ablation", action="store_true",
                    help="Fig. 8 of the paper: PixelOnly / PixelBox-NoSep / PixelBox pair-area times on the "
                    "first 9 whole-slide tiles with coordinates scaled x1..x5 (prints one JSON line)")
+    p.add_argument("--no-rasters", action="store_true",
+                   help="prepare the sets without pixel rasters (pair areas pixelize every pair window)")
     p.add_argument("--profile-once", action="store_true",
                    help="run a single step of --form and exit (for ncu captures; prints no bench line)")
     return p.parse_args()
@@ -122,7 +124,7 @@ def make_workload(config: int, seed: int, tiles: int):
 def kernel_source_hash() -> str:
     """Hash of the device code (the kernels whose DRAM traffic profiles/traffic.json records)."""
     h = hashlib.sha256()
-    for f in ("leaf64.cuh", "pixelbox.cuh", "scanline.cuh", "kernels.cuh"):
+    for f in ("leaf64.cuh", "pixelbox.cuh", "scanline.cuh", "kernels.cuh", "raster.cuh"):
         with open(os.path.join(ROOT, "paper_1208_0277_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -298,15 +300,18 @@ def ablation(args):
     n_ref = None
     for s in range(1, 6):
         w = W.scaled(base, s)
-        A, B = ctx.upload(w.A), ctx.upload(w.B)
+        A, B = ctx.upload(w.A, raster=False), ctx.upload(w.B, raster=False)
         pa, pb = ctx.candidate_pairs(A, B)
         n = pa.numel()
         n_ref = n_ref or n
-        ri, ru = O.pair_areas(w.A, w.B, pa.cpu().numpy().astype(np.int64), pb.cpu().numpy().astype(np.int64),
-                              method="rle")
+        _, ma = O.polygon_areas(w.A.off, w.A.xy, method="rle")
+        _, mb = O.polygon_areas(w.B.off, w.B.xy, method="rle")
+        opa, opb = O.candidate_pairs(ma, w.A.tile, mb, w.B.tile)
+        ri, ru = O.pair_areas(w.A, w.B, opa, opb, method="rle")
         inter = torch.empty(n, dtype=torch.int64, device=dev)
         uni = torch.empty_like(inter)
-        row = {"scale": s, "pairs": n, "mean_window_px": None, "parity": True}
+        row = {"scale": s, "pairs": n, "mean_window_px": None,
+               "parity": bool(np.array_equal(pa.cpu().numpy(), opa) and np.array_equal(pb.cpu().numpy(), opb))}
         mbr_a, mbr_b = A.mbr[pa.long()].cpu().numpy(), B.mbr[pb.long()].cpu().numpy()
         ww = np.maximum(0, np.minimum(mbr_a[:, 2], mbr_b[:, 2]) - np.maximum(mbr_a[:, 0], mbr_b[:, 0]))
         wh = np.maximum(0, np.minimum(mbr_a[:, 3], mbr_b[:, 3]) - np.maximum(mbr_a[:, 1], mbr_b[:, 1]))
@@ -328,6 +333,20 @@ def ablation(args):
                 if best is None or ms < best[0]:
                     best = (ms, T)
             row[name] = {"ms": round(best[0], 4), "T": best[1]}
+        # each polygon pixelized once into a raster kept with the set; pairs AND two rasters
+        Ar, Br = ctx.upload(w.A), ctx.upload(w.B)
+        for name, mode in (("Rasters", P.MODE_PLAIN), ("Rasters persistent", P.MODE_PERSISTENT)):
+            inter.fill_(-7)
+            ms = timed(lambda: ctx.pair_areas(Ar, Br, pa, pb, mode=mode, out=(inter, uni)))
+            ok = bool(np.array_equal(inter.cpu().numpy(), ri) and np.array_equal(uni.cpu().numpy(), ru))
+            row["parity"] = row["parity"] and ok
+            row[name] = {"ms": round(ms, 4)}
+        specs = [(Ar.off, Ar.xy, Ar.tile, (Ar.mbr, Ar.area, Ar.raster)),
+                 (Br.off, Br.xy, Br.tile, (Br.mbr, Br.area, Br.raster))]
+        plain = [(Ar.off, Ar.xy, Ar.tile, (A.mbr, A.area)), (Br.off, Br.xy, Br.tile, (B.mbr, B.area))]
+        row["prepare_ms"] = {"with_rasters": round(timed(lambda: ctx.prepare_sets(specs, bands=False)), 4),
+                             "without": round(timed(lambda: ctx.prepare_sets(plain, bands=False, raster=False)), 4)}
+        del Ar, Br
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
     # Sec. 3.2's closed form for rectilinear sets (area_method SHOELACE) against the pixel count
@@ -342,14 +361,16 @@ def ablation(args):
     shoe = {"polygons": stairs.n, "vertices": stairs.n_vertices}
     for name, method in (("rows", P.AREA_ROWS), ("shoelace", P.AREA_SHOELACE)):
         ctx.set_param("area_method", method)
-        d = ctx.prepare(d_off, d_xy)
-        ms = timed(lambda: ctx.prepare(d_off, d_xy, out=(d.mbr, d.area)))
+        d = ctx.prepare(d_off, d_xy, raster=False)
+        ms = timed(lambda: ctx.prepare(d_off, d_xy, out=(d.mbr, d.area), raster=False))
         shoe[name] = {"ms": round(ms, 4), "exact": bool(np.array_equal(d.area.cpu().numpy()[: stairs.n], ref_area))}
     ctx.set_param("area_method", P.AREA_ROWS)
     print(json.dumps({"shoelace_prepare": shoe}), file=sys.stderr, flush=True)
     line = {"ablation": "Sec. 5.2 Fig. 8: PixelOnly vs PixelBox-NoSep vs PixelBox, coordinates scaled x1..x5; "
-                        "leaves as 32-pixel strips tested against every edge (the paper's per-pixel test), and "
-                        "'+words': leaves from per-row parity words (this build's default)",
+                        "leaves as 32-pixel strips tested against every edge (the paper's per-pixel test), "
+                        "'+words': leaves from per-row parity words, and 'Rasters': every polygon pixelized once "
+                        "when its set is prepared (this build's default), pairs ANDing two rasters "
+                        "(prepare_ms: both sets, with and without the rasters)",
             "workload": "first 9 tiles of the whole slide (seed 1), same candidate pairs at every scale",
             "pairs": n_ref, "unit": "ms per pair-area launch (median of 7, CUDA events)", "rows": rows,
             "shoelace_prepare": dict(shoe, note="sccg_prepare of 200,000 staircases (100 copies of 2,000 seeded "
@@ -452,6 +473,20 @@ FORM_NAMES = {"tiles": "one kernel launch per tile",
 
 
 _ALU = {}
+RASTER_BYTES_PER_PAIR = 88    # pa, pb; two MBRs; two raster offsets; two areas; inter and uni written
+RASTER_BYTES_PER_WORD = 8     # one 32-bit word of each raster per (row, word) of a pair window
+
+
+def hbm_peak() -> dict:
+    """The measured HBM copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json, written by the
+    measurement of the machine), else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        return {"gbs": float(m["hbm_gbs"]), "note": f"measured: {m.get('how', 'copy bandwidth')}"}
+    except (OSError, ValueError, KeyError):
+        return {"gbs": 6800.0, "note": "fallback: 6.8 TB/s, one earlier copy measurement on a GB300"}
 
 
 def alu_peak(device: int) -> dict:
@@ -556,17 +591,27 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         "Ambr": torch.empty((nA, 4), dtype=torch.int32, device=dev), "Aarea": torch.empty(nA, dtype=torch.int64, device=dev),
         "Bmbr": torch.empty((nB, 4), dtype=torch.int32, device=dev), "Barea": torch.empty(nB, dtype=torch.int64, device=dev),
     }
-    A = ctx.prepare(devb["Aoff"], devb["Axy"], devb["Atile"], out=(outs["Ambr"], outs["Aarea"]))
-    B = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
+    rasters = not args.no_rasters
+    A = ctx.prepare(devb["Aoff"], devb["Axy"], devb["Atile"], out=(outs["Ambr"], outs["Aarea"]), raster=rasters)
+    B = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]), raster=rasters)
+    # the sets' pixel rasters stay in device memory, their buffers reused by every later prepare
+    outs["Araster"], outs["Braster"] = A.raster, B.raster
+
+    def spec(name):
+        return (devb[name + "off"], devb[name + "xy"], devb[name + "tile"],
+                (outs[name + "mbr"], outs[name + "area"], outs[name + "raster"]))
+
     pa0, pb0, tpo0 = ctx.candidate_pairs(A, B, with_tile_offsets=True)
     n_pairs = int(pa0.numel())
     tuned = None
     if args.autotune == "on" or (args.autotune == "auto" and config in (3, 4, 5)):
         from paper_1208_0277_gb300 import tune
         tuned = tune.tune(ctx, A, B, pa0, pb0, mode=P.MODE_PLAIN if form_main == "tiles" else P.MODE_PERSISTENT)
-        tuned_prep = tune.tune_prepare(ctx, [(devb["Aoff"], devb["Axy"], devb["Atile"], (outs["Ambr"], outs["Aarea"])),
-                                             (devb["Boff"], devb["Bxy"], devb["Btile"], (outs["Bmbr"], outs["Barea"]))])
-        tuned["params"]["area_T"] = tuned_prep["area_T"]
+        if rasters:
+            tuned_prep = {"area_T": None, "ms": None, "table": [], "note": "sets with rasters: area_T does not apply"}
+        else:
+            tuned_prep = tune.tune_prepare(ctx, [spec("A"), spec("B")], raster=False)
+            tuned["params"]["area_T"] = tuned_prep["area_T"]
         tuned["prepare"] = tuned_prep
         print(f"config {config} autotune: {tuned['params']} ({len(tuned['table'])} trials, {tuned['ms']} ms; "
               f"prepare {tuned_prep['table']})", file=sys.stderr)
@@ -584,8 +629,7 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
     def step(form: str, phases=None):
         e = [ev() for _ in range(5)] if phases is not None else None
         if e: e[0].record(stream)
-        a, b = ctx.prepare_sets([(devb["Aoff"], devb["Axy"], devb["Atile"], (outs["Ambr"], outs["Aarea"])),
-                                 (devb["Boff"], devb["Bxy"], devb["Btile"], (outs["Bmbr"], outs["Barea"]))])
+        a, b = ctx.prepare_sets([spec("A"), spec("B")], raster=rasters)
         if e: e[1].record(stream)
         p_a, p_b, tpo = ctx.candidate_pairs(a, b, capacity=cap, with_tile_offsets=True, out=(pa, pb))
         tpo_box[0] = tpo
@@ -613,8 +657,7 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
     # one counting step (untimed): algorithmic work per phase for the roofline
     ctx.set_param("count_work", 1)
     ctx.work_counters(reset=True)
-    a_ = ctx.prepare(devb["Aoff"], devb["Axy"], devb["Atile"], out=(outs["Ambr"], outs["Aarea"]))
-    b_ = ctx.prepare(devb["Boff"], devb["Bxy"], devb["Btile"], out=(outs["Bmbr"], outs["Barea"]))
+    a_, b_ = ctx.prepare_sets([spec("A"), spec("B")], raster=rasters)
     work_prep = ctx.work_counters(reset=True)
     p_a, p_b, tpo = ctx.candidate_pairs(a_, b_, capacity=cap, with_tile_offsets=True, out=(pa, pb))
     if form_main == "tiles":
@@ -683,7 +726,9 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
     prm = ctx.params()
     side = math.isqrt(max(prm["split_pixels"], 1))
     streamed = prm["leaf_words"] and side * side < prm["T"]      # every item one leaf: streamed kernel
-    k_areas = ("k_pair_areas_plain" if form_main == "tiles" else
+    use_rasters = bool(rasters and prm["rasters"] and A.raster is not None and B.raster is not None)
+    k_areas = ("k_pair_raster" if use_rasters else
+               "k_pair_areas_plain" if form_main == "tiles" else
                ("k_pair_areas_leaf" if side <= 64 else "k_pair_areas_stream") if streamed else
                "k_pair_areas_persistent")
     traffic_tab = {}
@@ -707,7 +752,24 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
                                  "counted on device) per step / phase time (CUDA events)",
                 "work": wc}
 
-    r_areas = roof(k_areas, ph["pair_areas"], work_areas)
+    def roof_mem(kernel, phase_ms, wc):
+        # pair areas from rasters: bytes the method must move per pair (pair indices, two MBRs, two raster
+        # offsets, two areas, the two results) and per (row, word) unit (one word of each raster)
+        algo = RASTER_BYTES_PER_PAIR * n_pairs + RASTER_BYTES_PER_WORD * wc["raster_and"]
+        achieved = algo / (phase_ms / 1e3) / 1e9
+        peak = hbm_peak()
+        ent = traffic_tab.get(kernel, {})
+        traffic = (ent.get("bytes_per_step") if ent.get("source_hash") == kernel_source_hash() and
+                   ent.get("workload") == desc["workload"] else None)
+        return {"bound": "hbm", "achieved": achieved, "peak": peak["gbs"], "unit": "GB/s", "frac": achieved / peak["gbs"],
+                "traffic": traffic, "kernel": kernel, "phase_ms": phase_ms, "peak_note": peak["note"],
+                "achieved_note": f"algorithmic bytes ({RASTER_BYTES_PER_PAIR} per pair + {RASTER_BYTES_PER_WORD} per "
+                                 "(row, 32-pixel word) of the pair windows, counted on device) per step / phase "
+                                 "time (CUDA events)",
+                "algorithmic_bytes": algo, "work": wc}
+
+    r_areas = roof_mem(k_areas, ph["pair_areas"], work_areas) if use_rasters else \
+        roof(k_areas, ph["pair_areas"], work_areas)
     r_prep = roof("k_prepare", ph["prepare"], work_prep)
     roofline, roofline_other = (r_areas, r_prep) if ph["pair_areas"] >= ph["prepare"] else (r_prep, r_areas)
 
@@ -724,10 +786,16 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
                   "ms_per_step": main_r["ms"] / args.steps - ph["prepare"],
                   "note": "whole step minus the prepare phase (CUDA events): candidate pairs, pair areas and "
                           "unions, Jaccard on resident prepared sets"},
-        "rates": {"pixel_tests_per_s": work_areas["leaf_pixels"] / (ph["pair_areas"] / 1e3),
-                  "window_pixels_per_s": work_areas["window_pixels"] / (ph["pair_areas"] / 1e3),
-                  "note": "pixel tests = (pixel, polygon) memberships decided one pixel at a time in leaves; "
-                          "window pixels = pixels of the pair windows (or work items) resolved"},
+        "rates": ({"pixel_tests_per_s": work_prep["window_pixels"] / (ph["prepare"] / 1e3),
+                   "window_pixels_per_s": work_areas["window_pixels"] / (ph["pair_areas"] / 1e3),
+                   "note": "with rasters every (pixel, polygon) membership is decided once, in the prepare phase: "
+                           "pixel tests = pixels of the polygons' windows pixelized there, per second of that "
+                           "phase; window pixels = pixels of the pair windows resolved by ANDing rasters, per "
+                           "second of the pair-area phase"} if use_rasters else
+                  {"pixel_tests_per_s": work_areas["leaf_pixels"] / (ph["pair_areas"] / 1e3),
+                   "window_pixels_per_s": work_areas["window_pixels"] / (ph["pair_areas"] / 1e3),
+                   "note": "pixel tests = (pixel, polygon) memberships decided one pixel at a time in leaves; "
+                           "window pixels = pixels of the pair windows (or work items) resolved"}),
         "clocks": main_r["clocks"], "gpu_launches": main_r["launches"], "phases_ms": ph,
         "jaccard": {"J": main_r["J"]["J"], "Jprime": main_r["J"]["Jprime"], "n_nonzero": main_r["J"]["n_nonzero"]},
         "other_forms": {f: {"form": FORM_NAMES[f], "value": total_pairs * args.steps / (o["ms"] / 1e3),

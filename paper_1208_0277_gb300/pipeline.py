@@ -61,6 +61,7 @@ class _Side:
         self.tile = torch.empty(max(max_n, 1), dtype=torch.int32, device=dev)
         self.mbr = torch.empty((max(max_n, 1), 4), dtype=torch.int32, device=dev)
         self.area = torch.empty(max(max_n, 1), dtype=torch.int64, device=dev)
+        self.raster = None      # pixel rasters of the chunk, grown to the largest chunk by the first run
 
 
 class Pipeline:
@@ -164,9 +165,11 @@ class Pipeline:
             sa, sb = self.slots[slot]
             (a0, a1), (b0, b1) = self.ranges[k]
             with torch.cuda.stream(cs):
-                A, B = ctx.prepare_sets([(sa.off[:a1 - a0 + 1], sa.xy, sa.tile[:a1 - a0], (sa.mbr, sa.area)),
-                                         (sb.off[:b1 - b0 + 1], sb.xy, sb.tile[:b1 - b0], (sb.mbr, sb.area))],
-                                        stream=cs)
+                A, B = ctx.prepare_sets(
+                    [(sa.off[:a1 - a0 + 1], sa.xy, sa.tile[:a1 - a0], (sa.mbr, sa.area, sa.raster)),
+                     (sb.off[:b1 - b0 + 1], sb.xy, sb.tile[:b1 - b0], (sb.mbr, sb.area, sb.raster))], stream=cs)
+                sa.raster = A.raster if A.raster is not None else sa.raster
+                sb.raster = B.raster if B.raster is not None else sb.raster
                 while True:
                     try:
                         pa, pb = ctx.candidate_pairs(A, B, capacity=self.cap - P, stream=cs,

@@ -28,6 +28,9 @@ T_GRID = (2048, 4096, 8192, 16384, 65536)
 SPLIT_GRID = (1024, 2048, 4096, 16384)
 WPC_GRID = (2, 4, 8)
 LANES_GRID = (32, 1)       # threads per pair in the leaf path: one warp per item, or one lane per small pair
+# threads per pair with rasters: pairs of more (row, 32-pixel word) units than this get a CTA (-1: none)
+HEAVY_GRID = (-1, 256, 1024, 4096, 16384)
+CTAS_GRID = (0, 4, 8)      # resident CTAs per SM (0: occupancy maximum)
 # Work-item forms of the persistent queue, (split_pixels, T): items of split_pixels pixels are one
 # leaf each when split_pixels < T (streamed: windows up to 64 x 64 through the leaf kernel, larger
 # ones through the streamed kernel), otherwise they are subdivided into sampling boxes (staged
@@ -53,10 +56,12 @@ def _time(ctx, fn, reps: int, warm: int) -> float:
 
 def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: int = 1,
          t_grid=T_GRID, split_grid=SPLIT_GRID, wpc_grid=WPC_GRID, form_grid=FORM_GRID,
-         lanes_grid=LANES_GRID) -> dict:
+         lanes_grid=LANES_GRID, heavy_grid=HEAVY_GRID) -> dict:
     """For the persistent form, the best (split_pixels, T) pair of form_grid first; then coordinate
     descent over T, split_pixels (persistent form only) and warps_per_cta for the pair areas of
-    (pa, pb). Leaves ctx set to the best parameters. Returns
+    (pa, pb). When both sets keep pixel rasters (and the context uses them), the persistent form's
+    pair areas AND rasters instead, and the search is over raster_heavy (one warp or one CTA per
+    pair) and resident CTAs per SM. Leaves ctx set to the best parameters. Returns
     {"params": {...}, "ms": best, "table": [(params, ms), ...]}."""
     import torch
     n = pa.numel()
@@ -72,6 +77,25 @@ def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: in
         table.append((dict(params), round(ms, 4)))
         return ms
 
+    if best.get("rasters") and A.raster is not None and B.raster is not None and mode == MODE_PERSISTENT:
+        # pair areas from rasters: the only choice is how many threads a pair gets (one warp, or a
+        # whole CTA for pairs of more than raster_heavy (row, word) units), and resident CTAs per SM
+        keys = ("raster_heavy", "ctas_per_sm")
+        best_ms = run({k: best[k] for k in keys})
+        tried = {tuple(best[k] for k in keys)}
+        for name, grid in (("raster_heavy", heavy_grid), ("ctas_per_sm", CTAS_GRID)):
+            for v in grid:
+                trial = {k: best[k] for k in keys} | {name: v}
+                if tuple(trial[k] for k in keys) in tried:
+                    continue
+                tried.add(tuple(trial[k] for k in keys))
+                ms = run(trial)
+                if ms < best_ms:
+                    best_ms, best = ms, dict(best, **trial)
+        for k in keys:
+            ctx.set_param(k, best[k])
+        return {"params": {k: best[k] for k in keys}, "ms": round(best_ms, 4), "mode": "persistent (rasters)",
+                "table": table}
     keys = ("T", "split_pixels", "warps_per_cta", "pair_lanes")
     best_ms = run({k: best[k] for k in keys})
     if mode == MODE_PERSISTENT:
@@ -108,14 +132,15 @@ def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: in
 AREA_T_GRID = (8192, 65536, 262144)
 
 
-def tune_prepare(ctx, specs, reps: int = 3, warm: int = 1, grid=AREA_T_GRID) -> dict:
+def tune_prepare(ctx, specs, reps: int = 3, warm: int = 1, grid=AREA_T_GRID, raster: bool = False) -> dict:
     """area_T for sccg_prepare on the sets in specs ([(off, xy, tile, (mbr, area)), ...]): the box
-    size under which a polygon is one streamed leaf rather than counted by rows. Leaves ctx at the
-    best; returns {"area_T": best, "ms": best_ms, "table": [(area_T, ms), ...]}."""
+    size under which a polygon is one streamed leaf rather than counted by rows (sets prepared
+    without rasters; with rasters area_T does not apply). Leaves ctx at the best; returns
+    {"area_T": best, "ms": best_ms, "table": [(area_T, ms), ...]}."""
     table = []
     for v in grid:
         ctx.set_param("area_T", v)
-        table.append((v, round(_time(ctx, lambda: ctx.prepare_sets(specs), reps, warm), 4)))
+        table.append((v, round(_time(ctx, lambda: ctx.prepare_sets(specs, raster=raster), reps, warm), 4)))
     best = min(table, key=lambda t: t[1])
     ctx.set_param("area_T", best[0])
     return {"area_T": best[0], "ms": best[1], "table": table}

@@ -20,22 +20,31 @@ def test_cache_round_trip(tmp_path):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", [0, 1])
-def test_tuner_picks_from_its_grid_and_keeps_results_exact(mode):
+@pytest.mark.parametrize("mode,raster", [(0, False), (1, False), (1, True)])
+def test_tuner_picks_from_its_grid_and_keeps_results_exact(mode, raster):
+    """Without rasters the tuner searches T, the item size, warps per CTA and threads per item; with
+    rasters (persistent form) the threads per pair (raster_heavy: one warp or one CTA) and resident
+    CTAs per SM."""
     torch = pytest.importorskip("torch")
     import paper_1208_0277_gb300 as P
     P.build()
     w = W.single_tile(seed=9, n=600)
     ctx = P.Context(0)
-    A, B = ctx.upload(w.A), ctx.upload(w.B)
+    A, B = ctx.upload(w.A, raster=raster), ctx.upload(w.B, raster=raster)
     pa, pb = ctx.candidate_pairs(A, B)
     res = tune.tune(ctx, A, B, pa, pb, mode=mode, reps=2, warm=1)
     p = ctx.params()
-    assert res["params"]["T"] in tune.T_GRID + tuple(T for _, T in tune.FORM_GRID) + (8192,)
-    assert res["params"]["warps_per_cta"] in tune.WPC_GRID + (4,)
+    if raster:
+        assert res["params"]["raster_heavy"] in tune.HEAVY_GRID + (1024,)
+        assert res["params"]["ctas_per_sm"] in tune.CTAS_GRID
+        assert len(res["table"]) <= 1 + len(tune.HEAVY_GRID) + len(tune.CTAS_GRID)
+        assert len({tuple(sorted(t.items())) for t, _ in res["table"]}) == len(res["table"])   # none twice
+    else:
+        assert res["params"]["T"] in tune.T_GRID + tuple(T for _, T in tune.FORM_GRID) + (8192,)
+        assert res["params"]["warps_per_cta"] in tune.WPC_GRID + (4,)
+        assert len(res["table"]) >= 1 + len(tune.T_GRID) - 1
     for k, v in res["params"].items():
         assert p[k] == v
-    assert len(res["table"]) >= 1 + len(tune.T_GRID) - 1
     inter, uni = ctx.pair_areas(A, B, pa, pb, mode=mode)
     torch.cuda.synchronize()
     ref = O.cross_compare(w.A, w.B)
