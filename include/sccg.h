@@ -137,8 +137,11 @@ typedef struct sccg_polyset {
                                which sccg_prepare writes the set's pixel rasters: polygon i's window
                                of W x H pixels (its MBR) as H rows of ceil(W / 32) uint32 words, bit b
                                of word k of row r set iff pixel (minx + 32 k + b, miny + r) belongs to
-                               the polygon. Layout: int64 word offsets [n + 1] padded to 16 bytes,
-                               then the words (polygon i's start at word off[i]). */
+                               the polygon. Layout: int64 word offsets [n + 1] padded to 16 bytes
+                               (polygon i's words start at word off[i]; off[n] is the total), then
+                               the words: a slot of 128 words per polygon (polygon i's at word 128 i,
+                               holding its raster when its window is at most 64 x 64 pixels), then
+                               the rasters of the larger windows, in an order the call chooses. */
     int64_t raster_cap;     /* bytes available at raster */
     int64_t raster_bytes;   /* written by sccg_prepare when raster != NULL: bytes the rasters take
                                (offsets and words), whether they fitted or not */
@@ -159,13 +162,14 @@ typedef struct sccg_polyset {
  * Returns SCCG_EINVAL or SCCG_ERANGE for invalid sets (mbr/area contents then unspecified). */
 int sccg_prepare(sccg_ctx* ctx, sccg_polyset* s, void* stream);
 /* With s->raster set, sccg_prepare also writes the set's pixel rasters (Sec. 3.1's pixel membership,
- * decided once per polygon and kept in device memory): the MBRs are computed first, the rasters'
- * sizes scanned into their offsets, then each polygon is pixelized once, its ||p|| counted from its
- * raster. A pair's ||p n q|| is then the number of set bits of the AND of the two rasters over the
- * pair's window (sccg_pair_areas and the calls built on it, except SCCG_MODE_NOSEP), with the same
- * results. The area method does not apply to a set with rasters. When the rasters do not fit
- * (raster_bytes > raster_cap), nothing is written to the buffer, raster_ok is 0 and the set is
- * prepared as without rasters; sccg_raster_bytes gives the size beforehand. */
+ * decided once per polygon and kept in device memory): each polygon is pixelized once and its ||p||
+ * counted from its raster, the windows of at most 64 x 64 pixels into their slots in the pass that
+ * finds the MBRs, the larger ones after the synchronisation, once their sizes are known. A pair's
+ * ||p n q|| is then the number of set bits of the AND of the two rasters over the pair's window
+ * (sccg_pair_areas and the calls built on it, except SCCG_MODE_NOSEP), with the same results. The
+ * area method does not apply to a set with rasters. When the rasters do not fit (raster_bytes >
+ * raster_cap), raster_ok is 0 and the set is prepared as without rasters (the buffer's contents are
+ * then unspecified); sccg_raster_bytes gives the size beforehand. */
 
 /* Bytes the pixel rasters of set s take (offsets and words), for sizing s->raster. Computes and
  * writes the set's MBRs (s->mbr) on the way, validates the set as sccg_prepare does and SYNCHRONISES

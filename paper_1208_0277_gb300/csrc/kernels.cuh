@@ -154,11 +154,15 @@ struct PrepArgs {
     unsigned* big_n;
     int words;              // as AreasArgs::words
     int shoelace;           // 1: ||p|| of a polygon whose edges are all axis-parallel from its shoelace sum
-    // pixel rasters (MBR_IN: the MBRs were written by k_mbr and roff holds the rasters' word offsets)
-    const long long* roff;  // [n + 1]
-    uint32_t* rwords;       // raster words, written when roff[n] <= rcap_words
-    long long rcap_words;
+    // pixel rasters (RASTER): polygon i's words start at word rhead[i] of rwords; a window of at most
+    // 64 x 64 pixels has the slot of kRasterSlot words at kRasterSlot * i (written here when rleaf),
+    // larger ones are placed after the slots once their sizes are known (k_raster_place)
+    long long* rhead;       // [n + 1]
+    uint32_t* rwords;
+    int rleaf;              // 1: the header and the slots fit the buffer
 };
+
+constexpr int kRasterSlot = 128;        // words of a leaf window's raster slot: 64 rows of 2 words
 
 // Words of the pixel raster of a polygon whose window is W x H pixels: H rows of ceil(W / 32).
 __host__ __device__ inline long long raster_words_of(int W, int H)
@@ -166,15 +170,101 @@ __host__ __device__ inline long long raster_words_of(int W, int H)
     return (W > 0 && H > 0) ? (long long)H * ((W + 31) >> 5) : 0;
 }
 
-// a1 for sets that keep pixel rasters: MBR, validation and the word count of the raster of every
-// polygon (0 for an invalid one), one warp per polygon. k_prepare (MBR_IN) then reads the MBRs back
-// once the counts are scanned into the rasters' word offsets.
-__global__ void __launch_bounds__(256) k_mbr(const PrepArgs a, long long* words)
+// Sizing of a set's pixel rasters (sccg_raster_bytes): MBR, validation and, for every polygon whose
+// window is over 64 pixels wide or high, its raster's word count (0 for the others, which take a
+// fixed slot, and for invalid ones), one warp per polygon.
+__global__ void __launch_bounds__(256, 8) k_mbr(const PrepArgs a, long long* words)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
     long long first_bad = 0x7fffffffffffffffLL;
+    long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    // a memory-bound pass: the next polygon's offsets are loaded while this one's vertices are read,
+    // and each lane keeps four vertex loads in flight
+    long long o0 = 0, o1 = 0;
+    if (i < a.n) { o0 = a.off[i]; o1 = a.off[i + 1]; }
+    for (; i < a.n; i += nwarps) {
+        long long q0 = 0, q1 = 0;
+        if (i + nwarps < a.n) { q0 = a.off[i + nwarps]; q1 = a.off[i + nwarps + 1]; }
+        const long long nvl = o1 - o0;
+        const int2* v = reinterpret_cast<const int2*>(a.xy) + o0;
+        int e = 0;
+        int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -0x7fffffff, y1 = -0x7fffffff;
+        if (nvl < 3 || nvl > kMaxVertices) {
+            e = kErrFewVertices;
+        } else {
+            const int nv = (int)nvl;
+            for (int base = 0; base < nv; base += 128) {
+                int2 p[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = base + 32 * u + lane;
+                    p[u] = k < nv ? v[k] : v[0];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    x0 = min(x0, p[u].x); x1 = max(x1, p[u].x);
+                    y0 = min(y0, p[u].y); y1 = max(y1, p[u].y);
+                }
+            }
+            x0 = __reduce_min_sync(kFull, x0); y0 = __reduce_min_sync(kFull, y0);
+            x1 = __reduce_max_sync(kFull, x1); y1 = __reduce_max_sync(kFull, y1);
+            if (x0 < -kCoordLimit || y0 < -kCoordLimit || x1 > kCoordLimit || y1 > kCoordLimit ||
+                x1 - x0 > kExtentLimit || y1 - y0 > kExtentLimit)
+                e = kErrRange;
+        }
+        int t = 0;
+        if (a.tile) {
+            t = a.tile[i];
+            if (t < 0 || (i > 0 && a.tile[i - 1] > t)) e |= kErrTiles;
+        }
+        if (lane == 0) {
+            a.mbr[i] = make_int4(x0, y0, x1, y1);
+            words[i] = (e || (x1 - x0 <= 64 && y1 - y0 <= 64)) ? 0 : raster_words_of(x1 - x0, y1 - y0);
+        }
+        if (e) { err |= e; first_bad = min(first_bad, i); }
+        max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
+        if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
+        max_tile = max(max_tile, t);
+        o0 = q0;
+        o1 = q1;
+    }
+    if (lane == 0) {
+        if (err) { atomicOr(&a.stats->err, err); atomicMin(&a.stats->first_bad, first_bad); }
+        atomicMax(&a.stats->max_nv, max_nv);
+        atomicMax(&a.stats->max_extent, max_ext);
+        atomicMax(&a.stats->n_tiles, max_tile + 1);
+    }
+}
+
+// SCAN: a polygon whose window holds fewer than T pixels is pixelized here as one leaf, its edges
+// streamed from the ring (PixelBox's one-leaf case, cheapest for small windows; shared memory per
+// warp: one XorRows); every other one is listed for k_area_bands (by rows). Otherwise by PixelBox on
+// the polygon alone (per-warp WarpSmem), deferring polygons with more than defer_above vertices to
+// k_prepare_big.
+//
+// RASTER (sets that keep pixel rasters; SCAN only): a polygon whose window is at most 64 x 64 pixels
+// is pixelized here as one leaf and its rows are written to its raster slot (when rleaf); every
+// larger one is listed (its raster's words added to stats->raster_words) for k_raster_big, which
+// writes both its raster and ||p|| once the listed rasters are placed, or for k_area_bands when they
+// do not fit the buffer.
+template <int CAP, int STK, bool COUNT, bool SCAN, bool RASTER = false>
+__global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const PrepArgs a)
+{
+    static_assert(SCAN || !RASTER, "rasters are written by the streamed leaves");
+    SCCG_DYNAMIC_SMEM(int4, smem4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[SCAN ? 0 : warp];
+    char* wbytes = reinterpret_cast<char*>(smem4) + (SCAN ? warp * kPrepWarpBytes : 0);
+    XorRows& X = *reinterpret_cast<XorRows*>(wbytes);
+    Leaf64& L = *reinterpret_cast<Leaf64*>(wbytes);      // small windows use the same per-warp bytes
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    WorkCounters wc = {};
+    unsigned long long big_words = 0;
+    int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
+    long long first_bad = 0x7fffffffffffffffLL;
+    unsigned long long band_bytes = 0;
     for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
         const long long o0 = a.off[i], o1 = a.off[i + 1];
         const long long nvl = o1 - o0;
@@ -199,94 +289,13 @@ __global__ void __launch_bounds__(256) k_mbr(const PrepArgs a, long long* words)
                 x1 - x0 > kExtentLimit || y1 - y0 > kExtentLimit)
                 e = kErrRange;
         }
-        int t = 0;
-        if (a.tile) {
-            t = a.tile[i];
-            if (t < 0 || (i > 0 && a.tile[i - 1] > t)) e |= kErrTiles;
-        }
-        if (lane == 0) {
-            a.mbr[i] = make_int4(x0, y0, x1, y1);
-            words[i] = e ? 0 : raster_words_of(x1 - x0, y1 - y0);
-        }
-        if (e) { err |= e; first_bad = min(first_bad, i); }
-        max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
-        if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
-        max_tile = max(max_tile, t);
-    }
-    if (lane == 0) {
-        if (err) { atomicOr(&a.stats->err, err); atomicMin(&a.stats->first_bad, first_bad); }
-        atomicMax(&a.stats->max_nv, max_nv);
-        atomicMax(&a.stats->max_extent, max_ext);
-        atomicMax(&a.stats->n_tiles, max_tile + 1);
-    }
-}
-
-// SCAN: a polygon whose window holds fewer than T pixels is pixelized here as one leaf, its edges
-// streamed from the ring (PixelBox's one-leaf case, cheapest for small windows; shared memory per
-// warp: one XorRows); every other one is listed for k_area_bands (by rows). Otherwise by PixelBox on
-// the polygon alone (per-warp WarpSmem), deferring polygons with more than defer_above vertices to
-// k_prepare_big.
-//
-// MBR_IN (sets that keep pixel rasters; SCAN only): the MBRs come from k_mbr, which also validated
-// the set; a polygon whose window is at most 64 x 64 pixels is pixelized here as one leaf and its
-// rows are written to its raster, every larger one is listed for k_raster_big (which writes both its
-// raster and ||p||). When the rasters do not fit their buffer (roff[n] > rcap_words) nothing is
-// written to it and the listed polygons are counted by rows instead.
-template <int CAP, int STK, bool COUNT, bool SCAN, bool MBR_IN = false>
-__global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const PrepArgs a)
-{
-    static_assert(SCAN || !MBR_IN, "rasters are written by the streamed leaves");
-    SCCG_DYNAMIC_SMEM(int4, smem4);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem<CAP, STK>& S = reinterpret_cast<WarpSmem<CAP, STK>*>(smem4)[SCAN ? 0 : warp];
-    char* wbytes = reinterpret_cast<char*>(smem4) + (SCAN ? warp * kPrepWarpBytes : 0);
-    XorRows& X = *reinterpret_cast<XorRows*>(wbytes);
-    Leaf64& L = *reinterpret_cast<Leaf64*>(wbytes);      // small windows use the same per-warp bytes
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    WorkCounters wc = {};
-    const bool rfits = MBR_IN && a.rwords && a.roff[a.n] <= a.rcap_words;
-    if (MBR_IN && blockIdx.x == 0 && threadIdx.x == 0) a.stats->raster_words = (unsigned long long)a.roff[a.n];
-    int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
-    long long first_bad = 0x7fffffffffffffffLL;
-    unsigned long long band_bytes = 0;
-    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
-        const long long o0 = a.off[i], o1 = a.off[i + 1];
-        const long long nvl = o1 - o0;
-        const int2* v = reinterpret_cast<const int2*>(a.xy) + o0;
-        int e = 0;
-        int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -0x7fffffff, y1 = -0x7fffffff;
-        if (MBR_IN) {
-            const int4 m = a.mbr[i];
-            x0 = m.x; y0 = m.y; x1 = m.z; y1 = m.w;
-            // k_mbr reported these already; they only keep the polygon out of the arithmetic here
-            if (nvl < 3 || nvl > kMaxVertices || x0 < -kCoordLimit || y0 < -kCoordLimit || x1 > kCoordLimit ||
-                y1 > kCoordLimit || x1 - x0 > kExtentLimit || y1 - y0 > kExtentLimit)
-                e = kErrRange;
-        } else if (nvl < 3 || nvl > kMaxVertices) {
-            e = kErrFewVertices;
-        } else {
-            const int nv = (int)nvl;
-            for (int base = 0; base < nv; base += 32) {
-                const int k = base + lane;
-                if (k < nv) {
-                    const int2 p = v[k];
-                    x0 = min(x0, p.x); x1 = max(x1, p.x);
-                    y0 = min(y0, p.y); y1 = max(y1, p.y);
-                }
-            }
-            x0 = warp_min(x0); y0 = warp_min(y0);
-            x1 = warp_max(x1); y1 = warp_max(y1);
-            if (x0 < -kCoordLimit || y0 < -kCoordLimit || x1 > kCoordLimit || y1 > kCoordLimit ||
-                x1 - x0 > kExtentLimit || y1 - y0 > kExtentLimit)
-                e = kErrRange;
-        }
         uint32_t area = 0;
         // Rectilinear sets (Sec. 3.2's POLYAREA): when every edge of the ring is axis-parallel, ||p|| is
         // |twice the shoelace sum| / 2 (coordinates taken relative to the box corner, so every product
         // stays below 2^28 and the sum below 2^52); the caller's flag vouches that the ring is simple,
         // where this equals the pixel count. A ring with any other edge is counted by pixels below.
         bool closed_form = false;
-        if (SCAN && !MBR_IN && a.shoelace && e == 0) {
+        if (SCAN && !RASTER && a.shoelace && e == 0) {
             const int nv = (int)nvl;
             long long twice = 0;
             bool axis = true;
@@ -310,17 +319,21 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
         // SCAN: a polygon whose window is not small is deferred to k_area_bands (by rows).
         // Otherwise the large ones to k_prepare_big.
         const bool leaf_win = x1 - x0 <= kLeafSide && y1 - y0 <= kLeafSide;
-        const bool small_win = MBR_IN ? leaf_win : (long long)(x1 - x0) * (y1 - y0) < a.T;
+        const bool small_win = RASTER ? leaf_win : (long long)(x1 - x0) * (y1 - y0) < a.T;
         const bool by_rows = SCAN && !small_win;
         const bool defer = e == 0 && !closed_form && (by_rows || (!SCAN && a.defer_above > 0 && nvl > a.defer_above));
         if (lane == 0 && defer) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
+        if (RASTER && lane == 0) {
+            if (defer) big_words += (unsigned long long)raster_words_of(x1 - x0, y1 - y0);
+            else if (a.rleaf) a.rhead[i] = (long long)kRasterSlot * i;
+        }
         if (SCAN && e == 0 && !defer && !closed_form && x1 > x0 && y1 > y0) {
             if (leaf_win) {
                 area = leaf_area<COUNT>(v, (int)nvl, x0, y0, x1, y1, L, lane, wc);
-                if (MBR_IN && rfits) {
+                if (RASTER && a.rleaf) {
                     // the leaf's parity rows are the polygon's raster (one or two words per row)
                     const int W = x1 - x0, H = y1 - y0;
-                    uint32_t* out = a.rwords + a.roff[i];
+                    uint32_t* out = a.rwords + (long long)kRasterSlot * i;
                     const uint32_t vlo = low_mask(W), vhi = low_mask(max(W - 32, 0));
                     for (int r = lane; r < H; r += 32) {
                         if (W > 32) {
@@ -345,30 +358,27 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
             area = pixelbox<false, COUNT>(pp, x0, y0, x1, y1, a.T, a.words, S, lane, wc);
         }
         int t = 0;
-        if (!MBR_IN && a.tile) {
+        if (a.tile) {
             t = a.tile[i];
             if (t < 0 || (i > 0 && a.tile[i - 1] > t)) e |= kErrTiles;
         }
         if (lane == 0) {
-            if (!MBR_IN) a.mbr[i] = make_int4(x0, y0, x1, y1);
+            a.mbr[i] = make_int4(x0, y0, x1, y1);
             if (!defer) a.area[i] = (int64_t)area;
         }
         if (e == 0) band_bytes += (unsigned long long)band_block_size(v, (int)nvl, y0, y1, lane);
-        if (!MBR_IN) {
-            if (e) { err |= e; first_bad = min(first_bad, i); }
-            max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
-            if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
-            max_tile = max(max_tile, t);
-        }
+        if (e) { err |= e; first_bad = min(first_bad, i); }
+        max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
+        if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
+        max_tile = max(max_tile, t);
     }
     if (lane == 0) {
-        if (!MBR_IN) {
-            if (err) { atomicOr(&a.stats->err, err); atomicMin(&a.stats->first_bad, first_bad); }
-            atomicMax(&a.stats->max_nv, max_nv);
-            atomicMax(&a.stats->max_extent, max_ext);
-            atomicMax(&a.stats->n_tiles, max_tile + 1);
-        }
+        if (err) { atomicOr(&a.stats->err, err); atomicMin(&a.stats->first_bad, first_bad); }
+        atomicMax(&a.stats->max_nv, max_nv);
+        atomicMax(&a.stats->max_extent, max_ext);
+        atomicMax(&a.stats->n_tiles, max_tile + 1);
         if (band_bytes) atomicAdd(&a.stats->band_bytes, band_bytes);
+        if (RASTER && big_words) atomicAdd(&a.stats->raster_words, big_words);
     }
     if (COUNT) flush_counters(a.counters, wc);
 }

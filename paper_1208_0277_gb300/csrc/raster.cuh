@@ -3,7 +3,10 @@
 // The raster of polygon i is its window of W x H pixels (MBR [x0, x1) x [y0, y1)) as H rows of
 // nw = ceil(W / 32) words: bit b of word k of row r is set iff pixel (x0 + 32 k + b, y0 + r) belongs
 // to the polygon under the pixel-centre ray-casting rule of Sec. 3.1. Buffer layout: int64 off[n + 1]
-// (word offsets, the exclusive scan of the rasters' sizes) padded to 16 bytes, then the words.
+// (polygon i's first word; off[n] the total) padded to 16 bytes, then the words: a slot of
+// kRasterSlot words for every polygon (polygon i's at kRasterSlot * i, used when its window is at
+// most 64 x 64 pixels, so that k_prepare writes it in the same pass that finds the MBR), then the
+// rasters of the larger windows, placed once k_prepare has listed them.
 //
 // Every (pixel, polygon) membership is then decided once per polygon, when the set is prepared,
 // instead of once for every pair the polygon takes part in: ||p n q|| of a pair is the popcount of
@@ -174,6 +177,28 @@ __global__ void __launch_bounds__(128) k_raster_big(const int64_t* off, const in
         }
     }
     if (COUNT) flush_counters(counters, wc);
+}
+
+// Word counts of the rasters of the polygons k_prepare listed (windows over 64 pixels wide or high).
+__global__ void k_raster_sizes(const int* list, const unsigned* n_list, const int4* mbr, long long* words)
+{
+    const long long nl = *n_list;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nl; j += (long long)gridDim.x * blockDim.x) {
+        const int4 m = mbr[list[j]];
+        words[j] = raster_words_of(m.z - m.x, m.w - m.y);
+    }
+}
+
+// Header entries of the listed polygons, placed after the n leaf slots in list order (offs: the
+// exclusive scan of their word counts, offs[nl] their total), and rhead[n] = the rasters' total words.
+__global__ void k_raster_place(const int* list, const unsigned* n_list, const long long* offs, long long n,
+                               long long* rhead)
+{
+    const long long nl = *n_list;
+    const long long base = (long long)kRasterSlot * n;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nl; j += (long long)gridDim.x * blockDim.x)
+        rhead[list[j]] = base + offs[j];
+    if (blockIdx.x == 0 && threadIdx.x == 0) rhead[n] = base + offs[nl];
 }
 
 // ----------------------------------------------------------------------------------------------

@@ -250,20 +250,20 @@ int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
 
 int launch_mbr(sccg_ctx* ctx, const PrepArgs& a, long long* words, cudaStream_t st)
 {
-    const long long grid = grid_for(ctx, a.n, 8, 16);
+    const long long grid = grid_for(ctx, a.n, 8, 8);     // the resident CTAs, one polygon per warp in turn
     k_mbr<<<(unsigned)grid, 256, 0, st>>>(a, words);
     SCCG_LAUNCHED(ctx, "k_mbr");
     ctx->launches += 1;
     return SCCG_OK;
 }
 
-template <int CAP, bool SCAN, bool MBR_IN = false>
+template <int CAP, bool SCAN, bool RASTER = false>
 int launch_prepare(sccg_ctx* ctx, const PrepArgs& a, cudaStream_t st)
 {
     const int wpc = warps_for(ctx, CAP);
     const size_t smem = (SCAN ? kPrepWarpBytes : warp_smem<CAP>()) * wpc;    // SCAN: streamed leaves only
     const long long grid = grid_for(ctx, a.n, wpc, 64);
-    auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN, MBR_IN> : k_prepare<CAP, kStack, false, SCAN, MBR_IN>;
+    auto kfn = ctx->count_work ? k_prepare<CAP, kStack, true, SCAN, RASTER> : k_prepare<CAP, kStack, false, SCAN, RASTER>;
     int r = set_smem(ctx, kfn, smem);
     if (r) return r;
     kfn<<<(unsigned)grid, 32 * wpc, smem, st>>>(a);
@@ -959,6 +959,9 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         SCCG_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->fork_event, 0));
     }
     long long* roffs[kMaxPrepSets];
+    long long* rscan[kMaxPrepSets];
+    long long* rbsum[kMaxPrepSets];
+    bool rleaf[kMaxPrepSets];
     for (int k = 0; k < n_sets; ++k) {
         const sccg_polyset* s = sets + k;
         int* big_list = big_lists[k] = cv.take<int>(s->n + 1);
@@ -966,21 +969,19 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         cudaStream_t sk = (two_streams && (k & 1)) ? ctx->side_stream : st;
         roffs[k] = nullptr;
         if (s->raster && s->n > 0) {
-            // MBRs and raster sizes, the sizes scanned into offsets (in the buffer when its head fits),
-            // then one pixelization per polygon writing its raster
+            // one pass: MBR, validation, and the leaf windows pixelized into their raster slots; the
+            // larger windows are listed and drawn after the synchronisation
             const long long hb = raster_head_bytes(s->n);
-            long long* scratch = cv.take<long long>(s->n + 1);
-            long long* bsum = cv.take<long long>(s->n / kScanBlock + 2);
-            long long* roff = s->raster_cap >= hb ? static_cast<long long*>(s->raster) : scratch;
-            roffs[k] = roff;
+            rscan[k] = cv.take<long long>(s->n + 1);
+            rbsum[k] = cv.take<long long>(s->n / kScanBlock + 2);
+            rleaf[k] = s->raster_cap >= hb + 4LL * kRasterSlot * s->n;
+            roffs[k] = static_cast<long long*>(s->raster);
             PrepArgs a{s->n, s->off, s->xy, s->tile, reinterpret_cast<int4*>(s->mbr), s->area, stats + k,
                        ctx->params.area_T, ctx->counters, 0, big_list, big_n, ctx->params.leaf_words, 0,
-                       roff, s->raster_cap >= hb ? reinterpret_cast<uint32_t*>(static_cast<char*>(s->raster) + hb)
-                                                 : nullptr,
-                       (s->raster_cap - hb) / 4};
-            r = launch_mbr(ctx, a, roff, sk);
-            if (!r) r = device_scan(ctx, roff, s->n, roff, bsum, sk);
-            if (!r) r = launch_prepare<kCapSmall, true, true>(ctx, a, sk);
+                       rleaf[k] ? roffs[k] : nullptr,
+                       rleaf[k] ? reinterpret_cast<uint32_t*>(static_cast<char*>(s->raster) + hb) : nullptr,
+                       rleaf[k] ? 1 : 0};
+            r = launch_prepare<kCapSmall, true, true>(ctx, a, sk);
             if (r) return r;
         } else if (s->n > 0 && ctx->params.area_method != SCCG_AREA_PIXELBOX) {
             // polygons counted by rows are listed and counted after the sync (k_area_bands)
@@ -1018,8 +1019,20 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
         s->bands = nullptr;
         const bool rasters = roffs[k] != nullptr;
         if (rasters) {
-            s->raster_bytes = raster_head_bytes(s->n) + 4 * (long long)res.raster_words;
-            s->raster_ok = !res.err && s->raster_bytes <= s->raster_cap ? 1 : 0;
+            s->raster_bytes = raster_head_bytes(s->n) + 4 * (kRasterSlot * s->n + (long long)res.raster_words);
+            s->raster_ok = !res.err && rleaf[k] && s->raster_bytes <= s->raster_cap ? 1 : 0;
+            if (s->raster_ok) {
+                // the listed (larger) rasters after the slots, in list order
+                const unsigned nl = res.deferred;
+                const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>((nl + 255) / 256, 4LL * ctx->sm_count));
+                k_raster_sizes<<<g, 256, 0, st>>>(big_lists[k], &stats[k].deferred, reinterpret_cast<const int4*>(s->mbr),
+                                                  rscan[k]);
+                int rr = device_scan(ctx, rscan[k], nl, rscan[k], rbsum[k], st);
+                if (rr) return rr;
+                k_raster_place<<<g, 256, 0, st>>>(big_lists[k], &stats[k].deferred, rscan[k], s->n, roffs[k]);
+                SCCG_LAUNCHED(ctx, "k_raster_place");
+                ctx->launches += 2;
+            }
         }
         if (!res.err && res.deferred && (rasters || ctx->params.area_method != SCCG_AREA_PIXELBOX)) {
             // areas of the deferred polygons by rows; those with 1024 or more vertices from a
@@ -1119,7 +1132,7 @@ int sccg_raster_bytes(sccg_ctx* ctx, sccg_polyset* s, int64_t* bytes, void* stre
         snprintf(ctx->last_err, sizeof ctx->last_err, "coordinate/extent out of range at polygon %lld", res.first_bad);
         return SCCG_ERANGE;
     }
-    *bytes = raster_head_bytes(n) + 4 * total;
+    *bytes = raster_head_bytes(n) + 4 * (kRasterSlot * n + total);
     return SCCG_OK;
 }
 

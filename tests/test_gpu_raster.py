@@ -41,7 +41,7 @@ def decode_rasters(d):
     hb = (8 * (n + 1) + 15) & ~15
     off = buf[: 8 * (n + 1)].view(np.int64)
     words = buf[hb:].view(np.uint32)
-    assert off[0] == 0 and off[n] == words.size
+    assert off[n] == words.size
     return off, words, d.mbr.cpu().numpy()[:n]
 
 
@@ -50,11 +50,13 @@ def raster_bits(off, words, mbr, i):
     x0, y0, x1, y1 = (int(v) for v in mbr[i])
     Wd, H = x1 - x0, y1 - y0
     if Wd <= 0 or H <= 0:
-        assert off[i + 1] == off[i]
         return np.zeros((max(H, 0), max(Wd, 0)), dtype=bool)
     nw = (Wd + 31) // 32
-    assert off[i + 1] - off[i] == H * nw
-    w = np.ascontiguousarray(words[off[i]: off[i + 1]]).reshape(H, nw)
+    if Wd <= 64 and H <= 64:
+        assert off[i] == 128 * i                    # the polygon's slot
+    else:
+        assert off[i] >= 128 * len(mbr) and off[i] + H * nw <= words.size
+    w = np.ascontiguousarray(words[off[i]: off[i] + H * nw]).reshape(H, nw)
     bits = np.unpackbits(w.view(np.uint8).reshape(H, nw, 4), axis=2, bitorder="little").reshape(H, 32 * nw)
     assert not bits[:, Wd:].any(), f"bits beyond the window of polygon {i}"
     return bits[:, :Wd].astype(bool)
@@ -299,6 +301,9 @@ def test_raster_prepare_sets_matches_single_prepares(ctx):
     for d, P_ in zip(many, singles):
         one = ctx.upload(P_)
         assert d.c.raster_ok == 1 and d.c.raster_bytes == one.c.raster_bytes
-        for a, b in zip(decode_rasters(d), decode_rasters(one)):     # offsets, words, MBRs (not the padding)
-            np.testing.assert_array_equal(a, b)
+        # every polygon's raster (the unused parts of slots and the order of large rasters are free)
+        da, db = decode_rasters(d), decode_rasters(one)
+        np.testing.assert_array_equal(da[2], db[2])
+        for i in range(P_.n):
+            np.testing.assert_array_equal(raster_bits(*da, i), raster_bits(*db, i))
         np.testing.assert_array_equal(d.area.cpu().numpy(), one.area.cpu().numpy())
