@@ -37,24 +37,10 @@ struct WorkCounters {          // algorithmic work, accumulated only by the coun
     unsigned long long raster_and;    // (row, word) ANDs of two rasters over pairs' windows
 };
 
-__device__ __forceinline__ int warp_min(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-__device__ __forceinline__ int warp_max(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-__device__ __forceinline__ unsigned warp_sum(unsigned v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
+// Warp-wide reductions (redux.sync: one instruction each). Whole warp, converged.
+__device__ __forceinline__ int warp_min(int v) { return __reduce_min_sync(kFull, v); }
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(kFull, v); }
+__device__ __forceinline__ unsigned warp_sum(unsigned v) { return __reduce_add_sync(kFull, v); }
 
 // Stage edges [e0, e0 + cnt) of the ring v[0..nv) into E/R (whole warp; uniform trip count).
 // Edge record: int4 {ylo, dy, dx, xl} (lower endpoint first; a horizontal edge keeps its first

@@ -18,7 +18,7 @@
 // (c = crossing_count_r, Sec. 3.1 in doubled coordinates), so pixel x0 + t belongs to the polygon iff
 // an odd number of the row's crossings have c > t. Each crossing toggles bit c of a row of bits D;
 // pixel t is then the XOR of D's bits above t (an exclusive suffix XOR along the row). A pass covers
-// up to 32 * kDrawPieceWords columns (a piece starting at column cs) of a group of rows: a crossing
+// up to 32 PIECE columns (a piece starting at column cs) of a group of rows: a crossing
 // with c <= cs changes no pixel of the piece and is dropped, one with c beyond the piece toggles the
 // piece's overflow bit (position 32 nwp, after the piece's nwp words), which flips the whole piece.
 #pragma once
@@ -28,17 +28,20 @@
 
 namespace sccg {
 
-constexpr int kDrawPieceWords = 64;                          // columns per pass: 2048
-constexpr int kDrawWords = 32 * (kDrawPieceWords + 1);       // per-warp difference words
+// Per-warp difference words: 32 rows of a piece of PIECE words plus the overflow word. Polygons drawn
+// from their rings take pieces of 32 words (1024 columns: a small buffer, many resident warps);
+// polygons with band lists, whose passes are one 32-row band each, take 64 (2048 columns: each
+// band's list read half as often).
+template <int PIECE>
+struct DrawSmem {
+    uint32_t D[32 * (PIECE + 1)];
+};
 
 __host__ __device__ inline long long raster_head_bytes(long long n)
 {
     return (8 * (n + 1) + 15) & ~15LL;
 }
 
-struct DrawSmem {
-    uint32_t D[kDrawWords];
-};
 
 // Toggle the difference bits of the crossings of one group of edges (lane k holds edge
 // {ylo, dy, dx, xl}, lower endpoint first, when `has`) with window rows ya .. ya + nr - 1 (absolute
@@ -116,18 +119,20 @@ __device__ __forceinline__ uint32_t draw_finish(const uint32_t* D, int nr, int n
 }
 
 // Rasters and ||p|| of the polygons k_prepare listed (windows over 64 pixels wide or high), one warp
-// per polygon: pieces of up to 2048 columns, passes of as many rows as the per-warp difference words
-// hold. A polygon with a block in the band index (blob may be null) takes each 32-row band's edges
-// from the band's list; the others stream their whole ring once per pass.
-template <bool COUNT>
+// per polygon: pieces of up to 32 PIECE columns, passes of as many rows as the per-warp difference
+// words hold. BANDED: only the polygons with a block in the band index blob, each 32-row band's
+// edges taken from the band's list; otherwise only the others, which stream their whole ring once
+// per pass.
+template <bool COUNT, int PIECE, bool BANDED>
 __global__ void __launch_bounds__(128) k_raster_big(const int64_t* off, const int32_t* xy, const int4* mbr,
                                                     const char* blob, const int* list, const unsigned* n_list,
                                                     int64_t* area, const long long* roff, uint32_t* rwords,
                                                     WorkCounters* counters)
 {
+    constexpr int kWords = 32 * (PIECE + 1);
     SCCG_DYNAMIC_SMEM(int4, smem4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    DrawSmem& S = reinterpret_cast<DrawSmem*>(smem4)[warp];
+    DrawSmem<PIECE>& S = reinterpret_cast<DrawSmem<PIECE>*>(smem4)[warp];
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     WorkCounters wc = {};
     const long long nl = *n_list;
@@ -140,12 +145,13 @@ __global__ void __launch_bounds__(128) k_raster_big(const int64_t* off, const in
         const int W = m.z - m.x, H = m.w - m.y, nw = (W + 31) >> 5;
         uint32_t* out = rwords + roff[i];
         const char* blk = band_block(blob, i);
+        if ((blk != nullptr) != BANDED) continue;
         uint32_t acc = 0;
         unsigned long long ce = 0;
-        for (int cs = 0; cs < W; cs += 32 * kDrawPieceWords) {
-            const int nwp = min(kDrawPieceWords, nw - (cs >> 5));
+        for (int cs = 0; cs < W; cs += 32 * PIECE) {
+            const int nwp = min(PIECE, nw - (cs >> 5));
             // band lists cover 32 rows each (from the polygon's min y): one band per pass
-            const int nrmax = blk ? (1 << kBandShift) : kDrawWords / (nwp + 1);
+            const int nrmax = BANDED ? (1 << kBandShift) : kWords / (nwp + 1);
             for (int r0 = 0; r0 < H; r0 += nrmax) {
                 const int nr = min(nrmax, H - r0);
                 __syncwarp();

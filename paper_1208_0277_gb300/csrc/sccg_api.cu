@@ -248,6 +248,22 @@ int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
     return SCCG_OK;
 }
 
+template <int PIECE, bool BANDED>
+int launch_raster_big(sccg_ctx* ctx, const sccg_polyset* s, const char* blob, const int* list, const unsigned* n_list,
+                      unsigned n_host, const long long* rhead, uint32_t* rw, const int4* mbr, cudaStream_t st)
+{
+    const int wpc = 4;
+    const size_t smem = sizeof(DrawSmem<PIECE>) * wpc;
+    auto kfn = ctx->count_work ? k_raster_big<true, PIECE, BANDED> : k_raster_big<false, PIECE, BANDED>;
+    const int r = set_smem(ctx, kfn, smem);
+    if (r) return r;
+    const unsigned grid = (n_host + wpc - 1) / wpc;
+    kfn<<<grid, 32 * wpc, smem, st>>>(s->off, s->xy, mbr, blob, list, n_list, s->area, rhead, rw, ctx->counters);
+    SCCG_LAUNCHED(ctx, "k_raster_big");
+    ctx->launches += 1;
+    return SCCG_OK;
+}
+
 int launch_mbr(sccg_ctx* ctx, const PrepArgs& a, long long* words, cudaStream_t st)
 {
     const long long grid = grid_for(ctx, a.n, 8, 8);     // the resident CTAs, one polygon per warp in turn
@@ -1046,21 +1062,15 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
                 blob = static_cast<const char*>(ctx->aux[2]);
             }
             if (!rr && s->raster_ok) {
-                // rasters of the windows over 64 pixels wide or high, and their areas
-                const int wpc = 4;
-                const size_t smem = sizeof(DrawSmem) * wpc;
-                auto kfn = ctx->count_work ? k_raster_big<true> : k_raster_big<false>;
-                rr = set_smem(ctx, kfn, smem);
-                const unsigned grid = (unsigned)((res.deferred + wpc - 1) / wpc);
-                if (!rr) {
-                    kfn<<<grid, 32 * wpc, smem, st>>>(
-                        s->off, s->xy, reinterpret_cast<const int4*>(s->mbr), blob, big_lists[k], &stats[k].deferred,
-                        s->area, roffs[k],
-                        reinterpret_cast<uint32_t*>(static_cast<char*>(s->raster) + raster_head_bytes(s->n)),
-                        ctx->counters);
-                    SCCG_LAUNCHED(ctx, "k_raster_big");
-                    ctx->launches += 1;
-                }
+                // rasters of the windows over 64 pixels wide or high, and their areas: those drawn from
+                // their rings, then (when the set has a band index) those drawn band by band
+                uint32_t* rw = reinterpret_cast<uint32_t*>(static_cast<char*>(s->raster) + raster_head_bytes(s->n));
+                const int4* mbr = reinterpret_cast<const int4*>(s->mbr);
+                rr = launch_raster_big<32, false>(ctx, s, blob, big_lists[k], &stats[k].deferred, res.deferred,
+                                                  roffs[k], rw, mbr, st);
+                if (!rr && blob)
+                    rr = launch_raster_big<64, true>(ctx, s, blob, big_lists[k], &stats[k].deferred, res.deferred,
+                                                     roffs[k], rw, mbr, st);
             } else if (!rr) {
                 const int wpc = 4;
                 const size_t smem = sizeof(ScanSmem) * wpc;

@@ -104,7 +104,7 @@ def pair_run(ctx, w, mode, form="areas"):
 def edge_rings():
     """Windows of every size class the raster writers treat differently: 1..64 px (one or two words
     per row, written by the leaf), 65 px and more (difference rows), exactly 32 k px (the overflow
-    word of a piece), 2048 and 2049 px wide (one and two 2048-column pieces), thin and tall, zero
+    word of a piece), 1024, 1025, 2048 and 2049 px wide (one to three 1024-column pieces), thin and tall, zero
     height or width (no words), repeated vertices, a self-intersecting ring, steep spikes, and
     negative coordinates."""
     rs = []
@@ -115,6 +115,8 @@ def edge_rings():
         h = s // 2 + 1
         rs.append([[h, 0], [s + 1, h], [h, s + 1], [0, h]])                          # diamond
     rs.append([[0, 0], [2048, 0], [2048, 3], [1024, 40], [0, 3]])
+    rs.append([[0, 0], [1024, 0], [1024, 30], [512, 77], [0, 30]])
+    rs.append([[0, 0], [1025, 5], [1025, 9], [3, 66]])
     rs.append([[0, 0], [2049, 7], [2049, 9], [3, 45]])
     rs.append([[-1000, -1000], [3100, -990], [3096, -950], [-998, -951]])
     rs.append([[0, 0], [5, 0], [10, 0]])                                              # collinear: H = 0
@@ -158,6 +160,15 @@ def test_rasters_of_stars_medium_polygons_and_tissue(ctx):
     d = ctx.upload(h.A)
     assert d.bands is not None
     check_rasters(d, h.A)
+    # band lists wider than one 2048-column piece: zigzag tops of 1,101 vertices over 2,500 and 4,200 px
+    rs = []
+    for wdt, top in ((2500, 100), (4200, 70)):
+        zig = [[int(k * wdt / 1100), top - 10 * (k % 2)] for k in range(1101)]
+        rs.append(np.asarray([[0, 0], [wdt, -3]] + zig[::-1]))
+    ps = W.from_rings(rs)
+    d = ctx.upload(ps)
+    assert d.bands is not None
+    check_rasters(d, ps)
 
 
 def test_raster_areas_equal_the_non_raster_prepare(ctx):
