@@ -265,8 +265,13 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
     long long first_bad = 0x7fffffffffffffffLL;
     unsigned long long band_bytes = 0;
-    for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp; i < a.n; i += nwarps) {
-        const long long o0 = a.off[i], o1 = a.off[i + 1];
+    long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    // the next polygon's offsets are loaded while this one is pixelized
+    long long o0 = 0, o1 = 0;
+    if (i < a.n) { o0 = a.off[i]; o1 = a.off[i + 1]; }
+    for (; i < a.n; i += nwarps) {
+        long long q0 = 0, q1 = 0;
+        if (i + nwarps < a.n) { q0 = a.off[i + nwarps]; q1 = a.off[i + nwarps + 1]; }
         const long long nvl = o1 - o0;
         const int2* v = reinterpret_cast<const int2*>(a.xy) + o0;
         int e = 0;
@@ -371,6 +376,8 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
         max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
         if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
         max_tile = max(max_tile, t);
+        o0 = q0;
+        o1 = q1;
     }
     if (lane == 0) {
         if (err) { atomicOr(&a.stats->err, err); atomicMin(&a.stats->first_bad, first_bad); }
@@ -742,11 +749,12 @@ __device__ __forceinline__ bool pair_here(const int4& A, const int4& B, const Ti
 constexpr int kSmallPairs = 32;   // A polygons with at most this many pairs sort them in registers
 constexpr int kSerialCells = 64;  // A polygons probing more cells are counted by a whole CTA
 
-// One thread per A polygon: number of pairs. A polygons with more than kSmallPairs pairs, or whose
-// MBR covers more than kSerialCells cells (counted afterwards by k_probe_count_big), are listed for
-// the CTA paths.
+// One thread per A polygon: number of pairs, and the B polygons of the first kSmallPairs of them
+// (in the order found) in cand[j * nA + a] (j-major: consecutive threads write consecutive words).
+// A polygons with more than kSmallPairs pairs, or whose MBR covers more than kSerialCells cells
+// (counted afterwards by k_probe_count_big; cand[a] = -1 marks them), are listed for the CTA paths.
 __global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long long* counts, int* big_list,
-                                                     unsigned* big_n)
+                                                     unsigned* big_n, int* cand)
 {
     const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= p.nA) return;
@@ -755,18 +763,48 @@ __global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long lon
     if (probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) {
         if ((long long)(cx1 - cx0 + 1) * (cy1 - cy0 + 1) > kSerialCells) {
             counts[a] = 0;
+            cand[a] = -1;
             big_list[atomicAdd(big_n, 1u)] = (int)a;
             return;
         }
         for (int cy = cy0; cy <= cy1; ++cy)
             for (int cx = cx0; cx <= cx1; ++cx) {
                 const long long c = base + (long long)cy * g.gx + cx;
-                for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e)
-                    cnt += pair_here(A, p.mbrB[p.entries[e]], g, cx, cy);
+                for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e) {
+                    const int b = p.entries[e];
+                    if (pair_here(A, p.mbrB[b], g, cx, cy)) {
+                        if (cnt < kSmallPairs) cand[cnt * p.nA + a] = b;
+                        ++cnt;
+                    }
+                }
             }
     }
     counts[a] = cnt;
     if (cnt > kSmallPairs) big_list[atomicAdd(big_n, 1u)] = (int)a;
+}
+
+// One thread per A polygon with 1 to kSmallPairs pairs found by k_probe_count: its B polygons from
+// cand, sorted, written at offs[a] (the pairs in ascending (a, b) order).
+__global__ void __launch_bounds__(256) k_probe_emit_small(long long nA, const long long* __restrict__ offs,
+                                                          const int* __restrict__ cand, int32_t* pa, int32_t* pb,
+                                                          long long cap)
+{
+    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nA) return;
+    const long long o = offs[a], n = offs[a + 1] - o;
+    if (n == 0 || n > kSmallPairs) return;
+    const int b0 = cand[a];
+    if (b0 < 0) return;                       // many cells: written by the CTA path
+    int buf[kSmallPairs];
+    buf[0] = b0;
+    for (int k = 1; k < (int)n; ++k) {        // insertion into the sorted prefix
+        const int b = cand[k * nA + a];
+        int j = k;
+        while (j > 0 && buf[j - 1] > b) { buf[j] = buf[j - 1]; --j; }
+        buf[j] = b;
+    }
+    for (int j = 0; j < (int)n; ++j)
+        if (o + j < cap) { pa[o + j] = (int32_t)a; pb[o + j] = buf[j]; }
 }
 
 // One CTA per listed A polygon that covers more than kSerialCells cells: its pair count, cells
@@ -801,35 +839,6 @@ __global__ void __launch_bounds__(256) k_probe_count_big(const ProbeArgs p, cons
         }
         __syncthreads();
     }
-}
-
-// One thread per A polygon with at most kSmallPairs pairs: gather, sort by b, write at offs[a].
-__global__ void __launch_bounds__(256) k_probe_write_small(const ProbeArgs p, const long long* __restrict__ offs,
-                                                           int32_t* pa, int32_t* pb, long long cap)
-{
-    const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= p.nA) return;
-    const long long o = offs[a], n = offs[a + 1] - o;
-    if (n == 0 || n > kSmallPairs) return;
-    int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
-    if (!probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) return;
-    if ((long long)(cx1 - cx0 + 1) * (cy1 - cy0 + 1) > kSerialCells) return;     // the CTA path writes it
-    int buf[kSmallPairs];
-    int k = 0;
-    for (int cy = cy0; cy <= cy1; ++cy)
-        for (int cx = cx0; cx <= cx1; ++cx) {
-            const long long c = base + (long long)cy * g.gx + cx;
-            for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e) {
-                const int b = p.entries[e];
-                if (pair_here(A, p.mbrB[b], g, cx, cy) && k < kSmallPairs) {
-                    int j = k++;                    // insertion into the sorted prefix
-                    while (j > 0 && buf[j - 1] > b) { buf[j] = buf[j - 1]; --j; }
-                    buf[j] = b;
-                }
-            }
-        }
-    for (int j = 0; j < k; ++j)
-        if (o + j < cap) { pa[o + j] = (int32_t)a; pb[o + j] = buf[j]; }
 }
 
 // One CTA per listed A polygon (more than kSmallPairs pairs): mark its pairs in a shared bitmap

@@ -27,9 +27,10 @@ struct sccg_ctx {
     sccg_params params{};
     void* ws = nullptr;             // device scratch
     size_t ws_size = 0;
-    void* aux[3] = {nullptr, nullptr, nullptr};  // separately growable scratch (candidate-pair grid cells,
-                                                 // entries; prepare's temporary band index)
-    size_t aux_size[3] = {0, 0, 0};
+    // separately growable scratch: candidate-pair grid cells, cell entries, prepare's temporary band
+    // index, the candidate pairs' per-polygon B lists
+    void* aux[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t aux_size[4] = {0, 0, 0, 0};
     void* pinned = nullptr;         // small host-pinned staging area
     void* pinned_dev = nullptr;     // ... as addressed by kernels
     WorkCounters* counters = nullptr;   // device work counters (counting mode)
@@ -856,7 +857,7 @@ int sccg_ctx_destroy(sccg_ctx* ctx)
         DeviceGuard g(ctx->device);
         cudaDeviceSynchronize();
         if (ctx->ws) cudaFree(ctx->ws);
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             if (ctx->aux[k]) cudaFree(ctx->aux[k]);
         if (ctx->counters) cudaFree(ctx->counters);
         if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -1275,8 +1276,11 @@ int candidate_pairs_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset
     if (r) return r;
     unsigned* big_n = reinterpret_cast<unsigned*>(small);
     const unsigned ga = (unsigned)((std::max(nA, 1LL) + 255) / 256);
+    r = aux_reserve(ctx, 3, sizeof(int) * (size_t)kSmallPairs * (size_t)std::max(nA, 1LL));
+    if (r) return r;
+    int* cand = static_cast<int*>(ctx->aux[3]);
     if (nA > 0) {
-        k_probe_count<<<ga, 256, 0, st>>>(pr, counts, big_list, big_n);
+        k_probe_count<<<ga, 256, 0, st>>>(pr, counts, big_list, big_n, cand);
         k_probe_count_big<<<(unsigned)(2 * ctx->sm_count), 256, 0, st>>>(pr, big_list, big_n, counts);
         SCCG_LAUNCHED(ctx, "k_probe_count");
         ctx->launches += 2;
@@ -1284,7 +1288,7 @@ int candidate_pairs_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset
     r = device_scan(ctx, counts, nA, offs, bsum, st);
     if (r) return r;
     if (nA > 0 && capacity > 0) {
-        k_probe_write_small<<<ga, 256, 0, st>>>(pr, offs, pa, pb, capacity);
+        k_probe_emit_small<<<ga, 256, 0, st>>>(nA, offs, cand, pa, pb, capacity);
         k_probe_write_big<<<(unsigned)(2 * ctx->sm_count), 256, 0, st>>>(pr, bstart, offs, big_list, big_n, pa, pb,
                                                                         capacity);
         SCCG_LAUNCHED(ctx, "k_probe_write");
