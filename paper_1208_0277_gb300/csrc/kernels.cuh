@@ -334,22 +334,9 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
         }
         if (SCAN && e == 0 && !defer && !closed_form && x1 > x0 && y1 > y0) {
             if (leaf_win) {
-                area = leaf_area<COUNT>(v, (int)nvl, x0, y0, x1, y1, L, lane, wc);
-                if (RASTER && a.rleaf) {
-                    // the leaf's parity rows are the polygon's raster (one or two words per row)
-                    const int W = x1 - x0, H = y1 - y0;
-                    uint32_t* out = a.rwords + (long long)kRasterSlot * i;
-                    const uint32_t vlo = low_mask(W), vhi = low_mask(max(W - 32, 0));
-                    for (int r = lane; r < H; r += 32) {
-                        if (W > 32) {
-                            out[2 * r] = L.w[r];
-                            out[2 * r + 1] = L.w[64 + r] & vhi;
-                        } else {
-                            out[r] = L.w[r] & vlo;
-                        }
-                    }
-                    if (COUNT && lane == 0) wc.raster_out += (unsigned long long)raster_words_of(W, H);
-                }
+                // with rasters the leaf's parity rows are also the polygon's raster, written to its slot
+                area = leaf_area<COUNT>(v, (int)nvl, x0, y0, x1, y1, L, lane, wc,
+                                        RASTER && a.rleaf ? a.rwords + (long long)kRasterSlot * i : nullptr);
             } else {
                 area = area_stream<COUNT>(v, (int)nvl, x0, y0, x1, y1, X, lane, wc);
             }

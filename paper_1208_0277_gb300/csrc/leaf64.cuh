@@ -210,10 +210,11 @@ __device__ __forceinline__ uint32_t leaf_pixels(const Leaf64& L, int W, int H, b
 }
 
 // ||p|| of a polygon whose bounding box [x0, x1) x [y0, y1) is at most 64 x 64 pixels, as one leaf:
-// its ring streamed once. Whole warp, converged.
+// its ring streamed once. With out, the rows are also written there as the polygon's raster (H rows
+// of one or two words), in the pass that counts them. Whole warp, converged.
 template <bool COUNT>
 __device__ __forceinline__ uint32_t leaf_area(const int2* v, int nv, int x0, int y0, int x1, int y1, Leaf64& L,
-                                              int lane, WorkCounters& wc)
+                                              int lane, WorkCounters& wc, uint32_t* out = nullptr)
 {
     const int W = x1 - x0, H = y1 - y0;
     if (COUNT && lane == 0) wc.window_pixels += (unsigned long long)W * H;
@@ -223,7 +224,31 @@ __device__ __forceinline__ uint32_t leaf_area(const int2* v, int nv, int x0, int
     unsigned long long ce = 0;
     leaf_rings<COUNT>(v, nv, 0, v, 0, 0, x0, y0, W, H, L, lane, ce);
     __syncwarp();
-    const uint32_t a = leaf_pixels<COUNT>(L, W, H, false, lane, wc);
+    uint32_t a;
+    if (out) {
+        const uint32_t vlo = low_mask(W), vhi = low_mask(max(W - 32, 0));
+        uint32_t acc = 0;
+        for (int r = lane; r < H; r += 32) {
+            const uint32_t lo = L.w[r] & vlo;
+            if (W > 32) {
+                const uint32_t hi = L.w[64 + r] & vhi;
+                out[2 * r] = lo;
+                out[2 * r + 1] = hi;
+                acc += __popc(lo) + __popc(hi);
+            } else {
+                out[r] = lo;
+                acc += __popc(lo);
+            }
+            if (COUNT) {
+                wc.row_edges += W > 32 ? 2ull : 1ull;
+                wc.leaf_pixels += (unsigned long long)W;
+            }
+        }
+        a = __reduce_add_sync(kFull, acc);
+        if (COUNT && lane == 0) wc.raster_out += (unsigned long long)H * (W > 32 ? 2 : 1);
+    } else {
+        a = leaf_pixels<COUNT>(L, W, H, false, lane, wc);
+    }
     if (COUNT) wc.row_entries += ce;
     __syncwarp();
     return a;
