@@ -734,24 +734,33 @@ __device__ __forceinline__ bool pair_here(const int4& A, const int4& B, const Ti
 }
 
 constexpr int kSmallPairs = 32;   // A polygons with at most this many pairs sort them in registers
-constexpr int kSerialCells = 64;  // A polygons probing more cells are counted by a whole CTA
+constexpr int kThreadCells = 8;   // A polygons probing more cells are counted by a warp ...
+constexpr int kSerialCells = 64;  // ... and those probing more than this by a whole CTA
 
 // One thread per A polygon: number of pairs, and the B polygons of the first kSmallPairs of them
 // (in the order found) in cand[j * nA + a] (j-major: consecutive threads write consecutive words).
 // A polygons with more than kSmallPairs pairs, or whose MBR covers more than kSerialCells cells
-// (counted afterwards by k_probe_count_big; cand[a] = -1 marks them), are listed for the CTA paths.
+// (counted afterwards by k_probe_count_big; cand[a] = -1 marks them), are listed for the CTA paths;
+// those covering more than kThreadCells cells are listed for k_probe_count_mid (one warp each, so
+// that one thread's long walk over many cells does not hold up its warp).
 __global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long long* counts, int* big_list,
-                                                     unsigned* big_n, int* cand)
+                                                     unsigned* big_n, int* cand, int* mid_list, unsigned* mid_n)
 {
     const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= p.nA) return;
     int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
     long long cnt = 0;
     if (probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1)) {
-        if ((long long)(cx1 - cx0 + 1) * (cy1 - cy0 + 1) > kSerialCells) {
+        const long long ncell = (long long)(cx1 - cx0 + 1) * (cy1 - cy0 + 1);
+        if (ncell > kSerialCells) {
             counts[a] = 0;
             cand[a] = -1;
             big_list[atomicAdd(big_n, 1u)] = (int)a;
+            return;
+        }
+        if (ncell > kThreadCells) {
+            counts[a] = 0;
+            mid_list[atomicAdd(mid_n, 1u)] = (int)a;
             return;
         }
         for (int cy = cy0; cy <= cy1; ++cy)
@@ -768,6 +777,47 @@ __global__ void __launch_bounds__(256) k_probe_count(const ProbeArgs p, long lon
     }
     counts[a] = cnt;
     if (cnt > kSmallPairs) big_list[atomicAdd(big_n, 1u)] = (int)a;
+}
+
+// One warp per A polygon listed by k_probe_count for covering kThreadCells + 1 .. kSerialCells cells:
+// its pairs counted with the cells spread over the lanes, its first kSmallPairs partners kept in cand
+// (lane by lane: a warp prefix sum of the lanes' counts gives each lane its first slot), and, with
+// more than kSmallPairs pairs, listed for k_probe_write_big.
+__global__ void __launch_bounds__(256) k_probe_count_mid(const ProbeArgs p, const int* __restrict__ mid_list,
+                                                         const unsigned* __restrict__ mid_n, long long* counts,
+                                                         int* big_list, unsigned* big_n, int* cand)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long nm = *mid_n;
+    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + warp; j < nm; j += nwarps) {
+        const long long a = mid_list[j];
+        int4 A; TileGrid g; long long base; int cx0, cx1, cy0, cy1;
+        probe_range(p, a, A, g, base, cx0, cx1, cy0, cy1);     // true: listed by k_probe_count
+        const int ncx = cx1 - cx0 + 1;
+        const int ncell = ncx * (cy1 - cy0 + 1);
+        int cnt = 0;
+        for (int q = lane; q < ncell; q += 32) {
+            const int cx = cx0 + q % ncx, cy = cy0 + q / ncx;
+            const long long c = base + (long long)cy * g.gx + cx;
+            for (long long e = p.cell_off[c]; e < p.cell_off[c + 1]; ++e)
+                cnt += pair_here(A, p.mbrB[p.entries[e]], g, cx, cy);
+        }
+        int total;
+        int k = warp_excl(cnt, lane, total);
+        for (int q = lane; q < ncell && k < kSmallPairs; q += 32) {
+            const int cx = cx0 + q % ncx, cy = cy0 + q / ncx;
+            const long long c = base + (long long)cy * g.gx + cx;
+            for (long long e = p.cell_off[c]; e < p.cell_off[c + 1] && k < kSmallPairs; ++e) {
+                const int b = p.entries[e];
+                if (pair_here(A, p.mbrB[b], g, cx, cy)) cand[(long long)(k++) * p.nA + a] = b;
+            }
+        }
+        if (lane == 0) {
+            counts[a] = total;
+            if (total > kSmallPairs) big_list[atomicAdd(big_n, 1u)] = (int)a;
+        }
+    }
 }
 
 // One thread per A polygon with 1 to kSmallPairs pairs found by k_probe_count: its B polygons from

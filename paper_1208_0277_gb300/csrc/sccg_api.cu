@@ -1187,7 +1187,7 @@ int candidate_pairs_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset
     const long long nb = (nscan + kScanBlock - 1) / kScanBlock + 1;
     const size_t need = carve_size<long long>(n_tiles + 1) * 5 + carve_size<TileGrid>(n_tiles) +
                         carve_size<long long>(nA + 1) * 2 + carve_size<long long>(nb) +
-                        carve_size<int>(nA + 1) + carve_size<unsigned long long>(4) +
+                        carve_size<int>(nA + 1) * 2 + carve_size<unsigned long long>(4) +
                         carve_size<unsigned long long>(1);
     int r = ws_reserve(ctx, need);
     if (r) return r;
@@ -1202,7 +1202,8 @@ int candidate_pairs_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset
     long long* offs = cv.take<long long>(nA + 1);
     long long* bsum = cv.take<long long>(nb);
     int* big_list = cv.take<int>(nA + 1);
-    unsigned long long* small = cv.take<unsigned long long>(4);   // [0] big count (as unsigned)
+    int* mid_list = cv.take<int>(nA + 1);
+    unsigned long long* small = cv.take<unsigned long long>(4);   // [0] big count, [1] mid count (as unsigned)
     unsigned long long* ok = spec ? cv.take<unsigned long long>(1) : nullptr;
     long long* h = static_cast<long long*>(ctx->pinned);
     const int4* mA = reinterpret_cast<const int4*>(A->mbr);
@@ -1275,15 +1276,18 @@ int candidate_pairs_run(sccg_ctx* ctx, const sccg_polyset* A, const sccg_polyset
     r = zero_async(ctx, small, sizeof(unsigned long long) * 4, st);
     if (r) return r;
     unsigned* big_n = reinterpret_cast<unsigned*>(small);
+    unsigned* mid_n = reinterpret_cast<unsigned*>(small + 1);
     const unsigned ga = (unsigned)((std::max(nA, 1LL) + 255) / 256);
     r = aux_reserve(ctx, 3, sizeof(int) * (size_t)kSmallPairs * (size_t)std::max(nA, 1LL));
     if (r) return r;
     int* cand = static_cast<int*>(ctx->aux[3]);
     if (nA > 0) {
-        k_probe_count<<<ga, 256, 0, st>>>(pr, counts, big_list, big_n, cand);
+        k_probe_count<<<ga, 256, 0, st>>>(pr, counts, big_list, big_n, cand, mid_list, mid_n);
+        k_probe_count_mid<<<(unsigned)(8 * ctx->sm_count), 256, 0, st>>>(pr, mid_list, mid_n, counts, big_list, big_n,
+                                                                        cand);
         k_probe_count_big<<<(unsigned)(2 * ctx->sm_count), 256, 0, st>>>(pr, big_list, big_n, counts);
         SCCG_LAUNCHED(ctx, "k_probe_count");
-        ctx->launches += 2;
+        ctx->launches += 3;
     }
     r = device_scan(ctx, counts, nA, offs, bsum, st);
     if (r) return r;
