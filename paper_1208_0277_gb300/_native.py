@@ -88,7 +88,8 @@ class ParamsC(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("split_pixels", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("area_method", ctypes.c_int32), ("leaf_words", ctypes.c_int32), ("pair_lanes", ctypes.c_int32),
-                ("area_T", ctypes.c_int32), ("rasters", ctypes.c_int32), ("raster_heavy", ctypes.c_int32)]
+                ("area_T", ctypes.c_int32), ("rasters", ctypes.c_int32), ("raster_heavy", ctypes.c_int32),
+                ("raster_lanes", ctypes.c_int32)]
 
 
 class JaccardC(ctypes.Structure):

@@ -76,11 +76,13 @@ struct LeafEdge {
 
 // The crossing of an edge with a straddled row (N, words w and w + 64): XOR the prefix mask of its
 // c = ceil(clamp(N, 0, cap) / d2) crossed pixels into the row's halves (pixels beyond the window's
-// width are masked off when the rows are counted). WIDE: the window is over 32 pixels wide.
-template <bool WIDE>
+// width are masked off when the rows are counted). WIDE: the window is over 32 pixels wide. SELF: the
+// window is the polygon's own MBR, so no edge crosses beyond its width (N <= W d2 <= cap) and the upper
+// clamp is not needed.
+template <bool WIDE, bool SELF = false>
 __device__ __forceinline__ void leaf_cross(int N, int cap, float rc, int w, Leaf64& L)
 {
-    const int c = leaf_ceil_div(min(max(N, 0), cap), rc);
+    const int c = leaf_ceil_div(SELF ? max(N, 0) : min(max(N, 0), cap), rc);
     const uint32_t lo = low_mask(c);
     if (lo) atomicXor(&L.w[w], lo);
     if (WIDE) {
@@ -94,14 +96,17 @@ __device__ __forceinline__ void leaf_cross(int N, int cap, float rc, int w, Leaf
 // Longer ones: the batch's (edge, row) crossings are spread evenly over the lanes (warp prefix sum of
 // the spans; each lane finds its crossing's edge by a binary search over the lanes' offsets and
 // fetches it by shuffles). Whole warp, converged.
-template <bool COUNT, bool WIDE>
+template <bool COUNT, bool WIDE, bool SELF = false>
 __device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, int maxs, Leaf64& L, int lane,
                                              unsigned long long& entries)
 {
     if (COUNT) entries += (unsigned long long)e.span;
     if (maxs <= kLeafLoopSpan) {
-        for (int s = 0; s < maxs; ++s)
-            if (s < e.span) leaf_cross<WIDE>(e.N0 + s * e.dx2, e.cap, e.rc, e.w + s, L);
+#pragma unroll
+        for (int s = 0; s < kLeafLoopSpan; ++s) {
+            if (s >= maxs) break;
+            if (s < e.span) leaf_cross<WIDE, SELF>(e.N0 + s * e.dx2, e.cap, e.rc, e.w + s, L);
+        }
         return;
     }
     int total;
@@ -115,7 +120,7 @@ __device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, int maxs, Leaf64
         const int cap = __shfl_sync(kFull, e.cap, own);
         const int w = __shfl_sync(kFull, e.w, own);
         const float rc = __shfl_sync(kFull, e.rc, own);
-        if (t < total) leaf_cross<WIDE>(N0 + s * dx2, cap, rc, w + s, L);
+        if (t < total) leaf_cross<WIDE, SELF>(N0 + s * dx2, cap, rc, w + s, L);
     }
 }
 
@@ -125,33 +130,35 @@ __device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, int maxs, Leaf64
 // point right of x0 crosses no pixel centre of the window (every centre lies right of x = x0), and a
 // horizontal one straddles no row: both get span 0. Every product is below 2^30 under the library's
 // coordinate and extent limits (|N| <= (2 dy) |dx| + (2 |x0 - xl| + 1) dy with dy, |dx|, |x0 - xl|
-// at most 2^14 + 64). Whole warp, converged.
-template <bool COUNT>
+// at most 2^14 + 64). SELF: the window is the polygon's own MBR, so every edge lies inside it: its rows
+// from ylo to yhi are all window rows, and an edge on the left border crosses no pixel (its c is 0).
+// Whole warp, converged.
+template <bool COUNT, bool SELF = false>
 __device__ __forceinline__ void leaf_batch(bool has, int2 a, int2 b, int x0, int y0, int W, int H, int base,
                                            Leaf64& L, int lane, unsigned long long& entries)
 {
     const bool up = a.y <= b.y;
     const int ylo = up ? a.y : b.y, yhi = up ? b.y : a.y;
-    const int rlo = max(ylo, y0);
+    const int rlo = SELF ? ylo : max(ylo, y0);
     LeafEdge e;
-    e.span = (has && max(a.x, b.x) > x0) ? max(min(yhi, y0 + H) - rlo, 0) : 0;
+    e.span = SELF ? (has ? yhi - ylo : 0) : (has && max(a.x, b.x) > x0) ? max(min(yhi, y0 + H) - rlo, 0) : 0;
     const int maxs = __reduce_max_sync(kFull, e.span);
     if (maxs == 0) return;
     const int xl = up ? a.x : b.x;
     const int dy = yhi - ylo, dx = (up ? b.x : a.x) - xl;
     const int d2 = dy + dy;
     e.dx2 = dx + dx;
-    e.N0 = (2 * (rlo - ylo) + 1) * dx - (2 * (x0 - xl) + 1) * dy;
+    e.N0 = SELF ? dx - (2 * (x0 - xl) + 1) * dy : (2 * (rlo - ylo) + 1) * dx - (2 * (x0 - xl) + 1) * dy;
     e.cap = d2 << 6;
     e.rc = rcp_approx(small_int_to_float(max(d2, 1)));
     e.w = base + rlo - y0;
-    if (W > 32) leaf_batch_w<COUNT, true>(e, maxs, L, lane, entries);
-    else leaf_batch_w<COUNT, false>(e, maxs, L, lane, entries);
+    if (W > 32) leaf_batch_w<COUNT, true, SELF>(e, maxs, L, lane, entries);
+    else leaf_batch_w<COUNT, false, SELF>(e, maxs, L, lane, entries);
 }
 
 // The edges of ring vp[0 .. np) (rows at word basep) followed by those of ring vq[0 .. nq) (rows at
 // baseq; nq may be 0), 32 at a time. Whole warp, converged; the trip count is warp-uniform.
-template <bool COUNT>
+template <bool COUNT, bool SELF = false>
 __device__ __forceinline__ void leaf_rings(const int2* vp, int np, int basep, const int2* vq, int nq, int baseq,
                                            int x0, int y0, int W, int H, Leaf64& L, int lane,
                                            unsigned long long& entries)
@@ -169,7 +176,7 @@ __device__ __forceinline__ void leaf_rings(const int2* vp, int np, int basep, co
             a = v[kk];
             b = v[kk + 1 == n ? 0 : kk + 1];
         }
-        leaf_batch<COUNT>(has, a, b, x0, y0, W, H, isq ? baseq : basep, L, lane, entries);
+        leaf_batch<COUNT, SELF>(has, a, b, x0, y0, W, H, isq ? baseq : basep, L, lane, entries);
     }
 }
 
@@ -222,7 +229,7 @@ __device__ __forceinline__ uint32_t leaf_area(const int2* v, int nv, int x0, int
     leaf_clear(L, W, H, false, lane);
     __syncwarp();
     unsigned long long ce = 0;
-    leaf_rings<COUNT>(v, nv, 0, v, 0, 0, x0, y0, W, H, L, lane, ce);
+    leaf_rings<COUNT, true>(v, nv, 0, v, 0, 0, x0, y0, W, H, L, lane, ce);
     __syncwarp();
     uint32_t a;
     if (out) {

@@ -265,11 +265,12 @@ __device__ __forceinline__ uint32_t raster_and_word(const uint32_t* ra, const ui
 }
 
 // Light pairs: each warp takes 32 consecutive pairs (a chunk); lane j reads pair j's MBRs, raster
-// offsets and areas into a shared table, then the warp goes through the chunk's pairs one by one,
-// lanes over the overlap's rows, and writes the 32 results together. Heavy pairs (more than
+// offsets and areas into a shared table, then the warp goes through the chunk's pairs G lanes per
+// pair (32 / G pairs at a time, so that their row loads are in flight together), lanes over the
+// overlap's rows, and writes the 32 results together. Heavy pairs (more than
 // heavy_words (row, word) units) are listed for k_pair_raster_heavy. A pair whose indices are out of
 // range gets -1.
-template <bool COUNT>
+template <bool COUNT, int G>
 __global__ void __launch_bounds__(256) k_pair_raster(const RasterPairArgs a)
 {
     __shared__ RPair tab[8][32];
@@ -302,22 +303,39 @@ __global__ void __launch_bounds__(256) k_pair_raster(const RasterPairArgs a)
         __syncwarp();
         unsigned todo = __ballot_sync(kFull, light && tab[warp][lane].H > 0);
         uint32_t mine = 0;
+        // G lanes per pair: the warp takes 32 / G of the chunk's pairs at a time, one per lane group
+        const int grp = lane / G, gl = lane % G;
+        const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (grp * G));
         while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const RPair t = tab[warp][j];
-            const int nwo = (t.W + 31) >> 5;
-            uint32_t acc = 0;
-            for (int r = lane; r < t.H; r += 32) {
-                const uint32_t* ra = a.rwA + t.pA + (long long)r * t.nwa;
-                const uint32_t* rb = a.rwB + t.pB + (long long)r * t.nwb;
-                for (int q = 0; q < nwo; ++q) acc += raster_and_word(ra, rb, t, q);
+            int my = -1;
+#pragma unroll
+            for (int g = 0; g < 32 / G; ++g) {
+                if (todo) {
+                    const int j = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    if (g == grp) my = j;
+                }
             }
-            const uint32_t tot = __reduce_add_sync(kFull, acc);
-            if (lane == j) mine = tot;
-            if (COUNT && lane == 0) {
-                wc.raster_and += (unsigned long long)t.H * nwo;
-                wc.window_pixels += (unsigned long long)t.W * t.H;
+            uint32_t acc = 0;
+            if (my >= 0) {
+                const RPair t = tab[warp][my];
+                const int nwo = (t.W + 31) >> 5;
+                for (int r = gl; r < t.H; r += G) {
+                    const uint32_t* ra = a.rwA + t.pA + (long long)r * t.nwa;
+                    const uint32_t* rb = a.rwB + t.pB + (long long)r * t.nwb;
+                    for (int q = 0; q < nwo; ++q) acc += raster_and_word(ra, rb, t, q);
+                }
+                if (COUNT && gl == 0) {
+                    wc.raster_and += (unsigned long long)t.H * nwo;
+                    wc.window_pixels += (unsigned long long)t.W * t.H;
+                }
+            }
+            const uint32_t tot = __reduce_add_sync(gmask, acc);
+#pragma unroll
+            for (int g = 0; g < 32 / G; ++g) {
+                const uint32_t tg = __shfl_sync(kFull, tot, g * G);
+                const int jg = __shfl_sync(kFull, my, g * G);
+                if (lane == jg) mine = tg;
             }
         }
         if (k < a.n && (light || !valid)) {

@@ -471,7 +471,10 @@ int raster_launch(sccg_ctx* ctx, const AreasArgs& a, bool persistent, cudaStream
     RasterPairArgs ra{a.n, a.nA, a.nB, a.pa, a.pb,
                       a.mbrA, a.areaA, a.roffA, a.rwA, a.mbrB, a.areaB, a.roffB, a.rwB,
                       a.inter, a.uni, -1, nullptr, nullptr, nullptr, a.counters};
-    auto kfn = ctx->count_work ? k_pair_raster<true> : k_pair_raster<false>;
+    const int G = ctx->params.raster_lanes;
+    auto kfn = ctx->count_work ? (G == 8 ? k_pair_raster<true, 8> : G == 16 ? k_pair_raster<true, 16> : k_pair_raster<true, 32>)
+                               : (G == 8 ? k_pair_raster<false, 8> : G == 16 ? k_pair_raster<false, 16>
+                                                                             : k_pair_raster<false, 32>);
     if (!persistent) {
         const long long grid = grid_for(ctx, (a.n + 31) / 32, 8, 16);
         kfn<<<(unsigned)grid, 256, 0, st>>>(ra);
@@ -656,10 +659,10 @@ int parse_params(const char* js, sccg_params* p)
 {
     if (!js) return SCCG_OK;
     static const char* names[] = {"T", "warps_per_cta", "split_pixels", "ctas_per_sm", "area_method", "leaf_words",
-                                  "pair_lanes", "area_T", "rasters", "raster_heavy"};
+                                  "pair_lanes", "area_T", "rasters", "raster_heavy", "raster_lanes"};
     int32_t* fields[] = {&p->T, &p->warps_per_cta, &p->split_pixels, &p->ctas_per_sm, &p->area_method,
-                         &p->leaf_words, &p->pair_lanes, &p->area_T, &p->rasters, &p->raster_heavy};
-    for (int k = 0; k < 10; ++k) {
+                         &p->leaf_words, &p->pair_lanes, &p->area_T, &p->rasters, &p->raster_heavy, &p->raster_lanes};
+    for (int k = 0; k < 11; ++k) {
         char key[64];
         snprintf(key, sizeof key, "\"%s\"", names[k]);
         const char* at = strstr(js, key);
@@ -687,6 +690,7 @@ int validate_params(const sccg_params& p)
     if (p.area_T < 2 || p.area_T > (1 << 28)) return SCCG_EINVAL;
     if (p.rasters != 0 && p.rasters != 1) return SCCG_EINVAL;
     if (p.raster_heavy < -1) return SCCG_EINVAL;
+    if (p.raster_lanes != 8 && p.raster_lanes != 16 && p.raster_lanes != 32) return SCCG_EINVAL;
     return SCCG_OK;
 }
 
@@ -818,6 +822,7 @@ int sccg_ctx_create(int device, const char* params_json, sccg_ctx** out)
     ctx->params.area_T = 65536;
     ctx->params.rasters = 1;
     ctx->params.raster_heavy = 1024;
+    ctx->params.raster_lanes = 32;
     int r = parse_params(params_json, &ctx->params);
     if (!r) r = validate_params(ctx->params);
     if (r) { delete ctx; return r; }
@@ -889,6 +894,7 @@ int sccg_ctx_set_param(sccg_ctx* ctx, const char* name, int64_t value)
     else if (!strcmp(name, "area_T")) p.area_T = (int32_t)value;
     else if (!strcmp(name, "rasters")) p.rasters = (int32_t)value;
     else if (!strcmp(name, "raster_heavy")) p.raster_heavy = (int32_t)value;
+    else if (!strcmp(name, "raster_lanes")) p.raster_lanes = (int32_t)value;
     else if (!strcmp(name, "count_work")) { ctx->count_work = value != 0; return SCCG_OK; }
     else if (!strcmp(name, "candidate_speculative")) {
         if (value < 0 || value > 2) return SCCG_EINVAL;

@@ -31,6 +31,7 @@ LANES_GRID = (32, 1)       # threads per pair in the leaf path: one warp per ite
 # threads per pair with rasters: pairs of more (row, 32-pixel word) units than this get a CTA (-1: none)
 HEAVY_GRID = (-1, 256, 1024, 4096, 16384)
 CTAS_GRID = (0, 4, 8)      # resident CTAs per SM (0: occupancy maximum)
+RASTER_LANES_GRID = (8, 16, 32)   # threads per light pair with rasters
 # Work-item forms of the persistent queue, (split_pixels, T): items of split_pixels pixels are one
 # leaf each when split_pixels < T (streamed: windows up to 64 x 64 through the leaf kernel, larger
 # ones through the streamed kernel), otherwise they are subdivided into sampling boxes (staged
@@ -60,8 +61,8 @@ def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: in
     """For the persistent form, the best (split_pixels, T) pair of form_grid first; then coordinate
     descent over T, split_pixels (persistent form only) and warps_per_cta for the pair areas of
     (pa, pb). When both sets keep pixel rasters (and the context uses them), the persistent form's
-    pair areas AND rasters instead, and the search is over raster_heavy (one warp or one CTA per
-    pair) and resident CTAs per SM. Leaves ctx set to the best parameters. Returns
+    pair areas AND rasters instead, and the search is over the threads per pair (raster_lanes, and
+    raster_heavy: which pairs get a whole CTA) and resident CTAs per SM. Leaves ctx set to the best parameters. Returns
     {"params": {...}, "ms": best, "table": [(params, ms), ...]}."""
     import torch
     n = pa.numel()
@@ -78,12 +79,12 @@ def tune(ctx, A, B, pa, pb, mode: int = MODE_PERSISTENT, reps: int = 3, warm: in
         return ms
 
     if best.get("rasters") and A.raster is not None and B.raster is not None and mode == MODE_PERSISTENT:
-        # pair areas from rasters: the only choice is how many threads a pair gets (one warp, or a
-        # whole CTA for pairs of more than raster_heavy (row, word) units), and resident CTAs per SM
-        keys = ("raster_heavy", "ctas_per_sm")
+        # pair areas from rasters: the choices are how many threads a pair gets (8, 16 or 32 lanes, or
+        # a whole CTA for pairs of more than raster_heavy (row, word) units), and resident CTAs per SM
+        keys = ("raster_lanes", "raster_heavy", "ctas_per_sm")
         best_ms = run({k: best[k] for k in keys})
         tried = {tuple(best[k] for k in keys)}
-        for name, grid in (("raster_heavy", heavy_grid), ("ctas_per_sm", CTAS_GRID)):
+        for name, grid in (("raster_lanes", RASTER_LANES_GRID), ("raster_heavy", heavy_grid), ("ctas_per_sm", CTAS_GRID)):
             for v in grid:
                 trial = {k: best[k] for k in keys} | {name: v}
                 if tuple(trial[k] for k in keys) in tried:

@@ -136,7 +136,12 @@ def test_tile_pair_offsets_and_one_launch_per_tile(ctx):
     i2, u2 = ctx.pair_areas(A, B, pa, pb)
     np.testing.assert_array_equal(inter.cpu().numpy(), i2.cpu().numpy())
     np.testing.assert_array_equal(uni.cpu().numpy(), u2.cpu().numpy())
-    ref_i, ref_u = O.pair_areas(w.A, w.B, pa_h, pb.cpu().numpy(), method="rle")
+    _, mbr_a = O.polygon_areas(w.A.off, w.A.xy, method="rle")
+    _, mbr_b = O.polygon_areas(w.B.off, w.B.xy, method="rle")
+    opa, opb = O.candidate_pairs(mbr_a, w.A.tile, mbr_b, w.B.tile)
+    np.testing.assert_array_equal(pa_h, opa)
+    np.testing.assert_array_equal(pb.cpu().numpy(), opb)
+    ref_i, ref_u = O.pair_areas(w.A, w.B, opa, opb, method="rle")
     np.testing.assert_array_equal(inter.cpu().numpy(), ref_i)
     np.testing.assert_array_equal(uni.cpu().numpy(), ref_u)
 

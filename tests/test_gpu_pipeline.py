@@ -30,8 +30,13 @@ def test_pipeline_equals_resident_path_and_oracle(chunks, initial, growth):
     np.testing.assert_array_equal(uni, r["uni"].cpu().numpy())
     for k in ("sum_inter", "sum_union", "n_nonzero", "n_pairs", "J", "Jprime"):
         assert J[k] == r["jaccard"][k], k
-    idx = np.arange(0, len(pa), max(1, len(pa) // 2000))
-    ri, ru = O.pair_areas(w.A, w.B, pa[idx], pb[idx], method="rle")
+    _, mbr_a = O.polygon_areas(w.A.off, w.A.xy, method="rle")
+    _, mbr_b = O.polygon_areas(w.B.off, w.B.xy, method="rle")
+    opa, opb = O.candidate_pairs(mbr_a, w.A.tile, mbr_b, w.B.tile)
+    np.testing.assert_array_equal(pa, opa)
+    np.testing.assert_array_equal(pb, opb)
+    idx = np.arange(0, len(opa), max(1, len(opa) // 2000))
+    ri, ru = O.pair_areas(w.A, w.B, opa[idx], opb[idx], method="rle")
     np.testing.assert_array_equal(inter[idx], ri)
     np.testing.assert_array_equal(uni[idx], ru)
     pa2, _, inter2, _, J2 = pipe.run()                  # a second run reuses the buffers

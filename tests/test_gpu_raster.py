@@ -101,6 +101,13 @@ def pair_run(ctx, w, mode, form="areas"):
         inter.cpu().numpy(), uni.cpu().numpy()
 
 
+def oracle_pairs(w):
+    """The oracle's candidate pairs (from its own MBRs)."""
+    _, mbr_a = O.polygon_areas(w.A.off, w.A.xy, method="rle")
+    _, mbr_b = O.polygon_areas(w.B.off, w.B.xy, method="rle")
+    return O.candidate_pairs(mbr_a, w.A.tile, mbr_b, w.B.tile)
+
+
 def edge_rings():
     """Windows of every size class the raster writers treat differently: 1..64 px (one or two words
     per row, written by the leaf), 65 px and more (difference rows), exactly 32 k px (the overflow
@@ -195,16 +202,14 @@ def test_raster_pair_areas_match_oracle(ctx, form, mode):
              W.subset_tiles(W.batched_uneven(seed=2, n_tiles=40), [0, 5, 7, 11])]
     for w in cases:
         A, B, pa, pb, inter, uni = pair_run(ctx, w, mode, form)
-        _, mbr_a = O.polygon_areas(w.A.off, w.A.xy, method="rle")
-        _, mbr_b = O.polygon_areas(w.B.off, w.B.xy, method="rle")
-        ref_pa, ref_pb = O.candidate_pairs(mbr_a, w.A.tile, mbr_b, w.B.tile)
+        ref_pa, ref_pb = oracle_pairs(w)
         np.testing.assert_array_equal(pa, ref_pa)
         np.testing.assert_array_equal(pb, ref_pb)
         ri, ru = O.pair_areas(w.A, w.B, ref_pa, ref_pb, method="rle")
         np.testing.assert_array_equal(inter, ri)
         np.testing.assert_array_equal(uni, ru)
-    idx = np.arange(0, len(pa), max(1, len(pa) // 200))
-    bi, bu = O.pair_areas(w.A, w.B, pa[idx], pb[idx], method="brute")
+    idx = np.arange(0, len(ref_pa), max(1, len(ref_pa) // 200))
+    bi, bu = O.pair_areas(w.A, w.B, ref_pa[idx], ref_pb[idx], method="brute")
     np.testing.assert_array_equal(inter[idx], bi)
     np.testing.assert_array_equal(uni[idx], bu)
 
@@ -223,9 +228,28 @@ def test_raster_heavy_threshold_and_switch_keep_results(sccg, heavy):
     np.testing.assert_array_equal(inter, i0.cpu().numpy())
     np.testing.assert_array_equal(uni, u0.cpu().numpy())
     if heavy == 1024:
-        ri, ru = O.pair_areas(w.A, w.B, pa, pb, method="rle")
+        ref_pa, ref_pb = oracle_pairs(w)
+        np.testing.assert_array_equal(pa, ref_pa)
+        np.testing.assert_array_equal(pb, ref_pb)
+        ri, ru = O.pair_areas(w.A, w.B, ref_pa, ref_pb, method="rle")
         np.testing.assert_array_equal(inter, ri)
         np.testing.assert_array_equal(uni, ru)
+
+
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+def test_raster_lanes_per_pair_keep_results(sccg, lanes):
+    """8, 16 or 32 lanes per light pair (the pair's rows spread over its lane group): the same
+    results as the oracle on nuclei and on uneven tiles with polygons up to 400 px."""
+    c = sccg.Context(0, {"raster_lanes": lanes})
+    for w in (W.single_tile(seed=12, n=700), W.subset_tiles(W.batched_uneven(seed=4, n_tiles=30), [1, 2, 9])):
+        for mode in (0, 1):
+            A, B, pa, pb, inter, uni = pair_run(c, w, mode)
+            ref_pa, ref_pb = oracle_pairs(w)
+            np.testing.assert_array_equal(pa, ref_pa)
+            np.testing.assert_array_equal(pb, ref_pb)
+            ri, ru = O.pair_areas(w.A, w.B, ref_pa, ref_pb, method="rle")
+            np.testing.assert_array_equal(inter, ri)
+            np.testing.assert_array_equal(uni, ru)
 
 
 def test_raster_pairs_with_invalid_indices(ctx):

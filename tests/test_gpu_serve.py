@@ -18,6 +18,12 @@ def resident():
     ctx = P.Context(0)
     A, B = ctx.upload(w.A), ctx.upload(w.B)
     pa, pb, tpo = ctx.candidate_pairs(A, B, with_tile_offsets=True)
+    # the oracle's own candidate pairs (from its MBRs) are the device's: the oracle is fed these
+    _, mbr_a = O.polygon_areas(w.A.off, w.A.xy, method="rle")
+    _, mbr_b = O.polygon_areas(w.B.off, w.B.xy, method="rle")
+    opa, opb = O.candidate_pairs(mbr_a, w.A.tile, mbr_b, w.B.tile)
+    np.testing.assert_array_equal(pa.cpu().numpy(), opa)
+    np.testing.assert_array_equal(pb.cpu().numpy(), opb)
     return P, w, ctx, A, B, pa, pb, tpo
 
 
@@ -43,7 +49,8 @@ def test_results_alone_equal_results_in_the_mix(resident):
             alone = srv.submit(serve.Job(jobs[i].p0, jobs[i].p1, jobs[i].tile)).result(timeout=60)
             assert alone.batch_jobs == 1
             same(alone, mixed[i])
-        pa_h, pb_h = pa.cpu().numpy().astype(np.int64), pb.cpu().numpy().astype(np.int64)
+        pa_h, pb_h = O.candidate_pairs(O.polygon_areas(w.A.off, w.A.xy, method="rle")[1], w.A.tile,
+                                    O.polygon_areas(w.B.off, w.B.xy, method="rle")[1], w.B.tile)
         for i in rng.choice(len(jobs), 10, replace=False):
             j = jobs[i]
             ri, ru = O.pair_areas(w.A, w.B, pa_h[j.p0:j.p1], pb_h[j.p0:j.p1], method="rle")
@@ -82,7 +89,8 @@ def test_cancelled_jobs_are_dropped_and_the_server_keeps_serving(resident):
         cancelled = [f.cancel() for f in futs[::2]]          # those still queued are cancelled
         done = [f.result(timeout=120) for f in futs[1::2]]
         assert any(cancelled)
-        pa_h, pb_h = pa.cpu().numpy().astype(np.int64), pb.cpu().numpy().astype(np.int64)
+        pa_h, pb_h = O.candidate_pairs(O.polygon_areas(w.A.off, w.A.xy, method="rle")[1], w.A.tile,
+                                    O.polygon_areas(w.B.off, w.B.xy, method="rle")[1], w.B.tile)
         j = jobs[1]
         ri, ru = O.pair_areas(w.A, w.B, pa_h[j.p0:j.p1], pb_h[j.p0:j.p1], method="rle")
         np.testing.assert_array_equal(done[0].inter, ri)
@@ -106,7 +114,8 @@ def test_admission_waits_for_device_memory(resident):
         assert srv.arena.free == [(0, 24_000)]                  # every range came back
         with pytest.raises(ValueError):
             srv.submit(serve.Job(0, 20_001))                     # more than a slot holds
-        pa_h, pb_h = pa.cpu().numpy().astype(np.int64), pb.cpu().numpy().astype(np.int64)
+        pa_h, pb_h = O.candidate_pairs(O.polygon_areas(w.A.off, w.A.xy, method="rle")[1], w.A.tile,
+                                    O.polygon_areas(w.B.off, w.B.xy, method="rle")[1], w.B.tile)
         for i in rng.choice(len(jobs), 8, replace=False):
             j = jobs[i]
             ri, ru = O.pair_areas(w.A, w.B, pa_h[j.p0:j.p1], pb_h[j.p0:j.p1], method="rle")

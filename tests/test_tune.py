@@ -36,8 +36,9 @@ def test_tuner_picks_from_its_grid_and_keeps_results_exact(mode, raster):
     p = ctx.params()
     if raster:
         assert res["params"]["raster_heavy"] in tune.HEAVY_GRID + (1024,)
+        assert res["params"]["raster_lanes"] in tune.RASTER_LANES_GRID
         assert res["params"]["ctas_per_sm"] in tune.CTAS_GRID
-        assert len(res["table"]) <= 1 + len(tune.HEAVY_GRID) + len(tune.CTAS_GRID)
+        assert len(res["table"]) <= 1 + len(tune.HEAVY_GRID) + len(tune.CTAS_GRID) + len(tune.RASTER_LANES_GRID)
         assert len({tuple(sorted(t.items())) for t, _ in res["table"]}) == len(res["table"])   # none twice
     else:
         assert res["params"]["T"] in tune.T_GRID + tuple(T for _, T in tune.FORM_GRID) + (8192,)
