@@ -23,11 +23,12 @@
 #define SCCG_ITEM_BOUNDS __launch_bounds__(256)
 #endif
 // The kernels whose leaves stream their edges need little shared memory, so registers set their
-// occupancy: at least 5 resident CTAs of 256 threads for k_prepare (measured best on the whole slide
-// and the uneven tiles) and 4 for k_pair_areas_stream (the heavy tail's large items; 6.6 against
-// 7.4 ms with 6).
+// occupancy: at least 4 resident CTAs of 256 threads for k_prepare (64 registers: with its table of
+// 32 polygons per warp, 10.75 ms for both prepares of the uneven tiles against 11.24 ms with 5 and
+// 12.49 ms with 3) and 4 for k_pair_areas_stream (the heavy tail's large items; 6.6 against 7.4 ms
+// with 6).
 #ifndef SCCG_PREP_MIN_BLOCKS
-#define SCCG_PREP_MIN_BLOCKS 5
+#define SCCG_PREP_MIN_BLOCKS 4
 #endif
 #ifndef SCCG_STREAM_MIN_BLOCKS
 #define SCCG_STREAM_MIN_BLOCKS 4
@@ -265,13 +266,30 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
     long long first_bad = 0x7fffffffffffffffLL;
     unsigned long long band_bytes = 0;
-    long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    // the next polygon's offsets are loaded while this one is pixelized
-    long long o0 = 0, o1 = 0;
-    if (i < a.n) { o0 = a.off[i]; o1 = a.off[i + 1]; }
-    for (; i < a.n; i += nwarps) {
-        long long q0 = 0, q1 = 0;
-        if (i + nwarps < a.n) { q0 = a.off[i + nwarps]; q1 = a.off[i + nwarps + 1]; }
+    // Each warp takes 32 consecutive polygons at a time: lane j loads polygon j's offsets and tile ids
+    // (coalesced), the warp pixelizes the 32 one after another, lane j keeps polygon j's results, and
+    // the 32 MBRs, areas and raster offsets are stored together.
+    for (long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; c0 < a.n; c0 += nwarps * 32) {
+    const long long ij = c0 + lane;
+    long long oj0 = 0, oj1 = 0;
+    int tj = 0;
+    bool tbad = false;
+    if (ij < a.n) {
+        oj0 = a.off[ij];
+        oj1 = a.off[ij + 1];
+        if (a.tile) {
+            tj = a.tile[ij];
+            tbad = tj < 0 || (ij > 0 && a.tile[ij - 1] > tj);
+        }
+    }
+    const int cnt = (int)min(32LL, a.n - c0);
+    int4 my_mbr = make_int4(0, 0, 0, 0);
+    uint32_t my_area = 0;
+    bool my_defer = false;
+    int my_e = 0;
+    for (int j = 0; j < cnt; ++j) {
+        const long long i = c0 + j;
+        const long long o0 = __shfl_sync(kFull, oj0, j), o1 = __shfl_sync(kFull, oj1, j);
         const long long nvl = o1 - o0;
         const int2* v = reinterpret_cast<const int2*>(a.xy) + o0;
         int e = 0;
@@ -328,10 +346,7 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
         const bool by_rows = SCAN && !small_win;
         const bool defer = e == 0 && !closed_form && (by_rows || (!SCAN && a.defer_above > 0 && nvl > a.defer_above));
         if (lane == 0 && defer) a.big_list[atomicAdd(a.big_n, 1u)] = (int)i;
-        if (RASTER && lane == 0) {
-            if (defer) big_words += (unsigned long long)raster_words_of(x1 - x0, y1 - y0);
-            else if (a.rleaf) a.rhead[i] = (long long)kRasterSlot * i;
-        }
+        if (RASTER && lane == 0 && defer) big_words += (unsigned long long)raster_words_of(x1 - x0, y1 - y0);
         if (SCAN && e == 0 && !defer && !closed_form && x1 > x0 && y1 > y0) {
             if (leaf_win) {
                 // with rasters the leaf's parity rows are also the polygon's raster, written to its slot
@@ -349,23 +364,32 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
             const PolyPair pp{v, nv, res, v, nv, res};
             area = pixelbox<false, COUNT>(pp, x0, y0, x1, y1, a.T, a.words, S, lane, wc);
         }
-        int t = 0;
-        if (a.tile) {
-            t = a.tile[i];
-            if (t < 0 || (i > 0 && a.tile[i - 1] > t)) e |= kErrTiles;
-        }
-        if (lane == 0) {
-            a.mbr[i] = make_int4(x0, y0, x1, y1);
-            if (!defer) a.area[i] = (int64_t)area;
-        }
         if (e == 0) band_bytes += (unsigned long long)band_block_size(v, (int)nvl, y0, y1, lane);
-        if (e) { err |= e; first_bad = min(first_bad, i); }
-        max_nv = max(max_nv, (int)min(nvl, (long long)0x7fffffff));
-        if (e == 0) max_ext = max(max_ext, max(x1 - x0, y1 - y0));
-        max_tile = max(max_tile, t);
-        o0 = q0;
-        o1 = q1;
+        if (lane == j) {
+            my_mbr = make_int4(x0, y0, x1, y1);
+            my_area = area;
+            my_defer = defer;
+            my_e = e;
+        }
     }
+    if (ij < a.n) {
+        const int e = my_e | (tbad ? kErrTiles : 0);
+        a.mbr[ij] = my_mbr;
+        if (!my_defer) a.area[ij] = (int64_t)my_area;
+        if (RASTER && a.rleaf && !my_defer) a.rhead[ij] = (long long)kRasterSlot * ij;
+        if (e) { err |= e; first_bad = min(first_bad, ij); }
+        max_nv = max(max_nv, (int)min(oj1 - oj0, (long long)0x7fffffff));
+        if (e == 0) max_ext = max(max_ext, max(my_mbr.z - my_mbr.x, my_mbr.w - my_mbr.y));
+        max_tile = max(max_tile, tj);
+    }
+    }
+    // the lanes' statistics, reduced over the warp
+    err = (int)__reduce_or_sync(kFull, (unsigned)err);
+    max_nv = __reduce_max_sync(kFull, max_nv);
+    max_ext = __reduce_max_sync(kFull, max_ext);
+    max_tile = __reduce_max_sync(kFull, max_tile);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) first_bad = min(first_bad, __shfl_xor_sync(kFull, first_bad, o));
     if (lane == 0) {
         if (err) { atomicOr(&a.stats->err, err); atomicMin(&a.stats->first_bad, first_bad); }
         atomicMax(&a.stats->max_nv, max_nv);

@@ -71,14 +71,32 @@ class JobResult:
         return 1e3 * (self.t_done - self.t_arrival)
 
 
+class _BatchOut:
+    """The results of one batch, shared by its jobs' tickets: completing a batch is one write
+    (ready), whatever its number of jobs; each ticket cuts its own result out when asked."""
+    __slots__ = ("inter", "uni", "jac", "dst", "t_done", "k", "ready")
+
+    def __init__(self):
+        self.ready = False
+
+
 class Ticket:
     """The handle of a submitted job (a light future: one shared condition per server rather than a
     lock per job). result(timeout) blocks until the job's batch has completed; cancel() withdraws a
     job that has not been admitted to a batch yet."""
-    __slots__ = ("job", "_srv", "_res", "_state")     # state: 0 queued, 1 admitted, 2 done, 3 cancelled
+    # state: 0 queued, 1 admitted (to batch _bo as its job _j), 2 done, 3 cancelled
+    __slots__ = ("job", "_srv", "_res", "_state", "_bo", "_j")
 
     def __init__(self, job, srv):
-        self.job, self._srv, self._res, self._state = job, srv, None, 0
+        self.job, self._srv, self._res, self._state, self._bo, self._j = job, srv, None, 0, None, 0
+
+    def _finished(self) -> bool:
+        if self._state == 1 and self._bo is not None and self._bo.ready:
+            bo, j = self._bo, self._j
+            self._res = JobResult(bo.inter[bo.dst[j]:bo.dst[j + 1]], bo.uni[bo.dst[j]:bo.dst[j + 1]], bo.jac[j],
+                                  self.job.t_arrival, bo.t_done, bo.k)
+            self._state = 2
+        return self._state >= 2
 
     def cancel(self) -> bool:
         with self._srv.cv:
@@ -90,16 +108,16 @@ class Ticket:
         return self._state == 3
 
     def done(self) -> bool:
-        return self._state >= 2
+        return self._finished()
 
     def result(self, timeout: float | None = None):
-        if self._state != 2:
+        if not self._finished():
             with self._srv.done_cv:
-                ok = self._srv.done_cv.wait_for(lambda: self._state >= 2, timeout)
-            if self._state == 3:
-                raise cf.CancelledError()
+                ok = self._srv.done_cv.wait_for(self._finished, timeout)
             if not ok:
                 raise TimeoutError("job not completed in time")
+        if self._state == 3:
+            raise cf.CancelledError()
         return self._res
 
 
@@ -247,8 +265,9 @@ class Server:
     # ------------------------------------------------------------------ server side
     def _form(self):
         """Pending jobs in arrival order that fit one batch and the arena's largest free range
-        (called with self.cv held). Cancelled jobs are dropped."""
+        (called with self.cv held), admitted to one batch record. Cancelled jobs are dropped."""
         jobs, npairs = [], 0
+        bo = _BatchOut()
         room = min(self.cap_pairs, self.arena.largest())
         while self.pending and len(jobs) < self.cap_jobs:
             t = self.pending[0]
@@ -261,10 +280,11 @@ class Server:
                     self.waited_for_memory += 1
                 break
             self.pending.popleft()
+            t._bo, t._j = bo, len(jobs)
             t._state = 1
             jobs.append(t)
             npairs += n
-        return jobs, npairs
+        return jobs, npairs, bo
 
     def _batch_loop(self):
         import torch
@@ -274,7 +294,7 @@ class Server:
                     if self.stop:
                         return
                     if self.pending and self.free:
-                        jobs, npairs = self._form()
+                        jobs, npairs, bo = self._form()
                         if jobs:
                             break
                     self.cv.wait(timeout=0.01)
@@ -303,7 +323,7 @@ class Server:
                 slot.h_jres[:48 * k].copy_(slot.jres[:48 * k], non_blocking=True)
                 slot.event.record(slot.stream)
             with slot.cv:
-                slot.batch = (jobs, dst, start, npairs)
+                slot.batch = (jobs, dst, start, npairs, bo)
                 slot.cv.notify()
             with self.cv:
                 self.batches += 1
@@ -317,24 +337,23 @@ class Server:
                     slot.cv.wait(timeout=0.01)
                 if slot.batch is None:
                     return
-                jobs, dst, start, npairs = slot.batch
+                jobs, dst, start, npairs, bo = slot.batch
             slot.event.synchronize()
             now = time.perf_counter()
             k = len(jobs)
             # out of the slot's pinned staging before the slot is reused (torch's copy runs on several
             # cores and without the interpreter lock)
-            inter = slot.h_inter[:npairs].clone().numpy()
-            uni = slot.h_uni[:npairs].clone().numpy()
-            jac = Context.decode_jaccard_array(slot.h_jres[:48 * k].numpy())
+            bo.inter = slot.h_inter[:npairs].clone().numpy()
+            bo.uni = slot.h_uni[:npairs].clone().numpy()
+            bo.jac = Context.decode_jaccard_array(slot.h_jres[:48 * k].numpy())
+            bo.dst, bo.t_done, bo.k = dst, now, k
             with slot.cv:
                 slot.batch = None
             with self.cv:
                 self.arena.give(start, npairs)
                 self.free.append(slot_id)
                 self.cv.notify()
-            for j, t in enumerate(jobs):
-                t._res = JobResult(inter[dst[j]:dst[j + 1]], uni[dst[j]:dst[j + 1]], jac[j], t.job.t_arrival, now, k)
-                t._state = 2
+            bo.ready = True                      # every ticket of the batch is done (no per-job work here)
             with self.done_cv:
                 self.done_cv.notify_all()
 
