@@ -63,10 +63,10 @@ def parse_args():
     p.add_argument("--other-configs", type=str, default="auto",
                    help="comma-separated configs measured after the headline one in the same run and reported under "
                    "other_configs ('auto': 2,4 after config 3 or 5; 'none')")
-    p.add_argument("--serve-jobs", type=int, default=0, help="jobs per offered load (default 3000 for config 5, "
-                   "1000 otherwise)")
+    p.add_argument("--serve-jobs", type=int, default=0, help="jobs per offered load (default 20000 for configs "
+                   "3 and 5, 2000 otherwise)")
     p.add_argument("--serve-loads", type=str, default="", help="comma-separated offered loads (fractions of the "
-                   "measured peak); default 0.5,0.8,0.95 for config 5 and 0.8 otherwise; 'none' to skip")
+                   "measured peak); default 0.5,0.8,0.95 for configs 3 and 5 and 0.8 otherwise; 'none' to skip")
     p.add_argument("--tiles", type=int, default=0, help="restrict to the first N tiles (profiling runs)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -825,7 +825,19 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
             pipe.run()
         torch.cuda.synchronize()
         e_ms, _ = whole_job(1e3 * (time.perf_counter() - t0), n_pairs, dist, dev)
+        # the host link's own rate on this machine, for reading the end-to-end number (a 1 GiB pinned copy)
+        xh = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+        xd = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+        xd.copy_(xh, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            xd.copy_(xh, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * (1 << 30) / (time.perf_counter() - t0) / 1e9
+        del xh, xd
         out["e2e"] = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pipe.h2d_bytes,
+                      "h2d_gbs_pinned_copy": round(h2d_gbs, 1),
                       "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
                       "chunks": len(pipe.chunks), "chunk_growth": args.e2e_growth,
                       "same_results_as_device_run": e2e_same,
@@ -906,7 +918,8 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         loads_arg = args.serve_loads or ("0.5,0.8,0.95" if config in (3, 5) else "0.8")
         if loads_arg != "none":
             loads = [float(x) for x in loads_arg.split(",") if x]
-            n_jobs = args.serve_jobs or (3000 if config in (3, 5) else 1000)
+            # long enough traces that the last job's latency is a small part of the measured span
+            n_jobs = args.serve_jobs or (20000 if config in (3, 5) else 2000)
             serving = serving_results(A, B, pa[:n_pairs], pb[:n_pairs], tpo0, loads, n_jobs, local_rank)
             serving["jobs_per_load"] = n_jobs
             serving["job_pairs"] = "log-uniform 100-50,000, clipped to the tile's candidate pairs"

@@ -86,8 +86,9 @@ typedef struct sccg_params {
                                 than raster_heavy (row, 32-pixel word) units is done by a whole CTA
                                 instead of one warp (default 1024; -1: every pair by one warp). */
     int32_t raster_lanes;    /* pair areas from rasters: threads per (light) pair, 8, 16 or 32
-                                (default); a warp works on 32 / raster_lanes pairs at a time. Same
-                                results. */
+                                (default; a warp works on 32 / raster_lanes pairs at a time), or 1:
+                                a pair whose window is at most 64 x 64 pixels by one lane, the others
+                                by the warp. Same results. */
 } sccg_params;
 
 /* sccg_prepare's method for ||p||. ROWS: per pixel row, the crossing positions of the edges that

@@ -267,7 +267,8 @@ __device__ __forceinline__ uint32_t raster_and_word(const uint32_t* ra, const ui
 // Light pairs: each warp takes 32 consecutive pairs (a chunk); lane j reads pair j's MBRs, raster
 // offsets and areas into a shared table, then the warp goes through the chunk's pairs G lanes per
 // pair (32 / G pairs at a time, so that their row loads are in flight together), lanes over the
-// overlap's rows, and writes the 32 results together. Heavy pairs (more than
+// overlap's rows, and writes the 32 results together. G = 1: each lane does its own pair when the
+// window is at most 64 x 64 pixels, row after row, and the warp the others. Heavy pairs (more than
 // heavy_words (row, word) units) are listed for k_pair_raster_heavy. A pair whose indices are out of
 // range gets -1.
 template <bool COUNT, int G>
@@ -286,30 +287,48 @@ __global__ void __launch_bounds__(256) k_pair_raster(const RasterPairArgs a)
         }
         if (base >= a.n) break;
         const long long k = base + lane;
-        bool valid = false, light = false;
+        bool valid = false, light = false, own = false;
         long long sum_area = 0;
+        RPair t = {};
         if (k < a.n) {
             const int ia = a.pa[k], ib = a.pb[k];
             if (ia >= 0 && ia < a.nA && ib >= 0 && ib < a.nB) {
                 valid = true;
-                const RPair t = raster_window(a.mbrA[ia], a.mbrB[ib], a.roffA[ia], a.roffB[ib]);
+                t = raster_window(a.mbrA[ia], a.mbrB[ib], a.roffA[ia], a.roffB[ib]);
                 const long long units = (long long)t.H * ((t.W + 31) >> 5);
                 light = a.heavy_words < 0 || units <= a.heavy_words;
+                own = G == 1 && light && t.W <= kLeafSide && t.H <= kLeafSide;
                 sum_area = a.areaA[ia] + a.areaB[ib];
                 tab[warp][lane] = t;
                 if (!light) a.heavy[atomicAdd(a.heavy_n, 1ull)] = (unsigned long long)k;
             }
         }
         __syncwarp();
-        unsigned todo = __ballot_sync(kFull, light && tab[warp][lane].H > 0);
         uint32_t mine = 0;
-        // G lanes per pair: the warp takes 32 / G of the chunk's pairs at a time, one per lane group
-        const int grp = lane / G, gl = lane % G;
-        const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (grp * G));
+        if (G == 1 && own && t.H > 0) {
+            // one lane per pair whose window is at most 64 x 64 pixels: its rows one after another
+            const int nwo = (t.W + 31) >> 5;
+            const uint32_t* ra = a.rwA + t.pA;
+            const uint32_t* rb = a.rwB + t.pB;
+#pragma unroll 4
+            for (int r = 0; r < t.H; ++r)
+                for (int q = 0; q < nwo; ++q)
+                    mine += raster_and_word(ra + (long long)r * t.nwa, rb + (long long)r * t.nwb, t, q);
+            if (COUNT) {
+                wc.raster_and += (unsigned long long)t.H * nwo;
+                wc.window_pixels += (unsigned long long)t.W * t.H;
+            }
+        }
+        unsigned todo = __ballot_sync(kFull, light && !own && tab[warp][lane].H > 0);
+        // GW lanes per pair: the warp takes 32 / GW of the chunk's pairs at a time, one per lane group
+        // (with G = 1, the pairs no lane took alone go to the whole warp)
+        constexpr int GW = G == 1 ? 32 : G;
+        const int grp = lane / GW, gl = lane % GW;
+        const unsigned gmask = GW == 32 ? kFull : (((1u << GW) - 1u) << (grp * GW));
         while (todo) {
             int my = -1;
 #pragma unroll
-            for (int g = 0; g < 32 / G; ++g) {
+            for (int g = 0; g < 32 / GW; ++g) {
                 if (todo) {
                     const int j = __ffs(todo) - 1;
                     todo &= todo - 1;
@@ -318,23 +337,23 @@ __global__ void __launch_bounds__(256) k_pair_raster(const RasterPairArgs a)
             }
             uint32_t acc = 0;
             if (my >= 0) {
-                const RPair t = tab[warp][my];
-                const int nwo = (t.W + 31) >> 5;
-                for (int r = gl; r < t.H; r += G) {
-                    const uint32_t* ra = a.rwA + t.pA + (long long)r * t.nwa;
-                    const uint32_t* rb = a.rwB + t.pB + (long long)r * t.nwb;
-                    for (int q = 0; q < nwo; ++q) acc += raster_and_word(ra, rb, t, q);
+                const RPair u = tab[warp][my];
+                const int nwo = (u.W + 31) >> 5;
+                for (int r = gl; r < u.H; r += GW) {
+                    const uint32_t* ra = a.rwA + u.pA + (long long)r * u.nwa;
+                    const uint32_t* rb = a.rwB + u.pB + (long long)r * u.nwb;
+                    for (int q = 0; q < nwo; ++q) acc += raster_and_word(ra, rb, u, q);
                 }
                 if (COUNT && gl == 0) {
-                    wc.raster_and += (unsigned long long)t.H * nwo;
-                    wc.window_pixels += (unsigned long long)t.W * t.H;
+                    wc.raster_and += (unsigned long long)u.H * nwo;
+                    wc.window_pixels += (unsigned long long)u.W * u.H;
                 }
             }
             const uint32_t tot = __reduce_add_sync(gmask, acc);
 #pragma unroll
-            for (int g = 0; g < 32 / G; ++g) {
-                const uint32_t tg = __shfl_sync(kFull, tot, g * G);
-                const int jg = __shfl_sync(kFull, my, g * G);
+            for (int g = 0; g < 32 / GW; ++g) {
+                const uint32_t tg = __shfl_sync(kFull, tot, g * GW);
+                const int jg = __shfl_sync(kFull, my, g * GW);
                 if (lane == jg) mine = tg;
             }
         }

@@ -256,9 +256,13 @@ int launch_raster_big(sccg_ctx* ctx, const sccg_polyset* s, const char* blob, co
     const int wpc = 4;
     const size_t smem = sizeof(DrawSmem<PIECE>) * wpc;
     auto kfn = ctx->count_work ? k_raster_big<true, PIECE, BANDED> : k_raster_big<false, PIECE, BANDED>;
-    const int r = set_smem(ctx, kfn, smem);
+    int r = set_smem(ctx, kfn, smem);
+    unsigned resident = 0;
+    if (!r) r = persistent_grid(ctx, kfn, wpc, smem, &resident);
     if (r) return r;
-    const unsigned grid = (n_host + wpc - 1) / wpc;
+    // at most the resident CTAs: each warp then draws polygon after polygon (a CTA holding one polygon
+    // per warp would keep its slot until its largest polygon is done)
+    const unsigned grid = std::max(1u, std::min((n_host + wpc - 1) / wpc, resident));
     kfn<<<grid, 32 * wpc, smem, st>>>(s->off, s->xy, mbr, blob, list, n_list, s->area, rhead, rw, ctx->counters);
     SCCG_LAUNCHED(ctx, "k_raster_big");
     ctx->launches += 1;
@@ -472,9 +476,10 @@ int raster_launch(sccg_ctx* ctx, const AreasArgs& a, bool persistent, cudaStream
                       a.mbrA, a.areaA, a.roffA, a.rwA, a.mbrB, a.areaB, a.roffB, a.rwB,
                       a.inter, a.uni, -1, nullptr, nullptr, nullptr, a.counters};
     const int G = ctx->params.raster_lanes;
-    auto kfn = ctx->count_work ? (G == 8 ? k_pair_raster<true, 8> : G == 16 ? k_pair_raster<true, 16> : k_pair_raster<true, 32>)
-                               : (G == 8 ? k_pair_raster<false, 8> : G == 16 ? k_pair_raster<false, 16>
-                                                                             : k_pair_raster<false, 32>);
+    auto kfn = ctx->count_work ? (G == 1 ? k_pair_raster<true, 1> : G == 8 ? k_pair_raster<true, 8>
+                                  : G == 16 ? k_pair_raster<true, 16> : k_pair_raster<true, 32>)
+                               : (G == 1 ? k_pair_raster<false, 1> : G == 8 ? k_pair_raster<false, 8>
+                                  : G == 16 ? k_pair_raster<false, 16> : k_pair_raster<false, 32>);
     if (!persistent) {
         const long long grid = grid_for(ctx, (a.n + 31) / 32, 8, 16);
         kfn<<<(unsigned)grid, 256, 0, st>>>(ra);
@@ -690,7 +695,8 @@ int validate_params(const sccg_params& p)
     if (p.area_T < 2 || p.area_T > (1 << 28)) return SCCG_EINVAL;
     if (p.rasters != 0 && p.rasters != 1) return SCCG_EINVAL;
     if (p.raster_heavy < -1) return SCCG_EINVAL;
-    if (p.raster_lanes != 8 && p.raster_lanes != 16 && p.raster_lanes != 32) return SCCG_EINVAL;
+    if (p.raster_lanes != 1 && p.raster_lanes != 8 && p.raster_lanes != 16 && p.raster_lanes != 32)
+        return SCCG_EINVAL;
     return SCCG_OK;
 }
 

@@ -31,7 +31,7 @@ LANES_GRID = (32, 1)       # threads per pair in the leaf path: one warp per ite
 # threads per pair with rasters: pairs of more (row, 32-pixel word) units than this get a CTA (-1: none)
 HEAVY_GRID = (-1, 256, 1024, 4096, 16384)
 CTAS_GRID = (0, 4, 8)      # resident CTAs per SM (0: occupancy maximum)
-RASTER_LANES_GRID = (8, 16, 32)   # threads per light pair with rasters
+RASTER_LANES_GRID = (1, 8, 16, 32)   # threads per light pair with rasters
 # Work-item forms of the persistent queue, (split_pixels, T): items of split_pixels pixels are one
 # leaf each when split_pixels < T (streamed: windows up to 64 x 64 through the leaf kernel, larger
 # ones through the streamed kernel), otherwise they are subdivided into sampling boxes (staged

@@ -236,9 +236,9 @@ def test_raster_heavy_threshold_and_switch_keep_results(sccg, heavy):
         np.testing.assert_array_equal(uni, ru)
 
 
-@pytest.mark.parametrize("lanes", [8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 8, 16, 32])
 def test_raster_lanes_per_pair_keep_results(sccg, lanes):
-    """8, 16 or 32 lanes per light pair (the pair's rows spread over its lane group): the same
+    """1, 8, 16 or 32 lanes per light pair (the pair's rows spread over its lane group): the same
     results as the oracle on nuclei and on uneven tiles with polygons up to 400 px."""
     c = sccg.Context(0, {"raster_lanes": lanes})
     for w in (W.single_tile(seed=12, n=700), W.subset_tiles(W.batched_uneven(seed=4, n_tiles=30), [1, 2, 9])):
