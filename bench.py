@@ -820,9 +820,12 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         if dist:
             dist.barrier()
         n_e2e = max(3, args.steps // 2)
+        run_ms = []
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            pipe.run()
+            t1 = time.perf_counter()
+            pipe.run()                       # returns after its results are in host memory
+            run_ms.append(round(1e3 * (time.perf_counter() - t1), 2))
         torch.cuda.synchronize()
         e_ms, _ = whole_job(1e3 * (time.perf_counter() - t0), n_pairs, dist, dev)
         # the host link's own rate on this machine, for reading the end-to-end number (a 1 GiB pinned copy)
@@ -837,7 +840,7 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         h2d_gbs = 3 * (1 << 30) / (time.perf_counter() - t0) / 1e9
         del xh, xd
         out["e2e"] = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pipe.h2d_bytes,
-                      "h2d_gbs_pinned_copy": round(h2d_gbs, 1),
+                      "h2d_gbs_pinned_copy": round(h2d_gbs, 1), "run_ms": run_ms,
                       "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
                       "chunks": len(pipe.chunks), "chunk_growth": args.e2e_growth,
                       "same_results_as_device_run": e2e_same,

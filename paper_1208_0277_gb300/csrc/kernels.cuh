@@ -2038,9 +2038,51 @@ struct JPart {
 constexpr int kJScale = 84;
 constexpr long long kJaccardMaxPairs = 1LL << 43;
 
-// r = inter/union as an IEEE double, returned as r * 2^kJScale (exact, see above).
+// floor(N / d) and N - d floor(N / d) for d in [2^31, 2^32) and N < 2^64 with N / d < 2^33, in
+// exact integer arithmetic: an fp32 estimate of the quotient (relative error below 2^-22), the exact
+// remainder of that estimate (differences wrap modulo 2^64 but stay below 2^43 in magnitude, so
+// their signed reading is right), one fp32 correction from the remainder (error below 2), and the
+// last steps by comparison.
+__device__ __forceinline__ unsigned long long divmod_norm(unsigned long long N, unsigned d, unsigned long long& rem)
+{
+    const float rd = __frcp_rn((float)d);
+    unsigned long long q = (unsigned long long)(__ull2float_rn(N) * rd);
+    long long r = (long long)(N - q * (unsigned long long)d);
+    const long long c = (long long)(__ll2float_rn(r) * rd);
+    q += (unsigned long long)c;
+    r -= c * (long long)d;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (r < 0) { --q; r += d; }
+        if (r >= (long long)d) { ++q; r -= d; }
+    }
+    rem = (unsigned long long)r;
+    return q;
+}
+
+// r = inter/union as an IEEE double (rounded to nearest, ties to even), returned as r * 2^kJScale
+// (exact, see above). For 0 < inter <= union < 2^31 the quotient is formed in integers: with both
+// shifted to 32 bits (in, un in [2^31, 2^32)), r = (in / un) 2^(a - b) for their top-bit positions a,
+// b; its exponent e is a - b, or a - b - 1 when in < un; its 53-bit significand is
+// M = floor(in 2^t / un) with t = 52 + (a - b - e), by two divisions of a 64-bit by a 32-bit number
+// (the first quotient's remainder shifted up 32 bits for the second), and the remainder R rounds it
+// (up when 2R > un, or 2R = un and M is odd). Then r 2^kJScale = M 2^(e + 32). Other inputs take the
+// double division.
 __device__ __forceinline__ unsigned __int128 ratio_fixed(long long inter, long long uni)
 {
+    if (inter > 0 && inter <= uni && uni < (1LL << 31)) {
+        const unsigned i = (unsigned)inter, u = (unsigned)uni;
+        const int a = 31 - __clz(i), b = 31 - __clz(u);
+        const unsigned in = i << (31 - a), un = u << (31 - b);
+        const int e = a - b - (in < un ? 1 : 0);
+        const int t = 52 + (a - b - e);                          // 52 or 53
+        unsigned long long r1, r2;
+        const unsigned long long q1 = divmod_norm((unsigned long long)in << (t - 32), un, r1);
+        const unsigned long long q2 = divmod_norm(r1 << 32, un, r2);
+        unsigned long long M = (q1 << 32) + q2;                  // in [2^52, 2^53)
+        if (2 * r2 > un || (2 * r2 == un && (M & 1))) ++M;       // may reach 2^53: still exact
+        return (unsigned __int128)M << (e + 32);
+    }
     const double r = __ddiv_rn((double)inter, (double)uni);
     const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
     const int ex = (int)((bits >> 52) & 0x7ff);

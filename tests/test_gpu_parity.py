@@ -587,3 +587,32 @@ def test_full_density_uneven_tile(sccg):
     assert w.A.n == 20_000
     c = sccg.Context(0)
     assert_same(gpu_run(c, w, mode=1), O.cross_compare(w.A, w.B, method="rle"))
+
+
+def test_jaccard_ratios_are_the_ieee_quotients(ctx):
+    """Each ratio inter/union summed into J' is the IEEE double quotient (the library forms it in
+    integers): with one pair per segment, a segment's J' is that ratio alone. Quotients of every
+    magnitude from 2^-31 to 1, equal operands, powers of two and their neighbours, against numpy's
+    division; the whole set's J and J' against the oracle."""
+    rng = np.random.default_rng(17)
+    u = np.concatenate([
+        rng.integers(1, 200, 20000), rng.integers(1, 1 << 16, 20000), rng.integers(1 << 20, 1 << 31, 40000),
+        np.array([(1 << k) + d for k in range(1, 31) for d in (-1, 0, 1)]), np.full(1000, (1 << 31) - 1)])
+    frac = rng.random(u.size)
+    i = np.maximum(1, (frac * u).astype(np.int64))
+    i[:500] = u[:500]                               # ratio 1
+    i[500:1000] = 1                                 # the smallest ratios
+    i = np.minimum(i, u).astype(np.int64)
+    u = u.astype(np.int64)
+    inter, uni = torch.from_numpy(i).cuda(), torch.from_numpy(u).cuda()
+    seg = torch.arange(i.size + 1, dtype=torch.int64, device="cuda")
+    out = torch.zeros(48 * i.size, dtype=torch.uint8, device="cuda")
+    ctx.jaccard_segments(inter, uni, seg, out)
+    got = np.array([r["Jprime"] for r in ctx.decode_jaccard_array(out.cpu().numpy())])
+    want = i.astype(np.float64) / u.astype(np.float64)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, (i[bad[:5]], u[bad[:5]], got[bad[:5]], want[bad[:5]])
+    ref = O.jaccard(i, u)
+    res = ctx.jaccard(inter, uni)
+    for k in ("sum_inter", "sum_union", "n_nonzero", "J", "Jprime"):
+        assert res[k] == ref[k], k
