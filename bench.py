@@ -444,8 +444,10 @@ def serving_results(A, B, pa, pb, tpo, loads, n_jobs, device, seed=5):
         [f.result() for f in srv.submit_many(warm)]
         burst = serve.draw_jobs(rng, tpo, n_jobs)
         t0 = time.perf_counter()
-        res = [f.result() for f in srv.submit_many(burst)]
-        peak = serve.latency_summary(res, time.perf_counter() - t0)
+        futs = srv.submit_many(burst)
+        srv.drain()
+        res = [f.result() for f in futs]
+        peak = serve.latency_summary(res, max(r.t_done for r in res) - t0)
         mean_pairs = peak["pairs"] / peak["jobs"]
         out = {"peak": dict(peak, note="all jobs submitted at once"), "loads": [],
                "server": {"slots": len(srv.slots), "max_batch_pairs": srv.cap_pairs, "arena_pairs": srv.arena_pairs,

@@ -249,6 +249,15 @@ class Server:
             self.cv.notify()
         return tickets
 
+    def drain(self, timeout: float | None = None) -> bool:
+        """Wait until no job is queued and no batch is in flight (the results of every submitted job
+        are then ready; reading them costs the caller, not the server). False on timeout."""
+        def idle():
+            with self.cv:
+                return not self.pending and len(self.free) == len(self.slots)
+        with self.done_cv:
+            return self.done_cv.wait_for(idle, timeout)
+
     def close(self):
         with self.cv:
             self.stop = True
@@ -373,9 +382,10 @@ def draw_jobs(rng, tile_pair_off, n_jobs: int, lo: int = 100, hi: int = 50_000):
 
 def run_load(server: Server, jobs, rate_jobs_s: float, rng):
     """Replay a Poisson arrival trace at rate_jobs_s: every job is stamped with its scheduled arrival
-    time and submitted as soon as that time has passed (all jobs that are due go in one call, so a
-    slow client delays submission, which then counts in the latency, instead of thinning the load).
-    Returns (results, wall seconds from the first scheduled arrival to the last result)."""
+    time and submitted once that time has passed (all jobs that are due go in one call, so a slow
+    client delays submission, which then counts in the latency, instead of thinning the load; between
+    calls the client sleeps up to 1 ms instead of spinning). Returns (results, wall seconds from the
+    first scheduled arrival to the last completion)."""
     arrivals = np.cumsum(rng.exponential(1.0 / rate_jobs_s, len(jobs)))
     futs = []
     k = 0
@@ -388,10 +398,12 @@ def run_load(server: Server, jobs, rate_jobs_s: float, rng):
                 jobs[i].t_arrival = t0 + float(arrivals[i])
             futs += server.submit_many(jobs[k:j])
             k = j
-        else:
-            wait = float(arrivals[k]) - now
-            if wait > 0.0004:
-                time.sleep(wait - 0.0002)
+        if k < len(jobs):
+            # sleep (releasing the interpreter to the server's threads) rather than spin: jobs that
+            # fall due meanwhile go in with the next call, stamped with their scheduled arrival
+            wait = float(arrivals[k]) - (time.perf_counter() - t0)
+            time.sleep(min(max(wait, 0.0002), 0.001))
+    server.drain()                       # every job served before any result is cut out of its batch
     res = [f.result() for f in futs]
     return res, max(r.t_done for r in res) - (t0 + float(arrivals[0]))
 
