@@ -46,19 +46,36 @@ __host__ __device__ inline long long raster_head_bytes(long long n)
 // Toggle the difference bits of the crossings of one group of edges (lane k holds edge
 // {ylo, dy, dx, xl}, lower endpoint first, when `has`) with window rows ya .. ya + nr - 1 (absolute
 // y), piece columns cs .. cs + 32 nwp - 1 of a window whose left column is x0. Row q of the pass is
-// D[q * (nwp + 1) ...]. The (edge, row) crossings are spread evenly over the lanes (warp prefix sum of
-// the edges' row counts, owner found by binary search, edge fetched by shuffles). Whole warp,
-// converged; the trip count is warp-uniform.
+// D[q * (nwp + 1) ...]. When no edge of the group spans more than kLeafLoopSpan of the rows, each
+// lane walks its own edge's rows; otherwise the (edge, row) crossings are spread evenly over the
+// lanes (warp prefix sum of the edges' row counts, owner found by binary search, edge fetched by
+// shuffles). Whole warp, converged; the trip counts are warp-uniform.
 __device__ __forceinline__ void draw_group(bool has, int ylo, int dy, int dx, int xl, int x0, int ya, int nr, int cs,
                                            int nwp, uint32_t* D, int lane, unsigned long long& entries)
 {
     int cnt = 0;
     if (has && max(xl, xl + dx) > x0 + cs) cnt = max(0, min(ylo + dy, ya + nr) - max(ylo, ya));
-    int total;
-    const int excl = warp_excl(cnt, lane, total);
-    if (total == 0) return;
+    const int maxc = __reduce_max_sync(kFull, cnt);
+    if (maxc == 0) return;
     const float r2 = cnt > 0 ? __frcp_rn((float)(2 * dy)) : 0.0f;     // dy > 0 whenever cnt > 0
     const int stride = nwp + 1, pmax = 32 * nwp;
+    if (maxc <= kLeafLoopSpan) {
+        // short spans: each lane walks its own edge's rows
+        const int y0e = max(ylo, ya);
+#pragma unroll
+        for (int s = 0; s < kLeafLoopSpan; ++s) {
+            if (s >= maxc) break;
+            if (s < cnt) {
+                const int y = y0e + s;
+                const int p = min(crossing_count_r(ylo, dy, dx, xl, y, x0, r2) - cs, pmax);
+                if (p > 0) atomicXor(&D[(y - ya) * stride + (p >> 5)], 1u << (p & 31));
+            }
+        }
+        entries += (unsigned long long)cnt;
+        return;
+    }
+    int total;
+    const int excl = warp_excl(cnt, lane, total);
     for (int t0 = 0; t0 < total; t0 += 32) {
         const int t = t0 + lane;
         const int own = flat_owner(excl, t);
