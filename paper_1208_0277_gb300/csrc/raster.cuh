@@ -135,46 +135,49 @@ __device__ __forceinline__ uint32_t draw_finish(const uint32_t* D, int nr, int n
     return acc;
 }
 
-// Rasters and ||p|| of the polygons k_prepare listed (windows over 64 pixels wide or high), one warp
-// per polygon: pieces of up to 32 PIECE columns, passes of as many rows as the per-warp difference
-// words hold. BANDED: only the polygons with a block in the band index blob, each 32-row band's
-// edges taken from the band's list; otherwise only the others, which stream their whole ring once
-// per pass.
+// Rasters and ||p|| of the polygons k_prepare listed (windows over 64 pixels wide or high): pieces of
+// up to 32 PIECE columns, passes of as many rows as the per-warp difference words hold. Otherwise
+// (BANDED false) only the polygons without a block in the band index blob, one warp each, streaming
+// the whole ring once per pass; BANDED: only the polygons with a block (large tissue regions), one
+// CTA each, its warps taking the 32-row bands in turn, each band's edges from the band's list, and
+// the warps' counts summed in shared memory.
 template <bool COUNT, int PIECE, bool BANDED>
-__global__ void __launch_bounds__(128) k_raster_big(const int64_t* off, const int32_t* xy, const int4* mbr,
+__global__ void __launch_bounds__(256) k_raster_big(const int64_t* off, const int32_t* xy, const int4* mbr,
                                                     const char* blob, const int* list, const unsigned* n_list,
                                                     int64_t* area, const long long* roff, uint32_t* rwords,
                                                     WorkCounters* counters)
 {
     constexpr int kWords = 32 * (PIECE + 1);
     SCCG_DYNAMIC_SMEM(int4, smem4);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ unsigned part[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     DrawSmem<PIECE>& S = reinterpret_cast<DrawSmem<PIECE>*>(smem4)[warp];
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     WorkCounters wc = {};
     const long long nl = *n_list;
-    for (long long j = (long long)blockIdx.x * (blockDim.x >> 5) + warp; j < nl; j += nwarps) {
+    const long long first = BANDED ? blockIdx.x : (long long)blockIdx.x * wpb + warp;
+    const long long step = BANDED ? gridDim.x : (long long)gridDim.x * wpb;
+    for (long long j = first; j < nl; j += step) {
         const long long i = list[j];
+        const char* blk = band_block(blob, i);
+        if ((blk != nullptr) != BANDED) continue;                // uniform per warp (per CTA when BANDED)
         const long long o0 = off[i];
         const int nv = (int)(off[i + 1] - o0);
         const int2* v = reinterpret_cast<const int2*>(xy) + o0;
         const int4 m = mbr[i];
         const int W = m.z - m.x, H = m.w - m.y, nw = (W + 31) >> 5;
         uint32_t* out = rwords + roff[i];
-        const char* blk = band_block(blob, i);
-        if ((blk != nullptr) != BANDED) continue;
         uint32_t acc = 0;
         unsigned long long ce = 0;
         for (int cs = 0; cs < W; cs += 32 * PIECE) {
             const int nwp = min(PIECE, nw - (cs >> 5));
             // band lists cover 32 rows each (from the polygon's min y): one band per pass
             const int nrmax = BANDED ? (1 << kBandShift) : kWords / (nwp + 1);
-            for (int r0 = 0; r0 < H; r0 += nrmax) {
+            for (int r0 = BANDED ? warp * nrmax : 0; r0 < H; r0 += BANDED ? wpb * nrmax : nrmax) {
                 const int nr = min(nrmax, H - r0);
                 __syncwarp();
                 for (int k = lane; k < nr * (nwp + 1); k += 32) S.D[k] = 0u;
                 __syncwarp();
-                if (blk) {
+                if (BANDED) {
                     const int nb = reinterpret_cast<const int*>(blk)[0];
                     const int* boff = reinterpret_cast<const int*>(blk) + 4;
                     const int4* ent = reinterpret_cast<const int4*>(blk + 16 + ((4LL * (2 * nb + 1) + 15) & ~15LL));
@@ -190,10 +193,21 @@ __global__ void __launch_bounds__(128) k_raster_big(const int64_t* off, const in
             }
         }
         acc = warp_sum(acc);
-        if (lane == 0) area[i] = (int64_t)acc;
+        if (BANDED) {
+            if (lane == 0) part[warp] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long t = 0;
+                for (int w = 0; w < wpb; ++w) t += part[w];
+                area[i] = (int64_t)t;
+            }
+            __syncthreads();
+        } else if (lane == 0) {
+            area[i] = (int64_t)acc;
+        }
         if (COUNT) {
             wc.scan_entries += ce;
-            if (lane == 0) {
+            if (lane == 0 && (!BANDED || warp == 0)) {
                 wc.raster_out += (unsigned long long)raster_words_of(W, H);
                 wc.window_pixels += (unsigned long long)W * H;
             }

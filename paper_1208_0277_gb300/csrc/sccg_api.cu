@@ -253,7 +253,7 @@ template <int PIECE, bool BANDED>
 int launch_raster_big(sccg_ctx* ctx, const sccg_polyset* s, const char* blob, const int* list, const unsigned* n_list,
                       unsigned n_host, const long long* rhead, uint32_t* rw, const int4* mbr, cudaStream_t st)
 {
-    const int wpc = 4;
+    const int wpc = BANDED ? 8 : 4;          // BANDED: one CTA per polygon, its warps taking bands in turn
     const size_t smem = sizeof(DrawSmem<PIECE>) * wpc;
     auto kfn = ctx->count_work ? k_raster_big<true, PIECE, BANDED> : k_raster_big<false, PIECE, BANDED>;
     int r = set_smem(ctx, kfn, smem);
@@ -262,7 +262,7 @@ int launch_raster_big(sccg_ctx* ctx, const sccg_polyset* s, const char* blob, co
     if (r) return r;
     // at most the resident CTAs: each warp then draws polygon after polygon (a CTA holding one polygon
     // per warp would keep its slot until its largest polygon is done)
-    const unsigned grid = std::max(1u, std::min((n_host + wpc - 1) / wpc, resident));
+    const unsigned grid = std::max(1u, std::min(BANDED ? n_host : (n_host + wpc - 1) / wpc, resident));
     kfn<<<grid, 32 * wpc, smem, st>>>(s->off, s->xy, mbr, blob, list, n_list, s->area, rhead, rw, ctx->counters);
     SCCG_LAUNCHED(ctx, "k_raster_big");
     ctx->launches += 1;
