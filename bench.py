@@ -20,6 +20,8 @@ slide (seed 1 + rank), no collective on the data path (weak scaling).
 from __future__ import annotations
 
 import argparse
+import contextlib
+import gc
 import math
 import hashlib
 import json
@@ -52,7 +54,7 @@ OPS_PER_SCAN_PAIR = 4      # one comparison while ranking a row's crossing value
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=40)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--form", choices=["tiles", "persistent", "graph"], default=None,
@@ -84,6 +86,10 @@ def parse_args():
                    help="prepare the sets without pixel rasters (pair areas pixelize every pair window)")
     p.add_argument("--profile-once", action="store_true",
                    help="run a single step of --form and exit (for ncu captures; prints no bench line)")
+    p.add_argument("--traffic-csv", type=str, default="",
+                   help="ncu --csv log of dram__bytes_read.sum/dram__bytes_write.sum of a --profile-once run on the "
+                        "first --tiles tiles: write the per-step DRAM traffic of the whole workload to "
+                        "profiles/traffic.json (scaled by vertices or pairs) and exit")
     return p.parse_args()
 
 
@@ -129,6 +135,21 @@ def kernel_source_hash() -> str:
         with open(os.path.join(ROOT, "paper_1208_0277_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+@contextlib.contextmanager
+def quiet_collector():
+    """No garbage-collector pass inside a timed region: the objects alive before it are collected
+    once and frozen (the interpreter's import-time objects alone make a full pass take a large
+    fraction of a step), and collection stays off until the region ends."""
+    gc.collect()
+    gc.freeze()
+    gc.disable()
+    try:
+        yield
+    finally:
+        gc.enable()
+        gc.unfreeze()
 
 
 # ------------------------------------------------------------------------------------------------
@@ -710,12 +731,13 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         if sampler:
             sampler.mark("t_start")
         start, end = ev(), ev()
-        start.record(stream)
-        J = None
-        for _ in range(args.steps):
-            J = step(form, phases)
-        end.record(stream)
-        torch.cuda.synchronize()
+        with quiet_collector():
+            start.record(stream)
+            J = None
+            for _ in range(args.steps):
+                J = step(form, phases)
+            end.record(stream)
+            torch.cuda.synchronize()
         if sampler:
             sampler.mark("t_end")
         clocks = sampler.stop() if sampler else None
@@ -834,15 +856,17 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        n_e2e = max(3, args.steps // 2)
+        n_e2e = max(3, args.steps // 4)
         run_ms = []
-        t0 = time.perf_counter()
-        for _ in range(n_e2e):
-            t1 = time.perf_counter()
-            pipe.run()                       # returns after its results are in host memory
-            run_ms.append(round(1e3 * (time.perf_counter() - t1), 2))
-        torch.cuda.synchronize()
-        e_ms, _ = whole_job(1e3 * (time.perf_counter() - t0), n_pairs, dist, dev)
+        with quiet_collector():
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                t1 = time.perf_counter()
+                pipe.run()                       # returns after its results are in host memory
+                run_ms.append(round(1e3 * (time.perf_counter() - t1), 2))
+            torch.cuda.synchronize()
+            t_e2e = time.perf_counter() - t0
+        e_ms, _ = whole_job(1e3 * t_e2e, n_pairs, dist, dev)
         # the host link's own rate on this machine, for reading the end-to-end number (a 1 GiB pinned copy)
         xh = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
         xd = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
@@ -856,6 +880,7 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
         del xh, xd
         out["e2e"] = {"value": total_pairs * n_e2e / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": pipe.h2d_bytes,
                       "h2d_gbs_pinned_copy": round(h2d_gbs, 1), "run_ms": run_ms,
+                      "median_run_ms": statistics.median(run_ms),
                       "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
                       "chunks": len(pipe.chunks), "chunk_growth": args.e2e_growth,
                       "same_results_as_device_run": e2e_same,
@@ -952,6 +977,75 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
     return out
 
 
+TRAFFIC_KERNELS = {   # kernel -> what its traffic grows with (per step: both sets' prepare, one pair pass)
+    "k_prepare": "vertices", "k_raster_big": "vertices", "k_pair_raster": "pairs",
+}
+
+
+def traffic_table(args):
+    """Per-step DRAM traffic of the dominant kernels on the whole workload, from one ncu capture of a
+    --profile-once step on its first --tiles tiles: each kernel's dram__bytes_read.sum +
+    dram__bytes_write.sum summed over the step's launches, scaled to the whole workload by the vertices
+    of both sets (the prepare kernels) or by the candidate pairs (the pair kernel)."""
+    import csv
+
+    import torch
+
+    import paper_1208_0277_gb300 as P
+
+    if not args.tiles:
+        raise SystemExit("--traffic-csv needs the --tiles of the captured run")
+    rows = list(csv.reader(open(args.traffic_csv)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    ki, mi, vi = (rows[hi].index(k) for k in ("Kernel Name", "Metric Name", "Metric Value"))
+    sub_bytes = {}
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or not r[mi].startswith("dram__bytes_"):
+            continue
+        name = r[ki].split("(")[0].replace("void ", "").split("<")[0].replace("sccg::", "").strip()
+        if name in TRAFFIC_KERNELS:
+            sub_bytes[name] = sub_bytes.get(name, 0) + int(float(r[vi].replace(",", "")))
+
+    torch.cuda.set_device(0)
+    P.build()
+    ctx = P.Context(0, json.loads(args.params) if args.params else None)
+    dev = torch.device("cuda", 0)
+
+    def units(tiles):
+        w, desc = make_workload(args.config, 1, tiles)
+        sets = []
+        for ps in (w.A, w.B):
+            sets.append(ctx.prepare(*(torch.from_numpy(getattr(ps, f)).to(dev) for f in ("off", "xy", "tile")),
+                                    raster=False))
+        pa, _ = ctx.candidate_pairs(sets[0], sets[1])
+        n = {"vertices": int(w.A.off[-1] + w.B.off[-1]), "pairs": int(pa.numel())}
+        del sets, pa
+        torch.cuda.empty_cache()
+        return n, desc
+
+    sub, _ = units(args.tiles)
+    whole, desc = units(0)
+    cmd = " ".join(sys.argv)
+    out = {}
+    for k, b in sorted(sub_bytes.items()):
+        by = TRAFFIC_KERNELS[k]
+        scale = whole[by] / sub[by]
+        out[k] = {"source_hash": kernel_source_hash(), "workload": desc["workload"],
+                  "bytes_per_step": int(b * scale),
+                  "note": f"dram__bytes_read.sum + dram__bytes_write.sum of the step's {k} launches on the first "
+                          f"{args.tiles} tiles ({b} bytes, {sub[by]} {by}), scaled by the {by} of the whole "
+                          f"workload ({whole[by]}: x{scale:.4f})"}
+    out["command"] = (f"python bench.py --config {args.config} --tiles {args.tiles} --profile-once --form graph "
+                      f"--autotune off --params '{args.params}'; ncu --metrics dram__bytes_read.sum,"
+                      "dram__bytes_write.sum,gpu__time_duration.sum --clock-control none -k regex:'k_prepare|"
+                      "k_raster_big|k_pair_raster' -s 4 -c 5 --csv --log-file traffic.csv (the same command); "
+                      + cmd)
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def other_configs_of(args) -> list:
     if args.other_configs == "auto":
         return [2, 4] if args.config in (3, 5) and not args.tiles else []
@@ -967,6 +1061,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.ablation:
         ablation(args)
+        return
+    if args.traffic_csv:
+        traffic_table(args)
         return
     if args.impl == "reference":
         if rank == 0:
