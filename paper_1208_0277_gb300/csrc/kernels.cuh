@@ -266,6 +266,11 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
     long long first_bad = 0x7fffffffffffffffLL;
     unsigned long long band_bytes = 0;
+    if (RASTER && a.rleaf) {
+        // leaf_area writing rasters keeps the leaf rows zero between polygons
+        for (int k = lane; k < kLeafWords; k += 32) L.w[k] = 0u;
+        __syncwarp();
+    }
     // Each warp takes 32 consecutive polygons at a time: lane j loads polygon j's offsets and tile ids
     // (coalesced), the warp pixelizes the 32 one after another, lane j keeps polygon j's results, and
     // the 32 MBRs, areas and raster offsets are stored together.

@@ -69,9 +69,12 @@ __device__ __forceinline__ int leaf_ceil_div(int D, float rc)
 // One edge held by a lane, set up against the window [x0, x0 + W) x [y0, y0 + H): it straddles
 // `span` rows from window row rlo - y0 on, whose words start at w = base + rlo - y0; at its s-th
 // row N = N0 + s * dx2. cap = 64 d2 (N is clamped to [0, cap]: at most 64 crossed pixels matter).
+// In the own-window form N0 and dx2 are also held as floats (N0f, dx2f): every N of a window of at
+// most 64 x 64 pixels is an integer of magnitude at most 129 * 64 + 129 * 64 < 2^24, so
+// fma(s, dx2f, N0f) is N exactly.
 struct LeafEdge {
     int N0, dx2, cap, w, span;
-    float rc;
+    float rc, N0f, dx2f;
 };
 
 // The crossing of an edge with a straddled row (N, words w and w + 64): XOR the prefix mask of its
@@ -83,6 +86,21 @@ template <bool WIDE, bool SELF = false>
 __device__ __forceinline__ void leaf_cross(int N, int cap, float rc, int w, Leaf64& L)
 {
     const int c = leaf_ceil_div(SELF ? max(N, 0) : min(max(N, 0), cap), rc);
+    const uint32_t lo = low_mask(c);
+    if (lo) atomicXor(&L.w[w], lo);
+    if (WIDE) {
+        const uint32_t hi = low_mask(max(c - 32, 0));
+        if (hi) atomicXor(&L.w[w + 64], hi);
+    }
+}
+
+// leaf_cross of the own-window form with N held exactly as a float (LeafEdge): the clamp at 0 and
+// the quotient of leaf_ceil_div on the float directly.
+template <bool WIDE>
+__device__ __forceinline__ void leaf_cross_f(float N, float rc, int w, Leaf64& L)
+{
+    const float q = __fmaf_rn(fmaxf(N, 0.0f), rc, -1.52587890625e-05f);
+    const int c = __float_as_int(__fadd_ru(q, 12582912.0f)) - 0x4B400000;
     const uint32_t lo = low_mask(c);
     if (lo) atomicXor(&L.w[w], lo);
     if (WIDE) {
@@ -105,7 +123,10 @@ __device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, int maxs, Leaf64
 #pragma unroll
         for (int s = 0; s < kLeafLoopSpan; ++s) {
             if (s >= maxs) break;
-            if (s < e.span) leaf_cross<WIDE, SELF>(e.N0 + s * e.dx2, e.cap, e.rc, e.w + s, L);
+            if (s < e.span) {
+                if (SELF) leaf_cross_f<WIDE>(__fmaf_rn((float)s, e.dx2f, e.N0f), e.rc, e.w + s, L);
+                else leaf_cross<WIDE>(e.N0 + s * e.dx2, e.cap, e.rc, e.w + s, L);
+            }
         }
         return;
     }
@@ -115,12 +136,18 @@ __device__ __forceinline__ void leaf_batch_w(const LeafEdge& e, int maxs, Leaf64
         const int t = t0 + lane;
         const int own = flat_owner(excl, t);
         const int s = t - __shfl_sync(kFull, excl, own);
-        const int N0 = __shfl_sync(kFull, e.N0, own);
-        const int dx2 = __shfl_sync(kFull, e.dx2, own);
-        const int cap = __shfl_sync(kFull, e.cap, own);
         const int w = __shfl_sync(kFull, e.w, own);
         const float rc = __shfl_sync(kFull, e.rc, own);
-        if (t < total) leaf_cross<WIDE, SELF>(N0 + s * dx2, cap, rc, w + s, L);
+        if (SELF) {
+            const float N0f = __shfl_sync(kFull, e.N0f, own);
+            const float dx2f = __shfl_sync(kFull, e.dx2f, own);
+            if (t < total) leaf_cross_f<WIDE>(__fmaf_rn(small_int_to_float(max(s, 0)), dx2f, N0f), rc, w + s, L);
+        } else {
+            const int N0 = __shfl_sync(kFull, e.N0, own);
+            const int dx2 = __shfl_sync(kFull, e.dx2, own);
+            const int cap = __shfl_sync(kFull, e.cap, own);
+            if (t < total) leaf_cross<WIDE>(N0 + s * dx2, cap, rc, w + s, L);
+        }
     }
 }
 
@@ -151,6 +178,10 @@ __device__ __forceinline__ void leaf_batch(bool has, int2 a, int2 b, int x0, int
     e.N0 = SELF ? dx - (2 * (x0 - xl) + 1) * dy : (2 * (rlo - ylo) + 1) * dx - (2 * (x0 - xl) + 1) * dy;
     e.cap = d2 << 6;
     e.rc = rcp_approx(small_int_to_float(max(d2, 1)));
+    if (SELF) {
+        e.N0f = __int2float_rn(e.N0);
+        e.dx2f = __int2float_rn(e.dx2);
+    }
     e.w = base + rlo - y0;
     if (W > 32) leaf_batch_w<COUNT, true, SELF>(e, maxs, L, lane, entries);
     else leaf_batch_w<COUNT, false, SELF>(e, maxs, L, lane, entries);
@@ -218,15 +249,19 @@ __device__ __forceinline__ uint32_t leaf_pixels(const Leaf64& L, int W, int H, b
 
 // ||p|| of a polygon whose bounding box [x0, x1) x [y0, y1) is at most 64 x 64 pixels, as one leaf:
 // its ring streamed once. With out, the rows are also written there as the polygon's raster (H rows
-// of one or two words), in the pass that counts them. Whole warp, converged.
+// of one or two words), in the pass that counts them, and cleared in that pass: the caller zeroes
+// P's rows once before its first call with out, and they are zero again after every call. Whole
+// warp, converged.
 template <bool COUNT>
 __device__ __forceinline__ uint32_t leaf_area(const int2* v, int nv, int x0, int y0, int x1, int y1, Leaf64& L,
                                               int lane, WorkCounters& wc, uint32_t* out = nullptr)
 {
     const int W = x1 - x0, H = y1 - y0;
     if (COUNT && lane == 0) wc.window_pixels += (unsigned long long)W * H;
-    __syncwarp();
-    leaf_clear(L, W, H, false, lane);
+    if (!out) {
+        __syncwarp();
+        leaf_clear(L, W, H, false, lane);
+    }
     __syncwarp();
     unsigned long long ce = 0;
     leaf_rings<COUNT, true>(v, nv, 0, v, 0, 0, x0, y0, W, H, L, lane, ce);
@@ -237,8 +272,10 @@ __device__ __forceinline__ uint32_t leaf_area(const int2* v, int nv, int x0, int
         uint32_t acc = 0;
         for (int r = lane; r < H; r += 32) {
             const uint32_t lo = L.w[r] & vlo;
+            L.w[r] = 0u;
             if (W > 32) {
                 const uint32_t hi = L.w[64 + r] & vhi;
+                L.w[64 + r] = 0u;
                 out[2 * r] = lo;
                 out[2 * r + 1] = hi;
                 acc += __popc(lo) + __popc(hi);
