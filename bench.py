@@ -846,27 +846,37 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
     # host sets (H2D of every input byte and D2H of every pair's indices and areas plus J each step)
     if full and not args.no_e2e:
         from paper_1208_0277_gb300.pipeline import HostSet, Pipeline
-        pipe = Pipeline(ctx, HostSet(host["Aoff"], host["Axy"], host["Atile"]),
-                        HostSet(host["Boff"], host["Bxy"], host["Btile"]), w.n_tiles, chunks=args.e2e_chunks,
-                        initial_pairs=n_pairs + 1024, growth=args.e2e_growth)
-        e_pa, _, e_inter, _, e_J = pipe.run()               # warm-up, and the same results as the device run
-        e2e_same = bool(len(e_pa) == n_pairs and e_J["J"] == main_r["J"]["J"] and
-                        e_J["Jprime"] == main_r["J"]["Jprime"])
-        pipe.run()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        hA = HostSet(host["Aoff"], host["Axy"], host["Atile"])
+        hB = HostSet(host["Boff"], host["Bxy"], host["Btile"])
         n_e2e = max(3, args.steps // 4)
-        run_ms = []
-        with quiet_collector():
-            t0 = time.perf_counter()
-            for _ in range(n_e2e):
-                t1 = time.perf_counter()
-                pipe.run()                       # returns after its results are in host memory
-                run_ms.append(round(1e3 * (time.perf_counter() - t1), 2))
+
+        def e2e_runs(copy):
+            pipe = Pipeline(ctx, hA, hB, w.n_tiles, chunks=args.e2e_chunks, initial_pairs=n_pairs + 1024,
+                            growth=args.e2e_growth, copy=copy)
+            e_pa, _, e_inter, _, e_J = pipe.run()           # warm-up, and the same results as the device run
+            same = bool(len(e_pa) == n_pairs and e_J["J"] == main_r["J"]["J"] and
+                        e_J["Jprime"] == main_r["J"]["Jprime"])
+            pipe.run()
             torch.cuda.synchronize()
-            t_e2e = time.perf_counter() - t0
+            if dist:
+                dist.barrier()
+            run_ms = []
+            with quiet_collector():
+                t0 = time.perf_counter()
+                for _ in range(n_e2e):
+                    t1 = time.perf_counter()
+                    pipe.run()                   # returns after its results are in host memory
+                    run_ms.append(round(1e3 * (time.perf_counter() - t1), 2))
+                torch.cuda.synchronize()
+                t_e2e = time.perf_counter() - t0
+            return pipe, same, run_ms, t_e2e
+
+        # the copy engines' form first (for comparison), then the SM copies the number is quoted on
+        pipe, same_engine, run_ms_engine, t_engine = e2e_runs("engine")
+        del pipe
+        pipe, e2e_same, run_ms, t_e2e = e2e_runs("sm")
         e_ms, _ = whole_job(1e3 * t_e2e, n_pairs, dist, dev)
+        e_ms_engine, _ = whole_job(1e3 * t_engine, n_pairs, dist, dev)
         # the host link's own rate on this machine, for reading the end-to-end number (a 1 GiB pinned copy)
         xh = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
         xd = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
@@ -883,7 +893,11 @@ def measure(args, config: int, rank: int, world: int, local_rank: int, dist, ful
                       "median_run_ms": statistics.median(run_ms),
                       "d2h_bytes_per_step": pipe.d2h_bytes, "ms_per_step": e_ms / n_e2e,
                       "chunks": len(pipe.chunks), "chunk_growth": args.e2e_growth,
-                      "same_results_as_device_run": e2e_same,
+                      "same_results_as_device_run": e2e_same and same_engine,
+                      "copies": "by the SMs (sccg_copy, 16 CTAs on high-priority streams)",
+                      "copy_engines": {"value": total_pairs * n_e2e / (e_ms_engine / 1e3),
+                                       "ms_per_step": e_ms_engine / n_e2e, "run_ms": run_ms_engine,
+                                       "median_run_ms": statistics.median(run_ms_engine)},
                       "how": "paper_1208_0277_gb300.pipeline: tiles in chunks, H2D of chunk k+1 overlapped with chunk "
                              "k (prepare, candidate pairs, persistent pair areas), results D2H as they finish, one "
                              "Jaccard; host wall clock"}

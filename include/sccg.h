@@ -345,6 +345,16 @@ int sccg_jaccard_segments(sccg_ctx* ctx, const int64_t* inter, const int64_t* un
                           const int64_t* seg_off, int32_t n_segments,
                           sccg_jaccard_result* out, void* stream);
 
+/* Copy of `bytes` bytes from src to dst by the SMs instead of the copy engines, for the pipelined
+ * front end (Sec. 4.1, Fig. 6: each chunk's polygons move host -> device while the previous chunk is
+ * compared). Each of dst and src is device memory of the context's device or page-locked host
+ * memory mapped into the device's address space (cudaHostAlloc / cudaHostRegister), which the
+ * kernel reads or writes directly over the host link; 16 CTAs of 512 threads keep that link full
+ * while leaving the other SMs to the comparison kernels. bytes and both addresses must be multiples
+ * of 4 and the ranges must not overlap. Asynchronous on `stream`. Returns SCCG_EINVAL for pageable
+ * or unknown memory, another device's memory, misalignment or overlap (nothing is launched). */
+int sccg_copy(sccg_ctx* ctx, void* dst, const void* src, int64_t bytes, void* stream);
+
 /* ------------------------------------------------------------------------------------------- */
 /* measurement                                                                                  */
 /* ------------------------------------------------------------------------------------------- */

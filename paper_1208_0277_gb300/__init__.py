@@ -359,6 +359,16 @@ class Context:
         self._check(self.lib.sccg_rebase_pairs(self.h, _ptr(pa) if n else None, _ptr(pb) if n else None, n,
                                                int(base_a), int(base_b), _stream(stream)), "sccg_rebase_pairs")
 
+    def copy(self, dst, src, stream=None):
+        """dst.copy_(src) by the SMs (sccg_copy): contiguous tensors of equal byte size, each on this
+        context's device or in page-locked host memory."""
+        nb = src.numel() * src.element_size()
+        if dst.numel() * dst.element_size() != nb or not (dst.is_contiguous() and src.is_contiguous()):
+            raise ValueError("copy: contiguous tensors of equal byte size")
+        if nb:
+            self._check(self.lib.sccg_copy(self.h, ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(src.data_ptr()),
+                                           nb, _stream(stream)), "sccg_copy")
+
     def work_counters(self, reset: bool = True) -> dict:
         a = (ctypes.c_uint64 * 12)()
         self._check(self.lib.sccg_work_counters(self.h, a, int(reset)), "sccg_work_counters")

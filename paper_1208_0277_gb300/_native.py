@@ -27,7 +27,7 @@ EXPORTS = [
     "sccg_pair_areas", "sccg_pair_areas_tiles", "sccg_batch_run", "sccg_launch_count", "sccg_jaccard",
     "sccg_jaccard_static", "sccg_work_counters", "sccg_build_bands", "sccg_gather_pairs",
     "sccg_jaccard_segments", "sccg_rebase_pairs", "sccg_prepare_sets", "sccg_contains", "sccg_touches",
-    "sccg_alu_probe", "sccg_ctx_reserve", "sccg_raster_bytes",
+    "sccg_alu_probe", "sccg_ctx_reserve", "sccg_raster_bytes", "sccg_copy",
 ]
 
 _lock = threading.Lock()
@@ -136,6 +136,7 @@ def load(path: str | None = None):
             "sccg_contains": ([V, PS, PS, V, V, V, I64, V, V], I),
             "sccg_touches": ([V, PS, PS, V, V, I64, V, V], I),
             "sccg_work_counters": ([V, ctypes.POINTER(ctypes.c_uint64), I], I),
+            "sccg_copy": ([V, V, V, I64, V], I),
             "sccg_alu_probe": ([I, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                I),
         }

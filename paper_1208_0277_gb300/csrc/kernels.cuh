@@ -1387,6 +1387,27 @@ __global__ void k_copy64(const unsigned long long* src, unsigned long long* dst,
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// Bulk copy by the SMs (sccg_copy): n units of T with a grid stride, four loads in flight per
+// thread; the tail_words 4-byte words after the units by the first threads of block 0. Either
+// side may be page-locked host memory addressed directly over the host link.
+template <class T>
+__global__ void __launch_bounds__(512) k_copy_units(const T* __restrict__ src, T* __restrict__ dst, long long n,
+                                                    const uint32_t* __restrict__ src_tail, uint32_t* __restrict__ dst_tail,
+                                                    int tail_words)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (; i + 3 * step < n; i += 4 * step) {
+        const T u0 = src[i], u1 = src[i + step], u2 = src[i + 2 * step], u3 = src[i + 3 * step];
+        dst[i] = u0;
+        dst[i + step] = u1;
+        dst[i + 2 * step] = u2;
+        dst[i + 3 * step] = u3;
+    }
+    for (; i < n; i += step) dst[i] = src[i];
+    if (blockIdx.x == 0 && (int)threadIdx.x < tail_words) dst_tail[threadIdx.x] = src_tail[threadIdx.x];
+}
+
 __global__ void k_zero32(uint32_t* p, long long n)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

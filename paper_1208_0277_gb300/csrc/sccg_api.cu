@@ -166,6 +166,7 @@ size_t carve_size(size_t count) { return ((count * sizeof(T) + 255) & ~size_t(25
 #ifndef SCCG_CAP_MID
 #define SCCG_CAP_MID 128
 #endif
+constexpr int kCopyCTAs = 16;      // CTAs of sccg_copy: 16 x 512 threads fill the host link (~211 GB/s)
 constexpr int kMaxPrepSets = 64;  // sets per sccg_prepare_sets call (their stats share the pinned page)
 static_assert(kMaxPrepSets * sizeof(PrepStats) <= 4096, "prepare stats must fit the pinned staging page");
 constexpr int kCapSmall = 64;     // edge buffer of the one-warp-per-item kernels (4 warps per CTA)
@@ -776,6 +777,23 @@ int static_parts_address(JPart** out)
 }
 
 // p is device (or managed) memory of device `dev`.
+// The address by which kernels on device dev reach p: device memory of dev, or page-locked host
+// memory mapped into the device's address space; nullptr for anything else (pageable host memory,
+// another device's memory, unknown pointers).
+void* device_view(const void* p, int dev)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return at.device == dev ? at.devicePointer : nullptr;
+    if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+    return nullptr;
+}
+
 bool is_device_ptr_on(const void* p, int dev)
 {
     if (!p) return false;
@@ -1616,6 +1634,46 @@ int sccg_jaccard(sccg_ctx* ctx, const int64_t* inter, const int64_t* uni, int64_
         SCCG_CUDA(ctx, cudaStreamSynchronize(st));
         memcpy(out, ctx->pinned, sizeof(JaccardOut));
     }
+    return SCCG_OK;
+}
+
+int sccg_copy(sccg_ctx* ctx, void* dst, const void* src, int64_t bytes, void* stream)
+{
+    if (!ctx || bytes < 0) return SCCG_EINVAL;
+    if (bytes == 0) return SCCG_OK;
+    if ((bytes & 3) || (reinterpret_cast<uintptr_t>(dst) & 3) || (reinterpret_cast<uintptr_t>(src) & 3))
+        return SCCG_EINVAL;
+    DeviceGuard g(ctx->device);
+    char* d = static_cast<char*>(device_view(dst, ctx->device));
+    const char* s = static_cast<const char*>(device_view(src, ctx->device));
+    if (!d || !s) {
+        snprintf(ctx->last_err, sizeof ctx->last_err,
+                 "sccg_copy: %s is neither device memory of this device nor page-locked host memory",
+                 d ? "src" : "dst");
+        return SCCG_EINVAL;
+    }
+    if (d < s + bytes && s < d + bytes) return SCCG_EINVAL;       // overlapping ranges
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the widest unit both addresses are aligned to; the remaining bytes (a multiple of 4) as words
+    const uintptr_t mis = reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(s);
+    const int unit = (mis & 15) == 0 ? 16 : (mis & 7) == 0 ? 8 : 4;
+    const long long n = bytes / unit;
+    const int tail = (int)((bytes - n * unit) / 4);
+    const long long per_cta = 512LL * 4 * unit;        // one pass of four loads per thread
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(kCopyCTAs, (n * unit + per_cta - 1) / per_cta));
+    const uint32_t* st_src = reinterpret_cast<const uint32_t*>(s + n * unit);
+    uint32_t* st_dst = reinterpret_cast<uint32_t*>(d + n * unit);
+    if (unit == 16)
+        k_copy_units<int4><<<grid, 512, 0, st>>>(reinterpret_cast<const int4*>(s), reinterpret_cast<int4*>(d), n,
+                                                 st_src, st_dst, tail);
+    else if (unit == 8)
+        k_copy_units<int2><<<grid, 512, 0, st>>>(reinterpret_cast<const int2*>(s), reinterpret_cast<int2*>(d), n,
+                                                 st_src, st_dst, tail);
+    else
+        k_copy_units<uint32_t><<<grid, 512, 0, st>>>(reinterpret_cast<const uint32_t*>(s), reinterpret_cast<uint32_t*>(d),
+                                                     n, st_src, st_dst, tail);
+    SCCG_LAUNCHED(ctx, "k_copy_units");
+    ctx->launches += 1;
     return SCCG_OK;
 }
 

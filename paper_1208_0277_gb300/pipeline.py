@@ -7,7 +7,11 @@ filtered and compared on the compute stream, into two alternating device buffers
 vertices, at tile boundaries) grow by a constant factor, so that the first copy, which nothing
 overlaps, is short while each later copy still ends before the work on the chunk before it (the
 copy moves a vertex faster than the kernels consume one). Results go back to pinned host memory on
-a third stream as each chunk finishes. Each chunk's
+a third stream as each chunk finishes. The copies are made by the SMs (sccg_copy: a few CTAs that
+read or write the pinned host buffers directly, on high-priority streams so that they start beside
+the comparison kernels); copy="engine" uses the DMA copy engines instead (cudaMemcpyAsync), whose
+host-to-device rate on the measured boxes dropped to about an eighth for 0.1-0.2 s at a time while
+the SM copies held the link's full rate. Each chunk's
 candidate pairs and areas land in one device result array (and are copied back to pinned host memory
 as they finish); the Jaccard reduction runs once over all pairs at the end, so J and J' are the same
 bits as for one call over the whole sets. Every step runs in the library's kernels (chunk-local pair
@@ -71,9 +75,11 @@ class Pipeline:
     growth: size ratio of consecutive chunks (1: equal chunks)."""
 
     def __init__(self, ctx, A: HostSet, B: HostSet, n_tiles: int, chunks: int = 3, mode: int = MODE_PERSISTENT,
-                 initial_pairs: int | None = None, growth: float = 1.5):
+                 initial_pairs: int | None = None, growth: float = 1.5, copy: str = "sm"):
         import torch
-        self.ctx, self.A, self.B, self.mode = ctx, A, B, mode
+        if copy not in ("sm", "engine"):
+            raise ValueError("copy: 'sm' or 'engine'")
+        self.ctx, self.A, self.B, self.mode, self.copy = ctx, A, B, mode, copy
         self.dev = torch.device("cuda", ctx.device)
         self.chunks = self._cut(A, B, n_tiles, max(1, min(chunks, n_tiles)), growth)
         self.ranges = [(A.range_of_tiles(t0, t1), B.range_of_tiles(t0, t1)) for t0, t1 in self.chunks]
@@ -82,9 +88,10 @@ class Pipeline:
         max_va = max(int(A.off_np[a1] - A.off_np[a0]) for (a0, a1), _ in self.ranges)
         max_vb = max(int(B.off_np[b1] - B.off_np[b0]) for _, (b0, b1) in self.ranges)
         self.slots = [(_Side(self.dev, max_na, max_va), _Side(self.dev, max_nb, max_vb)) for _ in range(2)]
-        self.copy_stream = torch.cuda.Stream(device=self.dev)
+        # the copy streams at the highest priority: their few CTAs are scheduled as soon as an SM has room
+        self.copy_stream = torch.cuda.Stream(device=self.dev, priority=-1)
         self.compute_stream = torch.cuda.Stream(device=self.dev)
-        self.d2h_stream = torch.cuda.Stream(device=self.dev)
+        self.d2h_stream = torch.cuda.Stream(device=self.dev, priority=-1)
         self.done = torch.cuda.Event()
         self.copied = [torch.cuda.Event() for _ in range(2)]
         self.freed = [torch.cuda.Event() for _ in range(2)]
@@ -143,10 +150,16 @@ class Pipeline:
             self.copy_stream.wait_event(self.freed[slot])
             for side, S, (off, tile, v0, v1) in zip(self.slots[slot], (self.A, self.B), self.staged[k]):
                 n = tile.numel()
-                side.off[:n + 1].copy_(off, non_blocking=True)
-                side.tile[:n].copy_(tile, non_blocking=True)
-                side.xy[:2 * (v1 - v0)].copy_(S.xy[2 * v0:2 * v1], non_blocking=True)
+                self._copy(side.off[:n + 1], off, self.copy_stream)
+                self._copy(side.tile[:n], tile, self.copy_stream)
+                self._copy(side.xy[:2 * (v1 - v0)], S.xy[2 * v0:2 * v1], self.copy_stream)
             self.copied[slot].record(self.copy_stream)
+
+    def _copy(self, dst, src, stream):
+        if self.copy == "sm":
+            self.ctx.copy(dst, src, stream=stream)
+        else:
+            dst.copy_(src, non_blocking=True)
 
     def run(self):
         """All candidate pairs (indices into the whole sets), their areas and the Jaccard result, in
@@ -191,7 +204,7 @@ class Pipeline:
                 self.d2h_stream.wait_event(self.done)
                 with torch.cuda.stream(self.d2h_stream):
                     for key in ("pa", "pb", "inter", "uni"):
-                        self.host[key][P:P + n].copy_(self.res[key][P:P + n], non_blocking=True)
+                        self._copy(self.host[key][P:P + n], self.res[key][P:P + n], self.d2h_stream)
             P += n
         with torch.cuda.stream(cs):
             J = ctx.jaccard(self.res["inter"][:P], self.res["uni"][:P], stream=cs)

@@ -10,15 +10,17 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("chunks,initial,growth", [(1, None, 1.75), (3, None, 1.75), (3, None, 1.0), (7, 1000, 1.75)])
-def test_pipeline_equals_resident_path_and_oracle(chunks, initial, growth):
+@pytest.mark.parametrize("chunks,initial,growth,copy", [(1, None, 1.75, "sm"), (3, None, 1.75, "sm"),
+                                                        (3, None, 1.0, "engine"), (7, 1000, 1.75, "sm"),
+                                                        (7, 1000, 1.75, "engine")])
+def test_pipeline_equals_resident_path_and_oracle(chunks, initial, growth, copy):
     import paper_1208_0277_gb300 as P
     from paper_1208_0277_gb300.pipeline import HostSet, Pipeline
     P.build()
     w = W.batched_uneven(seed=6, n_tiles=12, count_lo=50, count_hi=1500)
     ctx = P.Context(0)
     pipe = Pipeline(ctx, HostSet.from_polyset(w.A), HostSet.from_polyset(w.B), w.n_tiles, chunks=chunks,
-                    initial_pairs=initial, growth=growth)
+                    initial_pairs=initial, growth=growth, copy=copy)
     pa, pb, inter, uni, J = pipe.run()
     pa, pb, inter, uni = (np.array(x, dtype=np.int64) for x in (pa, pb, inter, uni))   # views of reused buffers
     A, B = ctx.upload(w.A), ctx.upload(w.B)
@@ -43,3 +45,53 @@ def test_pipeline_equals_resident_path_and_oracle(chunks, initial, growth):
     np.testing.assert_array_equal(pa2, pa)
     np.testing.assert_array_equal(inter2, inter)
     assert J2 == J
+
+
+@pytest.mark.parametrize("offset,nbytes", [(0, 1 << 20), (4, (1 << 20) + 12), (8, 4096 + 4), (12, 4), (0, 16 * 40000 + 8)])
+def test_sm_copy_moves_the_bytes_in_every_direction(offset, nbytes):
+    """sccg_copy between pinned host and device memory (both ways) and device to device, at every
+    alignment the unit choice distinguishes (16, 8, 4 bytes) with tails, equals the source."""
+    import paper_1208_0277_gb300 as P
+    P.build()
+    ctx = P.Context(0)
+    rng = np.random.default_rng(offset + nbytes)
+    n = nbytes // 4
+    src_h = torch.from_numpy(rng.integers(-2**31, 2**31, n + 8, dtype=np.int64).astype(np.int32)).pin_memory()
+    k = offset // 4
+    dev = torch.full((n + 8,), -1, dtype=torch.int32, device="cuda")
+    ctx.copy(dev[k:k + n], src_h[k:k + n])                      # host -> device
+    torch.cuda.synchronize()
+    got = dev.cpu()
+    assert torch.equal(got[k:k + n], src_h[k:k + n])
+    assert bool((got[:k] == -1).all()) and bool((got[k + n:] == -1).all())
+    back = torch.zeros(n + 8, dtype=torch.int32).pin_memory()
+    ctx.copy(back[k:k + n], dev[k:k + n])                       # device -> host
+    torch.cuda.synchronize()
+    assert torch.equal(back[k:k + n], src_h[k:k + n])
+    d2 = torch.zeros(n + 8, dtype=torch.int32, device="cuda")
+    ctx.copy(d2[k:k + n], dev[k:k + n])                         # device -> device
+    torch.cuda.synchronize()
+    assert torch.equal(d2[k:k + n].cpu(), src_h[k:k + n])
+
+
+def test_sm_copy_refuses_pageable_overlapping_and_misaligned_memory():
+    import ctypes
+    import paper_1208_0277_gb300 as P
+    P.build()
+    ctx = P.Context(0)
+    dev = torch.zeros(1024, dtype=torch.int32, device="cuda")
+    pageable = torch.zeros(1024, dtype=torch.int32)
+    assert not pageable.is_pinned()
+    with pytest.raises(P.SccgError):
+        ctx.copy(dev, pageable)                                  # pageable host memory
+    with pytest.raises(P.SccgError):
+        ctx.copy(pageable, dev)
+    with pytest.raises(P.SccgError):
+        ctx.copy(dev[100:600], dev[0:500])                       # overlapping ranges
+    lib, h = ctx.lib, ctx.h
+    pin = torch.zeros(1024, dtype=torch.int32).pin_memory()
+    assert lib.sccg_copy(h, ctypes.c_void_p(dev.data_ptr() + 2), ctypes.c_void_p(pin.data_ptr()), 64, None) != 0
+    assert lib.sccg_copy(h, ctypes.c_void_p(dev.data_ptr()), ctypes.c_void_p(pin.data_ptr()), 63, None) != 0
+    assert lib.sccg_copy(h, ctypes.c_void_p(dev.data_ptr()), ctypes.c_void_p(pin.data_ptr()), 0, None) == 0
+    torch.cuda.synchronize()
+    assert bool((dev == 0).all())
