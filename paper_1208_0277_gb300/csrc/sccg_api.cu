@@ -1644,6 +1644,9 @@ int sccg_copy(sccg_ctx* ctx, void* dst, const void* src, int64_t bytes, void* st
     if ((bytes & 3) || (reinterpret_cast<uintptr_t>(dst) & 3) || (reinterpret_cast<uintptr_t>(src) & 3))
         return SCCG_EINVAL;
     DeviceGuard g(ctx->device);
+    // bind the device's context to this host thread before the pointer queries: a thread that has
+    // made no other CUDA call yet has none current, and the queries then find no device address
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "sccg_copy");
     char* d = static_cast<char*>(device_view(dst, ctx->device));
     const char* s = static_cast<const char*>(device_view(src, ctx->device));
     if (!d || !s) {

@@ -318,18 +318,19 @@ class Server:
             slot.h_dst[:k + 1].copy_(torch.from_numpy(dst))
             rng = slice(start, start + npairs)
             with torch.cuda.stream(slot.stream):
-                slot.seg_src[:k].copy_(slot.h_src[:k], non_blocking=True)
-                slot.seg_dst[:k + 1].copy_(slot.h_dst[:k + 1], non_blocking=True)
                 c = slot.ctx
+                # host <-> device copies by the SMs (sccg_copy), like the pipelined front end's
+                c.copy(slot.seg_src[:k], slot.h_src[:k], stream=slot.stream)
+                c.copy(slot.seg_dst[:k + 1], slot.h_dst[:k + 1], stream=slot.stream)
                 c.gather_pairs(self.pa, self.pb, slot.seg_src[:k], slot.seg_dst[:k + 1], self.a_pa[rng],
                                self.a_pb[rng], stream=slot.stream)
                 c.pair_areas(self.A, self.B, self.a_pa[rng], self.a_pb[rng], mode=MODE_PERSISTENT,
                              out=(self.a_inter[rng], self.a_uni[rng]), stream=slot.stream)
                 c.jaccard_segments(self.a_inter[rng], self.a_uni[rng], slot.seg_dst[:k + 1], slot.jres,
                                    stream=slot.stream)
-                slot.h_inter[:npairs].copy_(self.a_inter[rng], non_blocking=True)
-                slot.h_uni[:npairs].copy_(self.a_uni[rng], non_blocking=True)
-                slot.h_jres[:48 * k].copy_(slot.jres[:48 * k], non_blocking=True)
+                c.copy(slot.h_inter[:npairs], self.a_inter[rng], stream=slot.stream)
+                c.copy(slot.h_uni[:npairs], self.a_uni[rng], stream=slot.stream)
+                c.copy(slot.h_jres[:48 * k], slot.jres[:48 * k], stream=slot.stream)
                 slot.event.record(slot.stream)
             with slot.cv:
                 slot.batch = (jobs, dst, start, npairs, bo)

@@ -95,3 +95,27 @@ def test_sm_copy_refuses_pageable_overlapping_and_misaligned_memory():
     assert lib.sccg_copy(h, ctypes.c_void_p(dev.data_ptr()), ctypes.c_void_p(pin.data_ptr()), 0, None) == 0
     torch.cuda.synchronize()
     assert bool((dev == 0).all())
+
+
+def test_sm_copy_from_a_fresh_host_thread():
+    """A host thread whose first CUDA call is sccg_copy (the serving loop's batcher) copies too."""
+    import threading
+    import paper_1208_0277_gb300 as P
+    P.build()
+    ctx = P.Context(0)
+    src = torch.arange(4096, dtype=torch.int32).pin_memory()
+    dev = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    errs = []
+
+    def work():
+        try:
+            ctx.copy(dev, src)
+            torch.cuda.synchronize()
+        except Exception as e:          # noqa: BLE001 - reported below
+            errs.append(e)
+    t = threading.Thread(target=work)
+    t.start()
+    t.join()
+    assert not errs, errs
+    assert torch.equal(dev.cpu(), src)
