@@ -288,6 +288,14 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
         }
     }
     const int cnt = (int)min(32LL, a.n - c0);
+    if (RASTER) {
+        // the take's 32 rings are contiguous: their lines are requested into L2 now (at most 64 KB),
+        // so that each polygon's vertex loads below wait on L2 rather than DRAM
+        const long long v0 = __shfl_sync(kFull, oj0, 0), v1 = __shfl_sync(kFull, oj1, cnt - 1);
+        const char* vb = reinterpret_cast<const char*>(a.xy) + 8 * v0;
+        const long long nbytes = min(8 * (v1 - v0), 65536LL);
+        for (long long o = 128LL * lane; o < nbytes; o += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(vb + o));
+    }
     int4 my_mbr = make_int4(0, 0, 0, 0);
     uint32_t my_area = 0;
     bool my_defer = false;
