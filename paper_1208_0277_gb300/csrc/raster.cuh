@@ -332,6 +332,15 @@ __global__ void __launch_bounds__(256) k_pair_raster(const RasterPairArgs a)
                 sum_area = a.areaA[ia] + a.areaB[ib];
                 tab[warp][lane] = t;
                 if (!light) a.heavy[atomicAdd(a.heavy_n, 1ull)] = (unsigned long long)k;
+                else if (t.H > 0) {
+                    // the window's rows of both rasters (contiguous, the first 1 KB of each) requested into
+                    // L2 now: the chunk's pairs are ANDed one group after another below
+                    const char* ra = reinterpret_cast<const char*>(a.rwA + t.pA);
+                    const char* rb = reinterpret_cast<const char*>(a.rwB + t.pB);
+                    const int na = min(4 * t.H * t.nwa, 1024), nb = min(4 * t.H * t.nwb, 1024);
+                    for (int o = 0; o < na; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(ra + o));
+                    for (int o = 0; o < nb; o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(rb + o));
+                }
             }
         }
         __syncwarp();
