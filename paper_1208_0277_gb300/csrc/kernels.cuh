@@ -59,7 +59,7 @@ struct PrepStats {
     long long first_bad;
     unsigned long long band_bytes;    // sum of the band index block sizes
     unsigned deferred;                // polygons listed for a second kernel (area not yet written)
-    unsigned pad;
+    unsigned next;                    // k_raster_big's claim counter over the listed polygons
     unsigned long long raster_words;  // words of the set's pixel rasters (sets that keep them)
 };
 

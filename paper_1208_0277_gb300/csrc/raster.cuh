@@ -135,17 +135,26 @@ __device__ __forceinline__ uint32_t draw_finish(const uint32_t* D, int nr, int n
     return acc;
 }
 
+// The next list position from a counter, for the whole warp. Whole warp, converged.
+__device__ __forceinline__ long long claim_next(unsigned* next, int lane)
+{
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(next, 1u);
+    return (long long)__shfl_sync(kFull, t, 0);
+}
+
 // Rasters and ||p|| of the polygons k_prepare listed (windows over 64 pixels wide or high): pieces of
 // up to 32 PIECE columns, passes of as many rows as the per-warp difference words hold. Otherwise
 // (BANDED false) only the polygons without a block in the band index blob, one warp each, streaming
 // the whole ring once per pass; BANDED: only the polygons with a block (large tissue regions), one
 // CTA each, its warps taking the 32-row bands in turn, each band's edges from the band's list, and
-// the warps' counts summed in shared memory.
+// the warps' counts summed in shared memory. next (BANDED false; zero at the launch): the list
+// position the next free warp takes, so that warps drawing small windows take more of them.
 template <bool COUNT, int PIECE, bool BANDED>
 __global__ void __launch_bounds__(256) k_raster_big(const int64_t* off, const int32_t* xy, const int4* mbr,
                                                     const char* blob, const int* list, const unsigned* n_list,
                                                     int64_t* area, const long long* roff, uint32_t* rwords,
-                                                    WorkCounters* counters)
+                                                    WorkCounters* counters, unsigned* next)
 {
     constexpr int kWords = 32 * (PIECE + 1);
     SCCG_DYNAMIC_SMEM(int4, smem4);
@@ -154,9 +163,10 @@ __global__ void __launch_bounds__(256) k_raster_big(const int64_t* off, const in
     DrawSmem<PIECE>& S = reinterpret_cast<DrawSmem<PIECE>*>(smem4)[warp];
     WorkCounters wc = {};
     const long long nl = *n_list;
-    const long long first = BANDED ? blockIdx.x : (long long)blockIdx.x * wpb + warp;
     const long long step = BANDED ? gridDim.x : (long long)gridDim.x * wpb;
-    for (long long j = first; j < nl; j += step) {
+    unsigned* const dyn = BANDED ? nullptr : next;
+    const long long first = dyn ? claim_next(dyn, lane) : BANDED ? blockIdx.x : (long long)blockIdx.x * wpb + warp;
+    for (long long j = first; j < nl; j = dyn ? claim_next(dyn, lane) : j + step) {
         const long long i = list[j];
         const char* blk = band_block(blob, i);
         if ((blk != nullptr) != BANDED) continue;                // uniform per warp (per CTA when BANDED)

@@ -252,7 +252,8 @@ int persistent_grid(sccg_ctx* ctx, K kfn, int wpc, size_t smem, unsigned* grid)
 
 template <int PIECE, bool BANDED>
 int launch_raster_big(sccg_ctx* ctx, const sccg_polyset* s, const char* blob, const int* list, const unsigned* n_list,
-                      unsigned n_host, const long long* rhead, uint32_t* rw, const int4* mbr, cudaStream_t st)
+                      unsigned n_host, const long long* rhead, uint32_t* rw, const int4* mbr, unsigned* next,
+                      cudaStream_t st)
 {
     const int wpc = BANDED ? 8 : 4;          // BANDED: one CTA per polygon, its warps taking bands in turn
     const size_t smem = sizeof(DrawSmem<PIECE>) * wpc;
@@ -264,7 +265,8 @@ int launch_raster_big(sccg_ctx* ctx, const sccg_polyset* s, const char* blob, co
     // at most the resident CTAs: each warp then draws polygon after polygon (a CTA holding one polygon
     // per warp would keep its slot until its largest polygon is done)
     const unsigned grid = std::max(1u, std::min(BANDED ? n_host : (n_host + wpc - 1) / wpc, resident));
-    kfn<<<grid, 32 * wpc, smem, st>>>(s->off, s->xy, mbr, blob, list, n_list, s->area, rhead, rw, ctx->counters);
+    kfn<<<grid, 32 * wpc, smem, st>>>(s->off, s->xy, mbr, blob, list, n_list, s->area, rhead, rw, ctx->counters,
+                                      BANDED ? nullptr : next);
     SCCG_LAUNCHED(ctx, "k_raster_big");
     ctx->launches += 1;
     return SCCG_OK;
@@ -1097,11 +1099,13 @@ int sccg_prepare_sets(sccg_ctx* ctx, sccg_polyset* sets, int n_sets, void* strea
                 // their rings, then (when the set has a band index) those drawn band by band
                 uint32_t* rw = reinterpret_cast<uint32_t*>(static_cast<char*>(s->raster) + raster_head_bytes(s->n));
                 const int4* mbr = reinterpret_cast<const int4*>(s->mbr);
+                // (the ring instance's warps take the listed polygons from a counter, stats[k].next, zero
+                // since the stats were initialised at the start of this call)
                 rr = launch_raster_big<32, false>(ctx, s, blob, big_lists[k], &stats[k].deferred, res.deferred,
-                                                  roffs[k], rw, mbr, st);
+                                                  roffs[k], rw, mbr, &stats[k].next, st);
                 if (!rr && blob)
                     rr = launch_raster_big<64, true>(ctx, s, blob, big_lists[k], &stats[k].deferred, res.deferred,
-                                                     roffs[k], rw, mbr, st);
+                                                     roffs[k], rw, mbr, nullptr, st);
             } else if (!rr) {
                 const int wpc = 4;
                 const size_t smem = sizeof(ScanSmem) * wpc;
