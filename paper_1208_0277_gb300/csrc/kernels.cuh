@@ -61,6 +61,8 @@ struct PrepStats {
     unsigned deferred;                // polygons listed for a second kernel (area not yet written)
     unsigned next;                    // k_raster_big's claim counter over the listed polygons
     unsigned long long raster_words;  // words of the set's pixel rasters (sets that keep them)
+    unsigned takes;                   // k_prepare's claim counter over the takes of 32 polygons
+    unsigned pad;
 };
 
 __device__ __forceinline__ void flush_counters(WorkCounters* out, const WorkCounters& wc)
@@ -250,6 +252,14 @@ __global__ void __launch_bounds__(256, 8) k_mbr(const PrepArgs a, long long* wor
 // larger one is listed (its raster's words added to stats->raster_words) for k_raster_big, which
 // writes both its raster and ||p|| once the listed rasters are placed, or for k_area_bands when they
 // do not fit the buffer.
+// The next take of k_prepare from its counter, for the whole warp. Whole warp, converged.
+__device__ __forceinline__ long long claim_take(unsigned* takes, int lane)
+{
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(takes, 1u);
+    return (long long)__shfl_sync(kFull, t, 0);
+}
+
 template <int CAP, int STK, bool COUNT, bool SCAN, bool RASTER = false>
 __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const PrepArgs a)
 {
@@ -260,7 +270,6 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
     char* wbytes = reinterpret_cast<char*>(smem4) + (SCAN ? warp * kPrepWarpBytes : 0);
     XorRows& X = *reinterpret_cast<XorRows*>(wbytes);
     Leaf64& L = *reinterpret_cast<Leaf64*>(wbytes);      // small windows use the same per-warp bytes
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     WorkCounters wc = {};
     unsigned long long big_words = 0;
     int err = 0, max_nv = 0, max_ext = 0, max_tile = -1;
@@ -271,10 +280,13 @@ __global__ void __launch_bounds__(256, SCCG_PREP_MIN_BLOCKS) k_prepare(const Pre
         for (int k = lane; k < kLeafWords; k += 32) L.w[k] = 0u;
         __syncwarp();
     }
-    // Each warp takes 32 consecutive polygons at a time: lane j loads polygon j's offsets and tile ids
-    // (coalesced), the warp pixelizes the 32 one after another, lane j keeps polygon j's results, and
-    // the 32 MBRs, areas and raster offsets are stored together.
-    for (long long c0 = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; c0 < a.n; c0 += nwarps * 32) {
+    // Each warp takes 32 consecutive polygons at a time (the next free take claimed from a counter, so
+    // that warps whose takes hold small rings take more of them): lane j loads polygon j's offsets and
+    // tile ids (coalesced), the warp pixelizes the 32 one after another, lane j keeps polygon j's
+    // results, and the 32 MBRs, areas and raster offsets are stored together.
+    const long long n_takes = (a.n + 31) / 32;
+    for (long long tk = claim_take(&a.stats->takes, lane); tk < n_takes; tk = claim_take(&a.stats->takes, lane)) {
+    const long long c0 = tk * 32;
     const long long ij = c0 + lane;
     long long oj0 = 0, oj1 = 0;
     int tj = 0;
