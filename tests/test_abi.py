@@ -87,3 +87,13 @@ def test_product_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, fn
                 assert "sccg_oracle" not in txt, fn
+
+
+def test_copy_refuses_a_missing_context_and_bad_sizes(lib):
+    """sccg_copy's host-side checks, before any CUDA call: no context, a negative size."""
+    f = lib.sccg_copy
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    buf = (ctypes.c_uint32 * 16)()
+    assert f(None, ctypes.addressof(buf), ctypes.addressof(buf), 64, None) != 0
+    assert f(None, ctypes.addressof(buf), ctypes.addressof(buf), -4, None) != 0

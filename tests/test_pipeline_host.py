@@ -46,3 +46,8 @@ def test_empty_tiles_and_sets():
     c = Pipeline._cut(A, B, 6, 3, 1.75)
     assert c[0][0] == 0 and c[-1][1] == 6
     assert all(t0 < t1 for t0, t1 in c)
+
+
+def test_copy_mode_is_checked_before_any_device_work():
+    with pytest.raises(ValueError):
+        Pipeline(None, None, None, 1, copy="dma")
