@@ -1039,7 +1039,8 @@ def traffic_table(args):
 
     sub, _ = units(args.tiles)
     whole, desc = units(0)
-    cmd = " ".join(sys.argv)
+    cmd = (f"python bench.py --config {args.config} --tiles {args.tiles} --autotune off --params '{args.params}' "
+           "--traffic-csv traffic.csv")
     out = {}
     for k, b in sorted(sub_bytes.items()):
         by = TRAFFIC_KERNELS[k]
@@ -1053,7 +1054,7 @@ def traffic_table(args):
                       f"--autotune off --params '{args.params}'; ncu --metrics dram__bytes_read.sum,"
                       "dram__bytes_write.sum,gpu__time_duration.sum --clock-control none -k regex:'k_prepare|"
                       "k_raster_big|k_pair_raster' -s 4 -c 5 --csv --log-file traffic.csv (the same command); "
-                      + cmd)
+                      + cmd + " (writes this file)")
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as fh:
         json.dump(out, fh, indent=1)
     print(json.dumps(out), flush=True)
